@@ -1,0 +1,410 @@
+"""FP64 CPU oracle for Sketched Leverage Score Ordering (Chin & Liang, ACML 2018).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or call this module.  The product path
+(the CUDA library under ``paper_1812_07903_gb300/``) never imports it, and this module
+imports nothing from the product: the two share no code.  The only thing both sides
+consume in common is seeded input data, produced by a module that holds none of the
+method's arithmetic.
+
+Every function is a plain, slow restatement of the paper's definitions in float64,
+written for a reader to check against the paper by eye.  Library primitives (matrix
+products, LAPACK's SVD, sorting) serve as single steps; nothing is blocked, fused or
+reordered beyond that.
+
+Randomness.  The paper's sketches are random; here every random draw comes from
+Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2,
+3", SC'11), written from its published definition.  The CUDA side implements the same
+generator independently.  Counter layouts (word 3 of the counter is a stream tag):
+
+  CountSketch row i      ctr=(lo(i), hi(i), 0, 1)  bucket=(w0*s)>>32, sign=1-2*(w1&1)
+  SRHT sign of row i     ctr=(lo(i), hi(i), 0, 2)  D_i = 1-2*(w0&1)
+  SRHT sample key of j   ctr=(lo(j), hi(j), 0, 3)  key_j = w0; keep the s smallest (key, j)
+  Gaussian entry (j, i)  ctr=(lo(i), hi(i), j, 4)  G_ji = bf16(BoxMuller(w0, w1))
+  JL entry (j, c)        ctr=(lo(c), hi(c), j, 5)  Pi_jc = BoxMuller(w0, w1) / sqrt(k)
+
+with key = (lo(seed), hi(seed)), BoxMuller(w0, w1) = sqrt(-2 ln u1) cos(2 pi u2),
+u1 = (w0 + 1) 2^-32 in (0, 1], u2 = w1 2^-32 in [0, 1).
+
+Parity status of each function is stated in its docstring; every function here is
+pinned by a test in ``tests/test_oracle_*.py`` to something other than itself.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11, Sec. 4 "Philox")
+# ---------------------------------------------------------------------------
+_PHILOX_M0 = np.uint64(0xD2511F53)
+_PHILOX_M1 = np.uint64(0xCD9E8D57)
+_PHILOX_W0 = 0x9E3779B9
+_PHILOX_W1 = 0xBB67AE85
+_MASK32 = np.uint64(0xFFFFFFFF)
+_SH32 = np.uint64(32)
+
+TAG_COUNTSKETCH = 1
+TAG_SRHT_SIGN = 2
+TAG_SRHT_SAMPLE = 3
+TAG_GAUSSIAN = 4
+TAG_JL = 5
+
+
+def philox4x32_10(c0, c1, c2, c3, key):
+    """Philox4x32 with 10 rounds, vectorised over the counter words.
+
+    Counter words are integer arrays (or scalars) holding 32-bit values; ``key`` is a
+    64-bit seed split into two 32-bit key words (low word first).  Each round multiplies
+    words 0 and 2 by the two Philox multipliers, and mixes the high halves with the odd
+    words and the round key; the key is bumped by the two Weyl constants between rounds.
+    Returns four uint64 arrays holding 32-bit outputs.
+    """
+    c = [np.asarray(x, dtype=np.uint64) & _MASK32 for x in (c0, c1, c2, c3)]
+    k0 = int(key) & 0xFFFFFFFF
+    k1 = (int(key) >> 32) & 0xFFFFFFFF
+    for r in range(10):
+        if r:
+            k0 = (k0 + _PHILOX_W0) & 0xFFFFFFFF
+            k1 = (k1 + _PHILOX_W1) & 0xFFFFFFFF
+        p0 = _PHILOX_M0 * c[0]
+        p1 = _PHILOX_M1 * c[2]
+        c = [
+            (p1 >> _SH32) ^ c[1] ^ np.uint64(k0),
+            p1 & _MASK32,
+            (p0 >> _SH32) ^ c[3] ^ np.uint64(k1),
+            p0 & _MASK32,
+        ]
+    return c
+
+
+def _split64(i):
+    i = np.asarray(i, dtype=np.uint64)
+    return i & _MASK32, i >> _SH32
+
+
+def box_muller(w0, w1):
+    """Standard normal from two 32-bit words: sqrt(-2 ln u1) cos(2 pi u2), in float64."""
+    u1 = (np.asarray(w0, dtype=np.float64) + 1.0) * 2.0**-32
+    u2 = np.asarray(w1, dtype=np.float64) * 2.0**-32
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def bf16_round(x):
+    """Round float64 values to bfloat16 (8 significant bits), round-to-nearest-even.
+
+    Done on the float64 bit pattern in one step (no double rounding through float32):
+    drop the low 45 mantissa bits, adding half an ulp minus one plus the kept lsb.
+    Valid for finite values inside bfloat16's normal range and zero, which covers every
+    Box-Muller output.  Returns float64 values that are exactly bfloat16-representable.
+    """
+    b = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    lsb = (b >> np.uint64(45)) & np.uint64(1)
+    b = (b + np.uint64((1 << 44) - 1) + lsb) & ~np.uint64((1 << 45) - 1)
+    return b.view(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Seeded sketch ingredients (Sec. 2.1 sketch families; Sec. 3.1.2 implementations)
+# ---------------------------------------------------------------------------
+def countsketch_hash(n, s, seed):
+    """CountSketch's pair of hash functions (Sec. 3.1.2): bucket h(i) in [s], sign(i) = +-1.
+
+    bucket = floor(w0 * s / 2^32) (multiply-shift), sign = 1 - 2 (w1 & 1).
+    """
+    lo, hi = _split64(np.arange(n, dtype=np.uint64))
+    w = philox4x32_10(lo, hi, 0, TAG_COUNTSKETCH, seed)
+    bucket = ((w[0] * np.uint64(s)) >> _SH32).astype(np.int64)
+    sign = 1.0 - 2.0 * (w[1] & np.uint64(1)).astype(np.float64)
+    return bucket, sign
+
+
+def srht_signs(n, seed):
+    """Diagonal of random signs D of the SRHT (Sec. 2.1, Sec. 3.1.2)."""
+    lo, hi = _split64(np.arange(n, dtype=np.uint64))
+    w = philox4x32_10(lo, hi, 0, TAG_SRHT_SIGN, seed)
+    return 1.0 - 2.0 * (w[0] & np.uint64(1)).astype(np.float64)
+
+
+def srht_sample(n_pad, s, seed):
+    """Row sample P of the SRHT: s distinct rows of the n_pad-point Hadamard transform.
+
+    A uniform s-subset drawn without replacement: each j gets a 32-bit key, and the s
+    smallest (key, j) pairs are kept.  Returned in ascending j, the row order of SX.
+    """
+    j = np.arange(n_pad, dtype=np.uint64)
+    lo, hi = _split64(j)
+    key = philox4x32_10(lo, hi, 0, TAG_SRHT_SAMPLE, seed)[0].astype(np.int64)
+    first = np.lexsort((j.astype(np.int64), key))[:s]
+    return np.sort(first).astype(np.int64)
+
+
+def gaussian_block(rows, cols, seed):
+    """Entries G[rows, cols] of the s x n Gaussian sketch matrix, before the 1/sqrt(s) scale.
+
+    G_ji = bf16(N(0,1)) with the normal from Philox at counter (lo(i), hi(i), j, 4).
+    """
+    rows = np.asarray(rows, dtype=np.uint64)
+    cols = np.asarray(cols, dtype=np.uint64)
+    J, I = np.meshgrid(rows, cols, indexing="ij")
+    lo, hi = _split64(I)
+    w = philox4x32_10(lo, hi, J, TAG_GAUSSIAN, seed)
+    return bf16_round(box_muller(w[0], w[1]))
+
+
+def jl_matrix(d, k, seed):
+    """Johnson-Lindenstrauss matrix Pi (d x k), entries N(0, 1/k), float64 (not rounded)."""
+    J, C = np.meshgrid(np.arange(d, dtype=np.uint64), np.arange(k, dtype=np.uint64), indexing="ij")
+    lo, hi = _split64(C)
+    w = philox4x32_10(lo, hi, J, TAG_JL, seed)
+    return box_muller(w[0], w[1]) / math.sqrt(k)
+
+
+def hadamard_entries(rows, cols):
+    """Entries of the unnormalised Sylvester-Walsh-Hadamard matrix: (-1)^popcount(j & i)."""
+    a = np.bitwise_and.outer(np.asarray(rows, dtype=np.uint64), np.asarray(cols, dtype=np.uint64))
+    return 1.0 - 2.0 * (np.bitwise_count(a) & 1).astype(np.float64)
+
+
+def next_pow2(n):
+    return 1 << max(0, int(n - 1).bit_length())
+
+
+# ---------------------------------------------------------------------------
+# Sketch SA (Algorithm 2/3 step 1).  S normalised so that E[S^T S] = I.
+# ---------------------------------------------------------------------------
+_CHUNK = 1 << 15
+
+
+def sketch_countsketch(X, s, seed):
+    """SX for CountSketch: row b of SX is the signed sum of the rows i with h(i) = b.
+
+    Written as the sparse product S X with S[h(i), i] = sign(i); each row of S sums its
+    nonzeros in ascending i.
+    """
+    import scipy.sparse as sp
+
+    n, d = X.shape
+    bucket, sign = countsketch_hash(n, s, seed)
+    SX = np.zeros((s, d), dtype=np.float64)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        S = sp.csr_matrix((sign[a:b], (bucket[a:b], np.arange(b - a))), shape=(s, b - a))
+        SX += S @ np.asarray(X[a:b], dtype=np.float64)
+    return SX
+
+
+def sketch_srht(X, s, seed):
+    """SX for the subsampled randomized Hadamard transform sqrt(n_pad/s) P (H/sqrt(n_pad)) D.
+
+    X is zero-padded to n_pad = 2^ceil(log2 n) rows (padding rows contribute nothing),
+    so SX = (1/sqrt(s)) H[sample, :n] D X with H the unnormalised Hadamard matrix.
+    """
+    n, d = X.shape
+    n_pad = next_pow2(n)
+    if s > n_pad:
+        raise ValueError("SRHT needs s <= n_pad")
+    D = srht_signs(n, seed)
+    sample = srht_sample(n_pad, s, seed)
+    SX = np.zeros((s, d), dtype=np.float64)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        H = hadamard_entries(sample, np.arange(a, b))
+        SX += H @ (D[a:b, None] * np.asarray(X[a:b], dtype=np.float64))
+    return SX / math.sqrt(s)
+
+
+def sketch_gaussian(X, s, seed):
+    """SX for the dense Gaussian sketch (1/sqrt(s)) G X, G_ji = bf16(N(0,1))."""
+    n, d = X.shape
+    SX = np.zeros((s, d), dtype=np.float64)
+    rows = np.arange(s)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        SX += gaussian_block(rows, np.arange(a, b), seed) @ np.asarray(X[a:b], dtype=np.float64)
+    return SX / math.sqrt(s)
+
+
+SKETCHES = {"countsketch": sketch_countsketch, "srht": sketch_srht, "gaussian": sketch_gaussian}
+
+
+def sketch(X, kind, s, seed):
+    """Algorithm 2/3 step 1: the sketch SA of the data matrix."""
+    return SKETCHES[kind](X, s, seed)
+
+
+# ---------------------------------------------------------------------------
+# Small solve: Householder QR -> R, SVD of R, rank, M (Algorithm 3 steps 2-4)
+# ---------------------------------------------------------------------------
+def householder_r(A):
+    """R factor of an unpivoted Householder QR of A (s x d, s >= d), in float64.
+
+    Column j: alpha = A[j, j], xnorm = ||A[j+1:, j]||.  If xnorm = 0 no reflection is
+    applied (H_j = I) and R_jj = alpha.  Otherwise beta = -sign(alpha) sqrt(alpha^2 +
+    xnorm^2) with sign(alpha) = +1 for alpha >= 0 (including -0), tau = (beta - alpha) /
+    beta, v = A[j:, j] / (alpha - beta) with v_0 = 1, R_jj = beta, and H_j = I - tau v v^T
+    is applied to the trailing columns.  Finally every row of R with a negative diagonal
+    is negated, so R_jj >= 0 (the unique R for full column rank A).
+    """
+    A = np.array(A, dtype=np.float64, copy=True)
+    s, d = A.shape
+    if s < d:
+        raise ValueError("householder_r needs s >= d")
+    for j in range(d):
+        alpha = A[j, j]
+        xnorm = math.sqrt(float(np.dot(A[j + 1:, j], A[j + 1:, j])))
+        if xnorm == 0.0:
+            continue
+        norm = math.sqrt(alpha * alpha + xnorm * xnorm)
+        beta = -norm if alpha >= 0.0 else norm
+        tau = (beta - alpha) / beta
+        v = A[j:, j] / (alpha - beta)
+        v[0] = 1.0
+        A[j, j] = beta
+        A[j + 1:, j] = 0.0
+        if j + 1 < d:
+            w = v @ A[j:, j + 1:]
+            A[j:, j + 1:] -= tau * np.outer(v, w)
+    R = np.triu(A[:d, :d])
+    neg = np.diag(R) < 0.0
+    R[neg, :] *= -1.0
+    return R
+
+
+def default_tau(s, d):
+    """Relative rank threshold when none is given: max(s, d) * 2^-52 (FP64 numerical rank)."""
+    return max(s, d) * 2.0**-52
+
+
+def svd_of_r(R):
+    """SVD of the small triangular factor, R = U_R diag(sigma) V^T, sigma descending.
+
+    A library step (LAPACK via numpy), as in the paper's own implementation (Sec. 3.1.1).
+    sigma equals the singular values of SX, and V its right singular vectors (Alg 3 step 2).
+    """
+    U, sigma, Vt = np.linalg.svd(R)
+    return sigma, Vt.T, U
+
+
+def numerical_rank(sigma, tau):
+    """Algorithm 3 step 3, read as a relative threshold: r = #{sigma_j > tau * sigma_1}."""
+    if sigma.size == 0 or sigma[0] == 0.0:
+        return 0
+    return int(np.count_nonzero(sigma > tau * sigma[0]))
+
+
+def m_matrix(sigma, V, U_R, rank, Pi):
+    """M = R^+_tau Pi = V_r diag(1/sigma_r) U_R,r^T Pi  (Pi is None: M = V_r diag(1/sigma_r)).
+
+    With Pi = I the scores ||x_i M||^2 equal Algorithm 3's ||x_i V' Sigma'^-1||^2 exactly,
+    because U_R,r has orthonormal columns.
+    """
+    Vr = V[:, :rank] / sigma[:rank]
+    if Pi is None:
+        return Vr
+    return Vr @ (U_R[:, :rank].T @ Pi)
+
+
+def row_scores(X, M):
+    """Algorithm 3 step 5: l_i = ||(X M)_i||^2 in float64, rows streamed in chunks."""
+    n = X.shape[0]
+    out = np.empty(n, dtype=np.float64)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        Y = np.asarray(X[a:b], dtype=np.float64) @ M
+        out[a:b] = np.einsum("ij,ij->i", Y, Y)
+    return out
+
+
+def sketched_svd(SX, tau=None):
+    """Sketched SVD (Algorithm 2/3 steps 2-3): R, sigma, V, U_R and numerical rank of SX."""
+    s, d = SX.shape
+    if tau is None or tau < 0:
+        tau = default_tau(s, d)
+    R = householder_r(SX)
+    sigma, V, U_R = svd_of_r(R)
+    return {"R": R, "sigma": sigma, "V": V, "U_R": U_R, "rank": numerical_rank(sigma, tau), "tau": tau}
+
+
+def scores_from_sketch(X, SX, tau=None, Pi=None):
+    """Algorithm 3 steps 2-5 from a given sketch SX: truncated basis, then row norms."""
+    sv = sketched_svd(SX, tau)
+    M = m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], Pi)
+    return row_scores(X, M), sv, M
+
+
+def sketched_leverage(X, kind, s, k, seed_S, seed_Pi, tau=None):
+    """Algorithm 3 (Approximate Leverage Score with Truncation) with a JL step.
+
+    k = 0 gives the algorithm exactly (Pi = I); k > 0 right-multiplies R^+_tau by the
+    seeded d x k JL matrix Pi.  Returns (scores, info dict).
+    """
+    d = X.shape[1]
+    SX = sketch(X, kind, s, seed_S)
+    Pi = jl_matrix(d, k, seed_Pi) if k > 0 else None
+    scores, sv, M = scores_from_sketch(X, SX, tau, Pi)
+    info = {
+        "rank": sv["rank"],
+        "sigma": sv["sigma"],
+        "tau": sv["tau"],
+        "R": sv["R"],
+        "M": M,
+        "SX": SX,
+        "score_sum": float(np.sum(scores)),
+    }
+    return scores, info
+
+
+def exact_leverage(X, tau=None):
+    """Exact leverage scores (Sec. 2.2; Algorithm 1): l_i = ||U_i||^2 over the numerical rank.
+
+    U from the thin SVD of X; columns kept where sigma_j > tau * sigma_1 (default tau =
+    max(n, d) 2^-52).  This is the diagonal of the hat matrix of the rank-r projection.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n, d = X.shape
+    if tau is None or tau < 0:
+        tau = default_tau(n, d)
+    U, sigma, _ = np.linalg.svd(X, full_matrices=False)
+    r = numerical_rank(sigma, tau)
+    return np.einsum("ij,ij->i", U[:, :r], U[:, :r])
+
+
+def exact_leverage_rows(X, rows, tau=None, block=_CHUNK):
+    """Exact leverage scores of selected rows of a tall X without forming U (n x d).
+
+    R_X from QR of X accumulated over row blocks (each step a LAPACK QR of [R; block]),
+    then the SVD of R_X: l_i = ||x_i V_r diag(1/sigma_r)||^2, equal to ||U_i||^2.
+    """
+    n, d = X.shape
+    if tau is None or tau < 0:
+        tau = default_tau(n, d)
+    R = np.zeros((0, d))
+    for a in range(0, n, block):
+        b = min(n, a + block)
+        R = np.linalg.qr(np.vstack([R, np.asarray(X[a:b], dtype=np.float64)]), mode="r")
+    _, sigma, Vt = np.linalg.svd(R)
+    r = numerical_rank(sigma, tau)
+    Y = np.asarray(X[rows], dtype=np.float64) @ (Vt[:r].T / sigma[:r])
+    return np.einsum("ij,ij->i", Y, Y)
+
+
+# ---------------------------------------------------------------------------
+# Ordering (Algorithm 4 step 4, policy "dec" of Sec. 5.2)
+# ---------------------------------------------------------------------------
+def order_dec(scores):
+    """Policy "dec": indices by decreasing score; ties by increasing index; NaN last.
+
+    -0 and +0 compare equal.  A stable sort of the negated scores.
+    """
+    sc = np.asarray(scores, dtype=np.float64)
+    key = np.where(np.isnan(sc), np.inf, -sc)
+    key = np.where(key == 0.0, 0.0, key)
+    return np.argsort(key, kind="stable").astype(np.int64)
+
+
+def sampling_probabilities(scores):
+    """Algorithm 4 step 3: P_i = l_i / sum_j l_j."""
+    sc = np.asarray(scores, dtype=np.float64)
+    return sc / np.sum(sc)

@@ -1,0 +1,121 @@
+"""Pins for the oracle's randomness: Philox4x32-10, bf16 rounding, Box-Muller, hashes.
+
+Each check compares against something other than the oracle itself: published
+known-answer vectors, torch's float32->bfloat16 conversion, scipy's Hadamard matrix,
+closed-form moments of the distributions.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+from scipy.linalg import hadamard
+
+from oracle import slso_oracle as O
+
+
+def _kat_rows(golden_dir):
+    rows = []
+    with open(os.path.join(golden_dir, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(x, 16) for x in line.split()])
+    return rows
+
+
+def test_philox_known_answers(golden_dir):
+    rows = _kat_rows(golden_dir)
+    assert len(rows) == 3
+    for r in rows:
+        c, k, want = r[0:4], r[4] | (r[5] << 32), r[6:10]
+        got = O.philox4x32_10(*c, k)
+        assert [int(x) for x in got] == want
+
+
+def test_philox_vectorised_matches_scalar():
+    i = np.arange(1000, dtype=np.uint64) * np.uint64(2654435761)
+    w = O.philox4x32_10(i & O._MASK32, i >> O._SH32, 7, 3, 0x1234567890ABCDEF)
+    for t in (0, 17, 999):
+        ii = int(i[t])
+        ws = O.philox4x32_10(ii & 0xFFFFFFFF, ii >> 32, 7, 3, 0x1234567890ABCDEF)
+        assert [int(x[t]) for x in w] == [int(x) for x in ws]
+
+
+def test_bf16_round_matches_torch_on_float32_values():
+    rng = np.random.default_rng(0)
+    x32 = (rng.standard_normal(200000) * np.exp(rng.uniform(-20, 20, 200000))).astype(np.float32)
+    want = torch.from_numpy(x32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = O.bf16_round(x32.astype(np.float64))
+    np.testing.assert_array_equal(got, want)
+
+
+def test_bf16_round_ties_to_even_and_no_double_rounding():
+    one = 1.0
+    ulp = 2.0**-7
+    # exact midpoints go to the even neighbour
+    assert O.bf16_round(np.array([one + ulp / 2]))[0] == one
+    assert O.bf16_round(np.array([one + 3 * ulp / 2]))[0] == one + 2 * ulp
+    # just above a midpoint rounds up even though float32 would first round it to the midpoint
+    x = one + ulp / 2 + 2.0**-40
+    assert np.float32(x) == np.float32(one + ulp / 2)
+    assert O.bf16_round(np.array([x]))[0] == one + ulp
+    assert O.bf16_round(np.array([-x]))[0] == -(one + ulp)
+    assert O.bf16_round(np.array([0.0]))[0] == 0.0
+
+
+def test_box_muller_is_standard_normal():
+    i = np.arange(400000, dtype=np.uint64)
+    w = O.philox4x32_10(i, 0, 0, 99, 42)
+    z = O.box_muller(w[0], w[1])
+    assert abs(z.mean()) < 5 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2.0 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+
+
+def test_countsketch_hash_uniform_buckets_and_balanced_signs():
+    n, s = 200000, 64
+    b, sg = O.countsketch_hash(n, s, 7)
+    assert b.min() >= 0 and b.max() < s
+    counts = np.bincount(b, minlength=s)
+    assert stats.chisquare(counts).pvalue > 1e-4
+    assert set(np.unique(sg)) == {-1.0, 1.0}
+    assert abs(sg.mean()) < 5 / math.sqrt(n)
+
+
+def test_hadamard_entries_match_scipy_sylvester():
+    n = 64
+    H = O.hadamard_entries(np.arange(n), np.arange(n))
+    np.testing.assert_array_equal(H, hadamard(n).astype(np.float64))
+
+
+def test_srht_sample_is_distinct_sorted_and_uniform():
+    n_pad, s = 1024, 100
+    hits = np.zeros(n_pad)
+    for seed in range(200):
+        smp = O.srht_sample(n_pad, s, seed)
+        assert smp.size == s and np.all(np.diff(smp) > 0) and smp[0] >= 0 and smp[-1] < n_pad
+        hits[smp] += 1
+    # each index kept with probability s / n_pad
+    expect = 200 * s / n_pad
+    assert stats.chisquare(hits, np.full(n_pad, expect)).pvalue > 1e-4
+
+
+def test_gaussian_entries_are_bf16_normal():
+    G = O.gaussian_block(np.arange(64), np.arange(5000), 11)
+    np.testing.assert_array_equal(G, O.bf16_round(G))
+    assert abs(G.mean()) < 5 / math.sqrt(G.size)
+    assert abs(G.var() - 1.0) < 0.02
+    # distinct (row, column) counters give independent-looking entries
+    assert abs(np.corrcoef(G[0], G[1])[0, 1]) < 0.05
+
+
+def test_jl_matrix_moments():
+    d, k = 300, 200
+    P = O.jl_matrix(d, k, 5)
+    assert P.shape == (d, k)
+    assert abs((P * P).sum() / d - 1.0) < 0.03  # E ||row||^2 = 1
+    P2 = O.jl_matrix(d, k, 6)
+    assert not np.allclose(P, P2)
