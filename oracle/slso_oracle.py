@@ -85,10 +85,35 @@ def _split64(i):
 
 
 def box_muller(w0, w1):
-    """Standard normal from two 32-bit words: sqrt(-2 ln u1) cos(2 pi u2), in float64."""
-    u1 = (np.asarray(w0, dtype=np.float64) + 1.0) * 2.0**-32
-    u2 = np.asarray(w1, dtype=np.float64) * 2.0**-32
-    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    """Standard normal from two 32-bit words: sqrt(-2 ln u1) cos(2 pi u2), in float64.
+
+    u1 = (w0 + 1) 2^-32 and u2 = w1 2^-32.  Both factors are evaluated from exact
+    arguments so the float64 value is accurate to a few ulp everywhere:
+    * ln u1 = log1p(-m 2^-32) with m = 2^32 - 1 - w0 when w0 >= 2^31, else log(u1);
+    * the angle 2 pi u2 is split into its octant o = w1 >> 29 and the exact fraction
+      a = (w1 mod 2^29) 2^-29, so cos(2 pi u2) is +-sin or +-cos of (pi/4) c with
+      c = a (even octant) or c = 1 - a (odd octant), c in [0, 1].
+    """
+    w0 = np.asarray(w0, dtype=np.uint64)
+    w1 = np.asarray(w1, dtype=np.uint64)
+    hi = w0 >= np.uint64(1 << 31)
+    m = (np.uint64(0xFFFFFFFF) - w0).astype(np.float64)
+    u1 = (w0.astype(np.float64) + 1.0) * 2.0**-32
+    ln_u1 = np.where(hi, np.log1p(-m * 2.0**-32), np.log(u1))
+    rho = np.sqrt(-2.0 * ln_u1)
+    octant = (w1 >> np.uint64(29)).astype(np.int64)
+    frac = (w1 & np.uint64((1 << 29) - 1)).astype(np.float64) * 2.0**-29
+    odd = (octant & 1) == 1
+    c = np.where(odd, 1.0 - frac, frac)
+    phi = (np.pi / 4.0) * c
+    sn, cs = np.sin(phi), np.cos(phi)
+    q = np.where(odd, (octant + 1) // 2, octant // 2)  # quarter turns, 0..4
+    # cos(q pi/2 + phi) for even octants, cos(q pi/2 - phi) for odd ones
+    val = np.select(
+        [q == 0, q == 1, q == 2, q == 3, q == 4],
+        [cs, np.where(odd, sn, -sn), -cs, np.where(odd, -sn, sn), cs],
+    )
+    return rho * val
 
 
 def bf16_round(x):

@@ -119,3 +119,24 @@ def test_jl_matrix_moments():
     assert abs((P * P).sum() / d - 1.0) < 0.03  # E ||row||^2 = 1
     P2 = O.jl_matrix(d, k, 6)
     assert not np.allclose(P, P2)
+
+
+def test_box_muller_accurate_to_few_ulp_against_high_precision():
+    """The float64 normal is within a few ulp (relative) of the exact value everywhere,
+    including u1 near 1 (tiny radius) and angles near the zeros of the cosine."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(3)
+    w0 = list(rng.integers(0, 2**32, 300)) + [0, 1, 2**31 - 1, 2**31, 2**32 - 2, 2**32 - 1]
+    w1 = list(rng.integers(0, 2**32, 300)) + [0, 2**30, 2**30 - 1, 2**30 + 1, 3 * 2**30 + 7, 2**29]
+    w0 = np.array(w0, dtype=np.uint64)
+    w1 = np.array(w1[: len(w0)], dtype=np.uint64)
+    got = O.box_muller(w0, w1)
+    for a, b, g in zip(w0, w1, got):
+        u1 = mpmath.mpf(int(a) + 1) / 2**32
+        u2 = mpmath.mpf(int(b)) / 2**32
+        exact = mpmath.sqrt(-2 * mpmath.log(u1)) * mpmath.cos(2 * mpmath.pi * u2)
+        if abs(exact) < 1e-30:  # an exact zero of the cosine, left at 1e-40 by mpmath
+            assert g == 0.0
+        else:
+            assert abs((g - exact) / exact) < 8 * 2.0**-53
