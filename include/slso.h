@@ -1,0 +1,151 @@
+/*
+ * slso.h -- C ABI of the GB300 (sm_103a) Sketched Leverage Score Ordering library.
+ *
+ * Method: Chin & Liang, "An Empirical Evaluation of Sketched SVD and its Application to
+ * Leverage Score Ordering" (ACML 2018).  Leverage scores (Sec. 2.2) of a tall data matrix
+ * X (n x d) are approximated by sketch-and-solve (Algorithm 2, with the truncation of
+ * Algorithm 3), and the scores induce the "dec" training order of Algorithm 4 / Sec. 5.2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major.  X has n rows of d elements with leading dimension ldx >= d
+ *   (elements, not bytes).  All array arguments are caller-owned DEVICE pointers unless
+ *   the name ends in _host; the library never frees them or keeps them past the call.
+ * - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as void*; NULL is
+ *   the legacy default stream).  Device outputs are valid once the stream has run.
+ *   When a host `info` pointer is passed, the call synchronises `stream` before it
+ *   returns so that `info` is filled; pass NULL to keep the call fully asynchronous.
+ * - Scratch memory comes from the handle's own device pool (cudaMalloc, grown on demand
+ *   and kept until slso_destroy).  A handle must be used by one host thread and one
+ *   stream at a time.
+ * - Every call returns an slso_status.  Argument, shape and dtype errors are detected
+ *   on the host before anything is enqueued.  slso_last_error() returns a message for
+ *   the calling thread's last failure.  No entry point throws or aborts.
+ * - Random draws use Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seeds, with
+ *   the counter layouts given beside each entry point; results depend only on the seeds,
+ *   the inputs and the shapes, not on the GPU or the launch configuration.
+ */
+#ifndef SLSO_H
+#define SLSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SLSO_OK = 0,
+  SLSO_ERR_INVALID_ARG = 1, /* NULL pointer, negative size, unknown enum value       */
+  SLSO_ERR_SHAPE = 2,       /* sizes violate a shape rule (e.g. s < d)               */
+  SLSO_ERR_DTYPE = 3,       /* dtype not supported for that argument                 */
+  SLSO_ERR_OOM = 4,         /* the handle's device pool could not grow               */
+  SLSO_ERR_CUDA = 5,        /* a CUDA runtime call failed (message has the detail)   */
+  SLSO_ERR_NONFINITE = 6,   /* input held NaN or Inf (reported through slso_info)    */
+  SLSO_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up                    */
+  SLSO_ERR_BUSY = 8,        /* serving: no slot or memory free for the job           */
+  SLSO_ERR_NOT_FOUND = 9    /* serving: unknown ticket                               */
+} slso_status;
+
+typedef enum { SLSO_F64 = 0, SLSO_F32 = 1, SLSO_BF16 = 2, SLSO_FP8_E4M3 = 3 } slso_dtype;
+
+/* Sketch families of Sec. 2.1 / Sec. 3.1.2, normalised so that E[S^T S] = I:
+ *  COUNTSKETCH  S[h(i), i] = sign(i); h, sign from Philox counter (lo i, hi i, 0, 1):
+ *               h = (w0 * s) >> 32, sign = 1 - 2 (w1 & 1).
+ *  SRHT         sqrt(n_pad/s) P (H/sqrt(n_pad)) D on X zero-padded to n_pad = 2^ceil(log2 n)
+ *               rows; D_i = 1 - 2 (w0 & 1) at counter (lo i, hi i, 0, 2); P keeps the s rows
+ *               j with the smallest (w0 at counter (lo j, hi j, 0, 3), j), in ascending j.
+ *  GAUSSIAN     (1/sqrt(s)) G, G_ji = bf16_rne(BoxMuller(w0, w1)) at counter (lo i, hi i, j, 4),
+ *               BoxMuller(w0, w1) = sqrt(-2 ln((w0+1) 2^-32)) cos(2 pi w1 2^-32), the bf16
+ *               rounding decided on the float64 value. */
+typedef enum { SLSO_COUNTSKETCH = 0, SLSO_SRHT = 1, SLSO_GAUSSIAN = 2 } slso_sketch_kind;
+
+typedef struct slso_handle slso_handle;
+
+typedef struct {
+  int32_t kind;        /* slso_sketch_kind                                                   */
+  int32_t compute;     /* dtype of the X.M contraction: F64, F32 (3xTF32-accurate), BF16, FP8 */
+  int64_t s;           /* sketch rows, d <= s (SRHT: s <= n_pad)                             */
+  int64_t k;           /* JL width; 0 means Pi = I (Algorithm 3 exactly); k <= 4096           */
+  uint64_t seed_S;     /* seed of the sketch S                                                */
+  uint64_t seed_Pi;    /* seed of Pi: Pi_jc = BoxMuller(w0, w1)/sqrt(k) at counter
+                          (lo c, hi c, j, 5)                                                  */
+  double tau;          /* relative rank threshold: keep sigma_j > tau sigma_1; < 0 selects
+                          max(s, d) 2^-52 (float64 numerical rank)                            */
+  double correct_frac; /* BF16/FP8 only: rescore the top ceil(frac n) rows in float32; 0 = off */
+} slso_params;
+
+typedef struct {
+  int64_t rank;          /* numerical rank r of SX (Algorithm 3 step 3)                       */
+  double sigma_max;      /* sigma_1(SX); NaN when the certified full-rank route was taken     */
+  double sigma_min_kept; /* sigma_r(SX); NaN on the certified route                          */
+  double score_sum;      /* sum of the returned scores (normaliser of P, Algorithm 4 step 3)  */
+  double tau;            /* the threshold actually used                                       */
+  int32_t nonfinite;     /* 1 if X held NaN or Inf                                            */
+  int32_t svd_route;     /* 1: R^+ from the SVD of R; 0: rank d certified, R^+ = R^-1          */
+} slso_info;
+
+/* Library / handle ------------------------------------------------------------------ */
+const char* slso_version(void);
+const char* slso_last_error(void);
+slso_status slso_create(slso_handle** handle, int device);
+slso_status slso_destroy(slso_handle* handle);
+/* Device bytes the handle's pool needs for slso_leverage + slso_order on these shapes. */
+slso_status slso_workspace_size(const slso_params* params, int64_t n, int64_t d, size_t* bytes);
+
+/* Sketch SX = S X  (Algorithm 2/3 step 1; Sec. 2.1 definition of the sketches).
+ * X: n x d (ldx) of dtype xdt in {F64, F32, BF16}.  SX: s x d float64, row-major, dense.
+ * CountSketch sums each bucket's rows in ascending row order with compensated float32
+ * (float64 for F64 X); SRHT and Gaussian accumulate partial sums in float32 (float64
+ * for F64 X) merged in float64 in a fixed order, so the result is deterministic.
+ * Errors: SHAPE if n < 1, d < 1, s < 1, ldx < d, or (SRHT) s > n_pad. */
+slso_status slso_sketch(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
+                        int32_t xdt, int32_t kind, int64_t s, uint64_t seed_S, double* SX,
+                        void* stream);
+
+/* Sketched SVD (title; Algorithm 2/3 steps 2-3): unpivoted Householder QR of SX (s x d,
+ * float64, s >= d) with R_jj >= 0, then the SVD of R (one-sided Jacobi, float64):
+ * sigma (d, descending) are the singular values of SX and V (d x d, row-major, column j
+ * the j-th right singular vector) its right singular vectors.  R (d x d) is written when
+ * non-NULL.  rank = #{sigma_j > tau sigma_1} (tau < 0: max(s, d) 2^-52) goes to info.
+ * Householder step j: no reflection when the subcolumn below the diagonal is exactly 0;
+ * otherwise beta = -sign(alpha) ||A[j:, j]|| with sign(+-0) = +1. */
+slso_status slso_sketched_svd(slso_handle* handle, const double* SX, int64_t s, int64_t d,
+                              double tau, double* sigma, double* V, double* R, slso_info* info,
+                              void* stream);
+
+/* Approximate leverage scores (Algorithm 3 with the JL projection Pi):
+ *   SX = S X;  R = householder_R(SX);  r = #{sigma_j(R) > tau sigma_1};
+ *   M = R^+_tau Pi = V_r Sigma_r^-1 U_R,r^T Pi  (Pi = I when k = 0);
+ *   scores_i = ||x_i M||^2.
+ * When ||R||_F ||R^-1||_F < 1e-3 / tau the rank is certified to be d and R^+_tau = R^-1
+ * exactly, so the SVD is skipped (info->svd_route = 0).  scores: n values, float64 when
+ * compute == F64, else float32.  compute F32 evaluates X.M to float32 accuracy on the
+ * tensor cores (three TF32 products); BF16 and FP8 round X and M (FP8 with per-column
+ * scales of X folded into M) and accumulate in float32.
+ * Errors: SHAPE as for slso_sketch plus k > 4096 or s < d; DTYPE for an unsupported
+ * (xdt, compute) pair. */
+slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
+                          int32_t xdt, const slso_params* params, void* scores, slso_info* info,
+                          void* stream);
+
+/* Policy "dec" of Sec. 5.2 (Algorithm 4 step 4): order[0..n) lists row indices by strictly
+ * decreasing score; equal scores (with -0 == +0) by increasing index; NaN last.  A stable
+ * LSD radix argsort on the 32-bit (F32 scores) or 64-bit (F64 scores) orderable key. */
+slso_status slso_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
+                       int64_t* order, void* stream);
+
+/* End-to-end call with HOST buffers: copies X_host (pinned or pageable) to the device,
+ * runs slso_leverage + slso_order, copies scores (float32, or float64 for F64 compute)
+ * and order back.  Synchronous.  Device buffers come from the handle's pool. */
+slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t n, int64_t d,
+                                int64_t ldx, int32_t xdt, const slso_params* params,
+                                void* scores_host, int64_t* order_host, slso_info* info,
+                                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLSO_H */

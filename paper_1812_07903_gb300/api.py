@@ -1,0 +1,165 @@
+"""Python binding of the C ABI: the same entry points, taking torch CUDA tensors.
+
+Only argument marshalling happens here; every step of the path runs in libslso's kernels.
+PyTorch provides device memory and the current stream.  There is no CPU fallback: without
+a CUDA device, or without the built library, these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+_XDT = {torch.float64: L.F64, torch.float32: L.F32, torch.bfloat16: L.BF16}
+
+
+def _stream(t=None):
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise TypeError("slso needs CUDA tensors (there is no CPU path)")
+
+
+class Handle:
+    """Owns an slso_handle (device scratch pool) on one device."""
+
+    def __init__(self, device=None):
+        lib = L.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("slso needs a CUDA device")
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self._h = ctypes.c_void_p()
+        L.check(lib.slso_create(ctypes.byref(self._h), dev))
+        self.device = dev
+
+    def close(self):
+        if self._h:
+            L.load().slso_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ptr(self):
+        return self._h
+
+
+_default = {}
+
+
+def default_handle():
+    dev = torch.cuda.current_device()
+    if dev not in _default:
+        _default[dev] = Handle(dev)
+    return _default[dev]
+
+
+def _x_args(X):
+    _require_cuda(X)
+    if X.dim() != 2 or X.dtype not in _XDT:
+        raise TypeError("X must be a 2-D float64/float32/bfloat16 CUDA tensor")
+    if X.stride(1) != 1:
+        raise ValueError("X rows must be contiguous (stride(1) == 1)")
+    n, d = X.shape
+    return n, d, X.stride(0), _XDT[X.dtype]
+
+
+def sketch(X, kind, s, seed, handle=None):
+    """slso_sketch: SX = S X as an s x d float64 tensor."""
+    h = handle or default_handle()
+    n, d, ldx, xdt = _x_args(X)
+    SX = torch.empty(s, d, dtype=torch.float64, device=X.device)
+    L.check(L.load().slso_sketch(h.ptr, X.data_ptr(), n, d, ldx, xdt, L.KIND[kind], s, seed,
+                                 SX.data_ptr(), _stream()))
+    return SX
+
+
+def sketched_svd(SX, tau=-1.0, want_r=True, handle=None):
+    """slso_sketched_svd: (sigma, V, R, info) of the s x d float64 sketch."""
+    h = handle or default_handle()
+    _require_cuda(SX)
+    if SX.dtype != torch.float64 or not SX.is_contiguous():
+        raise TypeError("SX must be a contiguous float64 CUDA tensor")
+    s, d = SX.shape
+    sigma = torch.empty(d, dtype=torch.float64, device=SX.device)
+    V = torch.empty(d, d, dtype=torch.float64, device=SX.device)
+    R = torch.empty(d, d, dtype=torch.float64, device=SX.device) if want_r else None
+    info = L.Info()
+    L.check(L.load().slso_sketched_svd(h.ptr, SX.data_ptr(), s, d, float(tau), sigma.data_ptr(),
+                                       V.data_ptr(), R.data_ptr() if R is not None else None,
+                                       ctypes.byref(info), _stream()))
+    return sigma, V, R, info.as_dict()
+
+
+def make_params(kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
+                correct_frac=0.0):
+    p = L.Params()
+    p.kind = L.KIND[kind]
+    p.compute = L.DTYPE[compute]
+    p.s = int(s)
+    p.k = int(k)
+    p.seed_S = int(seed_S)
+    p.seed_Pi = int(seed_Pi)
+    p.tau = float(tau)
+    p.correct_frac = float(correct_frac)
+    return p
+
+
+def leverage(X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
+             correct_frac=0.0, out=None, want_info=True, handle=None):
+    """slso_leverage: approximate leverage scores (float64 for compute='f64', else float32)."""
+    h = handle or default_handle()
+    n, d, ldx, xdt = _x_args(X)
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+    sdt = torch.float64 if compute == "f64" else torch.float32
+    scores = out if out is not None else torch.empty(n, dtype=sdt, device=X.device)
+    info = L.Info()
+    st = L.load().slso_leverage(h.ptr, X.data_ptr(), n, d, ldx, xdt, ctypes.byref(p), scores.data_ptr(),
+                                ctypes.byref(info) if want_info else None, _stream())
+    L.check(st)
+    return scores, (info.as_dict() if want_info else None)
+
+
+def order(scores, out=None, handle=None):
+    """slso_order: the "dec" ordering (int64 row indices) of a float32/float64 score vector."""
+    h = handle or default_handle()
+    _require_cuda(scores)
+    if scores.dtype not in (torch.float32, torch.float64) or not scores.is_contiguous():
+        raise TypeError("scores must be a contiguous float32/float64 CUDA tensor")
+    n = scores.numel()
+    o = out if out is not None else torch.empty(n, dtype=torch.int64, device=scores.device)
+    sdt = L.F32 if scores.dtype == torch.float32 else L.F64
+    L.check(L.load().slso_order(h.ptr, scores.data_ptr(), sdt, n, o.data_ptr(), _stream()))
+    return o
+
+
+def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
+                   compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None):
+    """slso_rank_rows_host: scores and order from a HOST matrix (copies inside the call)."""
+    h = handle or default_handle()
+    if X_host.is_cuda or X_host.dim() != 2 or X_host.dtype not in _XDT or X_host.stride(1) != 1:
+        raise TypeError("X_host must be a 2-D row-contiguous host tensor (float64/float32/bfloat16)")
+    n, d = X_host.shape
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+    sdt = torch.float64 if compute == "f64" else torch.float32
+    sc = scores_out if scores_out is not None else torch.empty(n, dtype=sdt)
+    od = order_out if order_out is not None else torch.empty(n, dtype=torch.int64)
+    info = L.Info()
+    L.check(L.load().slso_rank_rows_host(h.ptr, X_host.data_ptr(), n, d, X_host.stride(0), _XDT[X_host.dtype],
+                                         ctypes.byref(p), sc.data_ptr(), od.data_ptr(), ctypes.byref(info),
+                                         _stream()))
+    return sc, od, info.as_dict()
+
+
+def default_tau(s, d):
+    return max(s, d) * 2.0**-52
+

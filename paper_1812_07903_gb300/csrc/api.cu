@@ -1,0 +1,213 @@
+// C ABI entry points of libslso (declared in include/slso.h).
+//
+// Each entry point validates its arguments on the host, sizes its scratch by running its plan
+// against a measuring Arena, grows the handle's pool if needed, and then enqueues the plan on
+// the caller's stream.  Only an `info` request synchronises.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+using namespace slso;
+
+namespace {
+
+double default_tau(int64_t s, int64_t d) { return static_cast<double>(std::max(s, d)) * std::ldexp(1.0, -52); }
+
+int64_t next_pow2(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+slso_status check_x(const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt) {
+  if (!X) return fail(SLSO_ERR_INVALID_ARG, "X is NULL");
+  if (n < 1 || d < 1) return fail(SLSO_ERR_SHAPE, "need n >= 1 and d >= 1 (n=%lld, d=%lld)", (long long)n, (long long)d);
+  if (ldx < d) return fail(SLSO_ERR_SHAPE, "ldx=%lld < d=%lld", (long long)ldx, (long long)d);
+  if (n >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "n=%lld must be < 2^31", (long long)n);
+  if (xdt != SLSO_F64 && xdt != SLSO_F32 && xdt != SLSO_BF16)
+    return fail(SLSO_ERR_DTYPE, "X dtype %d not supported (F64, F32, BF16)", xdt);
+  return SLSO_OK;
+}
+
+slso_status check_sketch(int32_t kind, int64_t n, int64_t d, int64_t s) {
+  if (kind != SLSO_COUNTSKETCH && kind != SLSO_SRHT && kind != SLSO_GAUSSIAN)
+    return fail(SLSO_ERR_INVALID_ARG, "unknown sketch kind %d", kind);
+  if (s < 1) return fail(SLSO_ERR_SHAPE, "s=%lld must be >= 1", (long long)s);
+  if (s >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "s=%lld must be < 2^31", (long long)s);
+  if (kind == SLSO_SRHT && s > next_pow2(n))
+    return fail(SLSO_ERR_SHAPE, "SRHT needs s <= n_pad=%lld (s=%lld)", (long long)next_pow2(n), (long long)s);
+  (void)d;
+  return SLSO_OK;
+}
+
+slso_status check_params(const slso_params* p, int64_t n, int64_t d) {
+  if (!p) return fail(SLSO_ERR_INVALID_ARG, "params is NULL");
+  SLSO_TRY(check_sketch(p->kind, n, d, p->s));
+  if (p->s < d) return fail(SLSO_ERR_SHAPE, "need s >= d for the d x d factor R (s=%lld, d=%lld)", (long long)p->s, (long long)d);
+  if (p->k < 0 || p->k > 4096) return fail(SLSO_ERR_SHAPE, "k=%lld must be in [0, 4096]", (long long)p->k);
+  if (p->compute != SLSO_F64 && p->compute != SLSO_F32 && p->compute != SLSO_BF16 && p->compute != SLSO_FP8_E4M3)
+    return fail(SLSO_ERR_DTYPE, "unknown compute dtype %d", p->compute);
+  if (!(p->correct_frac >= 0.0 && p->correct_frac <= 1.0))
+    return fail(SLSO_ERR_INVALID_ARG, "correct_frac must be in [0, 1]");
+  if (std::isnan(p->tau)) return fail(SLSO_ERR_INVALID_ARG, "tau is NaN");
+  if (d > 8192) return fail(SLSO_ERR_SHAPE, "d=%lld exceeds 8192", (long long)d);
+  return SLSO_OK;
+}
+
+template <class Plan>
+slso_status run_plan(Handle& h, Plan&& plan) {
+  Arena m(nullptr, ~size_t(0), true);
+  SLSO_TRY(plan(m));
+  SLSO_TRY(ensure_pool(h, m.used()));
+  Arena real(h.pool, h.pool_cap, false);
+  SLSO_TRY(plan(real));
+  if (real.overflow()) return fail(SLSO_ERR_OOM, "internal: scratch plan overflowed the pool");
+  return SLSO_OK;
+}
+
+slso_status fill_info(Handle& h, cudaStream_t st, slso_info* info) {
+  SLSO_CHECK_CUDA(cudaMemcpyAsync(h.state_host, h.state, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  SLSO_CHECK_CUDA(cudaStreamSynchronize(st));
+  const DevState& d = *h.state_host;
+  info->rank = d.rank;
+  info->sigma_max = d.sigma_max;
+  info->sigma_min_kept = d.sigma_min_kept;
+  info->score_sum = d.score_sum;
+  info->tau = d.tau;
+  info->nonfinite = d.nonfinite;
+  info->svd_route = d.need_svd;
+  if (d.timeout) return fail(SLSO_ERR_TIMEOUT, "a bounded device wait gave up (kernel %d)", d.timeout);
+  if (d.nonfinite) return fail(SLSO_ERR_NONFINITE, "X holds NaN or Inf");
+  return SLSO_OK;
+}
+
+slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                          int32_t xdt, const slso_params* p, void* scores, cudaStream_t st) {
+  const double tau = p->tau < 0 ? default_tau(p->s, d) : p->tau;
+  double* SX = ar.take<double>(static_cast<size_t>(p->s) * d);
+  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, SX, st));
+  SolveOut so;
+  SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st));
+  const int64_t kk = p->k > 0 ? p->k : d;
+  SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, so.M, kk, p->compute, scores, p->correct_frac, st));
+  return SLSO_OK;
+}
+
+}  // namespace
+
+extern "C" slso_status slso_workspace_size(const slso_params* params, int64_t n, int64_t d, size_t* bytes) {
+  if (!bytes) return fail(SLSO_ERR_INVALID_ARG, "bytes is NULL");
+  SLSO_TRY(check_params(params, n, d));
+  Handle h;
+  h.num_sms = 148;
+  Arena m(nullptr, ~size_t(0), true);
+  const int32_t sdt = params->compute == SLSO_F64 ? SLSO_F64 : SLSO_F32;
+  SLSO_TRY(leverage_plan(h, m, reinterpret_cast<const void*>(16), n, d, d, SLSO_F32, params,
+                         reinterpret_cast<void*>(16), nullptr));
+  SLSO_TRY(order_scores(h, m, reinterpret_cast<const void*>(16), sdt, n, reinterpret_cast<int64_t*>(16), nullptr));
+  *bytes = m.used();
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_sketch(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
+                                   int32_t xdt, int32_t kind, int64_t s, uint64_t seed_S, double* SX,
+                                   void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  SLSO_TRY(check_x(X, n, d, ldx, xdt));
+  SLSO_TRY(check_sketch(kind, n, d, s));
+  if (!SX) return fail(SLSO_ERR_INVALID_ARG, "SX is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+  return run_plan(*h, [&](Arena& ar) { return run_sketch(*h, ar, X, n, d, ldx, xdt, kind, s, seed_S, SX, st); });
+}
+
+extern "C" slso_status slso_sketched_svd(slso_handle* handle, const double* SX, int64_t s, int64_t d,
+                                         double tau, double* sigma, double* V, double* R, slso_info* info,
+                                         void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (!SX || !sigma || !V) return fail(SLSO_ERR_INVALID_ARG, "SX, sigma and V must be non-NULL");
+  if (d < 1 || s < d) return fail(SLSO_ERR_SHAPE, "need 1 <= d <= s (s=%lld, d=%lld)", (long long)s, (long long)d);
+  if (d > 8192 || s >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "d <= 8192 and s < 2^31 required");
+  if (std::isnan(tau)) return fail(SLSO_ERR_INVALID_ARG, "tau is NaN");
+  const double t = tau < 0 ? default_tau(s, d) : tau;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+  SolveOut so;
+  SLSO_TRY(run_plan(*h, [&](Arena& ar) { return run_solve(*h, ar, SX, s, d, t, 0, 0, 1, &so, st); }));
+  SLSO_CHECK_CUDA(cudaMemcpyAsync(sigma, so.sigma, sizeof(double) * d, cudaMemcpyDeviceToDevice, st));
+  SLSO_CHECK_CUDA(cudaMemcpyAsync(V, so.V, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, st));
+  if (R) SLSO_CHECK_CUDA(cudaMemcpyAsync(R, so.R, sizeof(double) * d * d, cudaMemcpyDeviceToDevice, st));
+  if (info) return fill_info(*h, st, info);
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
+                                     int32_t xdt, const slso_params* params, void* scores, slso_info* info,
+                                     void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  SLSO_TRY(check_x(X, n, d, ldx, xdt));
+  SLSO_TRY(check_params(params, n, d));
+  if (!scores) return fail(SLSO_ERR_INVALID_ARG, "scores is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+  SLSO_TRY(run_plan(*h, [&](Arena& ar) { return leverage_plan(*h, ar, X, n, d, ldx, xdt, params, scores, st); }));
+  if (info) return fill_info(*h, st, info);
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
+                                  int64_t* order, void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (!scores || !order) return fail(SLSO_ERR_INVALID_ARG, "scores and order must be non-NULL");
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "need 1 <= n < 2^31");
+  if (sdt != SLSO_F32 && sdt != SLSO_F64) return fail(SLSO_ERR_DTYPE, "scores must be F32 or F64");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return run_plan(*h, [&](Arena& ar) { return order_scores(*h, ar, scores, sdt, n, order, st); });
+}
+
+extern "C" slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t n, int64_t d,
+                                           int64_t ldx, int32_t xdt, const slso_params* params,
+                                           void* scores_host, int64_t* order_host, slso_info* info,
+                                           void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  SLSO_TRY(check_x(X_host, n, d, ldx, xdt));
+  SLSO_TRY(check_params(params, n, d));
+  if (!scores_host || !order_host) return fail(SLSO_ERR_INVALID_ARG, "scores_host and order_host must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t esz = dtype_size(xdt);
+  const int32_t sdt = params->compute == SLSO_F64 ? SLSO_F64 : SLSO_F32;
+  const size_t ssz = dtype_size(sdt);
+  char* Xd = nullptr;
+  void* sc = nullptr;
+  int64_t* od = nullptr;
+  SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+  SLSO_TRY(run_plan(*h, [&](Arena& ar) {
+    Xd = ar.take<char>(static_cast<size_t>(n) * d * esz);
+    sc = ar.take<char>(static_cast<size_t>(n) * ssz);
+    od = ar.take<int64_t>(n);
+    if (!ar.measure()) {
+      if (ldx == d) {
+        SLSO_CHECK_CUDA(cudaMemcpyAsync(Xd, X_host, static_cast<size_t>(n) * d * esz, cudaMemcpyHostToDevice, st));
+      } else {
+        SLSO_CHECK_CUDA(cudaMemcpy2DAsync(Xd, d * esz, X_host, ldx * esz, d * esz, n, cudaMemcpyHostToDevice, st));
+      }
+    }
+    SLSO_TRY(leverage_plan(*h, ar, Xd, n, d, d, xdt, params, sc, st));
+    SLSO_TRY(order_scores(*h, ar, sc, sdt, n, od, st));
+    if (!ar.measure()) {
+      SLSO_CHECK_CUDA(cudaMemcpyAsync(scores_host, sc, static_cast<size_t>(n) * ssz, cudaMemcpyDeviceToHost, st));
+      SLSO_CHECK_CUDA(cudaMemcpyAsync(order_host, od, static_cast<size_t>(n) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
+    return SLSO_OK;
+  }));
+  if (info) return fill_info(*h, st, info);
+  SLSO_CHECK_CUDA(cudaStreamSynchronize(st));
+  return SLSO_OK;
+}

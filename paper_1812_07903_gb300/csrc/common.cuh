@@ -1,0 +1,298 @@
+// Internal definitions shared by the CUDA translation units of libslso.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <type_traits>
+
+#include "slso.h"
+
+namespace slso {
+
+// ------------------------------------------------------------------ errors
+slso_status fail(slso_status st, const char* fmt, ...);
+
+#define SLSO_CHECK_CUDA(expr)                                                                  \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::slso::fail(SLSO_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                          __FILE__, __LINE__);                                                 \
+  } while (0)
+
+#define SLSO_CHECK_LAUNCH() SLSO_CHECK_CUDA(cudaGetLastError())
+
+#define SLSO_TRY(expr)              \
+  do {                              \
+    slso_status s_ = (expr);        \
+    if (s_ != SLSO_OK) return s_;   \
+  } while (0)
+
+// ------------------------------------------------------------------ device status words
+// One per handle, in device memory.  Kernels only ever set fields (never wait on them).
+struct DevState {
+  int32_t nonfinite;     // X held NaN/Inf
+  int32_t need_svd;      // certification failed: take the SVD route
+  int32_t timeout;       // a bounded wait gave up (id of the kernel)
+  int32_t rank;          // numerical rank r
+  int32_t rotations;     // Jacobi: rotations applied in the current sweep
+  int32_t sweeps;        // Jacobi: sweeps run
+  int32_t pad0, pad1;
+  double sigma_max;      // sigma_1 (SVD route)
+  double sigma_min_kept; // sigma_r (SVD route)
+  double score_sum;
+  double tau;
+  double fro_r;          // ||R||_F
+  double fro_rinv;       // ||R^-1||_F
+};
+
+// ------------------------------------------------------------------ scratch arena
+// Every internal run function first takes all of its buffers from an Arena and only then
+// launches.  Run once with a measuring arena to size the pool, then for real.
+class Arena {
+ public:
+  Arena(char* base, size_t cap, bool measure) : base_(base), cap_(cap), off_(0), measure_(measure) {}
+  template <class T>
+  T* take(size_t count) {
+    size_t off = (off_ + 255) & ~size_t(255);
+    off_ = off + count * sizeof(T);
+    if (measure_ || off_ > cap_) return nullptr;
+    return reinterpret_cast<T*>(base_ + off);
+  }
+  bool measure() const { return measure_; }
+  size_t used() const { return off_; }
+  bool overflow() const { return off_ > cap_; }
+
+ private:
+  char* base_;
+  size_t cap_;
+  size_t off_;
+  bool measure_;
+};
+
+struct Handle {
+  int device = 0;
+  int num_sms = 0;
+  char* pool = nullptr;
+  size_t pool_cap = 0;
+  DevState* state = nullptr;       // device
+  DevState* state_host = nullptr;  // pinned mirror for info
+};
+
+slso_status ensure_pool(Handle& h, size_t bytes);
+slso_status check_handle(slso_handle* hp, Handle** out);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t dtype_size(int32_t dt) {
+  switch (dt) {
+    case SLSO_F64: return 8;
+    case SLSO_F32: return 4;
+    case SLSO_BF16: return 2;
+    case SLSO_FP8_E4M3: return 1;
+    default: return 0;
+  }
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: two 32x32->64 multiplies per round, Weyl key bumps.
+struct U32x4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint64_t key) {
+  uint32_t k0 = static_cast<uint32_t>(key), k1 = static_cast<uint32_t>(key >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+
+enum : uint32_t {
+  TAG_COUNTSKETCH = 1,
+  TAG_SRHT_SIGN = 2,
+  TAG_SRHT_SAMPLE = 3,
+  TAG_GAUSSIAN = 4,
+  TAG_JL = 5
+};
+
+// ------------------------------------------------------------------ Box-Muller
+// Normal deviate sqrt(-2 ln u1) cos(2 pi u2), u1 = (w0+1) 2^-32, u2 = w1 2^-32, evaluated from
+// exact arguments: ln u1 through log1p(-m 2^-32), m = 2^32-1-w0, when w0 >= 2^31; the angle is
+// reduced to its octant o = w1 >> 29 and an exact fraction c in [0,1] so that the cosine is
+// +-sin or +-cos of (pi/4) c.
+__device__ __forceinline__ double box_muller_f64(uint32_t w0, uint32_t w1) {
+  const double ln_u1 = (w0 >= 0x80000000u)
+                           ? log1p(-static_cast<double>(0xFFFFFFFFu - w0) * 0x1p-32)
+                           : log((static_cast<double>(w0) + 1.0) * 0x1p-32);
+  const double rho = sqrt(-2.0 * ln_u1);
+  const uint32_t oct = w1 >> 29;
+  const bool odd = oct & 1u;
+  const uint32_t f = w1 & 0x1FFFFFFFu;
+  const uint32_t ci = odd ? (0x20000000u - f) : f;  // exact integer in [0, 2^29]
+  const double arg = static_cast<double>(ci) * 0x1p-31;  // (pi/4) c = pi * arg
+  const double sn = sinpi(arg), cs = cospi(arg);
+  const uint32_t q = odd ? (oct + 1) >> 1 : oct >> 1;
+  double v;
+  switch (q) {
+    case 0: v = cs; break;
+    case 1: v = odd ? sn : -sn; break;
+    case 2: v = -cs; break;
+    case 3: v = odd ? -sn : sn; break;
+    default: v = cs; break;
+  }
+  return rho * v;
+}
+
+// Same formula in float32: a few ulp from the exact value (each factor within ~2 ulp).
+__device__ __forceinline__ float box_muller_f32(uint32_t w0, uint32_t w1) {
+  const float ln_u1 = (w0 >= 0x80000000u)
+                          ? log1pf(-static_cast<float>(0xFFFFFFFFu - w0) * 0x1p-32f)
+                          : logf((static_cast<float>(w0) + 1.0f) * 0x1p-32f);
+  const float rho = sqrtf(-2.0f * ln_u1);
+  const uint32_t oct = w1 >> 29;
+  const bool odd = oct & 1u;
+  const uint32_t f = w1 & 0x1FFFFFFFu;
+  const uint32_t ci = odd ? (0x20000000u - f) : f;
+  const float arg = static_cast<float>(ci) * 0x1p-31f;
+  const float sn = sinpif(arg), cs = cospif(arg);
+  const uint32_t q = odd ? (oct + 1) >> 1 : oct >> 1;
+  float v;
+  switch (q) {
+    case 0: v = cs; break;
+    case 1: v = odd ? sn : -sn; break;
+    case 2: v = -cs; break;
+    case 3: v = odd ? -sn : sn; break;
+    default: v = cs; break;
+  }
+  return rho * v;
+}
+
+// Round a float64 to bfloat16 (8 significant bits), nearest-even, in one step on the bits.
+__device__ __forceinline__ float bf16_round_f64(double x) {
+  unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned long long lsb = (b >> 45) & 1ull;
+  b = (b + ((1ull << 44) - 1ull) + lsb) & ~((1ull << 45) - 1ull);
+  return static_cast<float>(__longlong_as_double(static_cast<long long>(b)));
+}
+
+// bfloat16 value of the float64 normal deviate, with the rounding decided exactly as float64
+// rounding would decide it.  The float32 evaluation is within ~2^-21.7 (relative) of the exact
+// value; when it lies further than 128 float32 ulp (>= 2^-17 relative) from a bfloat16 rounding
+// midpoint its nearest-even rounding equals that of the exact value, otherwise the float64
+// evaluation decides.
+__device__ __forceinline__ float gaussian_bf16_value(uint32_t w0, uint32_t w1) {
+  const float z = box_muller_f32(w0, w1);
+  const uint32_t low = __float_as_uint(z) & 0xFFFFu;
+  const int dist = static_cast<int>(low) - 0x8000;
+  if (dist > 128 || dist < -128) return __bfloat162float(__float2bfloat16_rn(z));
+  return bf16_round_f64(box_muller_f64(w0, w1));
+}
+
+__device__ __forceinline__ float gaussian_entry(uint64_t seed, uint32_t row_j, uint64_t col_i) {
+  const U32x4 w = philox(static_cast<uint32_t>(col_i), static_cast<uint32_t>(col_i >> 32), row_j,
+                         TAG_GAUSSIAN, seed);
+  return gaussian_bf16_value(w.x, w.y);
+}
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_float(double v) { return static_cast<float>(v); }
+
+__device__ __forceinline__ float to_float_or_double(float v) { return v; }
+__device__ __forceinline__ float to_float_or_double(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_float_or_double(double v) { return v; }
+
+// Knuth's TwoSum: hi + lo accumulates x with the rounding error of every add kept in lo.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ void comp_add(float& hi, float& lo, float x) { two_sum_acc(hi, lo, x); }
+__device__ __forceinline__ void comp_add(double& hi, double& lo, double x) {
+  hi += x;
+  (void)lo;
+}
+
+// Descending-order radix keys: NaN -> all ones (last); -0 -> +0.
+__device__ __forceinline__ uint32_t desc_key_f32(float f) {
+  if (isnan(f)) return 0xFFFFFFFFu;
+  if (f == 0.0f) f = 0.0f;
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ~ord;
+}
+__device__ __forceinline__ unsigned long long desc_key_f64(double f) {
+  if (isnan(f)) return ~0ull;
+  if (f == 0.0) f = 0.0;
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(f));
+  const unsigned long long ord = (u >> 63) ? ~u : (u | (1ull << 63));
+  return ~ord;
+}
+
+// Bounded spin on a flag written by another CTA of the same (co-resident) grid.
+// Returns false after ~`limit` polls; the caller records a timeout and bails out.
+__device__ __forceinline__ bool wait_flag_geq(const volatile int* flag, int value, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    if (*flag >= value) return true;
+    __nanosleep(64);
+  }
+  return *flag >= value;
+}
+
+}  // namespace slso
+
+// ------------------------------------------------------------------ cross-TU host interface
+namespace slso {
+
+// sort.cu
+slso_status radix_sort_u32(Arena& ar, uint32_t* keys, uint32_t* vals, int64_t n, int bits,
+                           cudaStream_t st, uint32_t** keys_out, uint32_t** vals_out);
+slso_status radix_sort_u64(Arena& ar, unsigned long long* keys, uint32_t* vals, int64_t n,
+                           int bits, cudaStream_t st, unsigned long long** keys_out,
+                           uint32_t** vals_out);
+slso_status order_scores(Handle& h, Arena& ar, const void* scores, int32_t sdt, int64_t n,
+                         int64_t* order, cudaStream_t st);
+
+// sketch.cu
+slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                       int32_t xdt, int32_t kind, int64_t s, uint64_t seed, double* SX,
+                       cudaStream_t st);
+
+// solve.cu
+struct SolveOut {
+  double* M = nullptr;      // d x kk row-major float64 (kk = k, or d when k = 0)
+  double* sigma = nullptr;  // d (SVD route / sketched SVD)
+  double* V = nullptr;      // d x d row-major (column j = v_j)
+  double* R = nullptr;      // d x d row-major
+  int64_t kk = 0;
+};
+// mode 0: leverage (certified inverse or SVD); mode 1: sketched SVD only (always SVD).
+slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t d, double tau,
+                      int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st);
+
+// score.cu
+slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                       int32_t xdt, const double* M, int64_t kk, int32_t compute, void* scores,
+                       double correct_frac, cudaStream_t st);
+
+}  // namespace slso

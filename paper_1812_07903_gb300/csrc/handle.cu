@@ -1,0 +1,90 @@
+// Handle, device pool and error reporting of libslso.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace slso {
+
+static thread_local char g_last_error[1024] = "";
+
+slso_status fail(slso_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+slso_status ensure_pool(Handle& h, size_t bytes) {
+  if (bytes <= h.pool_cap) return SLSO_OK;
+  // Growing frees the old block; cudaFree waits for work in flight on the device.
+  if (h.pool) {
+    SLSO_CHECK_CUDA(cudaFree(h.pool));
+    h.pool = nullptr;
+    h.pool_cap = 0;
+  }
+  const size_t cap = (bytes + (size_t(2) << 20) - 1) & ~((size_t(2) << 20) - 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h.pool), cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h.pool = nullptr;
+    return fail(SLSO_ERR_OOM, "device pool of %zu bytes could not be allocated: %s", cap,
+                cudaGetErrorString(e));
+  }
+  h.pool_cap = cap;
+  return SLSO_OK;
+}
+
+slso_status check_handle(slso_handle* hp, Handle** out) {
+  if (!hp) return fail(SLSO_ERR_INVALID_ARG, "handle is NULL");
+  Handle* h = reinterpret_cast<Handle*>(hp);
+  SLSO_CHECK_CUDA(cudaSetDevice(h->device));
+  *out = h;
+  return SLSO_OK;
+}
+
+}  // namespace slso
+
+using namespace slso;
+
+extern "C" const char* slso_version(void) { return "slso-gb300 0.1 (sm_103a)"; }
+
+extern "C" const char* slso_last_error(void) { return g_last_error; }
+
+extern "C" slso_status slso_create(slso_handle** handle, int device) {
+  if (!handle) return fail(SLSO_ERR_INVALID_ARG, "handle out-pointer is NULL");
+  *handle = nullptr;
+  int count = 0;
+  SLSO_CHECK_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count)
+    return fail(SLSO_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, count);
+  SLSO_CHECK_CUDA(cudaSetDevice(device));
+  Handle* h = new Handle();
+  h->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->state), sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->state_host), sizeof(DevState));
+  if (e == cudaSuccess) e = cudaMemset(h->state, 0, sizeof(DevState));
+  if (e != cudaSuccess) {
+    if (h->state) cudaFree(h->state);
+    if (h->state_host) cudaFreeHost(h->state_host);
+    delete h;
+    return fail(SLSO_ERR_CUDA, "slso_create: %s", cudaGetErrorString(e));
+  }
+  *handle = reinterpret_cast<slso_handle*>(h);
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_destroy(slso_handle* handle) {
+  if (!handle) return SLSO_OK;
+  Handle* h = reinterpret_cast<Handle*>(handle);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->pool) cudaFree(h->pool);
+  if (h->state) cudaFree(h->state);
+  if (h->state_host) cudaFreeHost(h->state_host);
+  delete h;
+  return SLSO_OK;
+}

@@ -1,0 +1,564 @@
+// FP64 small solve on the sketch (Algorithm 2/3 steps 2-4):
+//
+//   R      unpivoted Householder QR of SX (s x d), R_jj >= 0          qr_kernel
+//   route  ||R||_F ||R^-1||_F < 1e-3/tau certifies rank d, so R^+_tau = R^-1 exactly
+//   M      = R^-1 Pi (certified)  or  V_r Sigma_r^-1 U_R,r^T Pi (one-sided Jacobi SVD of R)
+//
+// All steps run on the GPU in float64.  The route is decided on the device (no host
+// synchronisation); kernels of the route not taken return immediately.
+//
+// QR layout: SX is transposed to column-major A (column l at A + l*s).  A persistent
+// cooperative grid owns columns round-robin (column l belongs to CTA l % G).  Step j: the owner
+// of column j forms the reflector (beta, tau, v stored in place as LAPACK does) and publishes a
+// per-column ready flag; every CTA applies it to its own columns > j.  The owner of column j+1
+// updates that column first and immediately forms the next reflector, so steps pipeline and
+// the only synchronisation is one bounded flag wait per step.
+#include <algorithm>
+#include <cmath>
+
+#include <math_constants.h>
+
+#include "common.cuh"
+
+namespace slso {
+
+namespace {
+
+constexpr int kQrThreads = 512;
+constexpr long long kWaitPolls = 1LL << 24;  // ~1-2 s before a wait gives up
+
+__device__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void transpose_kernel(const double* __restrict__ in, int64_t rows, int64_t cols,
+                                 double* __restrict__ out) {
+  // in: rows x cols row-major; out: cols x rows row-major (= in column-major)
+  __shared__ double tile[32][33];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32, c0 = static_cast<int64_t>(blockIdx.x) * 32;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int64_t r = r0 + rr, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[rr][threadIdx.x] = in[r * cols + c];
+  }
+  __syncthreads();
+  for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
+    const int64_t c = c0 + cc, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][cc];
+  }
+}
+
+// Householder reflector of column j (run by every thread of the owning CTA).
+__device__ void make_reflector(double* __restrict__ A, int s, int j, double* __restrict__ taus,
+                               int* __restrict__ ready, double* red) {
+  double* col = A + static_cast<int64_t>(j) * s;
+  const double alpha = col[j];
+  double part = 0.0;
+  for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) part += col[i] * col[i];
+  const double xn2 = block_sum(part, red);
+  double tau = 0.0;
+  if (xn2 != 0.0) {
+    const double norm = sqrt(alpha * alpha + xn2);
+    const double beta = alpha >= 0.0 ? -norm : norm;
+    tau = (beta - alpha) / beta;
+    const double den = alpha - beta;
+    for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) col[i] = col[i] / den;
+    if (threadIdx.x == 0) col[j] = beta;
+  }
+  if (threadIdx.x == 0) taus[j] = tau;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(&ready[j], 1);
+}
+
+template <bool V_SMEM>
+__global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ A, int s, int d,
+                                                           int* __restrict__ ready,
+                                                           double* __restrict__ taus,
+                                                           DevState* __restrict__ state) {
+  extern __shared__ double vs[];
+  __shared__ double red[33];
+  __shared__ int s_abort;
+  const int G = gridDim.x, me = blockIdx.x;
+  if (threadIdx.x == 0) s_abort = 0;
+  __syncthreads();
+  if (me == 0) make_reflector(A, s, 0, taus, ready, red);
+  for (int j = 0; j < d; ++j) {
+    // smallest column > j owned by this CTA
+    int lf = j + 1 + ((me - (j + 1)) % G + G) % G;
+    if (lf >= d) break;  // nothing of ours is left to update
+    if (threadIdx.x == 0) {
+      if (!wait_flag_geq(ready + j, 1, kWaitPolls)) {
+        atomicExch(&state->timeout, 1);
+        s_abort = 1;
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const double tau = __ldcg(taus + j);
+    const double* vg = A + static_cast<int64_t>(j) * s;
+    if (tau == 0.0) {  // H_j = I
+      if (lf == j + 1) make_reflector(A, s, j + 1, taus, ready, red);
+      continue;
+    }
+    if (V_SMEM) {
+      for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) vs[i] = __ldcg(vg + i);
+      __syncthreads();
+    }
+    for (int l = lf; l < d; l += G) {
+      double* col = A + static_cast<int64_t>(l) * s;
+      double part = 0.0;
+      for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x)
+        part += (V_SMEM ? vs[i] : __ldcg(vg + i)) * col[i];
+      const double c = col[j] + block_sum(part, red);
+      const double tc = tau * c;
+      for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x)
+        col[i] -= tc * (V_SMEM ? vs[i] : __ldcg(vg + i));
+      if (threadIdx.x == 0) col[j] -= tc;
+      __syncthreads();
+      if (l == j + 1) make_reflector(A, s, j + 1, taus, ready, red);
+    }
+  }
+}
+
+// R (d x d row-major) from the QR storage, rows negated where the diagonal is negative.
+__global__ void r_extract_kernel(const double* __restrict__ A, int64_t s, int64_t d,
+                                 double* __restrict__ R, double* __restrict__ sgn) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * d;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / d, l = e % d;
+    const double sg = A[i * s + i] < 0.0 ? -1.0 : 1.0;
+    R[e] = (l >= i) ? sg * A[l * s + i] : 0.0;
+    if (l == 0) sgn[i] = sg;
+  }
+}
+
+// sum of squares of n values into *out (one CTA, fixed order)
+__global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+  __shared__ double red[33];
+  double part = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += x[i] * x[i];
+  const double t = block_sum(part, red);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// Column c of R^-1 (column-major, d x d) by back substitution R x = e_c, column-oriented.
+__global__ void trinv_kernel(const double* __restrict__ A, int64_t s, int64_t d,
+                             const double* __restrict__ sgn, double* __restrict__ Rinv) {
+  extern __shared__ double b[];
+  const int64_t c = blockIdx.x;
+  for (int64_t i = threadIdx.x; i <= c; i += blockDim.x) b[i] = (i == c) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int64_t k = c; k >= 0; --k) {
+    const double rkk = sgn[k] * A[k * s + k];
+    const double xk = b[k] / rkk;
+    __syncthreads();
+    if (threadIdx.x == 0) b[k] = xk;
+    for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] -= sgn[i] * A[k * s + i] * xk;
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Rinv[c * d + i] = (i <= c) ? b[i] : 0.0;
+}
+
+__global__ void certify_kernel(DevState* __restrict__ st, const double* __restrict__ fro2,
+                               int64_t d, double tau, int force_svd) {
+  const double fr = sqrt(fro2[0]), fi = sqrt(fro2[1]);
+  st->fro_r = fr;
+  st->fro_rinv = fi;
+  st->tau = tau;
+  const bool ok = !force_svd && isfinite(fi) && fi > 0.0 && fr * fi < 1e-3 / tau;
+  st->need_svd = ok ? 0 : 1;
+  if (ok) {
+    st->rank = static_cast<int32_t>(d);
+    st->sigma_max = CUDART_NAN;
+    st->sigma_min_kept = CUDART_NAN;
+  }
+}
+
+__global__ void pi_kernel(int64_t d, int64_t k, uint64_t seed, double* __restrict__ Pi) {
+  const double sk = sqrt(static_cast<double>(k));
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * k;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t j = e / k, c = e % k;
+    const U32x4 w = philox(static_cast<uint32_t>(c), static_cast<uint32_t>(static_cast<uint64_t>(c) >> 32),
+                           static_cast<uint32_t>(j), TAG_JL, seed);
+    Pi[e] = box_muller_f64(w.x, w.y) / sk;
+  }
+}
+
+// C (m x n, row-major) = A (m x K) B (K x n); element (r, c) of A at A[r*ars + c*acs].
+// Runs only when guard == nullptr or *guard == want.
+__global__ void gemm_f64_kernel(int64_t m, int64_t n, int64_t K, const double* __restrict__ A,
+                                int64_t ars, int64_t acs, const double* __restrict__ B, int64_t brs,
+                                int64_t bcs, double* __restrict__ C, const int32_t* guard, int want) {
+  if (guard && *guard != want) return;
+  __shared__ double As[32][33], Bs[32][33];
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32, c0 = static_cast<int64_t>(blockIdx.x) * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t k0 = 0; k0 < K; k0 += 32) {
+    for (int t = threadIdx.x; t < 32 * 32; t += 256) {
+      const int a = t / 32, b = t % 32;
+      const int64_t r = r0 + a, kk = k0 + b;
+      As[a][b] = (r < m && kk < K) ? A[r * ars + kk * acs] : 0.0;
+      const int64_t kb = k0 + a, c = c0 + b;
+      Bs[a][b] = (kb < K && c < n) ? B[kb * brs + c * bcs] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double bv = Bs[kk][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(As[ty * 4 + q][kk], bv, acc[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t r = r0 + ty * 4 + q, c = c0 + tx;
+    if (r < m && c < n) C[r * n + c] = acc[q];
+  }
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi SVD of R
+__device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, unsigned int nblocks,
+                             int* abort_flag) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd(const_cast<unsigned int*>(gen), 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > kWaitPolls || *abort_flag) {
+          s_ok = 0;
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok;
+}
+
+// W: dp x dp column-major (column p at W + p*dp), V likewise; dp even, column d.. are zero.
+__global__ void __launch_bounds__(256) jacobi_kernel(double* __restrict__ W, double* __restrict__ V,
+                                                     int d, int dp, int max_sweeps,
+                                                     DevState* __restrict__ st,
+                                                     unsigned int* bar, int* rot_count,
+                                                     int require_svd_flag) {
+  if (require_svd_flag && st->need_svd == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * wpb;
+  const double tol = sqrt(static_cast<double>(dp)) * 0x1p-53;
+  int* abort_flag = reinterpret_cast<int*>(bar + 2);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int local_rot = 0;
+    for (int r = 0; r < dp - 1; ++r) {
+      for (int kp = gw; kp < dp / 2; kp += nwarps) {
+        const int p = (kp == 0) ? 0 : ((r + kp - 1) % (dp - 1)) + 1;
+        const int t2 = dp - 1 - kp;
+        const int q = ((r + t2 - 1) % (dp - 1)) + 1;
+        if (p >= d || q >= d) continue;
+        double* wp = W + static_cast<int64_t>(p) * dp;
+        double* wq = W + static_cast<int64_t>(q) * dp;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = lane; i < d; i += 32) {
+          const double x = wp[i], y = wq[i];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+          b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+          g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
+        }
+        if (g != 0.0 && fabs(g) > tol * sqrt(a * b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          const double sn = c * t;
+          for (int i = lane; i < d; i += 32) {
+            const double x = wp[i], y = wq[i];
+            wp[i] = c * x - sn * y;
+            wq[i] = sn * x + c * y;
+          }
+          double* vp = V + static_cast<int64_t>(p) * dp;
+          double* vq = V + static_cast<int64_t>(q) * dp;
+          for (int i = lane; i < d; i += 32) {
+            const double x = vp[i], y = vq[i];
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
+          }
+          ++local_rot;
+        }
+        __syncwarp();
+      }
+      if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+        if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+        return;
+      }
+    }
+    if (lane == 0 && local_rot) atomicAdd(rot_count + sweep, local_rot);
+    if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+      if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+      return;
+    }
+    const int total = *reinterpret_cast<volatile int*>(rot_count + sweep);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->sweeps = sweep + 1;
+    if (total == 0) break;
+  }
+}
+
+__global__ void jacobi_init_kernel(const double* __restrict__ R, int64_t d, int64_t dp,
+                                   double* __restrict__ W, double* __restrict__ V) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < dp * dp;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t col = e / dp, row = e % dp;
+    W[e] = (row < d && col < d) ? R[row * d + col] : 0.0;
+    V[e] = (row == col) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void colnorm_kernel(const double* __restrict__ W, int64_t d, int64_t dp, double* __restrict__ sig,
+                               const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t col = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  if (col >= d) return;
+  double a = 0.0;
+  for (int64_t i = lane; i < d; i += 32) a = fma(W[col * dp + i], W[col * dp + i], a);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+  if (lane == 0) sig[col] = sqrt(a);
+}
+
+// Sort sigma descending (ties by column index), rank, and the scaled factors:
+//   sigma_out (d), Vout (d x d row-major, column a = v_(a)), Vs = V_r diag(1/sigma_r) (d x d,
+//   zero columns beyond r), Ur (d x d, column a = w_(a) / sigma_(a) for a < r, else 0).
+__global__ void svd_finalize_kernel(const double* __restrict__ W, const double* __restrict__ Vw,
+                                    const double* __restrict__ sig, int64_t d, int64_t dp, double tau,
+                                    double* __restrict__ sigma_out, double* __restrict__ Vout,
+                                    double* __restrict__ Vs, double* __restrict__ Ur, int* __restrict__ perm,
+                                    DevState* __restrict__ st, const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  // one CTA
+  // NaN (from non-finite input) ranks below every number, so the order stays total and perm
+  // is a permutation.
+  for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
+    int64_t pos = 0;
+    const double sj = isnan(sig[j]) ? -1.0 : sig[j];
+    for (int64_t i = 0; i < d; ++i) {
+      const double si = isnan(sig[i]) ? -1.0 : sig[i];
+      pos += (si > sj) || (si == sj && i < j);
+    }
+    perm[pos] = static_cast<int>(j);
+  }
+  __syncthreads();
+  __shared__ double s_max;
+  __shared__ int s_rank;
+  if (threadIdx.x == 0) {
+    s_max = sig[perm[0]];
+    int r = 0;
+    if (s_max > 0.0)
+      for (int64_t a = 0; a < d; ++a) r += sig[perm[a]] > tau * s_max;
+    s_rank = r;
+    st->rank = r;
+    st->sigma_max = s_max;
+    st->sigma_min_kept = r > 0 ? sig[perm[r - 1]] : 0.0;
+    st->tau = tau;
+  }
+  __syncthreads();
+  const int r = s_rank;
+  for (int64_t e = threadIdx.x; e < d * d; e += blockDim.x) {
+    const int64_t i = e / d, a = e % d;
+    const int j = perm[a];
+    const double sj = sig[j];
+    const double v = Vw[static_cast<int64_t>(j) * dp + i];
+    if (Vout) Vout[e] = v;
+    if (Vs) Vs[e] = (a < r) ? v / sj : 0.0;
+    if (Ur) Ur[e] = (a < r) ? W[static_cast<int64_t>(j) * dp + i] / sj : 0.0;
+  }
+  if (sigma_out)
+    for (int64_t a = threadIdx.x; a < d; a += blockDim.x) sigma_out[a] = sig[perm[a]];
+}
+
+__global__ void copy_guarded_kernel(const double* __restrict__ a, int64_t n, double* __restrict__ b,
+                                    const int32_t* guard, int want) {
+  if (guard && *guard != want) return;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    b[i] = a[i];
+}
+
+// Rinv column-major -> row-major copy (M for k = 0 on the certified route)
+__global__ void rinv_rowmajor_kernel(const double* __restrict__ Rinv, int64_t d, double* __restrict__ M,
+                                     const int32_t* guard) {
+  if (guard && *guard != 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * d;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / d, c = e % d;
+    M[e] = Rinv[c * d + i];
+  }
+}
+
+int grid1d(int64_t n, const Handle& h) {
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8LL * h.num_sms)));
+}
+
+slso_status launch_gemm(int64_t m, int64_t n, int64_t K, const double* A, int64_t ars, int64_t acs,
+                        const double* B, int64_t brs, int64_t bcs, double* C, const int32_t* guard,
+                        int want, cudaStream_t st) {
+  dim3 grid(static_cast<unsigned>(ceil_div(n, 32)), static_cast<unsigned>(ceil_div(m, 32)));
+  gemm_f64_kernel<<<grid, 256, 0, st>>>(m, n, K, A, ars, acs, B, brs, bcs, C, guard, want);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
+}  // namespace
+
+slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t d, double tau,
+                      int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st) {
+  const int64_t dp = d + (d & 1);
+  const int64_t kk = (k > 0) ? k : d;
+  double* A = ar.take<double>(static_cast<size_t>(s) * d);
+  int* ready = ar.take<int>(d);
+  double* taus = ar.take<double>(d);
+  double* R = ar.take<double>(static_cast<size_t>(d) * d);
+  double* sgn = ar.take<double>(d);
+  double* fro2 = ar.take<double>(2);
+  double* Rinv = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  double* Pi = (k > 0) ? ar.take<double>(static_cast<size_t>(d) * k) : nullptr;
+  double* W = ar.take<double>(static_cast<size_t>(dp) * dp);
+  double* Vw = ar.take<double>(static_cast<size_t>(dp) * dp);
+  double* sig = ar.take<double>(d);
+  int* perm = ar.take<int>(d);
+  unsigned int* bar = ar.take<unsigned int>(4);
+  int* rot = ar.take<int>(64);
+  double* Vs = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  double* Ur = (mode == 0 && k > 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  double* Z = (mode == 0 && k > 0) ? ar.take<double>(static_cast<size_t>(d) * k) : nullptr;
+  double* M = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * kk) : nullptr;
+  double* sigma_out = (mode == 1) ? ar.take<double>(d) : nullptr;
+  double* Vout = (mode == 1) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  if (ar.measure()) return SLSO_OK;
+  if (s > 24576 * 8) return fail(SLSO_ERR_SHAPE, "sketch rows s=%lld exceed the QR limit", (long long)s);
+
+  // ---- QR
+  {
+    dim3 g(static_cast<unsigned>(ceil_div(d, 32)), static_cast<unsigned>(ceil_div(s, 32)));
+    transpose_kernel<<<g, dim3(32, 8), 0, st>>>(SX, s, d, A);
+    SLSO_CHECK_LAUNCH();
+  }
+  SLSO_CHECK_CUDA(cudaMemsetAsync(ready, 0, sizeof(int) * d, st));
+  {
+    const bool vsm = s <= 24576;
+    const size_t smem = vsm ? sizeof(double) * s : 0;
+    void* fn = vsm ? reinterpret_cast<void*>(qr_kernel<true>) : reinterpret_cast<void*>(qr_kernel<false>);
+    SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int occ = 0;
+    SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQrThreads, smem));
+    if (occ < 1) return fail(SLSO_ERR_CUDA, "QR kernel cannot be resident (smem %zu)", smem);
+    int G = static_cast<int>(std::min<int64_t>(h.num_sms, d));
+    int s_i = static_cast<int>(s), d_i = static_cast<int>(d);
+    void* args[] = {&A, &s_i, &d_i, &ready, &taus, &h.state};
+    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, st));
+  }
+  r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(A, s, d, R, sgn);
+  SLSO_CHECK_LAUNCH();
+  sumsq_kernel<<<1, 1024, 0, st>>>(R, d * d, fro2);
+  SLSO_CHECK_LAUNCH();
+
+  // ---- certified route: R^-1
+  if (mode == 0) {
+    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(A, s, d, sgn, Rinv);
+    SLSO_CHECK_LAUNCH();
+    sumsq_kernel<<<1, 1024, 0, st>>>(Rinv, d * d, fro2 + 1);
+    SLSO_CHECK_LAUNCH();
+  }
+  certify_kernel<<<1, 1, 0, st>>>(h.state, fro2, d, tau, mode == 1 ? 1 : 0);
+  SLSO_CHECK_LAUNCH();
+  const int32_t* need = &h.state->need_svd;
+  if (k > 0) {
+    pi_kernel<<<grid1d(d * k, h), 256, 0, st>>>(d, k, seed_pi, Pi);
+    SLSO_CHECK_LAUNCH();
+  }
+  if (mode == 0) {
+    if (k > 0) {
+      // M = R^-1 Pi, R^-1 column-major: element (i, m) at Rinv[m*d + i]
+      SLSO_TRY(launch_gemm(d, k, d, Rinv, 1, d, Pi, k, 1, M, need, 0, st));
+    } else {
+      rinv_rowmajor_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Rinv, d, M, need);
+      SLSO_CHECK_LAUNCH();
+    }
+  }
+
+  // ---- SVD route (always for mode 1)
+  jacobi_init_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(R, d, dp, W, Vw);
+  SLSO_CHECK_LAUNCH();
+  SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 4, st));
+  SLSO_CHECK_CUDA(cudaMemsetAsync(rot, 0, sizeof(int) * 64, st));
+  {
+    int occ = 0;
+    SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, 256, 0));
+    const int warps_needed = static_cast<int>(dp / 2);
+    int G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h.num_sms) * std::min(occ, 2),
+                                               ceil_div(warps_needed, 8)));
+    G = std::max(G, 1);
+    int d_i = static_cast<int>(d), dp_i = static_cast<int>(dp), sweeps = 60, req = (mode == 0) ? 1 : 0;
+    DevState* stp = h.state;
+    void* args[] = {&W, &Vw, &d_i, &dp_i, &sweeps, &stp, &bar, &rot, &req};
+    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_kernel), dim3(G), dim3(256),
+                                                args, 0, st));
+  }
+  const int32_t* guard = (mode == 0) ? need : nullptr;
+  colnorm_kernel<<<static_cast<unsigned>(ceil_div(d * 32, 256)), 256, 0, st>>>(W, d, dp, sig, guard);
+  SLSO_CHECK_LAUNCH();
+  svd_finalize_kernel<<<1, 1024, 0, st>>>(W, Vw, sig, d, dp, tau, sigma_out, Vout, Vs, Ur, perm, h.state, guard);
+  SLSO_CHECK_LAUNCH();
+  if (mode == 0) {
+    if (k > 0) {
+      // Z = Ur^T Pi (d x k), M = Vs Z
+      SLSO_TRY(launch_gemm(d, k, d, Ur, 1, d, Pi, k, 1, Z, need, 1, st));
+      SLSO_TRY(launch_gemm(d, k, d, Vs, d, 1, Z, k, 1, M, need, 1, st));
+    } else {
+      copy_guarded_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Vs, d * d, M, need, 1);
+      SLSO_CHECK_LAUNCH();
+    }
+  }
+  out->M = M;
+  out->kk = kk;
+  out->R = R;
+  out->sigma = sigma_out;
+  out->V = Vout;
+  return SLSO_OK;
+}
+
+}  // namespace slso

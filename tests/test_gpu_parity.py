@@ -1,0 +1,201 @@
+"""GPU parity: every entry point of the C ABI against the FP64 CPU oracle on the same inputs.
+
+Inputs are seeded and synthetic (paper_1812_07903_gb300.inputs), drawn on the CPU and copied to
+the device; the oracle never sees anything the CUDA path produced, except where a test checks
+a property of the GPU's own output (the ordering of the GPU's scores).
+
+Tolerances (stated per test):
+* float64 path: 1e-9 relative (float64 rounding amplified by the conditioning of SX);
+* float32 path: 1e-4 relative, the parity bound set for the float32 scores;
+* sketches: float32 butterflies / dot products against float64 sums, relative to max |SX|.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import slso_oracle as O
+from paper_1812_07903_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(X):
+    return X.to("cuda")
+
+
+def _np(X):
+    return X.double().numpy() if X.dtype != torch.bfloat16 else X.float().double().numpy()
+
+
+def _rel_to_max(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _max_rel(a, b, floor=0.0):
+    mask = np.abs(b) > floor
+    return float(np.max(np.abs(a[mask] - b[mask]) / np.abs(b[mask]))) if mask.any() else 0.0
+
+
+# ------------------------------------------------------------------ sketches
+CS_CASES = [(1, 1, 1), (33, 7, 5), (5000, 64, 256), (4097, 300, 1024), (20000, 784, 2048)]
+
+
+@pytest.mark.parametrize("n,d,s", CS_CASES)
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
+def test_countsketch_matches_oracle(n, d, s, dtype):
+    X = inputs.lognormal_rows(n, d, seed=n + d, dtype=dtype)
+    SX = api.sketch(_dev(X), "countsketch", s, 77).cpu().numpy()
+    want = O.sketch(_np(X), "countsketch", s, 77)
+    # compensated float32 (float64 for F64 X) against float64 sums
+    assert _rel_to_max(SX, want) < 1e-12
+
+
+def test_countsketch_ragged_leading_dimension():
+    Xf = inputs.lognormal_rows(3000, 70, seed=5, dtype=torch.float32)
+    Xd = _dev(Xf)[:, :67]  # ldx = 70, d = 67
+    SX = api.sketch(Xd, "countsketch", 512, 9).cpu().numpy()
+    want = O.sketch(_np(Xf)[:, :67], "countsketch", 512, 9)
+    assert _rel_to_max(SX, want) < 1e-12
+
+
+SRHT_CASES = [(1, 3, 1), (100, 5, 64), (5000, 64, 512), (20000, 100, 2048), (70000, 24, 1024)]
+
+
+@pytest.mark.parametrize("n,d,s", SRHT_CASES)
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_srht_matches_oracle(n, d, s, dtype):
+    X = inputs.lognormal_rows(n, d, seed=3 * n + d, dtype=dtype)
+    SX = api.sketch(_dev(X), "srht", s, 31).cpu().numpy()
+    want = O.sketch(_np(X), "srht", s, 31)
+    tol = 1e-12 if dtype == torch.float64 else 5e-6  # float32 butterflies, log2(n) levels
+    assert _rel_to_max(SX, want) < tol
+
+
+GAUSS_CASES = [(1, 2, 3), (100, 5, 64), (4096, 64, 256), (9000, 130, 200)]
+
+
+@pytest.mark.parametrize("n,d,s", GAUSS_CASES)
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64, torch.bfloat16])
+def test_gaussian_matches_oracle(n, d, s, dtype):
+    X = inputs.lognormal_rows(n, d, seed=7 * n + d, dtype=dtype)
+    SX = api.sketch(_dev(X), "gaussian", s, 41).cpu().numpy()
+    want = O.sketch(_np(X), "gaussian", s, 41)
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    assert _rel_to_max(SX, want) < tol
+
+
+# ------------------------------------------------------------------ small solve
+@pytest.mark.parametrize("s,d", [(1, 1), (7, 3), (256, 64), (1000, 257), (4096, 700)])
+def test_sketched_svd_matches_oracle(s, d):
+    rng = np.random.default_rng(s + d)
+    SX = rng.standard_normal((s, d)) * np.exp(rng.standard_normal(d))
+    sigma, V, R, info = api.sketched_svd(torch.from_numpy(SX).cuda())
+    sv = O.sketched_svd(SX)
+    np.testing.assert_allclose(R.cpu().numpy(), sv["R"], rtol=0, atol=1e-10 * np.abs(sv["R"]).max())
+    np.testing.assert_allclose(sigma.cpu().numpy(), sv["sigma"], rtol=1e-10, atol=1e-12 * sv["sigma"][0])
+    assert info["rank"] == sv["rank"] == d
+    # right singular vectors up to sign: |V_gpu^T V_oracle| = I
+    G = np.abs(V.cpu().numpy().T @ sv["V"])
+    np.testing.assert_allclose(np.diag(G), 1.0, atol=1e-8)
+
+
+def test_sketched_svd_zero_columns_and_rank():
+    rng = np.random.default_rng(3)
+    SX = rng.standard_normal((600, 40))
+    SX[:, [0, 7, 39]] = 0.0
+    sigma, V, R, info = api.sketched_svd(torch.from_numpy(SX).cuda())
+    sv = O.sketched_svd(SX)
+    assert info["rank"] == sv["rank"] == 37
+    np.testing.assert_allclose(R.cpu().numpy(), sv["R"], atol=1e-11 * np.abs(sv["R"]).max())
+    assert np.all(sigma.cpu().numpy()[-3:] == 0.0)
+
+
+# ------------------------------------------------------------------ leverage scores
+def test_plain_method_float64_lognormal_rows():
+    """Plain method in float64: 4096 x 64 lognormal-scaled rows, Gaussian s=256, k=32 and k=0."""
+    X = inputs.lognormal_rows(4096, 64, seed=1001)
+    for k in (32, 0):
+        sc, info = api.leverage(_dev(X), "gaussian", 256, k, 2001, 3001, compute="f64")
+        want, oinfo = O.sketched_leverage(X.numpy(), "gaussian", 256, k, 2001, 3001)
+        assert info["rank"] == oinfo["rank"] == 64
+        assert info["svd_route"] == 0
+        assert _max_rel(sc.cpu().numpy(), want) < 1e-9
+        assert abs(info["score_sum"] - want.sum()) < 1e-9 * want.sum()
+
+
+@pytest.mark.parametrize("kind,s", [("countsketch", 2048), ("srht", 1024), ("gaussian", 1024)])
+def test_float32_path_image_like_rank_deficient(kind, s):
+    """Image-like data with 68 zero columns: SVD route, rank 716, float32 scores within 1e-4."""
+    X, _ = inputs.image_like(n=6000, seed=1001)
+    sc, info = api.leverage(_dev(X), kind, s, 64, 2002, 3002, compute="f32")
+    want, oinfo = O.sketched_leverage(_np(X), kind, s, 64, 2002, 3002)
+    assert info["rank"] == oinfo["rank"] == 716
+    assert info["svd_route"] == 1
+    assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
+
+
+@pytest.mark.parametrize("n,d,s,k", [(20000, 256, 4096, 128), (3001, 100, 400, 0), (777, 33, 64, 16)])
+def test_float32_path_snr_student_t(n, d, s, k):
+    X = inputs.snr_student_t(n, d, rank=min(50, d // 2), seed=1003)
+    sc, info = api.leverage(_dev(X), "countsketch", s, k, 2003, 3003, compute="f32")
+    want, oinfo = O.sketched_leverage(_np(X), "countsketch", s, k, 2003, 3003)
+    assert info["rank"] == oinfo["rank"] == d
+    assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
+
+
+def test_bf16_path_median_error_against_float64():
+    X = inputs.snr_student_t(20000, 256, rank=50, seed=1003)
+    sc, info = api.leverage(_dev(X), "countsketch", 4096, 128, 2003, 3003, compute="bf16")
+    want, _ = O.sketched_leverage(_np(X), "countsketch", 4096, 128, 2003, 3003)
+    rel = np.abs(sc.cpu().numpy().astype(np.float64) - want) / want
+    assert np.median(rel) < 0.02
+
+
+def test_all_zero_matrix_gives_rank_zero_and_zero_scores():
+    X = torch.zeros(500, 8, dtype=torch.float32)
+    sc, info = api.leverage(_dev(X), "countsketch", 64, 4, 1, 2, compute="f32")
+    assert info["rank"] == 0 and info["svd_route"] == 1
+    assert torch.all(sc == 0)
+
+
+def test_nonfinite_input_is_reported():
+    X = inputs.lognormal_rows(300, 6, seed=1, dtype=torch.float32)
+    X[17, 3] = float("nan")
+    with pytest.raises(RuntimeError, match="NONFINITE"):
+        api.leverage(_dev(X), "countsketch", 64, 0, 1, 2, compute="f32")
+
+
+# ------------------------------------------------------------------ ordering
+@pytest.mark.parametrize("n", [1, 2, 31, 4096, 4097, 100003])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_order_is_stable_sort_of_gpu_scores(n, dtype):
+    g = torch.Generator().manual_seed(n)
+    sc = torch.rand(n, generator=g, dtype=torch.float64)
+    # many ties, signed zeros and NaNs
+    sc = torch.floor(sc * 50) / 50
+    if n > 10:
+        sc[::7] = 0.0
+        sc[1::11] = -0.0
+        sc[2::13] = float("nan")
+    sc = sc.to(dtype)
+    o = api.order(sc.cuda()).cpu().numpy()
+    want = O.order_dec(sc.double().numpy())
+    np.testing.assert_array_equal(o, want)
+
+
+def test_order_of_leverage_scores_end_to_end():
+    X = inputs.lognormal_rows(10000, 32, seed=12, dtype=torch.float32)
+    sc, _ = api.leverage(_dev(X), "countsketch", 1024, 0, 4, 5, compute="f32")
+    o = api.order(sc).cpu().numpy()
+    np.testing.assert_array_equal(o, O.order_dec(sc.cpu().numpy().astype(np.float64)))
+
+
+def test_host_entry_point_matches_device_entry_points():
+    X = inputs.lognormal_rows(5000, 48, seed=13, dtype=torch.float32)
+    sc_d, _ = api.leverage(_dev(X), "countsketch", 512, 16, 7, 8, compute="f32")
+    o_d = api.order(sc_d)
+    sc_h, o_h, info = api.rank_rows_host(X.pin_memory(), "countsketch", 512, 16, 7, 8, compute="f32")
+    assert torch.equal(sc_h, sc_d.cpu()) and torch.equal(o_h, o_d.cpu())
+    assert info["rank"] == 48
