@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the Sketched Leverage Score Ordering hot path on one GB300 (or N replicas).
+
+One step = slso_leverage (sketch -> FP64 QR -> certified R^-1 or SVD -> M -> scores) followed by
+slso_order (radix argsort into the "dec" order) over the whole matrix, X already resident in HBM.
+Workload: X 1,000,000 x 1024 float32 (rank-200 signal + noise at SNR 10, Student-t(3) row
+scaling), CountSketch s = 16384, JL width k = 128.  X (4.1 GB) is larger than L2, so no flush is
+needed between steps.
+
+Printed: one JSON line (rank 0).  `value` is scored rows/s of the float32 path over all ranks;
+the bfloat16 path, the end-to-end host-buffer call, per-stage times, the roofline of the dominant
+kernel, clocks, precision against the FP64 oracle and the oracle's own CPU throughput ride along.
+
+--impl reference times the FP64 CPU oracle instead (the only reference this method has), on a
+bounded sample of the same workload per step, scaled to rows/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "scored rows/s (BF16 vs FP32, ≤2% median rel err) + roofline %; p99 job latency"
+WORKLOAD = dict(n=1_000_000, d=1024, s=16384, k=128, kind="countsketch", xseed=1003, seed_S=2003, seed_Pi=3003)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070 / 1e3  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _config(n, d, s, k, kind):
+    return {
+        "workload": f"snr_student_t {n}x{d} float32 (rank-200 + SNR 10 noise, t(3) rows), "
+                    f"{kind} s={s}, JL k={k}; leverage + dec order",
+        "n": n, "d": d, "s": s, "k": k, "sketch": kind, "solve": "fp64 Householder QR, certified R^-1",
+        "l2": "inputs larger than L2 (X is 4.1 GB > 129 MB); no flush",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def oracle_throughput(n, d, s, k, kind, seed_S, seed_Pi, rows_sample, qr_steps, X_rows=None):
+    """Time the FP64 oracle on a bounded sample and scale to rows/s of the full workload.
+
+    Per-row stages (sketch, scores) are timed on `rows_sample` rows; the s x d Householder QR is
+    timed for its first `qr_steps` columns and scaled by the flop ratio of the full loop; the
+    SVD of R and M are timed whole.
+    """
+    import numpy as np
+    import torch
+
+    from oracle import slso_oracle as O
+    from paper_1812_07903_gb300 import inputs
+
+    if X_rows is None:
+        X_rows = inputs.snr_student_t(rows_sample, d, seed=WORKLOAD["xseed"], device="cpu").numpy()
+    Xs = np.asarray(X_rows[:rows_sample])
+    t0 = time.perf_counter()
+    SXs = O.sketch(Xs, kind, s, seed_S)
+    t_sketch = time.perf_counter() - t0
+    A = SXs if SXs.shape[0] >= d else np.vstack([SXs, np.zeros((d - SXs.shape[0], d))])
+    A = A + np.random.default_rng(0).standard_normal(A.shape) * 1e-3  # full rank, same cost
+    t0 = time.perf_counter()
+    O.householder_r(A, steps=qr_steps)
+    t_qr_part = time.perf_counter() - t0
+    work = lambda m: sum((s - j) * (d - j) for j in range(m))  # noqa: E731
+    t_qr = t_qr_part * work(d) / work(qr_steps)
+    R = O.householder_r_lapack(A)
+    t0 = time.perf_counter()
+    sig, V, U = O.svd_of_r(R)
+    Pi = O.jl_matrix(d, k, seed_Pi) if k > 0 else None
+    M = O.m_matrix(sig, V, U, d, Pi)
+    t_svd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.row_scores(Xs, M)
+    t_scores = time.perf_counter() - t0
+    total = (t_sketch + t_scores) * (n / rows_sample) + t_qr + t_svd
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    sample = (f"sketch+scores on {rows_sample} of {n} rows scaled by n; Householder loop on the first "
+              f"{qr_steps} of {d} columns scaled by its flop share; SVD of R and M timed whole")
+    return n / total, total, cores, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    W = WORKLOAD
+    n, d, s, k = W["n"], W["d"], W["s"], W["k"]
+    import numpy as np  # noqa: F401
+
+    from paper_1812_07903_gb300 import inputs
+
+    X_rows = inputs.snr_student_t(16384, d, seed=W["xseed"], device="cpu").numpy()
+    vals, totals = [], []
+    for it in range(args.warmup + args.steps):
+        v, tot, cores, sample = oracle_throughput(n, d, s, k, W["kind"], W["seed_S"], W["seed_Pi"],
+                                                  rows_sample=16384, qr_steps=16, X_rows=X_rows)
+        if it >= args.warmup:
+            vals.append(v)
+            totals.append(tot)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(totals) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(n, d, s, k, W["kind"]),
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"])
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP64 oracle comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1812_07903_gb300 import api, inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    W = dict(WORKLOAD)
+    n, d, s, k, kind = args.n, W["d"], W["s"], W["k"], W["kind"]
+    X = inputs.snr_student_t(n, d, seed=W["xseed"] + rank, device="cuda")
+    h = api.Handle(local)
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    scores_bf = torch.empty(n, dtype=torch.float32, device="cuda")
+    order = torch.empty(n, dtype=torch.int64, device="cuda")
+
+    def step(compute, out):
+        api.leverage(X, kind, s, k, W["seed_S"], W["seed_Pi"], compute=compute, out=out, want_info=False, handle=h)
+        api.order(out, out=order, handle=h)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(compute, out, steps, clocks=False):
+        for _ in range(args.warmup):
+            step(compute, out)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        api.profile(True, handle=h)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            step(compute, out)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        stages, launches = api.profile_read(handle=h)
+        api.profile(False, handle=h)
+        clk = sampler.stop() if sampler else None
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), stages, launches, clk
+
+    ms32, stages32, launches32, clk = timed("f32", scores, args.steps, clocks=True)
+    ms16, stages16, _, _ = timed("bf16", scores_bf, args.steps)
+    _, info = api.leverage(X, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", out=scores, handle=h)
+
+    value = world * n / (ms32 / 1e3)
+    value16 = world * n / (ms16 / 1e3)
+    peaks, peak_src = _peaks()
+
+    # ---- roofline of the dominant stage's kernel
+    per = {name: ms_ / max(c, 1) for name, (ms_, c) in stages32.items() if c}
+    dom = max(per, key=per.get)
+    if dom == "qr":
+        flops = 2.0 * s * d * d - 2.0 * d ** 3 / 3.0
+        ach = flops / (per["qr"] / 1e3) / 1e12
+        roof = {"kernel": "qr_kernel (FP64 Householder, cooperative)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.198)"}
+    elif dom == "sketch":
+        byts = n * d * 4.0 + s * d * 8.0
+        ach = byts / (per["sketch"] / 1e3) / 1e9
+        roof = {"kernel": "countsketch gather", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src}
+    else:
+        flops = 2.0 * n * d * k
+        ach = flops / (per[dom] / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "peak_source": "derived FP32 FMA peak"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(n, d, s, k, kind),
+        "roofline": roof, "gpu_launches": int(launches32),
+        "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages32.items() if c},
+        "bf16": {"value": value16, "unit": "rows/s", "ms_per_step": ms16,
+                 "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages16.items() if c}},
+        "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"]},
+        "clocks": clk,
+        "hbm_floor_ms": (2 * n * d * 4 + n * 12) / (peaks["hbm_gbs"] * 1e6),
+    }
+    line["hbm_roofline_frac_whole_step"] = line["hbm_floor_ms"] / ms32
+
+    # ---- end to end through the host-buffer entry point
+    if not args.no_e2e:
+        Xh = X.cpu().pin_memory()
+        sc_h = torch.empty(n, dtype=torch.float32).pin_memory()
+        od_h = torch.empty(n, dtype=torch.int64).pin_memory()
+        for _ in range(2):
+            api.rank_rows_host(Xh, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", scores_out=sc_h,
+                               order_out=od_h, handle=h)
+        barrier()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ke = max(3, args.steps // 2)
+        e0.record(st)
+        for _ in range(ke):
+            api.rank_rows_host(Xh, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", scores_out=sc_h,
+                               order_out=od_h, handle=h)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / ke
+        t = torch.tensor([ms_e], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e = float(t.item())
+        line["e2e"] = {"value": world * n / (ms_e / 1e3), "unit": "rows/s", "ms_per_step": ms_e,
+                       "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * (4 + 8)}
+        del Xh
+
+    # ---- precision against the FP64 oracle, and the oracle's own throughput (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_precision:
+        from oracle import slso_oracle as O
+
+        Xn = X.cpu().numpy()
+        t0 = time.perf_counter()
+        SX = O.sketch(Xn, kind, s, W["seed_S"])
+        sv = O.sketched_svd(SX, qr="lapack")
+        M = O.m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], O.jl_matrix(d, k, W["seed_Pi"]))
+        want = O.row_scores(Xn, M)
+        t_or = time.perf_counter() - t0
+        stats = {}
+        for name, got in (("f32", scores), ("bf16", scores_bf)):
+            g = got.cpu().numpy().astype(np.float64)
+            pos = want > 0
+            rel = np.abs(g[pos] - want[pos]) / want[pos]
+            top = max(1, math.ceil(0.01 * n))
+            og = set(O.order_dec(g)[:top].tolist())
+            ow = set(O.order_dec(want)[:top].tolist())
+            stats[name] = {"median_rel_err": float(np.median(rel)), "max_rel_err": float(np.max(rel)),
+                           "top1pct_overlap": len(og & ow) / top,
+                           "zero_rows": int(np.sum(~pos)), "zero_rows_nonzero_gpu": int(np.sum(g[~pos] != 0))}
+        line["precision_vs_fp64_oracle"] = stats
+        line["precision_vs_fp64_oracle"]["oracle_rank"] = sv["rank"]
+        line["precision_vs_fp64_oracle"]["oracle_seconds"] = t_or
+        if not args.no_cpu_baseline:
+            v, tot, cores, sample = oracle_throughput(n, d, s, k, kind, W["seed_S"], W["seed_Pi"],
+                                                      rows_sample=65536, qr_steps=96, X_rows=Xn)
+            line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle",
+                                    "sample": sample, "est_seconds_full_job": tot}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

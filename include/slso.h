@@ -144,6 +144,18 @@ slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t
                                 void* scores_host, int64_t* order_host, slso_info* info,
                                 void* stream);
 
+/* Instrumentation (no counterpart in the paper).  slso_profile(h, 1) resets and starts
+ * recording a CUDA event pair around every stage each call enqueues on its stream:
+ * 0 sketch, 1 Householder QR, 2 rest of the small solve (certificate, R^-1 or SVD, M),
+ * 3 scores (X.M + row norms), 4 ordering, 5 host<->device copies.  slso_profile_read
+ * waits for the recorded events and returns per-stage milliseconds and call counts
+ * (arrays of SLSO_STAGES) and the number of kernels this library launched (in this process)
+ * since slso_profile was called.  Recording stops after 4096 stages. */
+#define SLSO_STAGES 6
+slso_status slso_profile(slso_handle* handle, int enable);
+slso_status slso_profile_read(slso_handle* handle, double* stage_ms, int64_t* stage_calls,
+                              int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -262,7 +262,7 @@ def sketch(X, kind, s, seed):
 # ---------------------------------------------------------------------------
 # Small solve: Householder QR -> R, SVD of R, rank, M (Algorithm 3 steps 2-4)
 # ---------------------------------------------------------------------------
-def householder_r(A):
+def householder_r(A, steps=None):
     """R factor of an unpivoted Householder QR of A (s x d, s >= d), in float64.
 
     Column j: alpha = A[j, j], xnorm = ||A[j+1:, j]||.  If xnorm = 0 no reflection is
@@ -271,12 +271,14 @@ def householder_r(A):
     beta, v = A[j:, j] / (alpha - beta) with v_0 = 1, R_jj = beta, and H_j = I - tau v v^T
     is applied to the trailing columns.  Finally every row of R with a negative diagonal
     is negated, so R_jj >= 0 (the unique R for full column rank A).
+
+    ``steps`` stops after that many columns (only used to time a bounded sample).
     """
     A = np.array(A, dtype=np.float64, copy=True)
     s, d = A.shape
     if s < d:
         raise ValueError("householder_r needs s >= d")
-    for j in range(d):
+    for j in range(d if steps is None else min(d, steps)):
         alpha = A[j, j]
         xnorm = math.sqrt(float(np.dot(A[j + 1:, j], A[j + 1:, j])))
         if xnorm == 0.0:
@@ -292,6 +294,19 @@ def householder_r(A):
             w = v @ A[j:, j + 1:]
             A[j:, j + 1:] -= tau * np.outer(v, w)
     R = np.triu(A[:d, :d])
+    neg = np.diag(R) < 0.0
+    R[neg, :] *= -1.0
+    return R
+
+
+def householder_r_lapack(A):
+    """The same R through LAPACK's Householder QR (dgeqrf, via numpy), rows sign-normalised.
+
+    dgeqrf forms the same reflectors as ``householder_r`` (no reflection for an exactly zero
+    subcolumn, beta = -sign(alpha) ||x||), blocked for speed; used at sizes where the
+    column loop is too slow.  Agreement with ``householder_r`` is pinned by a test.
+    """
+    R = np.linalg.qr(np.asarray(A, dtype=np.float64), mode="r")
     neg = np.diag(R) < 0.0
     R[neg, :] *= -1.0
     return R
@@ -342,24 +357,24 @@ def row_scores(X, M):
     return out
 
 
-def sketched_svd(SX, tau=None):
+def sketched_svd(SX, tau=None, qr="loop"):
     """Sketched SVD (Algorithm 2/3 steps 2-3): R, sigma, V, U_R and numerical rank of SX."""
     s, d = SX.shape
     if tau is None or tau < 0:
         tau = default_tau(s, d)
-    R = householder_r(SX)
+    R = householder_r(SX) if qr == "loop" else householder_r_lapack(SX)
     sigma, V, U_R = svd_of_r(R)
     return {"R": R, "sigma": sigma, "V": V, "U_R": U_R, "rank": numerical_rank(sigma, tau), "tau": tau}
 
 
-def scores_from_sketch(X, SX, tau=None, Pi=None):
+def scores_from_sketch(X, SX, tau=None, Pi=None, qr="loop"):
     """Algorithm 3 steps 2-5 from a given sketch SX: truncated basis, then row norms."""
-    sv = sketched_svd(SX, tau)
+    sv = sketched_svd(SX, tau, qr)
     M = m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], Pi)
     return row_scores(X, M), sv, M
 
 
-def sketched_leverage(X, kind, s, k, seed_S, seed_Pi, tau=None):
+def sketched_leverage(X, kind, s, k, seed_S, seed_Pi, tau=None, qr="loop"):
     """Algorithm 3 (Approximate Leverage Score with Truncation) with a JL step.
 
     k = 0 gives the algorithm exactly (Pi = I); k > 0 right-multiplies R^+_tau by the
@@ -368,7 +383,7 @@ def sketched_leverage(X, kind, s, k, seed_S, seed_Pi, tau=None):
     d = X.shape[1]
     SX = sketch(X, kind, s, seed_S)
     Pi = jl_matrix(d, k, seed_Pi) if k > 0 else None
-    scores, sv, M = scores_from_sketch(X, SX, tau, Pi)
+    scores, sv, M = scores_from_sketch(X, SX, tau, Pi, qr)
     info = {
         "rank": sv["rank"],
         "sigma": sv["sigma"],

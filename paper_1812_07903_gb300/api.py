@@ -160,6 +160,22 @@ def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0,
     return sc, od, info.as_dict()
 
 
+def profile(enable=True, handle=None):
+    """slso_profile: start (or stop) per-stage event timing on the handle."""
+    h = handle or default_handle()
+    L.check(L.load().slso_profile(h.ptr, 1 if enable else 0))
+
+
+def profile_read(handle=None):
+    """slso_profile_read: {stage: (total ms, calls)} and the kernel launch count."""
+    h = handle or default_handle()
+    ms = (ctypes.c_double * len(L.STAGES))()
+    calls = (ctypes.c_int64 * len(L.STAGES))()
+    launches = ctypes.c_int64(0)
+    L.check(L.load().slso_profile_read(h.ptr, ms, calls, ctypes.byref(launches)))
+    return {name: (ms[i], calls[i]) for i, name in enumerate(L.STAGES)}, launches.value
+
+
 def default_tau(s, d):
     return max(s, d) * 2.0**-52
 

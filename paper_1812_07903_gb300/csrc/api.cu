@@ -87,11 +87,15 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st) {
   const double tau = p->tau < 0 ? default_tau(p->s, d) : p->tau;
   double* SX = ar.take<double>(static_cast<size_t>(p->s) * d);
+  prof_begin(h, ar, ST_SKETCH, st);
   SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, SX, st));
+  prof_end(h, ar, st);
   SolveOut so;
   SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st));
   const int64_t kk = p->k > 0 ? p->k : d;
+  prof_begin(h, ar, ST_SCORES, st);
   SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, so.M, kk, p->compute, scores, p->correct_frac, st));
+  prof_end(h, ar, st);
   return SLSO_OK;
 }
 
@@ -121,7 +125,12 @@ extern "C" slso_status slso_sketch(slso_handle* handle, const void* X, int64_t n
   if (!SX) return fail(SLSO_ERR_INVALID_ARG, "SX is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
-  return run_plan(*h, [&](Arena& ar) { return run_sketch(*h, ar, X, n, d, ldx, xdt, kind, s, seed_S, SX, st); });
+  return run_plan(*h, [&](Arena& ar) {
+    prof_begin(*h, ar, ST_SKETCH, st);
+    SLSO_TRY(run_sketch(*h, ar, X, n, d, ldx, xdt, kind, s, seed_S, SX, st));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  });
 }
 
 extern "C" slso_status slso_sketched_svd(slso_handle* handle, const double* SX, int64_t s, int64_t d,
@@ -168,7 +177,12 @@ extern "C" slso_status slso_order(slso_handle* handle, const void* scores, int32
   if (n < 1 || n >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "need 1 <= n < 2^31");
   if (sdt != SLSO_F32 && sdt != SLSO_F64) return fail(SLSO_ERR_DTYPE, "scores must be F32 or F64");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return run_plan(*h, [&](Arena& ar) { return order_scores(*h, ar, scores, sdt, n, order, st); });
+  return run_plan(*h, [&](Arena& ar) {
+    prof_begin(*h, ar, ST_ORDER, st);
+    SLSO_TRY(order_scores(*h, ar, scores, sdt, n, order, st));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  });
 }
 
 extern "C" slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t n, int64_t d,
@@ -192,6 +206,7 @@ extern "C" slso_status slso_rank_rows_host(slso_handle* handle, const void* X_ho
     Xd = ar.take<char>(static_cast<size_t>(n) * d * esz);
     sc = ar.take<char>(static_cast<size_t>(n) * ssz);
     od = ar.take<int64_t>(n);
+    prof_begin(*h, ar, ST_COPY, st);
     if (!ar.measure()) {
       if (ldx == d) {
         SLSO_CHECK_CUDA(cudaMemcpyAsync(Xd, X_host, static_cast<size_t>(n) * d * esz, cudaMemcpyHostToDevice, st));
@@ -199,12 +214,17 @@ extern "C" slso_status slso_rank_rows_host(slso_handle* handle, const void* X_ho
         SLSO_CHECK_CUDA(cudaMemcpy2DAsync(Xd, d * esz, X_host, ldx * esz, d * esz, n, cudaMemcpyHostToDevice, st));
       }
     }
+    prof_end(*h, ar, st);
     SLSO_TRY(leverage_plan(*h, ar, Xd, n, d, d, xdt, params, sc, st));
+    prof_begin(*h, ar, ST_ORDER, st);
     SLSO_TRY(order_scores(*h, ar, sc, sdt, n, od, st));
+    prof_end(*h, ar, st);
+    prof_begin(*h, ar, ST_COPY, st);
     if (!ar.measure()) {
       SLSO_CHECK_CUDA(cudaMemcpyAsync(scores_host, sc, static_cast<size_t>(n) * ssz, cudaMemcpyDeviceToHost, st));
       SLSO_CHECK_CUDA(cudaMemcpyAsync(order_host, od, static_cast<size_t>(n) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     }
+    prof_end(*h, ar, st);
     return SLSO_OK;
   }));
   if (info) return fill_info(*h, st, info);

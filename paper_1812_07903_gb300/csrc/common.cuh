@@ -23,7 +23,14 @@ slso_status fail(slso_status st, const char* fmt, ...);
                           __FILE__, __LINE__);                                                 \
   } while (0)
 
-#define SLSO_CHECK_LAUNCH() SLSO_CHECK_CUDA(cudaGetLastError())
+// Every kernel launch is followed by exactly one SLSO_CHECK_LAUNCH (cooperative launches call
+// note_launch), which also counts the launch for slso_profile_read.
+void note_launch();
+#define SLSO_CHECK_LAUNCH()      \
+  do {                           \
+    ::slso::note_launch();       \
+    SLSO_CHECK_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define SLSO_TRY(expr)              \
   do {                              \
@@ -73,6 +80,15 @@ class Arena {
   bool measure_;
 };
 
+// Stage timing for slso_profile / slso_profile_read: event pairs recorded on the caller's
+// stream around each stage, summed when read.
+enum Stage { ST_SKETCH = 0, ST_QR = 1, ST_SOLVE = 2, ST_SCORES = 3, ST_ORDER = 4, ST_COPY = 5, ST_COUNT = 6 };
+
+struct ProfRecord {
+  int stage;
+  cudaEvent_t a, b;
+};
+
 struct Handle {
   int device = 0;
   int num_sms = 0;
@@ -80,7 +96,17 @@ struct Handle {
   size_t pool_cap = 0;
   DevState* state = nullptr;       // device
   DevState* state_host = nullptr;  // pinned mirror for info
+  bool prof = false;
+  ProfRecord* recs = nullptr;      // capacity kProfCap
+  int nrec = 0;
+  int open_rec = -1;
+  long long launches_at_enable = 0;
 };
+constexpr int kProfCap = 4096;
+
+// Begin / end a timed stage on stream st (no-ops unless profiling is on).
+void prof_begin(Handle& h, const Arena& ar, int stage, cudaStream_t st);
+void prof_end(Handle& h, const Arena& ar, cudaStream_t st);
 
 slso_status ensure_pool(Handle& h, size_t bytes);
 slso_status check_handle(slso_handle* hp, Handle** out);

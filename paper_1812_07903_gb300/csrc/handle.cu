@@ -1,4 +1,5 @@
 // Handle, device pool and error reporting of libslso.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -8,6 +9,27 @@
 namespace slso {
 
 static thread_local char g_last_error[1024] = "";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(Handle& h, const Arena& ar, int stage, cudaStream_t st) {
+  if (!h.prof || ar.measure() || h.nrec >= kProfCap) return;
+  ProfRecord& r = h.recs[h.nrec];
+  if (!r.a) {
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+  }
+  r.stage = stage;
+  cudaEventRecord(r.a, st);
+  h.open_rec = h.nrec++;
+}
+
+void prof_end(Handle& h, const Arena& ar, cudaStream_t st) {
+  if (!h.prof || ar.measure() || h.open_rec < 0) return;
+  cudaEventRecord(h.recs[h.open_rec].b, st);
+  h.open_rec = -1;
+}
 
 slso_status fail(slso_status st, const char* fmt, ...) {
   va_list ap;
@@ -83,8 +105,51 @@ extern "C" slso_status slso_destroy(slso_handle* handle) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   if (h->pool) cudaFree(h->pool);
+  if (h->recs) {
+    for (int i = 0; i < kProfCap; ++i)
+      if (h->recs[i].a) {
+        cudaEventDestroy(h->recs[i].a);
+        cudaEventDestroy(h->recs[i].b);
+      }
+    delete[] h->recs;
+  }
   if (h->state) cudaFree(h->state);
   if (h->state_host) cudaFreeHost(h->state_host);
   delete h;
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_profile(slso_handle* handle, int enable) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (!h->recs) {
+    h->recs = new ProfRecord[kProfCap];
+    for (int i = 0; i < kProfCap; ++i) h->recs[i] = ProfRecord{0, nullptr, nullptr};
+  }
+  h->prof = enable != 0;
+  h->nrec = 0;
+  h->open_rec = -1;
+  h->launches_at_enable = g_launches.load();
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_profile_read(slso_handle* handle, double* stage_ms, int64_t* stage_calls,
+                                         int64_t* launches) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (!stage_ms || !stage_calls || !launches) return fail(SLSO_ERR_INVALID_ARG, "NULL output");
+  for (int i = 0; i < SLSO_STAGES; ++i) {
+    stage_ms[i] = 0.0;
+    stage_calls[i] = 0;
+  }
+  for (int i = 0; i < h->nrec; ++i) {
+    const ProfRecord& r = h->recs[i];
+    SLSO_CHECK_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    SLSO_CHECK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    stage_ms[r.stage] += ms;
+    stage_calls[r.stage] += 1;
+  }
+  *launches = g_launches.load() - h->launches_at_enable;
   return SLSO_OK;
 }

@@ -472,6 +472,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   if (s > 24576 * 8) return fail(SLSO_ERR_SHAPE, "sketch rows s=%lld exceed the QR limit", (long long)s);
 
   // ---- QR
+  prof_begin(h, ar, ST_SOLVE, st);
   {
     dim3 g(static_cast<unsigned>(ceil_div(d, 32)), static_cast<unsigned>(ceil_div(s, 32)));
     transpose_kernel<<<g, dim3(32, 8), 0, st>>>(SX, s, d, A);
@@ -489,7 +490,12 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     int G = static_cast<int>(std::min<int64_t>(h.num_sms, d));
     int s_i = static_cast<int>(s), d_i = static_cast<int>(d);
     void* args[] = {&A, &s_i, &d_i, &ready, &taus, &h.state};
+    prof_end(h, ar, st);
+    prof_begin(h, ar, ST_QR, st);
     SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, st));
+    note_launch();
+    prof_end(h, ar, st);
+    prof_begin(h, ar, ST_SOLVE, st);
   }
   r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(A, s, d, R, sgn);
   SLSO_CHECK_LAUNCH();
@@ -537,6 +543,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     void* args[] = {&W, &Vw, &d_i, &dp_i, &sweeps, &stp, &bar, &rot, &req};
     SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_kernel), dim3(G), dim3(256),
                                                 args, 0, st));
+    note_launch();
   }
   const int32_t* guard = (mode == 0) ? need : nullptr;
   colnorm_kernel<<<static_cast<unsigned>(ceil_div(d * 32, 256)), 256, 0, st>>>(W, d, dp, sig, guard);
@@ -553,6 +560,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
       SLSO_CHECK_LAUNCH();
     }
   }
+  prof_end(h, ar, st);
   out->M = M;
   out->kk = kk;
   out->R = R;

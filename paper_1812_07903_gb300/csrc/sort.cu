@@ -138,7 +138,9 @@ slso_status radix_sort_impl(Arena& ar, K* keys, uint32_t* vals, int64_t n, int b
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     radix_hist_kernel<K><<<ntiles, kThreads, 0, st>>>(ka, n, shift, hist, ntiles);
+    SLSO_CHECK_LAUNCH();
     radix_scan_kernel<<<1, 1024, 0, st>>>(hist, static_cast<int64_t>(kRadix) * ntiles);
+    SLSO_CHECK_LAUNCH();
     radix_scatter_kernel<K><<<ntiles, kThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles);
     SLSO_CHECK_LAUNCH();
     K* tk = ka; ka = kb; kb = tk;
@@ -194,14 +196,18 @@ slso_status order_scores(Handle& h, Arena& ar, const void* scores, int32_t sdt, 
   if (sdt == SLSO_F32) {
     uint32_t* keys = ar.take<uint32_t>(n);
     uint32_t* kres = nullptr;
-    if (!ar.measure())
+    if (!ar.measure()) {
       keys_from_f32_kernel<<<grid, 256, 0, st>>>(static_cast<const float*>(scores), n, keys, vals);
+      SLSO_CHECK_LAUNCH();
+    }
     SLSO_TRY(radix_sort_u32(ar, keys, vals, n, 32, st, &kres, &vres));
   } else {
     unsigned long long* keys = ar.take<unsigned long long>(n);
     unsigned long long* kres = nullptr;
-    if (!ar.measure())
+    if (!ar.measure()) {
       keys_from_f64_kernel<<<grid, 256, 0, st>>>(static_cast<const double*>(scores), n, keys, vals);
+      SLSO_CHECK_LAUNCH();
+    }
     SLSO_TRY(radix_sort_u64(ar, keys, vals, n, 64, st, &kres, &vres));
   }
   if (ar.measure()) return SLSO_OK;

@@ -245,3 +245,23 @@ def test_image_like_rank_is_live_column_count():
     for kind, s in (("countsketch", 2048), ("srht", 1024)):
         _, info = O.sketched_leverage(X, kind, s, 0, 2002, 0)
         assert info["rank"] == 716
+
+
+def test_lapack_householder_matches_column_loop_including_zero_columns():
+    """dgeqrf and the column loop give the same R, also for exactly zero columns (leftover rows)."""
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((400, 30)) * np.exp(rng.standard_normal(30))
+    A[:, [4, 17]] = 0.0
+    R1, R2 = O.householder_r(A), O.householder_r_lapack(A)
+    np.testing.assert_allclose(R2, R1, rtol=0, atol=1e-12 * np.abs(R1).max())
+    assert np.any(R1[4, 5:] != 0.0)  # the leftover row of a zero column is not zero
+    B = rng.standard_normal((300, 50))
+    np.testing.assert_allclose(O.householder_r_lapack(B), O.householder_r(B), atol=1e-12 * np.abs(B).max() * 20)
+
+
+def test_partial_householder_steps_are_a_prefix():
+    rng = np.random.default_rng(22)
+    A = rng.standard_normal((80, 12))
+    R = O.householder_r(A)
+    Rp = O.householder_r(A, steps=5)
+    np.testing.assert_allclose(Rp[:5], R[:5], atol=1e-13)
