@@ -1,7 +1,8 @@
 // Row scores l_i = ||(X M)_i||^2 (Algorithm 3 steps 4-5): the product X M is never written;
 // each tile reduces its squared entries per row in the epilogue.
 //
-// SIMT kernel: CTA tile of 64 rows x 64 columns of Y, K-steps of 16 through shared memory,
+// The tensor-core kernel (score_tc.cu) takes float32 and bfloat16 X whenever k <= 256; this
+// SIMT kernel covers the rest (float64, k > 256, unaligned X): CTA tile of 64 rows x 64 columns of Y, K-steps of 16 through shared memory,
 // 4x4 outputs per thread.  Per-row partial sums of squares of each 64-column block go to
 // part[cb][i]; a second kernel adds the column blocks in ascending order.
 //   compute F64: float64 products and sums.
@@ -95,20 +96,41 @@ __global__ void score_combine_kernel(const Acc* __restrict__ part, int64_t n, in
   }
 }
 
+// Sum of the scores (normaliser of P, Algorithm 4 step 3) in two fixed-order stages:
+// kSumBlocks contiguous chunks, then one thread adds the chunk sums in order.
+constexpr int kSumBlocks = 128;
+
 template <class Out>
-__global__ void score_sum_kernel(const Out* __restrict__ scores, int64_t n, DevState* __restrict__ st) {
+__global__ void score_sum_partial_kernel(const Out* __restrict__ scores, int64_t n, double* __restrict__ part) {
   __shared__ double red[32];
-  double part = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += static_cast<double>(scores[i]);
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double p = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) p += static_cast<double>(scores[i]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  for (int o = 16; o > 0; o >>= 1) p += __shfl_down_sync(0xFFFFFFFFu, p, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
-    st->score_sum = t;
+    part[blockIdx.x] = t;
   }
+}
+
+__global__ void score_sum_final_kernel(const double* __restrict__ part, DevState* __restrict__ st) {
+  double t = 0.0;
+  for (int b = 0; b < kSumBlocks; ++b) t += part[b];
+  st->score_sum = t;
+}
+
+template <class Out>
+slso_status launch_score_sum(Handle& h, const Out* scores, int64_t n, double* part, cudaStream_t st) {
+  score_sum_partial_kernel<Out><<<kSumBlocks, 256, 0, st>>>(scores, n, part);
+  SLSO_CHECK_LAUNCH();
+  score_sum_final_kernel<<<1, 1, 0, st>>>(part, h.state);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
 }
 
 __global__ void m_to_f32_kernel(const double* __restrict__ M, int64_t e, float* __restrict__ Mf) {
@@ -132,6 +154,7 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
                          const double* M, int64_t kk, int32_t compute, void* scores, cudaStream_t st) {
   const int64_t ncb = ceil_div(kk, kBn);
   dim3 grid(static_cast<unsigned>(ceil_div(n, kBm)), static_cast<unsigned>(ncb));
+  double* sums = ar.take<double>(kSumBlocks);
   if (compute == SLSO_F64) {
     double* part = ar.take<double>(static_cast<size_t>(ncb) * n);
     if (ar.measure()) return SLSO_OK;
@@ -139,9 +162,15 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
     SLSO_CHECK_LAUNCH();
     score_combine_kernel<double, double><<<grid1d(n, h), 256, 0, st>>>(part, n, ncb, static_cast<double*>(scores));
     SLSO_CHECK_LAUNCH();
-    score_sum_kernel<double><<<1, 1024, 0, st>>>(static_cast<double*>(scores), n, h.state);
-    SLSO_CHECK_LAUNCH();
-    return SLSO_OK;
+    return launch_score_sum<double>(h, static_cast<double*>(scores), n, sums, st);
+  }
+  bool used_tc = false;
+  SLSO_TRY(run_scores_tc(h, ar, X, n, d, ldx, std::is_same<T, float>::value ? SLSO_F32
+                                                : (std::is_same<T, double>::value ? SLSO_F64 : SLSO_BF16),
+                         M, kk, compute, static_cast<float*>(scores), &used_tc, st));
+  if (used_tc) {
+    if (ar.measure()) return SLSO_OK;
+    return launch_score_sum<float>(h, static_cast<float*>(scores), n, sums, st);
   }
   float* Mf = ar.take<float>(static_cast<size_t>(d) * kk);
   float* part = ar.take<float>(static_cast<size_t>(ncb) * n);
@@ -158,9 +187,7 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
   SLSO_CHECK_LAUNCH();
   score_combine_kernel<float, float><<<grid1d(n, h), 256, 0, st>>>(part, n, ncb, static_cast<float*>(scores));
   SLSO_CHECK_LAUNCH();
-  score_sum_kernel<float><<<1, 1024, 0, st>>>(static_cast<float*>(scores), n, h.state);
-  SLSO_CHECK_LAUNCH();
-  return SLSO_OK;
+  return launch_score_sum<float>(h, static_cast<float*>(scores), n, sums, st);
 }
 
 }  // namespace

@@ -8,11 +8,15 @@
 // synchronisation); kernels of the route not taken return immediately.
 //
 // QR layout: SX is transposed to column-major A (column l at A + l*s).  A persistent
-// cooperative grid owns columns round-robin (column l belongs to CTA l % G).  Step j: the owner
-// of column j forms the reflector (beta, tau, v stored in place as LAPACK does) and publishes a
-// per-column ready flag; every CTA applies it to its own columns > j.  The owner of column j+1
-// updates that column first and immediately forms the next reflector, so steps pipeline and
-// the only synchronisation is one bounded flag wait per step.
+// cooperative grid owns columns round-robin (column l belongs to CTA l % G); reflector j is
+// stored in place as LAPACK does (beta on the diagonal, v below it, tau aside) and announced by
+// a per-column ready flag, the only inter-CTA synchronisation (a bounded wait).
+//   qr_left_kernel (s <= 16384): left-looking; the owner holds its column in registers, applies
+//     every earlier reflector as it is announced (v staged in shared memory by one bulk copy),
+//     forms its own reflector and stores the column once.  HBM traffic is one read and one write
+//     of SX; the float64 FMA pipe and the per-reflector latency bound it.
+//   qr_kernel (larger s): right-looking; after reflector j is announced each CTA applies it to
+//     its own trailing columns, the owner of column j+1 first so the next reflector follows.
 #include <algorithm>
 #include <cmath>
 
@@ -46,8 +50,8 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void transpose_kernel(const double* __restrict__ in, int64_t rows, int64_t cols,
-                                 double* __restrict__ out) {
-  // in: rows x cols row-major; out: cols x rows row-major (= in column-major)
+                                 double* __restrict__ out, int64_t ldo) {
+  // in: rows x cols row-major; out: cols x rows with row stride ldo (= in column-major)
   __shared__ double tile[32][33];
   const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32, c0 = static_cast<int64_t>(blockIdx.x) * 32;
   for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
@@ -57,14 +61,14 @@ __global__ void transpose_kernel(const double* __restrict__ in, int64_t rows, in
   __syncthreads();
   for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
     const int64_t c = c0 + cc, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) out[c * rows + r] = tile[threadIdx.x][cc];
+    if (r < rows && c < cols) out[c * ldo + r] = tile[threadIdx.x][cc];
   }
 }
 
 // Householder reflector of column j (run by every thread of the owning CTA).
-__device__ void make_reflector(double* __restrict__ A, int s, int j, double* __restrict__ taus,
+__device__ void make_reflector(double* __restrict__ A, int s, int lda, int j, double* __restrict__ taus,
                                int* __restrict__ ready, double* red) {
-  double* col = A + static_cast<int64_t>(j) * s;
+  double* col = A + static_cast<int64_t>(j) * lda;
   const double alpha = col[j];
   double part = 0.0;
   for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x) part += col[i] * col[i];
@@ -85,7 +89,7 @@ __device__ void make_reflector(double* __restrict__ A, int s, int j, double* __r
 }
 
 template <bool V_SMEM>
-__global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ A, int s, int d,
+__global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ A, int s, int lda, int d,
                                                            int* __restrict__ ready,
                                                            double* __restrict__ taus,
                                                            DevState* __restrict__ state) {
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
   const int G = gridDim.x, me = blockIdx.x;
   if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
-  if (me == 0) make_reflector(A, s, 0, taus, ready, red);
+  if (me == 0) make_reflector(A, s, lda, 0, taus, ready, red);
   for (int j = 0; j < d; ++j) {
     // smallest column > j owned by this CTA
     int lf = j + 1 + ((me - (j + 1)) % G + G) % G;
@@ -110,9 +114,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
     __syncthreads();
     if (s_abort) return;
     const double tau = __ldcg(taus + j);
-    const double* vg = A + static_cast<int64_t>(j) * s;
+    const double* vg = A + static_cast<int64_t>(j) * lda;
     if (tau == 0.0) {  // H_j = I
-      if (lf == j + 1) make_reflector(A, s, j + 1, taus, ready, red);
+      if (lf == j + 1) make_reflector(A, s, lda, j + 1, taus, ready, red);
       continue;
     }
     if (V_SMEM) {
@@ -120,7 +124,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
       __syncthreads();
     }
     for (int l = lf; l < d; l += G) {
-      double* col = A + static_cast<int64_t>(l) * s;
+      double* col = A + static_cast<int64_t>(l) * lda;
       double part = 0.0;
       for (int i = j + 1 + threadIdx.x; i < s; i += blockDim.x)
         part += (V_SMEM ? vs[i] : __ldcg(vg + i)) * col[i];
@@ -130,53 +134,248 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
         col[i] -= tc * (V_SMEM ? vs[i] : __ldcg(vg + i));
       if (threadIdx.x == 0) col[j] -= tc;
       __syncthreads();
-      if (l == j + 1) make_reflector(A, s, j + 1, taus, ready, red);
+      if (l == j + 1) make_reflector(A, s, lda, j + 1, taus, ready, red);
     }
   }
 }
 
+// Left-looking variant for s <= RPT * 256: CTA c % G owns column c; it loads the column into
+// registers once (RPT rows per thread), applies reflectors 0..c-1 as they are announced, forms
+// reflector c, stores the column once and announces ready[c].  Each reflector's v is brought into
+// shared memory by one cp.async.bulk copy (completion on an mbarrier) and read from there by the
+// dot and update passes.  Every column is read and written exactly once; the float64 work is that
+// of the right-looking loop.  Reflector c needs reflector c-1 applied to column c, so reflectors
+// are announced in increasing order and one bounded wait on ready[j] covers reflector j.
+constexpr int kQrlThreads = 256;
+constexpr unsigned long long kMbarTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Bounded wait on an mbarrier phase (2 s of %globaltimer).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (ok) return true;
+    uint64_t t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (t1 - t0 > kMbarTimeoutNs) return false;
+  }
+}
+
+// Copy rows [j0, lda) of a column into buf (same offsets); bytes is a multiple of 16 because
+// lda and j0 are even, and both addresses are 16-byte aligned.
+__device__ __forceinline__ void bulk_stage(double* buf, const double* col, int j0, int lda, uint64_t* bar) {
+  const uint32_t bytes = static_cast<uint32_t>(lda - j0) * 8u;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(buf + j0)),
+      "l"(col + j0), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Block-wide sum with one barrier: warp partials into one of two alternating smem slots.
+__device__ __forceinline__ double block_sum_fast(double v, double (*slots)[kQrlThreads / 32], int& par) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  double* red = slots[par];
+  par ^= 1;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kQrlThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restrict__ A, int s, int lda, int d,
+                                                                 int* __restrict__ ready,
+                                                                 double* __restrict__ taus,
+                                                                 DevState* __restrict__ state) {
+  extern __shared__ __align__(128) double vsm[];  // lda doubles
+  __shared__ double slots[2][kQrlThreads / 32];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_abort;
+  int par = 0;
+  uint32_t phase = 0;
+  const int G = gridDim.x, tid = threadIdx.x;
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int known = -1;  // ready[0..known] observed (thread 0)
+  // thread 0: wait until reflector j is announced, then stage its v
+  auto issue = [&](int j) {
+    if (j > known) {
+      if (!wait_flag_geq(ready + j, 1, kWaitPolls)) {
+        atomicExch(&state->timeout, 1);
+        s_abort = 1;
+        return;
+      }
+      __threadfence();
+      known = j;
+    }
+    bulk_stage(vsm, A + static_cast<int64_t>(j) * lda, j & ~1, lda, &bar);
+  };
+  for (int c = blockIdx.x; c < d; c += G) {
+    double* col = A + static_cast<int64_t>(c) * lda;
+    double a[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = tid + r * kQrlThreads;
+      a[r] = (i < s) ? col[i] : 0.0;
+    }
+    if (c > 0 && tid == 0) issue(0);
+    for (int j = 0; j < c; ++j) {
+      const bool landed = s_abort ? false : mbar_wait_bounded(&bar, phase);
+      phase ^= 1;
+      if (!landed) {
+        if (tid == 0) atomicExch(&state->timeout, 1);
+        s_abort = 1;
+      }
+      __syncthreads();
+      if (s_abort) return;
+      const double tau = __ldcg(taus + j);
+      if (tau != 0.0) {
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int i = tid + r * kQrlThreads;
+          const double w = (i > j && i < s) ? vsm[i] : (i == j ? 1.0 : 0.0);
+          if ((r & 3) == 0) p0 = fma(w, a[r], p0);
+          else if ((r & 3) == 1) p1 = fma(w, a[r], p1);
+          else if ((r & 3) == 2) p2 = fma(w, a[r], p2);
+          else p3 = fma(w, a[r], p3);
+        }
+        const double tc = tau * block_sum_fast((p0 + p1) + (p2 + p3), slots, par);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+          const int i = tid + r * kQrlThreads;
+          const double w = (i > j && i < s) ? vsm[i] : (i == j ? 1.0 : 0.0);
+          a[r] = fma(-tc, w, a[r]);
+        }
+      }
+      __syncthreads();  // everyone is done with the staged v
+      if (tid == 0 && j + 1 < c) issue(j + 1);
+    }
+    // reflector c from rows >= c of the updated column
+    double alpha_part = 0.0, x2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = tid + r * kQrlThreads;
+      if (i > c && i < s) x2 = fma(a[r], a[r], x2);
+      if (i == c) alpha_part = a[r];
+    }
+    const double xn2 = block_sum_fast(x2, slots, par);
+    const double alpha = block_sum_fast(alpha_part, slots, par);
+    double tau = 0.0;
+    if (xn2 != 0.0) {
+      const double norm = sqrt(alpha * alpha + xn2);
+      const double beta = alpha >= 0.0 ? -norm : norm;
+      tau = (beta - alpha) / beta;
+      const double den = alpha - beta;
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = tid + r * kQrlThreads;
+        if (i > c && i < s) a[r] = a[r] / den;
+        if (i == c) a[r] = beta;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = tid + r * kQrlThreads;
+      if (i < s) col[i] = a[r];
+    }
+    if (tid == 0) taus[c] = tau;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicExch(&ready[c], 1);
+  }
+}
+
 // R (d x d row-major) from the QR storage, rows negated where the diagonal is negative.
-__global__ void r_extract_kernel(const double* __restrict__ A, int64_t s, int64_t d,
+__global__ void r_extract_kernel(const double* __restrict__ A, int64_t lda, int64_t d,
                                  double* __restrict__ R, double* __restrict__ sgn) {
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * d;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = e / d, l = e % d;
-    const double sg = A[i * s + i] < 0.0 ? -1.0 : 1.0;
-    R[e] = (l >= i) ? sg * A[l * s + i] : 0.0;
+    const double sg = A[i * lda + i] < 0.0 ? -1.0 : 1.0;
+    R[e] = (l >= i) ? sg * A[l * lda + i] : 0.0;
     if (l == 0) sgn[i] = sg;
   }
 }
 
-// sum of squares of n values into *out (one CTA, fixed order)
-__global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ out) {
+// Sum of squares in two fixed-order stages: block b of kSumBlocks sums a contiguous chunk into
+// part[b]; the consumer (certify_kernel) adds the kSumBlocks partials in order.
+constexpr int kSumBlocks = 64;
+
+__global__ void sumsq_partial_kernel(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
   __shared__ double red[33];
-  double part = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) part += x[i] * x[i];
-  const double t = block_sum(part, red);
-  if (threadIdx.x == 0) *out = t;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double p = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) p = fma(x[i], x[i], p);
+  const double t = block_sum(p, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// Column c of R^-1 (column-major, d x d) by back substitution R x = e_c, column-oriented.
-__global__ void trinv_kernel(const double* __restrict__ A, int64_t s, int64_t d,
-                             const double* __restrict__ sgn, double* __restrict__ Rinv) {
+// Column c of R^-1 (column-major, d x d): back substitution R x = e_c in 32-row blocks from the
+// bottom.  One warp solves each 32 x 32 diagonal block with shuffles; then all threads subtract
+// that block's contribution from the rows above (a GEMV over column-major R).  R_ik is
+// sgn_i * A[k*lda + i].
+__global__ void __launch_bounds__(256) trinv_kernel(const double* __restrict__ A, int64_t lda, int64_t d,
+                                                    const double* __restrict__ sgn, double* __restrict__ Rinv) {
   extern __shared__ double b[];
-  const int64_t c = blockIdx.x;
-  for (int64_t i = threadIdx.x; i <= c; i += blockDim.x) b[i] = (i == c) ? 1.0 : 0.0;
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i <= c; i += blockDim.x) b[i] = (i == c) ? 1.0 : 0.0;
   __syncthreads();
-  for (int64_t k = c; k >= 0; --k) {
-    const double rkk = sgn[k] * A[k * s + k];
-    const double xk = b[k] / rkk;
+  for (int hi = c; hi >= 0; hi -= 32) {
+    const int lo = hi >= 31 ? hi - 31 : 0;
+    if (warp == 0) {
+      const int row = lo + lane;
+      double y = (row <= hi) ? b[row] : 0.0;
+      const double sr = (row <= hi) ? sgn[row] : 0.0;
+      for (int k = hi; k >= lo; --k) {
+        const int o = k - lo;
+        const double rkk = sgn[k] * A[static_cast<int64_t>(k) * lda + k];
+        const double xk = __shfl_sync(0xFFFFFFFFu, y, o) / rkk;
+        if (lane == o) y = xk;
+        else if (lane < o) y -= sr * A[static_cast<int64_t>(k) * lda + row] * xk;
+      }
+      if (row <= hi) b[row] = y;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) b[k] = xk;
-    for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] -= sgn[i] * A[k * s + i] * xk;
+    for (int i = threadIdx.x; i < lo; i += blockDim.x) {
+      double acc = b[i];
+      const double si = sgn[i];
+      for (int k = lo; k <= hi; ++k) acc -= si * A[static_cast<int64_t>(k) * lda + i] * b[k];
+      b[i] = acc;
+    }
     __syncthreads();
   }
-  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Rinv[c * d + i] = (i <= c) ? b[i] : 0.0;
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Rinv[static_cast<int64_t>(c) * d + i] = (i <= c) ? b[i] : 0.0;
 }
 
 __global__ void certify_kernel(DevState* __restrict__ st, const double* __restrict__ fro2,
                                int64_t d, double tau, int force_svd) {
-  const double fr = sqrt(fro2[0]), fi = sqrt(fro2[1]);
+  double f0 = 0.0, f1 = 0.0;
+  for (int b = 0; b < kSumBlocks; ++b) {
+    f0 += fro2[b];
+    f1 += fro2[kSumBlocks + b];
+  }
+  const double fr = sqrt(f0), fi = sqrt(f1);
   st->fro_r = fr;
   st->fro_rinv = fi;
   st->tau = tau;
@@ -448,12 +647,13 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
                       int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st) {
   const int64_t dp = d + (d & 1);
   const int64_t kk = (k > 0) ? k : d;
-  double* A = ar.take<double>(static_cast<size_t>(s) * d);
+  const int64_t lda = s + (s & 1);  // even: 16-byte aligned columns for the bulk copies
+  double* A = ar.take<double>(static_cast<size_t>(lda) * d);
   int* ready = ar.take<int>(d);
   double* taus = ar.take<double>(d);
   double* R = ar.take<double>(static_cast<size_t>(d) * d);
   double* sgn = ar.take<double>(d);
-  double* fro2 = ar.take<double>(2);
+  double* fro2 = ar.take<double>(2 * kSumBlocks);
   double* Rinv = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* Pi = (k > 0) ? ar.take<double>(static_cast<size_t>(d) * k) : nullptr;
   double* W = ar.take<double>(static_cast<size_t>(dp) * dp);
@@ -469,44 +669,57 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* sigma_out = (mode == 1) ? ar.take<double>(d) : nullptr;
   double* Vout = (mode == 1) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   if (ar.measure()) return SLSO_OK;
-  if (s > 24576 * 8) return fail(SLSO_ERR_SHAPE, "sketch rows s=%lld exceed the QR limit", (long long)s);
 
   // ---- QR
   prof_begin(h, ar, ST_SOLVE, st);
   {
     dim3 g(static_cast<unsigned>(ceil_div(d, 32)), static_cast<unsigned>(ceil_div(s, 32)));
-    transpose_kernel<<<g, dim3(32, 8), 0, st>>>(SX, s, d, A);
+    transpose_kernel<<<g, dim3(32, 8), 0, st>>>(SX, s, d, A, lda);
     SLSO_CHECK_LAUNCH();
   }
   SLSO_CHECK_CUDA(cudaMemsetAsync(ready, 0, sizeof(int) * d, st));
   {
-    const bool vsm = s <= 24576;
-    const size_t smem = vsm ? sizeof(double) * s : 0;
-    void* fn = vsm ? reinterpret_cast<void*>(qr_kernel<true>) : reinterpret_cast<void*>(qr_kernel<false>);
+    // left-looking register-resident kernel when a column fits in registers, else right-looking
+    void* fn = nullptr;
+    size_t smem = sizeof(double) * lda;
+    int threads = kQrlThreads;
+    if (s <= 256) fn = reinterpret_cast<void*>(qr_left_kernel<1>);
+    else if (s <= 512) fn = reinterpret_cast<void*>(qr_left_kernel<2>);
+    else if (s <= 1024) fn = reinterpret_cast<void*>(qr_left_kernel<4>);
+    else if (s <= 2048) fn = reinterpret_cast<void*>(qr_left_kernel<8>);
+    else if (s <= 4096) fn = reinterpret_cast<void*>(qr_left_kernel<16>);
+    else if (s <= 8192) fn = reinterpret_cast<void*>(qr_left_kernel<32>);
+    else if (s <= 16384) fn = reinterpret_cast<void*>(qr_left_kernel<64>);
+    else {
+      const bool vsm = s <= 24576;
+      smem = vsm ? sizeof(double) * s : 0;
+      fn = vsm ? reinterpret_cast<void*>(qr_kernel<true>) : reinterpret_cast<void*>(qr_kernel<false>);
+      threads = kQrThreads;
+    }
     SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int occ = 0;
-    SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kQrThreads, smem));
+    SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
     if (occ < 1) return fail(SLSO_ERR_CUDA, "QR kernel cannot be resident (smem %zu)", smem);
     int G = static_cast<int>(std::min<int64_t>(h.num_sms, d));
-    int s_i = static_cast<int>(s), d_i = static_cast<int>(d);
-    void* args[] = {&A, &s_i, &d_i, &ready, &taus, &h.state};
+    int s_i = static_cast<int>(s), lda_i = static_cast<int>(lda), d_i = static_cast<int>(d);
+    void* args[] = {&A, &s_i, &lda_i, &d_i, &ready, &taus, &h.state};
     prof_end(h, ar, st);
     prof_begin(h, ar, ST_QR, st);
-    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kQrThreads), args, smem, st));
+    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, st));
     note_launch();
     prof_end(h, ar, st);
     prof_begin(h, ar, ST_SOLVE, st);
   }
-  r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(A, s, d, R, sgn);
+  r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(A, lda, d, R, sgn);
   SLSO_CHECK_LAUNCH();
-  sumsq_kernel<<<1, 1024, 0, st>>>(R, d * d, fro2);
+  sumsq_partial_kernel<<<kSumBlocks, 256, 0, st>>>(R, d * d, fro2);
   SLSO_CHECK_LAUNCH();
 
   // ---- certified route: R^-1
   if (mode == 0) {
-    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(A, s, d, sgn, Rinv);
+    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(A, lda, d, sgn, Rinv);
     SLSO_CHECK_LAUNCH();
-    sumsq_kernel<<<1, 1024, 0, st>>>(Rinv, d * d, fro2 + 1);
+    sumsq_partial_kernel<<<kSumBlocks, 256, 0, st>>>(Rinv, d * d, fro2 + kSumBlocks);
     SLSO_CHECK_LAUNCH();
   }
   certify_kernel<<<1, 1, 0, st>>>(h.state, fro2, d, tau, mode == 1 ? 1 : 0);

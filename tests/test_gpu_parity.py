@@ -199,3 +199,25 @@ def test_host_entry_point_matches_device_entry_points():
     sc_h, o_h, info = api.rank_rows_host(X.pin_memory(), "countsketch", 512, 16, 7, 8, compute="f32")
     assert torch.equal(sc_h, sc_d.cpu()) and torch.equal(o_h, o_d.cpu())
     assert info["rank"] == 48
+
+
+# ------------------------------------------------------------------ tensor-core scores
+@pytest.mark.parametrize("n,d,k", [(70, 16, 256), (1000, 100, 48), (12345, 320, 128), (4096, 1024, 16)])
+def test_tensor_core_float32_scores_match_oracle(n, d, k):
+    """3xTF32 tensor-core path: partial tiles, ragged K-blocks, N from 16 to 256."""
+    X = inputs.lognormal_rows(n, d, seed=n + k, dtype=torch.float32)
+    s = max(2 * d, 256)
+    sc, info = api.leverage(_dev(X), "countsketch", s, k, 5, 6, compute="f32")
+    want, oinfo = O.sketched_leverage(_np(X), "countsketch", s, k, 5, 6)
+    assert info["rank"] == oinfo["rank"] == d
+    assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
+
+
+@pytest.mark.parametrize("xdtype", [torch.float32, torch.bfloat16])
+def test_tensor_core_bf16_scores_close_to_oracle(xdtype):
+    """BF16 tensor-core paths (float32 X rounded in shared memory, or bfloat16 X loaded directly)."""
+    X = inputs.snr_student_t(9000, 512, rank=64, seed=7, dtype=xdtype)
+    sc, _ = api.leverage(_dev(X), "countsketch", 2048, 128, 8, 9, compute="bf16")
+    want, _ = O.sketched_leverage(_np(X), "countsketch", 2048, 128, 8, 9)
+    rel = np.abs(sc.cpu().numpy().astype(np.float64) - want) / want
+    assert np.median(rel) < 0.01 and np.max(rel) < 0.2
