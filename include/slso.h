@@ -144,6 +144,21 @@ slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t
                                 void* scores_host, int64_t* order_host, slso_info* info,
                                 void* stream);
 
+/* Ordering that allocates nothing (the paper has no counterpart; this exists for callers).
+ * Some callers cannot call cudaMalloc where they need an ordering: a process whose device
+ * memory is entirely owned by another framework's caching allocator, a service that forbids
+ * allocation after start-up so that its footprint and latency stay fixed, or code running
+ * while someone else records a CUDA graph.  slso_order_static computes exactly what slso_order
+ * computes, takes no handle, and uses as scratch one file-scope __device__ array sized for
+ * n <= 1048576 (2^20) scores, about 24.3 MB that every GPU loading the library keeps until the
+ * process exits.  scores: n values of dtype sdt (F32 or F64) on the current device; order: n
+ * int64 row indices.  Errors: SHAPE for n < 1 or n > 2^20, DTYPE, INVALID_ARG for NULL
+ * pointers.  The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls share the one
+ * array, so calls that can overlap on the GPU (different streams, no ordering between them)
+ * race and must be serialised by the caller; nothing in the array needs to start at zero. */
+slso_status slso_order_static(const void* scores, int32_t sdt, int64_t n, int64_t* order, void* stream);
+
 /* Instrumentation (no counterpart in the paper).  slso_profile(h, 1) resets and starts
  * recording a CUDA event pair around every stage each call enqueues on its stream:
  * 0 sketch, 1 Householder QR, 2 rest of the small solve (certificate, R^-1 or SVD, M),

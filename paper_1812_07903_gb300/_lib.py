@@ -21,7 +21,7 @@ DTYPE = {"f64": F64, "f32": F32, "bf16": BF16, "fp8": FP8_E4M3}
 EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
     "slso_sketch", "slso_sketched_svd", "slso_leverage", "slso_order", "slso_rank_rows_host",
-    "slso_profile", "slso_profile_read",
+    "slso_profile", "slso_profile_read", "slso_order_static",
 )
 STAGES = ("sketch", "qr", "solve", "scores", "order", "copy")
 
@@ -75,6 +75,7 @@ def load():
         "slso_order": ([vp, vp, i32, i64, vp, vp], i32),
         "slso_rank_rows_host": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), vp, vp,
                                  ctypes.POINTER(Info), vp], i32),
+        "slso_order_static": ([vp, i32, i64, vp, vp], i32),
         "slso_profile": ([vp, ctypes.c_int], i32),
         "slso_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_int64)], i32),
