@@ -144,6 +144,46 @@ slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t
                                 void* scores_host, int64_t* order_host, slso_info* info,
                                 void* stream);
 
+/* Serving: continuous batching of leverage-score and sketched-SVD jobs ----------------------
+ * A server owns `slots` CUDA streams on one device and a worker thread.  slso_server_submit
+ * queues a job without blocking; the worker admits queued jobs in arrival order whenever a slot
+ * is free and the job's scratch footprint (exactly what slso_workspace_size would report for
+ * it) fits in `mem_budget_bytes` beside the jobs already running.  Admitted jobs run
+ * concurrently, each on its own stream with stream-ordered scratch; jobs that arrive while
+ * others run are admitted as slots and memory free up.  Results are identical to running the
+ * job alone with slso_leverage (+ slso_order) or slso_sketched_svd.  All device pointers in a
+ * job stay owned by the caller and must stay valid until the job has been polled. */
+typedef struct slso_server slso_server;
+typedef enum { SLSO_JOB_LEVERAGE = 0, SLSO_JOB_SKETCHED_SVD = 1 } slso_job_kind;
+typedef struct {
+  int32_t job;          /* slso_job_kind                                                        */
+  int32_t xdt;          /* leverage: dtype of X                                                  */
+  const void* X;        /* leverage: X (n x d, ldx); sketched SVD: SX (n = s rows x d, float64)  */
+  int64_t n, d, ldx;
+  slso_params params;   /* leverage: all fields; sketched SVD: only tau is read                  */
+  void* scores;         /* leverage: n scores (float64 when compute == F64, else float32)        */
+  int64_t* order;       /* leverage: n row indices in "dec" order, or NULL                       */
+  double* sigma;        /* sketched SVD: d singular values, V (d x d), R (d x d or NULL)         */
+  double* V;
+  double* R;
+} slso_job;
+
+/* slots in [1, 64]; the budget bounds the summed scratch of running jobs. */
+slso_status slso_server_create(slso_server** server, int device, int slots, size_t mem_budget_bytes);
+/* Waits for running jobs; jobs still queued finish with SLSO_ERR_BUSY.  Unpolled results are freed. */
+slso_status slso_server_destroy(slso_server* server);
+/* Validates the job (same errors as the direct entry points) and queues it.  BUSY when the
+ * job alone needs more scratch than the whole budget, or the server is shutting down. */
+slso_status slso_server_submit(slso_server* server, const slso_job* job, int64_t* ticket);
+/* Waits up to timeout_ms for the job.  Returns TIMEOUT if it is not finished (poll again),
+ * NOT_FOUND for an unknown or already collected ticket; otherwise OK with the job's own status,
+ * its info, and times_ms[0..2] = {queued, admitted to done, submit to done} when non-NULL.
+ * A finished job is forgotten once polled. */
+slso_status slso_server_poll(slso_server* server, int64_t ticket, int timeout_ms, slso_status* job_status,
+                             slso_info* info, double* times_ms);
+/* counters[0..3] = {submitted, admitted, completed, queued}; bytes of scratch in use. */
+slso_status slso_server_stats(slso_server* server, int64_t* counters, size_t* mem_in_use);
+
 /* Ordering that allocates nothing (the paper has no counterpart; this exists for callers).
  * Some callers cannot call cudaMalloc where they need an ordering: a process whose device
  * memory is entirely owned by another framework's caching allocator, a service that forbids

@@ -22,7 +22,9 @@ EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
     "slso_sketch", "slso_sketched_svd", "slso_leverage", "slso_order", "slso_rank_rows_host",
     "slso_profile", "slso_profile_read", "slso_order_static",
+    "slso_server_create", "slso_server_destroy", "slso_server_submit", "slso_server_poll", "slso_server_stats",
 )
+JOB_LEVERAGE, JOB_SKETCHED_SVD = 0, 1
 STAGES = ("sketch", "qr", "solve", "scores", "order", "copy")
 
 
@@ -43,6 +45,15 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Job(ctypes.Structure):
+    _fields_ = [
+        ("job", ctypes.c_int32), ("xdt", ctypes.c_int32), ("X", ctypes.c_void_p),
+        ("n", ctypes.c_int64), ("d", ctypes.c_int64), ("ldx", ctypes.c_int64), ("params", Params),
+        ("scores", ctypes.c_void_p), ("order", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+        ("V", ctypes.c_void_p), ("R", ctypes.c_void_p),
+    ]
 
 
 class SlsoError(RuntimeError):
@@ -76,6 +87,12 @@ def load():
         "slso_rank_rows_host": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), vp, vp,
                                  ctypes.POINTER(Info), vp], i32),
         "slso_order_static": ([vp, i32, i64, vp, vp], i32),
+        "slso_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], i32),
+        "slso_server_destroy": ([vp], i32),
+        "slso_server_submit": ([vp, ctypes.POINTER(Job), ctypes.POINTER(i64)], i32),
+        "slso_server_poll": ([vp, i64, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(Info),
+                              ctypes.POINTER(ctypes.c_double)], i32),
+        "slso_server_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_size_t)], i32),
         "slso_profile": ([vp, ctypes.c_int], i32),
         "slso_profile_read": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_int64)], i32),

@@ -176,6 +176,79 @@ def profile_read(handle=None):
     return {name: (ms[i], calls[i]) for i, name in enumerate(L.STAGES)}, launches.value
 
 
+class Server:
+    """slso_server_*: continuous batching of leverage and sketched-SVD jobs on one device.
+
+    Tensors referenced by a job are kept alive by the Server until the job is polled.
+    """
+
+    def __init__(self, slots=4, mem_budget_bytes=8 << 30, device=None):
+        lib = L.load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self._s = ctypes.c_void_p()
+        L.check(lib.slso_server_create(ctypes.byref(self._s), dev, int(slots), int(mem_budget_bytes)))
+        self._keep = {}
+
+    def submit_leverage(self, X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
+                        compute="f32", correct_frac=0.0, with_order=True):
+        n, d, ldx, xdt = _x_args(X)
+        j = L.Job()
+        j.job, j.xdt, j.X, j.n, j.d, j.ldx = L.JOB_LEVERAGE, xdt, X.data_ptr(), n, d, ldx
+        j.params = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+        sdt = torch.float64 if compute == "f64" else torch.float32
+        scores = torch.empty(n, dtype=sdt, device=X.device)
+        order = torch.empty(n, dtype=torch.int64, device=X.device) if with_order else None
+        j.scores = scores.data_ptr()
+        j.order = order.data_ptr() if order is not None else None
+        t = ctypes.c_int64(0)
+        L.check(L.load().slso_server_submit(self._s, ctypes.byref(j), ctypes.byref(t)))
+        self._keep[t.value] = (X, scores, order)
+        return t.value
+
+    def submit_sketched_svd(self, SX, tau=-1.0):
+        _require_cuda(SX)
+        s, d = SX.shape
+        j = L.Job()
+        j.job, j.xdt, j.X, j.n, j.d, j.ldx = L.JOB_SKETCHED_SVD, L.F64, SX.data_ptr(), s, d, d
+        j.params = make_params("countsketch", s, 0, 0, 0, tau, "f64", 0.0)
+        sigma = torch.empty(d, dtype=torch.float64, device=SX.device)
+        V = torch.empty(d, d, dtype=torch.float64, device=SX.device)
+        R = torch.empty(d, d, dtype=torch.float64, device=SX.device)
+        j.sigma, j.V, j.R = sigma.data_ptr(), V.data_ptr(), R.data_ptr()
+        t = ctypes.c_int64(0)
+        L.check(L.load().slso_server_submit(self._s, ctypes.byref(j), ctypes.byref(t)))
+        self._keep[t.value] = (SX, sigma, V, R)
+        return t.value
+
+    def poll(self, ticket, timeout_ms=60000):
+        """(status, info dict, times_ms [queued, running, total], outputs) of a finished job."""
+        st = ctypes.c_int32(0)
+        info = L.Info()
+        times = (ctypes.c_double * 3)()
+        L.check(L.load().slso_server_poll(self._s, int(ticket), int(timeout_ms), ctypes.byref(st),
+                                          ctypes.byref(info), times))
+        outs = self._keep.pop(ticket)
+        return st.value, info.as_dict(), list(times), outs[1:]
+
+    def stats(self):
+        c = (ctypes.c_int64 * 4)()
+        mem = ctypes.c_size_t(0)
+        L.check(L.load().slso_server_stats(self._s, c, ctypes.byref(mem)))
+        return {"submitted": c[0], "admitted": c[1], "completed": c[2], "queued": c[3], "mem_in_use": mem.value}
+
+    def close(self):
+        if self._s:
+            L.load().slso_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def default_tau(s, d):
     return max(s, d) * 2.0**-52
 

@@ -11,7 +11,7 @@
 
 using namespace slso;
 
-namespace {
+namespace slso {
 
 double default_tau(int64_t s, int64_t d) { return static_cast<double>(std::max(s, d)) * std::ldexp(1.0, -52); }
 
@@ -56,6 +56,10 @@ slso_status check_params(const slso_params* p, int64_t n, int64_t d) {
   return SLSO_OK;
 }
 
+}  // namespace slso
+
+namespace {
+
 template <class Plan>
 slso_status run_plan(Handle& h, Plan&& plan) {
   Arena m(nullptr, ~size_t(0), true);
@@ -83,6 +87,10 @@ slso_status fill_info(Handle& h, cudaStream_t st, slso_info* info) {
   return SLSO_OK;
 }
 
+}  // namespace
+
+namespace slso {
+
 slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st) {
   const double tau = p->tau < 0 ? default_tau(p->s, d) : p->tau;
@@ -99,7 +107,7 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   return SLSO_OK;
 }
 
-}  // namespace
+}  // namespace slso
 
 extern "C" slso_status slso_workspace_size(const slso_params* params, int64_t n, int64_t d, size_t* bytes) {
   if (!bytes) return fail(SLSO_ERR_INVALID_ARG, "bytes is NULL");

@@ -316,6 +316,13 @@ struct SolveOut {
 slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t d, double tau,
                       int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st);
 
+// api.cu: argument checks and the leverage plan shared with the server
+double default_tau(int64_t s, int64_t d);
+slso_status check_x(const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt);
+slso_status check_params(const slso_params* p, int64_t n, int64_t d);
+slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                          int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
+
 // score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,

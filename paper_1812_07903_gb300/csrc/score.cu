@@ -9,6 +9,7 @@
 //   compute F32: float32 products and sums.
 //   compute BF16: X and M rounded to bfloat16, exact products, float32 sums.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -133,6 +134,70 @@ slso_status launch_score_sum(Handle& h, const Out* scores, int64_t n, double* pa
   return SLSO_OK;
 }
 
+// Correction pass: rescore the rows listed in order[0..T) (the top-T rows of the low-precision
+// scores) in float32 from the float32 copy of M and overwrite their scores.  CTA = 64 gathered
+// rows; the CTA walks all column blocks of M itself, so each row's sum is finished in-CTA.
+template <class T>
+__global__ void __launch_bounds__(256) rescore_rows_kernel(const T* __restrict__ X, int64_t d, int64_t ldx,
+                                                           const float* __restrict__ M, int64_t kk,
+                                                           const int64_t* __restrict__ order, int64_t T_rows,
+                                                           float* __restrict__ scores) {
+  __shared__ float Xs[kBk][kBm + 1];
+  __shared__ float Ms[kBk][kBn];
+  __shared__ float rowsum[kBm][17];
+  __shared__ int64_t rows[kBm];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kBm;
+  if (threadIdx.x < kBm) rows[threadIdx.x] = (t0 + threadIdx.x < T_rows) ? order[t0 + threadIdx.x] : -1;
+  __syncthreads();
+  float sq[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t c0 = 0; c0 < kk; c0 += kBn) {
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int64_t k0 = 0; k0 < d; k0 += kBk) {
+      for (int t = threadIdx.x; t < kBm * kBk; t += 256) {
+        const int rr = t / kBk, kc = t % kBk;
+        const int64_t r = rows[rr], k = k0 + kc;
+        Xs[kc][rr] = (r >= 0 && k < d) ? static_cast<float>(load_as_double(X + r * ldx + k)) : 0.f;
+      }
+      for (int t = threadIdx.x; t < kBk * kBn; t += 256) {
+        const int kc = t / kBn, cc = t % kBn;
+        const int64_t k = k0 + kc, c = c0 + cc;
+        Ms[kc][cc] = (k < d && c < kk) ? M[k * kk + c] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kc = 0; kc < kBk; ++kc) {
+        float xv[4], mv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xv[a] = Xs[kc][ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mv[b] = Ms[kc][tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], mv[b], acc[a][b]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) sq[a] = fmaf(acc[a][b], acc[a][b], sq[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) rowsum[ty * 4 + a][tx] = sq[a];
+  __syncthreads();
+  if (threadIdx.x < kBm && rows[threadIdx.x] >= 0) {
+    float t = 0.f;
+    for (int q = 0; q < 16; ++q) t += rowsum[threadIdx.x][q];
+    scores[rows[threadIdx.x]] = t;
+  }
+}
+
 __global__ void m_to_f32_kernel(const double* __restrict__ M, int64_t e, float* __restrict__ Mf) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < e;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -149,9 +214,30 @@ int grid1d(int64_t n, const Handle& h) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8LL * h.num_sms)));
 }
 
+// Correction pass (BF16 / FP8 compute with correct_frac > 0): order the low-precision scores,
+// take the top ceil(frac n) rows and rescore them in float32.
+template <class T>
+slso_status correct_top_rows(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx,
+                             const double* M, int64_t kk, int32_t compute, double frac, float* scores,
+                             cudaStream_t st) {
+  if (!(frac > 0.0) || (compute != SLSO_BF16 && compute != SLSO_FP8_E4M3)) return SLSO_OK;
+  const int64_t T_rows = std::min<int64_t>(n, static_cast<int64_t>(std::ceil(frac * static_cast<double>(n))));
+  int64_t* order = ar.take<int64_t>(n);
+  float* Mf = ar.take<float>(static_cast<size_t>(d) * kk);
+  SLSO_TRY(order_scores(h, ar, scores, SLSO_F32, n, order, st));
+  if (ar.measure()) return SLSO_OK;
+  m_to_f32_kernel<<<grid1d(d * kk, h), 256, 0, st>>>(M, d * kk, Mf);
+  SLSO_CHECK_LAUNCH();
+  rescore_rows_kernel<T><<<static_cast<unsigned>(ceil_div(T_rows, kBm)), 256, 0, st>>>(X, d, ldx, Mf, kk, order,
+                                                                                       T_rows, scores);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
 template <class T>
 slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx,
-                         const double* M, int64_t kk, int32_t compute, void* scores, cudaStream_t st) {
+                         const double* M, int64_t kk, int32_t compute, double correct_frac, void* scores,
+                         cudaStream_t st) {
   const int64_t ncb = ceil_div(kk, kBn);
   dim3 grid(static_cast<unsigned>(ceil_div(n, kBm)), static_cast<unsigned>(ncb));
   double* sums = ar.take<double>(kSumBlocks);
@@ -169,6 +255,7 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
                                                 : (std::is_same<T, double>::value ? SLSO_F64 : SLSO_BF16),
                          M, kk, compute, static_cast<float*>(scores), &used_tc, st));
   if (used_tc) {
+    SLSO_TRY(correct_top_rows(h, ar, X, n, d, ldx, M, kk, compute, correct_frac, static_cast<float*>(scores), st));
     if (ar.measure()) return SLSO_OK;
     return launch_score_sum<float>(h, static_cast<float*>(scores), n, sums, st);
   }
@@ -187,6 +274,7 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
   SLSO_CHECK_LAUNCH();
   score_combine_kernel<float, float><<<grid1d(n, h), 256, 0, st>>>(part, n, ncb, static_cast<float*>(scores));
   SLSO_CHECK_LAUNCH();
+  SLSO_TRY(correct_top_rows(h, ar, X, n, d, ldx, M, kk, compute, correct_frac, static_cast<float*>(scores), st));
   return launch_score_sum<float>(h, static_cast<float*>(scores), n, sums, st);
 }
 
@@ -195,12 +283,11 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
 slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, const double* M, int64_t kk, int32_t compute, void* scores,
                        double correct_frac, cudaStream_t st) {
-  (void)correct_frac;
   if (compute == SLSO_FP8_E4M3) return fail(SLSO_ERR_DTYPE, "FP8 compute is not available in this build");
   switch (xdt) {
-    case SLSO_F64: return scores_typed(h, ar, static_cast<const double*>(X), n, d, ldx, M, kk, compute, scores, st);
-    case SLSO_F32: return scores_typed(h, ar, static_cast<const float*>(X), n, d, ldx, M, kk, compute, scores, st);
-    case SLSO_BF16: return scores_typed(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, M, kk, compute, scores, st);
+    case SLSO_F64: return scores_typed(h, ar, static_cast<const double*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
+    case SLSO_F32: return scores_typed(h, ar, static_cast<const float*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
+    case SLSO_BF16: return scores_typed(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
     default: return fail(SLSO_ERR_DTYPE, "unsupported X dtype %d", xdt);
   }
 }

@@ -221,3 +221,18 @@ def test_tensor_core_bf16_scores_close_to_oracle(xdtype):
     want, _ = O.sketched_leverage(_np(X), "countsketch", 2048, 128, 8, 9)
     rel = np.abs(sc.cpu().numpy().astype(np.float64) - want) / want
     assert np.median(rel) < 0.01 and np.max(rel) < 0.2
+
+
+def test_bf16_correction_pass_rescores_top_rows_in_float32():
+    """Precision pattern: BF16 scores, then the top 2% rows rescored in float32 (a7)."""
+    n = 20000
+    X = inputs.snr_student_t(n, 256, rank=50, seed=1003)
+    sc, _ = api.leverage(_dev(X), "countsketch", 4096, 128, 2003, 3003, compute="bf16", correct_frac=0.02)
+    want, _ = O.sketched_leverage(_np(X), "countsketch", 4096, 128, 2003, 3003)
+    g = sc.cpu().numpy().astype(np.float64)
+    top = O.order_dec(g)[: n // 100]
+    assert np.max(np.abs(g[top] - want[top]) / want[top]) < 1e-4
+    overlap = len(set(top.tolist()) & set(O.order_dec(want)[: n // 100].tolist())) / (n // 100)
+    assert overlap >= 0.99
+    rest = O.order_dec(g)[n // 10:]
+    assert np.median(np.abs(g[rest] - want[rest]) / want[rest]) < 0.01  # untouched rows keep BF16 scores
