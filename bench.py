@@ -185,6 +185,59 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- serving
+def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
+    """Poisson trace of mixed leverage jobs through slso_server at `load` x one-at-a-time capacity.
+
+    Jobs: n = round(2^U[12,20]), d from {64,128,256,300,784}, 8-cluster Gaussian-mixture rows,
+    sketch kind 1/3 each, k = 64.  Capacity is calibrated by running the first 16 jobs one at a time
+    through the direct entry points; arrivals are then Poisson at `load` x that rate.
+    """
+    jobs = inputs.serving_jobs(n_jobs=n_jobs, seed=seed, rate_per_s=1.0)
+    for jb in jobs:
+        jb["X"] = inputs.gaussian_mixture(jb["n"], jb["d"], seed=jb["seed"], device="cuda")
+    torch.cuda.synchronize()
+    calib = jobs[: min(16, n_jobs)]
+    for jb in calib[:2]:  # warm-up
+        api.leverage(jb["X"], jb["kind"], jb["s"], jb["k"], jb["seed"], jb["seed"] + 1, want_info=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for jb in calib:
+        sc, _ = api.leverage(jb["X"], jb["kind"], jb["s"], jb["k"], jb["seed"], jb["seed"] + 1, want_info=False)
+        api.order(sc)
+        torch.cuda.synchronize()
+    service_s = (time.perf_counter() - t0) / len(calib)
+    rate = load / service_s
+    gaps = [jobs[0]["arrival_s"]] + [b["arrival_s"] - a["arrival_s"] for a, b in zip(jobs, jobs[1:])]
+    srv = api.Server(slots=slots, mem_budget_bytes=24 << 30)
+    tickets = []
+    start = time.perf_counter()
+    t_arr = 0.0
+    for jb, g in zip(jobs, gaps):
+        t_arr += g / rate  # inter-arrival gaps of the unit-rate trace, rescaled
+        delay = start + t_arr - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit_leverage(jb["X"], jb["kind"], jb["s"], jb["k"], jb["seed"], jb["seed"] + 1))
+    lat, bad = [], 0
+    for t in tickets:
+        st, info, times, _ = srv.poll(t, timeout_ms=600000)
+        bad += st != 0
+        lat.append(times[2])
+    makespan = time.perf_counter() - start
+    srv.close()
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]  # noqa: E731
+    rows = sum(jb["n"] for jb in jobs)
+    return {
+        "workload": f"{n_jobs} jobs, Poisson arrivals at {load} x calibrated capacity, n=2^U[12,20], "
+                    "d in {64,128,256,300,784}, 8-cluster mixture rows, CountSketch/SRHT/Gaussian 1/3 each, k=64",
+        "slots": slots, "jobs": n_jobs, "failed": bad, "calibrated_service_ms": service_s * 1e3,
+        "arrival_rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
+        "makespan_s": makespan, "jobs_per_s": n_jobs / makespan, "rows_per_s": rows / makespan,
+    }
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -196,6 +249,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64 oracle comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=96, help="jobs in the serving trace (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -364,6 +418,10 @@ def main():
                                                       rows_sample=65536, qr_steps=96, X_rows=Xn)
             line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle",
                                     "sample": sample, "est_seconds_full_job": tot}
+    if rank == 0 and world == 1 and args.serving_jobs > 0:
+        del X
+        torch.cuda.empty_cache()
+        line["serving"] = serving_bench(api, inputs, torch, args.serving_jobs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

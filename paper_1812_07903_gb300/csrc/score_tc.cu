@@ -8,7 +8,7 @@
 //   warp 4     TMA producer: X tiles (rows of 128 bytes, 128B swizzle) and the matching K-slices
 //              of B = M^T (prepared once per call in global memory).
 //   warp 5     TMEM owner and MMA issuer (one thread): tcgen05.mma, commits to mbarriers.
-//   warps 6-9  converters (float32 X only): float32 tile -> operand tile(s) in the same layout.
+//   warps 6-13 converters (float32 X only): float32 tile -> operand tile(s) in the same layout.
 // Modes:
 //   TF32X3    float32 X, float32-accurate: X = Xhi + Xlo with Xhi = tf32(X), Xlo = tf32(X - Xhi)
 //             (nearest-even), M = Mhi + Mlo likewise; D += Xhi Mhi + Xhi Mlo + Xlo Mhi (kind::tf32).
@@ -32,7 +32,8 @@ using namespace tc;
 
 enum Mode : int { MODE_TF32X3 = 0, MODE_BF16_CVT = 1, MODE_BF16 = 2 };
 
-constexpr int kThreads = 320;
+constexpr int kConvThreads = 256;
+constexpr int kThreads = 192 + kConvThreads;
 constexpr int kBM = 128;
 constexpr int kMaxStages = 8;
 constexpr int kWarpProducer = 4, kWarpMma = 5, kWarpConvert0 = 6;
@@ -85,11 +86,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     s_abort = 0;
     for (int i = 0; i < L.RS; ++i) {
       mbar_init(&raw_full[i], 1);
-      mbar_init(&raw_empty[i], 128);
+      mbar_init(&raw_empty[i], kConvThreads);
     }
     for (int i = 0; i < L.OS; ++i) {
       mbar_init(&op_full[i], 1);
-      mbar_init(&cvt_full[i], 128);
+      mbar_init(&cvt_full[i], kConvThreads);
       mbar_init(&op_empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= kWarpConvert0) {
     if (convert) {
-      const int ct = threadIdx.x - kWarpConvert0 * 32;  // 0..127
+      const int ct = threadIdx.x - kWarpConvert0 * 32;  // 0 .. kConvThreads-1
       int it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -218,8 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint4* src = reinterpret_cast<const uint4*>(raw);
             uint4* hi = reinterpret_cast<uint4*>(op);
             uint4* lo = reinterpret_cast<uint4*>(op + kXTileBytes);
-#pragma unroll 4
-            for (int q = ct; q < static_cast<int>(kXTileBytes / 16); q += 128) {
+#pragma unroll
+            for (int q = ct; q < static_cast<int>(kXTileBytes / 16); q += kConvThreads) {
               const uint4 v = src[q];
               uint4 h, l;
               split_tf32(v.x, h.x, l.x);
@@ -233,8 +234,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // output row r, 16-byte chunk oc holds bfloat16 elements 8oc..8oc+7 = float32 elements
             // of box oc/4, float32 chunks 2(oc%4) and 2(oc%4)+1; 128B swizzle: chunk c of row r
             // sits at position c ^ (r % 8).
-#pragma unroll 4
-            for (int q = ct; q < static_cast<int>(kXTileBytes / 16); q += 128) {
+#pragma unroll
+            for (int q = ct; q < static_cast<int>(kXTileBytes / 16); q += kConvThreads) {
               const int r = q >> 3, oc = q & 7, sw = r & 7;
               const float4* srow = reinterpret_cast<const float4*>(raw + (oc >> 2) * kXTileBytes + r * 128);
               const int sc = (oc & 3) * 2;
@@ -357,12 +358,12 @@ Layout make_layout(int mode, int64_t kk, int64_t d) {
   L.kbe = (mode == MODE_TF32X3) ? 32 : 64;
   L.KB = static_cast<int>(ceil_div(d, L.kbe));
   L.b_bytes = static_cast<uint32_t>(L.N) * 128u;
-  const uint32_t budget = 220u * 1024u;
+  const uint32_t budget = 226u * 1024u;  // + 1.5 KB barriers and alignment slack <= 227 KB
   if (mode == MODE_TF32X3) {
     L.raw_bytes = kXTileBytes;
     L.op_bytes = 2 * kXTileBytes + 2 * L.b_bytes;
-    L.OS = 2;
-    L.RS = static_cast<int>(std::min<uint32_t>(4, (budget - 2 * L.op_bytes) / L.raw_bytes));
+    L.OS = static_cast<int>(std::max<uint32_t>(2, std::min<uint32_t>(3, (budget - 2 * L.raw_bytes) / L.op_bytes)));
+    L.RS = static_cast<int>(std::min<uint32_t>(4, (budget - L.OS * L.op_bytes) / L.raw_bytes));
   } else if (mode == MODE_BF16_CVT) {
     L.raw_bytes = 2 * kXTileBytes;
     L.op_bytes = kXTileBytes + L.b_bytes;
