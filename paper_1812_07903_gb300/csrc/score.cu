@@ -283,7 +283,6 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
 slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, const double* M, int64_t kk, int32_t compute, void* scores,
                        double correct_frac, cudaStream_t st) {
-  if (compute == SLSO_FP8_E4M3) return fail(SLSO_ERR_DTYPE, "FP8 compute is not available in this build");
   switch (xdt) {
     case SLSO_F64: return scores_typed(h, ar, static_cast<const double*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
     case SLSO_F32: return scores_typed(h, ar, static_cast<const float*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);

@@ -14,10 +14,14 @@
 //             (nearest-even), M = Mhi + Mlo likewise; D += Xhi Mhi + Xhi Mlo + Xlo Mhi (kind::tf32).
 //   BF16_CVT  float32 X rounded to bfloat16 in shared memory, M in bfloat16 (kind::f16).
 //   BF16      bfloat16 X loaded directly (kind::f16).
+//   FP8_F32 / FP8_BF16  float32 or bfloat16 X scaled per column by c_j = 448 / max_i |x_ij| and
+//             rounded to e4m3 in shared memory; B = e4m3(e M^T diag(1/c)) with one scale e for
+//             M; the epilogue multiplies each row's sum of squares by 1/e^2 (kind::f8f6f4).
 // All accumulation is float32 in TMEM.  Every mbarrier wait is bounded; a timeout sets an error
 // word that the host reports as SLSO_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -30,7 +34,7 @@ namespace {
 
 using namespace tc;
 
-enum Mode : int { MODE_TF32X3 = 0, MODE_BF16_CVT = 1, MODE_BF16 = 2 };
+enum Mode : int { MODE_TF32X3 = 0, MODE_BF16_CVT = 1, MODE_BF16 = 2, MODE_FP8_F32 = 3, MODE_FP8_BF16 = 4 };
 
 constexpr int kConvThreads = 256;
 constexpr int kThreads = 192 + kConvThreads;
@@ -45,6 +49,9 @@ struct Layout {
   int KB;        // K-blocks
   int kbe;       // K elements per block: 32 (float32 operands) or 64 (bfloat16 operands)
   int RS, OS;    // raw / operand stages
+  int raw_boxes; // X boxes (128 rows x 128 bytes) per K-block
+  int box_cols;  // X columns per box: 32 (float32 X) or 64 (bfloat16 X)
+  uint32_t x_op_bytes;  // X operand bytes in an operand stage
   uint32_t raw_bytes, b_bytes, op_bytes;
   uint32_t raw_off, op_off, bar_off, smem_bytes;
   uint32_t tmem_cols;
@@ -65,6 +72,7 @@ __device__ __forceinline__ void split_tf32(uint32_t x, uint32_t& hi, uint32_t& l
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB0,
                     const __grid_constant__ CUtensorMap tmB1, const Layout L, int64_t n, int ntiles,
+                    const float* __restrict__ cscale, const float* __restrict__ post_scale,
                     float* __restrict__ scores, DevState* __restrict__ state) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) &
@@ -127,19 +135,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t rph = (it / L.RS) & 1u;
           if (!mbar_wait(&raw_empty[rs], rph ^ 1u, abort_flag)) { ok = false; break; }
           unsigned char* raw = smem + L.raw_off + rs * L.raw_bytes;
-          if (L.mode == MODE_TF32X3) {
-            mbar_arrive_expect_tx(&op_full[os], 2 * L.b_bytes);
-            tma_load_2d(op + 2 * kXTileBytes, &tmB0, &op_full[os], x, 0);
-            tma_load_2d(op + 2 * kXTileBytes + L.b_bytes, &tmB1, &op_full[os], x, 0);
-            mbar_arrive_expect_tx(&raw_full[rs], kXTileBytes);
-            tma_load_2d(raw, &tmX, &raw_full[rs], x, y);
-          } else {  // bfloat16 operands from float32 X: two 32-column float32 boxes per K-block
-            mbar_arrive_expect_tx(&op_full[os], L.b_bytes);
-            tma_load_2d(op + kXTileBytes, &tmB0, &op_full[os], x, 0);
-            mbar_arrive_expect_tx(&raw_full[rs], 2 * kXTileBytes);
-            tma_load_2d(raw, &tmX, &raw_full[rs], x, y);
-            tma_load_2d(raw + kXTileBytes, &tmX, &raw_full[rs], x + 32, y);
-          }
+          const int nb = (L.mode == MODE_TF32X3) ? 2 : 1;  // B tiles per stage
+          mbar_arrive_expect_tx(&op_full[os], nb * L.b_bytes);
+          tma_load_2d(op + L.x_op_bytes, &tmB0, &op_full[os], x, 0);
+          if (nb == 2) tma_load_2d(op + L.x_op_bytes + L.b_bytes, &tmB1, &op_full[os], x, 0);
+          mbar_arrive_expect_tx(&raw_full[rs], L.raw_boxes * kXTileBytes);
+          for (int b = 0; b < L.raw_boxes; ++b)
+            tma_load_2d(raw + b * kXTileBytes, &tmX, &raw_full[rs], x + b * L.box_cols, y);
         }
       }
       if (!ok) {
@@ -155,7 +157,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == kWarpMma) {
     if (lane == 0) {
+      const bool fp8 = L.mode == MODE_FP8_F32 || L.mode == MODE_FP8_BF16;
       const uint32_t id = (L.mode == MODE_TF32X3) ? idesc(FMT_TF32, FMT_TF32, kBM, L.N)
+                          : fp8                   ? idesc(FMT_E4M3, FMT_E4M3, kBM, L.N)
                                                   : idesc(FMT_BF16, FMT_BF16, kBM, L.N);
       int it = 0, tcount = 0;
       bool ok = true;
@@ -188,7 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
               const uint64_t o = static_cast<uint64_t>(ks * 2);
-              mma_f16(d_tmem, a + o, b + o, id, (kb | ks) != 0);
+              if (fp8) mma_f8(d_tmem, a + o, b + o, id, (kb | ks) != 0);
+              else mma_f16(d_tmem, a + o, b + o, id, (kb | ks) != 0);
             }
           }
           mma_commit(&op_empty[os]);
@@ -230,6 +235,47 @@ __global__ void __launch_bounds__(kThreads, 1)
               hi[q] = h;
               lo[q] = l;
             }
+          } else if (L.mode == MODE_FP8_F32 || L.mode == MODE_FP8_BF16) {
+            // output row r, 16-byte chunk oc holds e4m3 elements 16oc..16oc+15 of this K-block,
+            // i.e. X columns kb*128 + 16oc + t, each multiplied by its column scale first
+            const float* cs = cscale + static_cast<int64_t>(kb) * 128;
+#pragma unroll 2
+            for (int q = ct; q < static_cast<int>(kXTileBytes / 16); q += kConvThreads) {
+              const int r = q >> 3, oc = q & 7, sw = r & 7;
+              float f[16];
+              if (L.mode == MODE_FP8_F32) {  // four 32-column float32 boxes per K-block
+                const float4* srow = reinterpret_cast<const float4*>(raw + (oc >> 1) * kXTileBytes + r * 128);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                  const float4 v = srow[((oc & 1) * 4 + t) ^ sw];
+                  f[4 * t] = v.x; f[4 * t + 1] = v.y; f[4 * t + 2] = v.z; f[4 * t + 3] = v.w;
+                }
+              } else {  // two 64-column bfloat16 boxes per K-block
+                const uint4* srow = reinterpret_cast<const uint4*>(raw + (oc >> 2) * kXTileBytes + r * 128);
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                  const uint4 v = srow[((oc & 3) * 2 + t) ^ sw];
+                  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    f[8 * t + 2 * u] = __uint_as_float(w[u] << 16);
+                    f[8 * t + 2 * u + 1] = __uint_as_float(w[u] & 0xFFFF0000u);
+                  }
+                }
+              }
+              const float4* sc4 = reinterpret_cast<const float4*>(cs + oc * 16);
+              uint32_t o[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const float4 c = __ldg(sc4 + t);
+                const __nv_fp8x2_storage_t lo2 =
+                    __nv_cvt_float2_to_fp8x2(make_float2(f[4 * t] * c.x, f[4 * t + 1] * c.y), __NV_SATFINITE, __NV_E4M3);
+                const __nv_fp8x2_storage_t hi2 =
+                    __nv_cvt_float2_to_fp8x2(make_float2(f[4 * t + 2] * c.z, f[4 * t + 3] * c.w), __NV_SATFINITE, __NV_E4M3);
+                o[t] = static_cast<uint32_t>(lo2) | (static_cast<uint32_t>(hi2) << 16);
+              }
+              reinterpret_cast<uint4*>(op + r * 128)[oc ^ sw] = make_uint4(o[0], o[1], o[2], o[3]);
+            }
           } else {
             // output row r, 16-byte chunk oc holds bfloat16 elements 8oc..8oc+7 = float32 elements
             // of box oc/4, float32 chunks 2(oc%4) and 2(oc%4)+1; 128B swizzle: chunk c of row r
@@ -263,6 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {  // warps 0-3: epilogue; warp w reads TMEM lanes 32w..32w+31 = tile rows 32w..32w+31
+    const float post = post_scale ? *post_scale : 1.0f;
     int tcount = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
@@ -284,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(&acc_empty[ab]);
       const int64_t row = static_cast<int64_t>(tile) * kBM + warp * 32 + lane;
-      if (row < n) scores[row] = sum;
+      if (row < n) scores[row] = sum * post;
     }
     if (!ok && lane == 0) {
       atomicExch(&s_abort, 1);
@@ -355,25 +402,23 @@ Layout make_layout(int mode, int64_t kk, int64_t d) {
   Layout L{};
   L.mode = mode;
   L.N = static_cast<int>(ceil_div(kk, 32) * 32);  // whole 32-column TMEM loads in the epilogue
-  L.kbe = (mode == MODE_TF32X3) ? 32 : 64;
+  const bool fp8 = mode == MODE_FP8_F32 || mode == MODE_FP8_BF16;
+  L.kbe = (mode == MODE_TF32X3) ? 32 : (fp8 ? 128 : 64);  // one 128-byte operand row per K-block
   L.KB = static_cast<int>(ceil_div(d, L.kbe));
   L.b_bytes = static_cast<uint32_t>(L.N) * 128u;
+  L.box_cols = (mode == MODE_BF16 || mode == MODE_FP8_BF16) ? 64 : 32;
+  L.raw_boxes = (mode == MODE_BF16) ? 0 : L.kbe / L.box_cols;
+  L.x_op_bytes = (mode == MODE_TF32X3) ? 2 * kXTileBytes : kXTileBytes;
   const uint32_t budget = 226u * 1024u;  // + 1.5 KB barriers and alignment slack <= 227 KB
-  if (mode == MODE_TF32X3) {
-    L.raw_bytes = kXTileBytes;
-    L.op_bytes = 2 * kXTileBytes + 2 * L.b_bytes;
-    L.OS = static_cast<int>(std::max<uint32_t>(2, std::min<uint32_t>(3, (budget - 2 * L.raw_bytes) / L.op_bytes)));
-    L.RS = static_cast<int>(std::min<uint32_t>(4, (budget - L.OS * L.op_bytes) / L.raw_bytes));
-  } else if (mode == MODE_BF16_CVT) {
-    L.raw_bytes = 2 * kXTileBytes;
-    L.op_bytes = kXTileBytes + L.b_bytes;
-    L.OS = static_cast<int>(std::min<uint32_t>(4, budget / 2 / L.op_bytes));
-    L.RS = static_cast<int>(std::min<uint32_t>(4, (budget - L.OS * L.op_bytes) / L.raw_bytes));
-  } else {
-    L.raw_bytes = 0;
-    L.op_bytes = kXTileBytes + L.b_bytes;
+  L.raw_bytes = static_cast<uint32_t>(L.raw_boxes) * kXTileBytes;
+  L.op_bytes = L.x_op_bytes + (mode == MODE_TF32X3 ? 2 : 1) * L.b_bytes;
+  if (mode == MODE_BF16) {
     L.OS = static_cast<int>(std::min<uint32_t>(kMaxStages, budget / L.op_bytes));
     L.RS = 1;
+  } else {
+    // as many operand stages as leave room for two raw stages (at most 3), then raw stages
+    L.OS = static_cast<int>(std::max<uint32_t>(2, std::min<uint32_t>(3, (budget - 2 * L.raw_bytes) / L.op_bytes)));
+    L.RS = static_cast<int>(std::min<uint32_t>(4, (budget - L.OS * L.op_bytes) / L.raw_bytes));
   }
   L.raw_off = 0;
   L.op_off = L.raw_bytes * static_cast<uint32_t>(mode == MODE_BF16 ? 0 : L.RS);
@@ -383,6 +428,58 @@ Layout make_layout(int mode, int64_t kk, int64_t d) {
   while (cols < static_cast<uint32_t>(2 * L.N)) cols <<= 1;
   L.tmem_cols = cols;
   return L;
+}
+
+// max_i |x_ij| per column (as float bits; values are >= 0 so integer max orders them).
+template <class T>
+__global__ void colabsmax_kernel(const T* __restrict__ X, int64_t n, int64_t d, int64_t ldx, int64_t rows_per_cta,
+                                 unsigned int* __restrict__ colmax) {
+  const int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  float m = 0.0f;
+  for (int64_t r = r0; r < r1; ++r) m = fmaxf(m, fabsf(to_float(X[r * ldx + c])));
+  atomicMax(colmax + c, __float_as_uint(m));
+}
+
+// Column scales c_j = 448 / max |x_:j| (1 for empty or padded columns), and the single scale e of
+// M' = diag(1/c) M: e = 448 / max |M'| and post = 1/e^2.
+__global__ void fp8_scales_kernel(const unsigned int* __restrict__ colmax, const double* __restrict__ M, int64_t d,
+                                  int64_t kk, int64_t Kpad, float* __restrict__ cscale, float* __restrict__ escale) {
+  __shared__ float red[32];
+  for (int64_t j = threadIdx.x; j < Kpad; j += blockDim.x) {
+    const float a = j < d ? __uint_as_float(colmax[j]) : 0.0f;
+    cscale[j] = a > 0.0f ? 448.0f / a : 1.0f;
+  }
+  __syncthreads();
+  float m = 0.0f;
+  for (int64_t e = threadIdx.x; e < d * kk; e += blockDim.x)
+    m = fmaxf(m, static_cast<float>(fabs(M[e]) / static_cast<double>(cscale[e / kk])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+    const float e = t > 0.0f ? 448.0f / t : 1.0f;
+    escale[0] = e;
+    escale[1] = 1.0f / (e * e);
+  }
+}
+
+// B = e4m3(e M^T diag(1/c)) as N x Kpad bytes, K contiguous.
+__global__ void prep_b_fp8_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
+                                  const float* __restrict__ cscale, const float* __restrict__ escale,
+                                  __nv_fp8_storage_t* __restrict__ B) {
+  const float e = escale[0];
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N * Kpad;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = i / Kpad, k = i % Kpad;
+    const float m = (c < kk && k < d) ? static_cast<float>(M[k * kk + c] / static_cast<double>(cscale[k])) * e : 0.0f;
+    B[i] = __nv_cvt_float_to_fp8(m, __NV_SATFINITE, __NV_E4M3);
+  }
 }
 
 }  // namespace
@@ -397,17 +494,28 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   if (xdt == SLSO_F32 && compute == SLSO_F32) mode = MODE_TF32X3;
   if (xdt == SLSO_F32 && compute == SLSO_BF16) mode = MODE_BF16_CVT;
   if (xdt == SLSO_BF16 && compute == SLSO_BF16) mode = MODE_BF16;
+  if (xdt == SLSO_F32 && compute == SLSO_FP8_E4M3) mode = MODE_FP8_F32;
+  if (xdt == SLSO_BF16 && compute == SLSO_FP8_E4M3) mode = MODE_FP8_BF16;
   if (mode < 0 || kk > 256 || kk < 1) return SLSO_OK;
   const size_t esz = dtype_size(xdt);
   if (reinterpret_cast<uintptr_t>(X) % 16 != 0 || (ldx * esz) % 16 != 0) return SLSO_OK;
   if (!encode_fn()) return SLSO_OK;
   const Layout L = make_layout(mode, kk, d);
   const int64_t Kpad = static_cast<int64_t>(L.KB) * L.kbe;
+  const bool fp8 = mode == MODE_FP8_F32 || mode == MODE_FP8_BF16;
   void* B0 = nullptr;
   void* B1 = nullptr;
+  unsigned int* colmax = nullptr;
+  float* cscale = nullptr;
+  float* escale = nullptr;
   if (mode == MODE_TF32X3) {
     B0 = ar.take<float>(static_cast<size_t>(L.N) * Kpad);
     B1 = ar.take<float>(static_cast<size_t>(L.N) * Kpad);
+  } else if (fp8) {
+    B0 = ar.take<__nv_fp8_storage_t>(static_cast<size_t>(L.N) * Kpad);
+    colmax = ar.take<unsigned int>(d);
+    cscale = ar.take<float>(Kpad);
+    escale = ar.take<float>(2);
   } else {
     B0 = ar.take<__nv_bfloat16>(static_cast<size_t>(L.N) * Kpad);
   }
@@ -416,19 +524,33 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   const int pg = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.N * Kpad, 256), 4LL * h.num_sms)));
   CUtensorMap mX, mB0, mB1;
   bool ok;
+  const CUtensorMapDataType xdt_map = (xdt == SLSO_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  ok = make_map(&mX, xdt_map, X, d, n, ldx * esz, static_cast<uint32_t>(L.box_cols), kBM);
   if (mode == MODE_TF32X3) {
     prep_b_tf32_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<float*>(B0), static_cast<float*>(B1));
     SLSO_CHECK_LAUNCH();
-    ok = make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * 4, 32, kBM) &&
-         make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, 32, L.N) &&
+    ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, 32, L.N) &&
          make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, 32, L.N);
+  } else if (fp8) {
+    SLSO_CHECK_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * d, st));
+    const int64_t rows_per_cta = std::max<int64_t>(1024, ceil_div(n, 256));
+    dim3 g(static_cast<unsigned>(ceil_div(d, 256)), static_cast<unsigned>(ceil_div(n, rows_per_cta)));
+    if (xdt == SLSO_F32)
+      colabsmax_kernel<float><<<g, 256, 0, st>>>(static_cast<const float*>(X), n, d, ldx, rows_per_cta, colmax);
+    else
+      colabsmax_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), n, d, ldx,
+                                                        rows_per_cta, colmax);
+    SLSO_CHECK_LAUNCH();
+    fp8_scales_kernel<<<1, 1024, 0, st>>>(colmax, M, d, kk, Kpad, cscale, escale);
+    SLSO_CHECK_LAUNCH();
+    prep_b_fp8_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, cscale, escale,
+                                          static_cast<__nv_fp8_storage_t*>(B0));
+    SLSO_CHECK_LAUNCH();
+    ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_UINT8, B0, Kpad, L.N, Kpad, 128, L.N);
+    mB1 = mB0;
   } else {
     prep_b_bf16_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<__nv_bfloat16*>(B0));
     SLSO_CHECK_LAUNCH();
-    if (mode == MODE_BF16_CVT)
-      ok = make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * 4, 32, kBM);
-    else
-      ok = make_map(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, X, d, n, ldx * 2, 64, kBM);
     ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B0, Kpad, L.N, Kpad * 2, 64, L.N);
     mB1 = mB0;
   }
@@ -437,7 +559,8 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   const int grid = std::min(ntiles, h.num_sms);
   SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(L.smem_bytes)));
-  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, L, n, ntiles, scores, h.state);
+  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, L, n, ntiles, cscale,
+                                                        fp8 ? escale + 1 : nullptr, scores, h.state);
   SLSO_CHECK_LAUNCH();
   return SLSO_OK;
 }

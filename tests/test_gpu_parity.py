@@ -236,3 +236,39 @@ def test_bf16_correction_pass_rescores_top_rows_in_float32():
     assert overlap >= 0.99
     rest = O.order_dec(g)[n // 10:]
     assert np.median(np.abs(g[rest] - want[rest]) / want[rest]) < 0.01  # untouched rows keep BF16 scores
+
+
+@pytest.mark.parametrize("xdtype", [torch.float32, torch.bfloat16])
+def test_fp8_scores_with_column_scaling_close_to_oracle(xdtype):
+    """FP8 e4m3 tensor-core path with per-column X scales folded into M."""
+    n = 12000
+    X = inputs.snr_student_t(n, 384, rank=64, seed=17, dtype=xdtype)
+    X[:, 5] *= 1000.0  # a column on another scale: per-column scaling keeps it representable
+    want, _ = O.sketched_leverage(_np(X), "countsketch", 2048, 128, 8, 9)
+    sc, _ = api.leverage(_dev(X), "countsketch", 2048, 128, 8, 9, compute="fp8")
+    rel = np.abs(sc.cpu().numpy().astype(np.float64) - want) / want
+    assert np.median(rel) < 0.03
+    sc, _ = api.leverage(_dev(X), "countsketch", 2048, 128, 8, 9, compute="fp8", correct_frac=0.02)
+    g = sc.cpu().numpy().astype(np.float64)
+    top = O.order_dec(g)[: n // 100]
+    assert np.max(np.abs(g[top] - want[top]) / want[top]) < 1e-4
+    assert len(set(top.tolist()) & set(O.order_dec(want)[: n // 100].tolist())) >= 0.97 * (n // 100)
+
+
+def test_large_bf16_matrix_precision_ladder():
+    """Outlier-subspace bf16 matrix (reduced n): FP32, BF16 and FP8 score error and top-1% overlap."""
+    n, d, s, k = 60000, 3072, 6144, 256
+    X, _ = inputs.outlier_subspace(n, d, seed=1005)
+    want, oinfo = O.sketched_leverage(_np(X), "countsketch", s, k, 2005, 3005, qr="lapack")
+    top_w = set(O.order_dec(want)[: n // 100].tolist())
+    res = {}
+    for comp in ("f32", "bf16", "fp8"):
+        sc, info = api.leverage(_dev(X), "countsketch", s, k, 2005, 3005, compute=comp)
+        assert info["rank"] == oinfo["rank"] == d
+        g = sc.cpu().numpy().astype(np.float64)
+        rel = np.abs(g - want) / want
+        res[comp] = (np.median(rel), np.max(rel), len(set(O.order_dec(g)[: n // 100].tolist()) & top_w) / (n // 100))
+    print(res)
+    assert res["f32"][1] < 1e-4
+    assert res["bf16"][0] < 0.02
+    assert res["fp8"][0] < 0.05
