@@ -317,6 +317,10 @@ def main():
     ms16, stages16, _, _ = timed("bf16", scores_bf, args.steps)
     scores_bc = torch.empty(n, dtype=torch.float32, device="cuda")
     msbc, stagesbc, _, _ = timed("bf16", scores_bc, args.steps, correct=CORRECT_FRAC)
+    scores_f8 = torch.empty(n, dtype=torch.float32, device="cuda")
+    ms8, stages8, _, _ = timed("fp8", scores_f8, args.steps)
+    scores_f8c = torch.empty(n, dtype=torch.float32, device="cuda")
+    ms8c, stages8c, _, _ = timed("fp8", scores_f8c, args.steps, correct=CORRECT_FRAC)
     _, info = api.leverage(X, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", out=scores, handle=h)
 
     value = world * n / (ms32 / 1e3)
@@ -354,6 +358,11 @@ def main():
         "bf16_corrected": {"value": world * n / (msbc / 1e3), "unit": "rows/s", "ms_per_step": msbc,
                            "correct_frac": CORRECT_FRAC,
                            "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stagesbc.items() if c}},
+        "fp8": {"value": world * n / (ms8 / 1e3), "unit": "rows/s", "ms_per_step": ms8,
+                "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages8.items() if c}},
+        "fp8_corrected": {"value": world * n / (ms8c / 1e3), "unit": "rows/s", "ms_per_step": ms8c,
+                          "correct_frac": CORRECT_FRAC,
+                          "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages8c.items() if c}},
         "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"]},
         "clocks": clk,
         "hbm_floor_ms": (2 * n * d * 4 + n * 12) / (peaks["hbm_gbs"] * 1e6),
@@ -400,7 +409,8 @@ def main():
         want = O.row_scores(Xn, M)
         t_or = time.perf_counter() - t0
         stats = {}
-        for name, got in (("f32", scores), ("bf16", scores_bf), ("bf16_corrected", scores_bc)):
+        for name, got in (("f32", scores), ("bf16", scores_bf), ("bf16_corrected", scores_bc), ("fp8", scores_f8),
+                          ("fp8_corrected", scores_f8c)):
             g = got.cpu().numpy().astype(np.float64)
             pos = want > 0
             rel = np.abs(g[pos] - want[pos]) / want[pos]
