@@ -9,12 +9,18 @@
 //
 // QR layout: SX is transposed to column-major A (column l at A + l*s).  A persistent
 // cooperative grid owns columns round-robin (column l belongs to CTA l % G); reflector j is
-// stored in place as LAPACK does (beta on the diagonal, v below it, tau aside) and announced by
-// a per-column ready flag, the only inter-CTA synchronisation (a bounded wait).
+// stored in place (beta on the diagonal, its vector below it, coefficients aside) and announced
+// by a per-column ready flag, the only inter-CTA synchronisation (a bounded wait).
 //   qr_left_kernel (s <= 16384): left-looking; the owner holds its column in registers, applies
-//     every earlier reflector as it is announced (v staged in shared memory by one bulk copy),
-//     forms its own reflector and stores the column once.  HBM traffic is one read and one write
-//     of SX; the float64 FMA pipe and the per-reflector latency bound it.
+//     every earlier reflector as it is announced (the vector staged in shared memory by one bulk
+//     copy), forms its own reflector and stores the column once.  HBM traffic is one read and one
+//     write of SX; the float64 FMA pipe and the chain of reflectors bound it.  Forming reflector
+//     c sits on that chain (column c+1 waits for it), so it is kept to one pass: the norm is
+//     accumulated while reflector c-1 is applied, and the vector is published unscaled,
+//     u = den * v with den = alpha - beta, beside g = tau/den and 1/den, so that a consumer
+//     applies H = I - tau v v^T as x -= g ((u^T x) / den) u.  Scaling by 1/den in the owner
+//     would put one float64 division (or multiply) per row on the chain; on GB300's float64
+//     pipe that alone cost more than applying a reflector.
 //   qr_kernel (larger s): right-looking; after reflector j is announced each CTA applies it to
 //     its own trailing columns, the owner of column j+1 first so the next reflector follows.
 #include <algorithm>
@@ -140,21 +146,30 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
 }
 
 // Left-looking variant for s <= RPT * 256: CTA c % G owns column c; it loads the column into
-// registers once (RPT rows per thread), applies reflectors 0..c-1 as they are announced, forms
-// reflector c, stores the column once and announces ready[c].  Each reflector's v is brought into
-// shared memory by one cp.async.bulk copy (completion on an mbarrier) and read from there by the
-// dot and update passes.  Every column is read and written exactly once; the float64 work is that
-// of the right-looking loop.  Reflector c needs reflector c-1 applied to column c, so reflectors
-// are announced in increasing order and one bounded wait on ready[j] covers reflector j.
+// registers once (RPT rows per thread, in pairs of adjacent rows so loads and stores are 16
+// bytes), applies reflectors 0..c-1 as they are announced, forms reflector c, stores the column
+// once and announces ready[c].  Every column is read and written exactly once; the float64 work
+// is that of the right-looking loop.  Reflector c needs reflector c-1 applied to column c, so
+// reflectors are announced in increasing order and one bounded wait on ready[j] covers
+// reflector j.
+//
+// Each reflector's vector is brought into shared memory by cp.async.bulk copies in two halves
+// (rows [0, HA) and [HA, lda)), each completing on its own mbarrier.  The dot pass reads half A
+// then half B; the update pass does the same, and as soon as every thread is past half A the
+// next vector's half A is copied in while the update of half B runs, so the copy latency is
+// hidden.  On GB300 the float64 pipe retires about 2 lanes per clock per SM, so redundant float64
+// adds are expensive: reductions add 2 + 5 + 3 values per thread (chains, warp, warps), not the
+// 8-way sum every thread would otherwise repeat.
 constexpr int kQrlThreads = 256;
 constexpr unsigned long long kMbarTimeoutNs = 2000000000ull;
+static_assert(kQrlThreads == 256, "block_sum_fast reduces exactly 8 warp partials");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Bounded wait on an mbarrier phase (2 s of %globaltimer).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase (2 s of %globaltimer); gives up early when *abort is set.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, const volatile int* abort) {
   uint64_t t0;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
   while (true) {
@@ -163,141 +178,252 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     if (ok) return true;
+    if (abort && *abort) return false;
     uint64_t t1;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
     if (t1 - t0 > kMbarTimeoutNs) return false;
   }
 }
 
-// Copy rows [j0, lda) of a column into buf (same offsets); bytes is a multiple of 16 because
-// lda and j0 are even, and both addresses are 16-byte aligned.
-__device__ __forceinline__ void bulk_stage(double* buf, const double* col, int j0, int lda, uint64_t* bar) {
-  const uint32_t bytes = static_cast<uint32_t>(lda - j0) * 8u;
+// Copy rows [lo, hi) of a column into buf (same offsets), completion on bar; an empty range
+// only arrives.  lo and hi are even, so the size is a multiple of 16 bytes and both addresses
+// are 16-byte aligned.
+__device__ __forceinline__ void bulk_stage(double* buf, const double* col, int lo, int hi, uint64_t* bar) {
+  if (hi <= lo) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+    return;
+  }
+  const uint32_t bytes = static_cast<uint32_t>(hi - lo) * 8u;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(buf + j0)),
-      "l"(col + j0), "r"(bytes), "r"(smem_addr(bar))
+          smem_addr(buf + lo)),
+      "l"(col + lo), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
 
-// Block-wide sum with one barrier: warp partials into one of two alternating smem slots.
+// Block-wide sum (256 threads) with one barrier: warp butterflies, warp partials into one of two
+// alternating slots, then a 3-level butterfly over the 8 partials.  Every thread returns the same
+// bits (lane 0's value is broadcast).
 __device__ __forceinline__ double block_sum_fast(double v, double (*slots)[kQrlThreads / 32], int& par) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   double* red = slots[par];
   par ^= 1;
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < kQrlThreads / 32; ++w) t += red[w];
-  return t;
+  double t = lane < kQrlThreads / 32 ? red[lane] : 0.0;
+  t += __shfl_xor_sync(0xFFFFFFFFu, t, 4);
+  t += __shfl_xor_sync(0xFFFFFFFFu, t, 2);
+  t += __shfl_xor_sync(0xFFFFFFFFu, t, 1);
+  return __shfl_sync(0xFFFFFFFFu, t, 0);
 }
 
+// Element of reflector j's vector at row i: u_i (staged) below the head, den at the head.
+__device__ __forceinline__ double refl_elem(double staged, int i, int j, int s, double head) {
+  return (i > j && i < s) ? staged : (i == j ? head : 0.0);
+}
+
+// Dot of the staged vector with pairs [Q0, Q1) of the column: two chains (even, odd rows).
+template <int Q0, int Q1>
+__device__ __forceinline__ void dot_pairs(const double* a, const double* vsm, int t2, int lda, int j, int s,
+                                          double head, double& p0, double& p1) {
+#pragma unroll
+  for (int q = Q0; q < Q1; ++q) {
+    const int i = 2 * kQrlThreads * q + t2;
+    double2 w = make_double2(0.0, 0.0);
+    if (i < lda) w = *reinterpret_cast<const double2*>(vsm + i);
+    p0 = fma(refl_elem(w.x, i, j, s, head), a[2 * q], p0);
+    p1 = fma(refl_elem(w.y, i + 1, j, s, head), a[2 * q + 1], p1);
+  }
+}
+
+// a -= tc * u over pairs [Q0, Q1); with NORM also the squared norm of rows > c (x0, x1) and the
+// element at row c (to *alpha) of the updated column.
+template <int Q0, int Q1, bool NORM>
+__device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2, int lda, int j, int s,
+                                           double head, double tc, int c, double& x0, double& x1,
+                                           double* alpha) {
+#pragma unroll
+  for (int q = Q0; q < Q1; ++q) {
+    const int i = 2 * kQrlThreads * q + t2;
+    double2 w = make_double2(0.0, 0.0);
+    if (i < lda) w = *reinterpret_cast<const double2*>(vsm + i);
+    a[2 * q] = fma(-tc, refl_elem(w.x, i, j, s, head), a[2 * q]);
+    a[2 * q + 1] = fma(-tc, refl_elem(w.y, i + 1, j, s, head), a[2 * q + 1]);
+    if (NORM) {
+      if (i > c && i < s) x0 = fma(a[2 * q], a[2 * q], x0);
+      if (i + 1 > c && i + 1 < s) x1 = fma(a[2 * q + 1], a[2 * q + 1], x1);
+      if (i == c) *alpha = a[2 * q];
+      if (i + 1 == c) *alpha = a[2 * q + 1];
+    }
+  }
+}
+
+// Per-column coefficients of the unscaled reflectors: coef[4c] = g = tau/den (0: H_c = I),
+// coef[4c+1] = 1/den, coef[4c+2] = den (the vector's head element).
 template <int RPT>
 __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restrict__ A, int s, int lda, int d,
                                                                  int* __restrict__ ready,
-                                                                 double* __restrict__ taus,
+                                                                 double* __restrict__ coef,
                                                                  DevState* __restrict__ state) {
+  static_assert(RPT % 2 == 0, "rows are held in pairs");
+  constexpr int P = RPT / 2;                    // row pairs per thread
+  constexpr int QA = P / 2;                     // pairs in staging half A
+  constexpr int HA = 2 * kQrlThreads * QA;      // rows in staging half A
   extern __shared__ __align__(128) double vsm[];  // lda doubles
   __shared__ double slots[2][kQrlThreads / 32];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ double s_alpha;
+  __shared__ double s_coef[3];  // coefficients of the staged reflector (written before arming full[0])
+  __shared__ int s_abort;       // hint only: lets waits give up early once a wait or stage failed
   int par = 0;
   uint32_t phase = 0;
-  const int G = gridDim.x, tid = threadIdx.x;
+  const int G = gridDim.x, tid = threadIdx.x, t2 = 2 * threadIdx.x;
   if (tid == 0) {
     s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[1])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  int known = -1;  // ready[0..known] observed (thread 0)
-  // thread 0: wait until reflector j is announced, then stage its v
-  auto issue = [&](int j) {
+  volatile int* abort_flag = &s_abort;
+  bool bad = false;  // this thread saw a failed wait; decided on by __syncthreads_or
+  // thread 0 only: reflectors observed, copies issued and not yet waited for
+  int known = -1;
+  bool pend[2] = {false, false};
+  uint32_t pend_par[2] = {0u, 0u};
+  // thread 0: stage half h of reflector j's vector (consumers wait on parity `par_next`)
+  auto stage = [&](int j, int h, uint32_t par_next) {
+    if (*abort_flag) return;
     if (j > known) {
       if (!wait_flag_geq(ready + j, 1, kWaitPolls)) {
-        atomicExch(&state->timeout, 1);
-        s_abort = 1;
+        bad = true;
+        *abort_flag = 1;
         return;
       }
       __threadfence();
+      asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk-copy reads
       known = j;
     }
-    bulk_stage(vsm, A + static_cast<int64_t>(j) * lda, j & ~1, lda, &bar);
+    if (h == 0) {
+      s_coef[0] = __ldcg(coef + 4 * j);
+      s_coef[1] = __ldcg(coef + 4 * j + 1);
+      s_coef[2] = __ldcg(coef + 4 * j + 2);
+    }
+    const int j0 = j & ~1;
+    const double* src = A + static_cast<int64_t>(j) * lda;
+    if (h == 0) bulk_stage(vsm, src, j0, HA < lda ? HA : lda, &full[0]);
+    else bulk_stage(vsm, src, j0 > HA ? j0 : HA, lda, &full[1]);
+    pend[h] = true;
+    pend_par[h] = par_next;
+  };
+  // thread 0 on abort: let issued copies land before the CTA exits
+  auto drain = [&]() {
+    for (int h = 0; h < 2; ++h)
+      if (pend[h]) mbar_wait_bounded(&full[h], pend_par[h], nullptr);
   };
   for (int c = blockIdx.x; c < d; c += G) {
     double* col = A + static_cast<int64_t>(c) * lda;
     double a[RPT];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int i = tid + r * kQrlThreads;
-      a[r] = (i < s) ? col[i] : 0.0;
+    for (int q = 0; q < P; ++q) {
+      const int i = 2 * kQrlThreads * q + t2;
+      double2 v = make_double2(0.0, 0.0);
+      if (i < lda) v = __ldcg(reinterpret_cast<const double2*>(col + i));
+      a[2 * q] = i < s ? v.x : 0.0;
+      a[2 * q + 1] = i + 1 < s ? v.y : 0.0;
     }
-    if (c > 0 && tid == 0) issue(0);
+    double x0 = 0.0, x1 = 0.0;  // squared norm of rows > c, accumulated with the last update
+    bool fused = false;
+    if (c > 0 && tid == 0) {
+      stage(0, 0, phase);
+      stage(0, 1, phase);
+    }
     for (int j = 0; j < c; ++j) {
-      const bool landed = s_abort ? false : mbar_wait_bounded(&bar, phase);
-      phase ^= 1;
-      if (!landed) {
-        if (tid == 0) atomicExch(&state->timeout, 1);
-        s_abort = 1;
+      if (mbar_wait_bounded(&full[0], phase, abort_flag)) {
+        if (tid == 0) pend[0] = false;
+      } else {
+        bad = true;
+        *abort_flag = 1;
       }
-      __syncthreads();
-      if (s_abort) return;
-      const double tau = __ldcg(taus + j);
-      if (tau != 0.0) {
-        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          const int i = tid + r * kQrlThreads;
-          const double w = (i > j && i < s) ? vsm[i] : (i == j ? 1.0 : 0.0);
-          if ((r & 3) == 0) p0 = fma(w, a[r], p0);
-          else if ((r & 3) == 1) p1 = fma(w, a[r], p1);
-          else if ((r & 3) == 2) p2 = fma(w, a[r], p2);
-          else p3 = fma(w, a[r], p3);
-        }
-        const double tc = tau * block_sum_fast((p0 + p1) + (p2 + p3), slots, par);
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          const int i = tid + r * kQrlThreads;
-          const double w = (i > j && i < s) ? vsm[i] : (i == j ? 1.0 : 0.0);
-          a[r] = fma(-tc, w, a[r]);
-        }
+      // the same bits in every thread: written once by thread 0 before it armed full[0]
+      const double g = s_coef[0], inv = s_coef[1], head = s_coef[2];
+      double p0 = 0.0, p1 = 0.0, tc = 0.0;
+      if (g != 0.0) dot_pairs<0, QA>(a, vsm, t2, lda, j, s, head, p0, p1);
+      if (mbar_wait_bounded(&full[1], phase, abort_flag)) {
+        if (tid == 0) pend[1] = false;
+      } else {
+        bad = true;
+        *abort_flag = 1;
       }
-      __syncthreads();  // everyone is done with the staged v
-      if (tid == 0 && j + 1 < c) issue(j + 1);
+      const bool last = (j + 1 == c) && g != 0.0;
+      if (g != 0.0) {
+        dot_pairs<QA, P>(a, vsm, t2, lda, j, s, head, p0, p1);
+        tc = g * (block_sum_fast(p0 + p1, slots, par) * inv);
+        if (last) axpy_pairs<0, QA, true>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
+        else axpy_pairs<0, QA, false>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
+      }
+      // half A of this vector is consumed; any failed wait or stage so far ends the kernel
+      if (__syncthreads_or(bad)) {
+        if (tid == 0) {
+          atomicExch(&state->timeout, 1);
+          drain();
+        }
+        return;
+      }
+      if (tid == 0 && j + 1 < c) stage(j + 1, 0, phase ^ 1u);
+      if (g != 0.0) {
+        if (last) axpy_pairs<QA, P, true>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
+        else axpy_pairs<QA, P, false>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
+      }
+      __syncthreads();  // half B consumed
+      if (tid == 0 && j + 1 < c) stage(j + 1, 1, phase ^ 1u);
+      phase ^= 1u;
+      fused = last;
     }
-    // reflector c from rows >= c of the updated column
-    double alpha_part = 0.0, x2 = 0.0;
+    if (!fused) {
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int i = tid + r * kQrlThreads;
-      if (i > c && i < s) x2 = fma(a[r], a[r], x2);
-      if (i == c) alpha_part = a[r];
+      for (int q = 0; q < P; ++q) {
+        const int i = 2 * kQrlThreads * q + t2;
+        if (i > c && i < s) x0 = fma(a[2 * q], a[2 * q], x0);
+        if (i + 1 > c && i + 1 < s) x1 = fma(a[2 * q + 1], a[2 * q + 1], x1);
+        if (i == c) s_alpha = a[2 * q];
+        if (i + 1 == c) s_alpha = a[2 * q + 1];
+      }
     }
-    const double xn2 = block_sum_fast(x2, slots, par);
-    const double alpha = block_sum_fast(alpha_part, slots, par);
-    double tau = 0.0;
+    // reflector c: beta = -sign(alpha) ||(alpha, x)||, tau = (beta - alpha) / beta; no
+    // reflection when the subcolumn below the diagonal is exactly zero.  s_alpha was written
+    // before the reduction's barrier by the thread holding row c.
+    const double xn2 = block_sum_fast(x0 + x1, slots, par);
+    const double alpha = s_alpha;
+    double g = 0.0, inv = 0.0, den = 0.0;
     if (xn2 != 0.0) {
       const double norm = sqrt(alpha * alpha + xn2);
       const double beta = alpha >= 0.0 ? -norm : norm;
-      tau = (beta - alpha) / beta;
-      const double den = alpha - beta;
+      const double tau = (beta - alpha) / beta;
+      den = alpha - beta;
+      inv = 1.0 / den;
+      g = tau * inv;
 #pragma unroll
-      for (int r = 0; r < RPT; ++r) {
-        const int i = tid + r * kQrlThreads;
-        if (i > c && i < s) a[r] = a[r] / den;
-        if (i == c) a[r] = beta;
+      for (int q = 0; q < P; ++q) {
+        const int i = 2 * kQrlThreads * q + t2;
+        if (i == c) a[2 * q] = beta;
+        if (i + 1 == c) a[2 * q + 1] = beta;
       }
     }
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int i = tid + r * kQrlThreads;
-      if (i < s) col[i] = a[r];
+    for (int q = 0; q < P; ++q) {
+      const int i = 2 * kQrlThreads * q + t2;
+      if (i < lda) *reinterpret_cast<double2*>(col + i) = make_double2(a[2 * q], a[2 * q + 1]);
     }
-    if (tid == 0) taus[c] = tau;
+    if (tid == 0) {
+      coef[4 * c] = g;
+      coef[4 * c + 1] = inv;
+      coef[4 * c + 2] = den;
+    }
     __threadfence();
     __syncthreads();
     if (tid == 0) atomicExch(&ready[c], 1);
@@ -650,7 +776,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   const int64_t lda = s + (s & 1);  // even: 16-byte aligned columns for the bulk copies
   double* A = ar.take<double>(static_cast<size_t>(lda) * d);
   int* ready = ar.take<int>(d);
-  double* taus = ar.take<double>(d);
+  double* taus = ar.take<double>(4 * d);  // qr_kernel: tau per column; qr_left_kernel: 4 coefficients
   double* R = ar.take<double>(static_cast<size_t>(d) * d);
   double* sgn = ar.take<double>(d);
   double* fro2 = ar.take<double>(2 * kSumBlocks);
@@ -683,8 +809,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     void* fn = nullptr;
     size_t smem = sizeof(double) * lda;
     int threads = kQrlThreads;
-    if (s <= 256) fn = reinterpret_cast<void*>(qr_left_kernel<1>);
-    else if (s <= 512) fn = reinterpret_cast<void*>(qr_left_kernel<2>);
+    if (s <= 512) fn = reinterpret_cast<void*>(qr_left_kernel<2>);
     else if (s <= 1024) fn = reinterpret_cast<void*>(qr_left_kernel<4>);
     else if (s <= 2048) fn = reinterpret_cast<void*>(qr_left_kernel<8>);
     else if (s <= 4096) fn = reinterpret_cast<void*>(qr_left_kernel<16>);
