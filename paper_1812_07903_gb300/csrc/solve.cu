@@ -153,16 +153,24 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
 // reflectors are announced in increasing order and one bounded wait on ready[j] covers
 // reflector j.
 //
-// Each reflector's vector is brought into shared memory by cp.async.bulk copies in two halves
-// (rows [0, HA) and [HA, lda)), each completing on its own mbarrier.  The dot pass reads half A
-// then half B; the update pass does the same, and as soon as every thread is past half A the
-// next vector's half A is copied in while the update of half B runs, so the copy latency is
-// hidden.  On GB300 the float64 pipe retires about 2 lanes per clock per SM, so redundant float64
-// adds are expensive: reductions add 2 + 5 + 3 values per thread (chains, warp, warps), not the
-// 8-way sum every thread would otherwise repeat.
+// Storage: R's column c (rows 0..c) goes to Rc (column-major, leading dimension d); column c of
+// A becomes reflector c's unscaled vector over all rows: zeros above row c, den = alpha - beta at
+// row c, the subcolumn below (and zero padding rows).  A consumer therefore stages the whole
+// column and uses it as is: the dot and update passes have no per-row conditions.
+//
+// Staging: the vector is copied by cp.async.bulk in two fixed halves (rows [0, HA) and [HA, lda))
+// completing on full[0], full[1].  After its update pass over a half each warp arrives on that
+// half's empty barrier; thread 0 waits for all 8 warps there before copying the next vector into
+// it, so the copy of half A overlaps the update of half B and no CTA-wide barrier is needed.
+//
+// Reductions: on GB300 every float64 warp instruction costs the SM the same ~19 clocks however
+// many lanes are active, and a dependent chain of them is latency-bound while the other warps
+// wait.  Each reduction therefore writes the 256 per-thread partials to shared memory and lets
+// warp 0 alone sum them (8 values per lane, then a 5-level butterfly) and form the scalar.
 constexpr int kQrlThreads = 256;
+constexpr int64_t kQrlMaxS = 16384;  // s up to this uses qr_left_kernel (64 rows per thread)
+constexpr int kQrlWarps = kQrlThreads / 32;
 constexpr unsigned long long kMbarTimeoutNs = 2000000000ull;
-static_assert(kQrlThreads == 256, "block_sum_fast reduces exactly 8 warp partials");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -185,12 +193,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Copy rows [lo, hi) of a column into buf (same offsets), completion on bar; an empty range
 // only arrives.  lo and hi are even, so the size is a multiple of 16 bytes and both addresses
 // are 16-byte aligned.
 __device__ __forceinline__ void bulk_stage(double* buf, const double* col, int lo, int hi, uint64_t* bar) {
   if (hi <= lo) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+    mbar_arrive(bar);
     return;
   }
   const uint32_t bytes = static_cast<uint32_t>(hi - lo) * 8u;
@@ -203,56 +215,41 @@ __device__ __forceinline__ void bulk_stage(double* buf, const double* col, int l
       : "memory");
 }
 
-// Block-wide sum (256 threads) with one barrier: warp butterflies, warp partials into one of two
-// alternating slots, then a 3-level butterfly over the 8 partials.  Every thread returns the same
-// bits (lane 0's value is broadcast).
-__device__ __forceinline__ double block_sum_fast(double v, double (*slots)[kQrlThreads / 32], int& par) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  double* red = slots[par];
-  par ^= 1;
+// Sum of the 256 values in red (warp 0 only; every lane returns the same bits): lane l adds
+// red[l + 32 m] for m = 0..7 in a fixed tree, then a 5-level butterfly.
+__device__ __forceinline__ double warp0_sum256(const double* red) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = lane < kQrlThreads / 32 ? red[lane] : 0.0;
-  t += __shfl_xor_sync(0xFFFFFFFFu, t, 4);
-  t += __shfl_xor_sync(0xFFFFFFFFu, t, 2);
-  t += __shfl_xor_sync(0xFFFFFFFFu, t, 1);
-  return __shfl_sync(0xFFFFFFFFu, t, 0);
-}
-
-// Element of reflector j's vector at row i: u_i (staged) below the head, den at the head.
-__device__ __forceinline__ double refl_elem(double staged, int i, int j, int s, double head) {
-  return (i > j && i < s) ? staged : (i == j ? head : 0.0);
+  double v[kQrlWarps];
+#pragma unroll
+  for (int m = 0; m < kQrlWarps; ++m) v[m] = red[lane + 32 * m];
+  double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+  return t;
 }
 
 // Dot of the staged vector with pairs [Q0, Q1) of the column: two chains (even, odd rows).
 template <int Q0, int Q1>
-__device__ __forceinline__ void dot_pairs(const double* a, const double* vsm, int t2, int lda, int j, int s,
-                                          double head, double& p0, double& p1) {
+__device__ __forceinline__ void dot_pairs(const double* a, const double* vsm, int t2, double& p0, double& p1) {
 #pragma unroll
   for (int q = Q0; q < Q1; ++q) {
-    const int i = 2 * kQrlThreads * q + t2;
-    double2 w = make_double2(0.0, 0.0);
-    if (i < lda) w = *reinterpret_cast<const double2*>(vsm + i);
-    p0 = fma(refl_elem(w.x, i, j, s, head), a[2 * q], p0);
-    p1 = fma(refl_elem(w.y, i + 1, j, s, head), a[2 * q + 1], p1);
+    const double2 w = *reinterpret_cast<const double2*>(vsm + 2 * kQrlThreads * q + t2);
+    p0 = fma(w.x, a[2 * q], p0);
+    p1 = fma(w.y, a[2 * q + 1], p1);
   }
 }
 
 // a -= tc * u over pairs [Q0, Q1); with NORM also the squared norm of rows > c (x0, x1) and the
 // element at row c (to *alpha) of the updated column.
 template <int Q0, int Q1, bool NORM>
-__device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2, int lda, int j, int s,
-                                           double head, double tc, int c, double& x0, double& x1,
-                                           double* alpha) {
+__device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2, double tc, int c, int s,
+                                           double& x0, double& x1, double* alpha) {
 #pragma unroll
   for (int q = Q0; q < Q1; ++q) {
     const int i = 2 * kQrlThreads * q + t2;
-    double2 w = make_double2(0.0, 0.0);
-    if (i < lda) w = *reinterpret_cast<const double2*>(vsm + i);
-    a[2 * q] = fma(-tc, refl_elem(w.x, i, j, s, head), a[2 * q]);
-    a[2 * q + 1] = fma(-tc, refl_elem(w.y, i + 1, j, s, head), a[2 * q + 1]);
+    const double2 w = *reinterpret_cast<const double2*>(vsm + i);
+    a[2 * q] = fma(-tc, w.x, a[2 * q]);
+    a[2 * q + 1] = fma(-tc, w.y, a[2 * q + 1]);
     if (NORM) {
       if (i > c && i < s) x0 = fma(a[2 * q], a[2 * q], x0);
       if (i + 1 > c && i + 1 < s) x1 = fma(a[2 * q + 1], a[2 * q + 1], x1);
@@ -263,9 +260,10 @@ __device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2,
 }
 
 // Per-column coefficients of the unscaled reflectors: coef[4c] = g = tau/den (0: H_c = I),
-// coef[4c+1] = 1/den, coef[4c+2] = den (the vector's head element).
+// coef[4c+1] = 1/den.  Dynamic shared memory: 2 * kQrlThreads * (RPT/2) doubles.
 template <int RPT>
 __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restrict__ A, int s, int lda, int d,
+                                                                 double* __restrict__ Rc,
                                                                  int* __restrict__ ready,
                                                                  double* __restrict__ coef,
                                                                  DevState* __restrict__ state) {
@@ -273,57 +271,67 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
   constexpr int P = RPT / 2;                    // row pairs per thread
   constexpr int QA = P / 2;                     // pairs in staging half A
   constexpr int HA = 2 * kQrlThreads * QA;      // rows in staging half A
-  extern __shared__ __align__(128) double vsm[];  // lda doubles
-  __shared__ double slots[2][kQrlThreads / 32];
+  constexpr int VROWS = 2 * kQrlThreads * P;    // rows of the staging buffer (>= lda)
+  extern __shared__ __align__(128) double vsm[];
+  __shared__ double red[kQrlThreads];
   __shared__ __align__(8) uint64_t full[2];
+  __shared__ __align__(8) uint64_t empty[2];
   __shared__ double s_alpha;
-  __shared__ double s_coef[3];  // coefficients of the staged reflector (written before arming full[0])
+  __shared__ double s_coef[2];  // g, 1/den of the staged reflector (written before arming full[0])
+  __shared__ double s_scalar;   // warp 0's result of a reduction
   __shared__ int s_abort;       // hint only: lets waits give up early once a wait or stage failed
-  int par = 0;
-  uint32_t phase = 0;
-  const int G = gridDim.x, tid = threadIdx.x, t2 = 2 * threadIdx.x;
+  const int G = gridDim.x, tid = threadIdx.x, t2 = 2 * threadIdx.x, lane = threadIdx.x & 31;
+  for (int i = lda + tid; i < VROWS; i += kQrlThreads) vsm[i] = 0.0;  // never written by a copy
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[0])), "r"(kQrlWarps));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[1])), "r"(kQrlWarps));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   volatile int* abort_flag = &s_abort;
-  bool bad = false;  // this thread saw a failed wait; decided on by __syncthreads_or
-  // thread 0 only: reflectors observed, copies issued and not yet waited for
-  int known = -1;
-  bool pend[2] = {false, false};
-  uint32_t pend_par[2] = {0u, 0u};
-  // thread 0: stage half h of reflector j's vector (consumers wait on parity `par_next`)
-  auto stage = [&](int j, int h, uint32_t par_next) {
+  bool bad = false;   // this thread saw a failed wait; decided on by __syncthreads_or
+  uint32_t nvec = 0;  // vectors consumed so far by this CTA (phase of full/empty barriers)
+  // thread 0 only
+  int known = -1;        // ready[0..known] observed
+  uint32_t staged = 0;   // vectors staged so far (both halves issued)
+  uint32_t issued[2] = {0u, 0u};  // copies issued per half
+  // thread 0: stage reflector j's vector as vector number `staged` (both halves, each after
+  // every warp released the previous vector's half)
+  auto stage_half = [&](int j, int h) {
     if (*abort_flag) return;
-    if (j > known) {
-      if (!wait_flag_geq(ready + j, 1, kWaitPolls)) {
-        bad = true;
-        *abort_flag = 1;
-        return;
-      }
-      __threadfence();
-      asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk-copy reads
-      known = j;
+    if (staged > 0 && !mbar_wait_bounded(&empty[h], (staged - 1) & 1u, abort_flag)) {
+      bad = true;
+      *abort_flag = 1;
+      return;
     }
     if (h == 0) {
+      if (j > known) {
+        if (!wait_flag_geq(ready + j, 1, kWaitPolls)) {
+          bad = true;
+          *abort_flag = 1;
+          return;
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk-copy reads
+        known = j;
+      }
       s_coef[0] = __ldcg(coef + 4 * j);
       s_coef[1] = __ldcg(coef + 4 * j + 1);
-      s_coef[2] = __ldcg(coef + 4 * j + 2);
     }
-    const int j0 = j & ~1;
     const double* src = A + static_cast<int64_t>(j) * lda;
-    if (h == 0) bulk_stage(vsm, src, j0, HA < lda ? HA : lda, &full[0]);
-    else bulk_stage(vsm, src, j0 > HA ? j0 : HA, lda, &full[1]);
-    pend[h] = true;
-    pend_par[h] = par_next;
+    if (h == 0) bulk_stage(vsm, src, 0, HA, &full[0]);
+    else bulk_stage(vsm, src, HA, lda, &full[1]);
+    ++issued[h];
+    if (h == 1) ++staged;
   };
-  // thread 0 on abort: let issued copies land before the CTA exits
+  // thread 0 on abort: let every issued copy land before the CTA exits (at most one per half
+  // is ahead of the consumers)
   auto drain = [&]() {
     for (int h = 0; h < 2; ++h)
-      if (pend[h]) mbar_wait_bounded(&full[h], pend_par[h], nullptr);
+      if (issued[h] > nvec) mbar_wait_bounded(&full[h], nvec & 1u, nullptr);
   };
   for (int c = blockIdx.x; c < d; c += G) {
     double* col = A + static_cast<int64_t>(c) * lda;
@@ -339,34 +347,28 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
     double x0 = 0.0, x1 = 0.0;  // squared norm of rows > c, accumulated with the last update
     bool fused = false;
     if (c > 0 && tid == 0) {
-      stage(0, 0, phase);
-      stage(0, 1, phase);
+      stage_half(0, 0);
+      stage_half(0, 1);
     }
     for (int j = 0; j < c; ++j) {
-      if (mbar_wait_bounded(&full[0], phase, abort_flag)) {
-        if (tid == 0) pend[0] = false;
-      } else {
+      const uint32_t par = nvec & 1u;
+      if (!mbar_wait_bounded(&full[0], par, abort_flag)) {
         bad = true;
         *abort_flag = 1;
       }
       // the same bits in every thread: written once by thread 0 before it armed full[0]
-      const double g = s_coef[0], inv = s_coef[1], head = s_coef[2];
-      double p0 = 0.0, p1 = 0.0, tc = 0.0;
-      if (g != 0.0) dot_pairs<0, QA>(a, vsm, t2, lda, j, s, head, p0, p1);
-      if (mbar_wait_bounded(&full[1], phase, abort_flag)) {
-        if (tid == 0) pend[1] = false;
-      } else {
+      const double g = s_coef[0], inv = s_coef[1];
+      double p0 = 0.0, p1 = 0.0;
+      if (g != 0.0) dot_pairs<0, QA>(a, vsm, t2, p0, p1);
+      if (!mbar_wait_bounded(&full[1], par, abort_flag)) {
         bad = true;
         *abort_flag = 1;
       }
-      const bool last = (j + 1 == c) && g != 0.0;
       if (g != 0.0) {
-        dot_pairs<QA, P>(a, vsm, t2, lda, j, s, head, p0, p1);
-        tc = g * (block_sum_fast(p0 + p1, slots, par) * inv);
-        if (last) axpy_pairs<0, QA, true>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
-        else axpy_pairs<0, QA, false>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
+        dot_pairs<QA, P>(a, vsm, t2, p0, p1);
+        red[tid] = p0 + p1;
       }
-      // half A of this vector is consumed; any failed wait or stage so far ends the kernel
+      // any failed wait or stage so far ends the kernel (uniformly)
       if (__syncthreads_or(bad)) {
         if (tid == 0) {
           atomicExch(&state->timeout, 1);
@@ -374,14 +376,33 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
         }
         return;
       }
-      if (tid == 0 && j + 1 < c) stage(j + 1, 0, phase ^ 1u);
+      const bool last = (j + 1 == c) && g != 0.0;
       if (g != 0.0) {
-        if (last) axpy_pairs<QA, P, true>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
-        else axpy_pairs<QA, P, false>(a, vsm, t2, lda, j, s, head, tc, c, x0, x1, &s_alpha);
+        if (tid < 32) {
+          const double sum = warp0_sum256(red);
+          if (lane == 0) s_scalar = g * (sum * inv);
+        }
+        __syncthreads();
+        const double tc = s_scalar;
+        if (last) axpy_pairs<0, QA, true>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        else axpy_pairs<0, QA, false>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[0]);
+        if (tid == 0 && j + 1 < c) stage_half(j + 1, 0);
+        if (last) axpy_pairs<QA, P, true>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        else axpy_pairs<QA, P, false>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[1]);
+      } else {
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&empty[0]);
+          mbar_arrive(&empty[1]);
+        }
+        if (tid == 0 && j + 1 < c) stage_half(j + 1, 0);
       }
-      __syncthreads();  // half B consumed
-      if (tid == 0 && j + 1 < c) stage(j + 1, 1, phase ^ 1u);
-      phase ^= 1u;
+      if (tid == 0 && j + 1 < c) stage_half(j + 1, 1);
+      ++nvec;
       fused = last;
     }
     if (!fused) {
@@ -395,11 +416,16 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       }
     }
     // reflector c: beta = -sign(alpha) ||(alpha, x)||, tau = (beta - alpha) / beta; no
-    // reflection when the subcolumn below the diagonal is exactly zero.  s_alpha was written
-    // before the reduction's barrier by the thread holding row c.
-    const double xn2 = block_sum_fast(x0 + x1, slots, par);
-    const double alpha = s_alpha;
-    double g = 0.0, inv = 0.0, den = 0.0;
+    // reflection when the subcolumn below the diagonal is exactly zero
+    red[tid] = x0 + x1;
+    __syncthreads();
+    if (tid < 32) {
+      const double xn2 = warp0_sum256(red);
+      if (lane == 0) s_scalar = xn2;
+    }
+    __syncthreads();
+    const double xn2 = s_scalar, alpha = s_alpha;
+    double g = 0.0, inv = 0.0, den = 0.0, rcc = alpha;
     if (xn2 != 0.0) {
       const double norm = sqrt(alpha * alpha + xn2);
       const double beta = alpha >= 0.0 ? -norm : norm;
@@ -407,22 +433,24 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       den = alpha - beta;
       inv = 1.0 / den;
       g = tau * inv;
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int i = 2 * kQrlThreads * q + t2;
-        if (i == c) a[2 * q] = beta;
-        if (i + 1 == c) a[2 * q + 1] = beta;
-      }
+      rcc = beta;
     }
+    double* rcol = Rc + static_cast<int64_t>(c) * d;
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int i = 2 * kQrlThreads * q + t2;
-      if (i < lda) *reinterpret_cast<double2*>(col + i) = make_double2(a[2 * q], a[2 * q + 1]);
+      if (i < lda) {
+        double2 v;
+        v.x = (i < c) ? 0.0 : (i == c ? den : a[2 * q]);
+        v.y = (i + 1 < c) ? 0.0 : (i + 1 == c ? den : a[2 * q + 1]);
+        *reinterpret_cast<double2*>(col + i) = v;
+        if (i <= c) rcol[i] = (i == c) ? rcc : a[2 * q];
+        if (i + 1 <= c) rcol[i + 1] = (i + 1 == c) ? rcc : a[2 * q + 1];
+      }
     }
     if (tid == 0) {
       coef[4 * c] = g;
       coef[4 * c + 1] = inv;
-      coef[4 * c + 2] = den;
     }
     __threadfence();
     __syncthreads();
@@ -777,6 +805,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* A = ar.take<double>(static_cast<size_t>(lda) * d);
   int* ready = ar.take<int>(d);
   double* taus = ar.take<double>(4 * d);  // qr_kernel: tau per column; qr_left_kernel: 4 coefficients
+  double* Rc = ar.take<double>(static_cast<size_t>(d) * d);  // qr_left_kernel: R column-major
   double* R = ar.take<double>(static_cast<size_t>(d) * d);
   double* sgn = ar.take<double>(d);
   double* fro2 = ar.take<double>(2 * kSumBlocks);
@@ -807,15 +836,25 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   {
     // left-looking register-resident kernel when a column fits in registers, else right-looking
     void* fn = nullptr;
-    size_t smem = sizeof(double) * lda;
     int threads = kQrlThreads;
-    if (s <= 512) fn = reinterpret_cast<void*>(qr_left_kernel<2>);
-    else if (s <= 1024) fn = reinterpret_cast<void*>(qr_left_kernel<4>);
-    else if (s <= 2048) fn = reinterpret_cast<void*>(qr_left_kernel<8>);
-    else if (s <= 4096) fn = reinterpret_cast<void*>(qr_left_kernel<16>);
-    else if (s <= 8192) fn = reinterpret_cast<void*>(qr_left_kernel<32>);
-    else if (s <= 16384) fn = reinterpret_cast<void*>(qr_left_kernel<64>);
-    else {
+    int rpt = 0;  // rows per thread of the left-looking kernel (0: right-looking)
+    if (s <= 512) rpt = 2;
+    else if (s <= 1024) rpt = 4;
+    else if (s <= 2048) rpt = 8;
+    else if (s <= 4096) rpt = 16;
+    else if (s <= 8192) rpt = 32;
+    else if (s <= kQrlMaxS) rpt = 64;
+    switch (rpt) {
+      case 2: fn = reinterpret_cast<void*>(qr_left_kernel<2>); break;
+      case 4: fn = reinterpret_cast<void*>(qr_left_kernel<4>); break;
+      case 8: fn = reinterpret_cast<void*>(qr_left_kernel<8>); break;
+      case 16: fn = reinterpret_cast<void*>(qr_left_kernel<16>); break;
+      case 32: fn = reinterpret_cast<void*>(qr_left_kernel<32>); break;
+      case 64: fn = reinterpret_cast<void*>(qr_left_kernel<64>); break;
+      default: break;
+    }
+    size_t smem = sizeof(double) * kQrlThreads * rpt;  // staging buffer of the left-looking kernel
+    if (rpt == 0) {
       const bool vsm = s <= 24576;
       smem = vsm ? sizeof(double) * s : 0;
       fn = vsm ? reinterpret_cast<void*>(qr_kernel<true>) : reinterpret_cast<void*>(qr_kernel<false>);
@@ -827,22 +866,27 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     if (occ < 1) return fail(SLSO_ERR_CUDA, "QR kernel cannot be resident (smem %zu)", smem);
     int G = static_cast<int>(std::min<int64_t>(h.num_sms, d));
     int s_i = static_cast<int>(s), lda_i = static_cast<int>(lda), d_i = static_cast<int>(d);
-    void* args[] = {&A, &s_i, &lda_i, &d_i, &ready, &taus, &h.state};
+    void* args_left[] = {&A, &s_i, &lda_i, &d_i, &Rc, &ready, &taus, &h.state};
+    void* args_right[] = {&A, &s_i, &lda_i, &d_i, &ready, &taus, &h.state};
     prof_end(h, ar, st);
     prof_begin(h, ar, ST_QR, st);
-    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, st));
+    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), rpt ? args_left : args_right, smem, st));
     note_launch();
     prof_end(h, ar, st);
     prof_begin(h, ar, ST_SOLVE, st);
   }
-  r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(A, lda, d, R, sgn);
+  // the upper triangle of R: Rc (leading dimension d) from the left-looking kernel, else in A
+  const bool left = s <= kQrlMaxS;
+  const double* Rsrc = left ? Rc : A;
+  const int64_t ldr = left ? d : lda;
+  r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Rsrc, ldr, d, R, sgn);
   SLSO_CHECK_LAUNCH();
   sumsq_partial_kernel<<<kSumBlocks, 256, 0, st>>>(R, d * d, fro2);
   SLSO_CHECK_LAUNCH();
 
   // ---- certified route: R^-1
   if (mode == 0) {
-    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(A, lda, d, sgn, Rinv);
+    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rsrc, ldr, d, sgn, Rinv);
     SLSO_CHECK_LAUNCH();
     sumsq_partial_kernel<<<kSumBlocks, 256, 0, st>>>(Rinv, d * d, fro2 + kSumBlocks);
     SLSO_CHECK_LAUNCH();
