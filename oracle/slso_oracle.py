@@ -168,14 +168,24 @@ def srht_sample(n_pad, s, seed):
 def gaussian_block(rows, cols, seed):
     """Entries G[rows, cols] of the s x n Gaussian sketch matrix, before the 1/sqrt(s) scale.
 
-    G_ji = bf16(N(0,1)) with the normal from Philox at counter (lo(i), hi(i), j, 4).
+    G_ji = bf16(N(0,1)).  Four consecutive columns share one Philox block: the block of
+    column i is b = i // 4 with counter (lo(b), hi(b), j, 4), and its words (w0, w1, w2, w3)
+    give the two independent normals of a Box-Muller pair each,
+      i % 4 = 0: rho(w0) cos(2 pi w1 2^-32)      i % 4 = 1: rho(w0) sin(2 pi w1 2^-32)
+      i % 4 = 2: rho(w2) cos(2 pi w3 2^-32)      i % 4 = 3: rho(w2) sin(2 pi w3 2^-32)
+    with sin(2 pi w 2^-32) = cos(2 pi (w - 2^30) 2^-32) evaluated by ``box_muller`` on the
+    shifted word (exact modulo 2^32).
     """
     rows = np.asarray(rows, dtype=np.uint64)
     cols = np.asarray(cols, dtype=np.uint64)
     J, I = np.meshgrid(rows, cols, indexing="ij")
-    lo, hi = _split64(I)
+    lo, hi = _split64(I >> np.uint64(2))
     w = philox4x32_10(lo, hi, J, TAG_GAUSSIAN, seed)
-    return bf16_round(box_muller(w[0], w[1]))
+    r = I & np.uint64(3)
+    wa = np.where(r < 2, w[0], w[2])
+    wb = np.where(r < 2, w[1], w[3])
+    wb = np.where((r & np.uint64(1)) == 1, (wb - np.uint64(1 << 30)) & _MASK32, wb)
+    return bf16_round(box_muller(wa, wb))
 
 
 def jl_matrix(d, k, seed):

@@ -112,6 +112,56 @@ def test_gaussian_entries_are_bf16_normal():
     assert abs(np.corrcoef(G[0], G[1])[0, 1]) < 0.05
 
 
+def test_gaussian_four_entries_per_philox_block():
+    """Columns 4b..4b+3 of row j come from one Philox block (lo b, hi b, j, 4): entries 4b, 4b+1
+    are rho(w0) cos, rho(w0) sin of the angle 2 pi w1 2^-32 (so their squares sum to
+    -2 ln((w0+1) 2^-32)), entries 4b+2, 4b+3 likewise from (w2, w3).  Checked against
+    high-precision values computed from the Philox words alone."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    rows = np.array([0, 5, 77])
+    cols = np.arange(4 * 6) + 4 * (2**32 + 3)  # blocks whose index has a nonzero high word
+    G = O.gaussian_block(rows, cols, 1234)
+    for a, j in enumerate(rows):
+        for b in range(6):
+            blk = int(cols[4 * b]) // 4
+            w = O.philox4x32_10(np.uint64(blk & 0xFFFFFFFF), np.uint64(blk >> 32), np.uint64(j),
+                                O.TAG_GAUSSIAN, 1234)
+            w = [int(x) for x in w]
+            for pair in range(2):
+                wr, wt = w[2 * pair], w[2 * pair + 1]
+                rho = mpmath.sqrt(-2 * mpmath.log(mpmath.mpf(wr + 1) / 2**32))
+                th = 2 * mpmath.pi * mpmath.mpf(wt) / 2**32
+                for k, exact in enumerate((rho * mpmath.cos(th), rho * mpmath.sin(th))):
+                    got = G[a, 4 * b + 2 * pair + k]
+                    # bf16 keeps 8 significant bits: within half a bf16 ulp of the exact value
+                    assert abs(got - float(exact)) <= 2.0**-8 * abs(float(exact)) + 1e-30
+
+
+def test_gaussian_cos_sin_entries_uncorrelated():
+    G = O.gaussian_block(np.arange(4000), np.arange(8), 99)
+    for k in range(0, 8, 2):
+        assert abs(np.corrcoef(G[:, k], G[:, k + 1])[0, 1]) < 0.05
+    assert abs(np.corrcoef(G[:, 0], G[:, 2])[0, 1]) < 0.05
+
+
+def test_box_muller_sine_by_shifted_word():
+    """sin(2 pi w 2^-32) is evaluated as the cosine of the word shifted by 2^30 (mod 2^32)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    rng = np.random.default_rng(4)
+    w0 = np.array(list(rng.integers(0, 2**32, 200)) + [2**31, 7], dtype=np.uint64)
+    w1 = np.array(list(rng.integers(0, 2**32, 200)) + [0, 2**30], dtype=np.uint64)
+    got = O.box_muller(w0, (w1 - np.uint64(2**30)) & np.uint64(0xFFFFFFFF))
+    for a, b, g in zip(w0, w1, got):
+        rho = mpmath.sqrt(-2 * mpmath.log(mpmath.mpf(int(a) + 1) / 2**32))
+        exact = rho * mpmath.sin(2 * mpmath.pi * mpmath.mpf(int(b)) / 2**32)
+        if abs(exact) < 1e-30:
+            assert g == 0.0
+        else:
+            assert abs(g - float(exact)) <= 8 * np.spacing(abs(float(exact)))
+
+
 def test_jl_matrix_moments():
     d, k = 300, 200
     P = O.jl_matrix(d, k, 5)
