@@ -216,23 +216,101 @@ __device__ __forceinline__ float bf16_round_f64(double x) {
   return static_cast<float>(__longlong_as_double(static_cast<long long>(b)));
 }
 
-// bfloat16 value of the float64 normal deviate, with the rounding decided exactly as float64
-// rounding would decide it.  The float32 evaluation is within ~2^-21.7 (relative) of the exact
-// value; when it lies further than 128 float32 ulp (>= 2^-17 relative) from a bfloat16 rounding
-// midpoint its nearest-even rounding equals that of the exact value, otherwise the float64
-// evaluation decides.
-__device__ __forceinline__ float gaussian_bf16_value(uint32_t w0, uint32_t w1) {
-  const float z = box_muller_f32(w0, w1);
-  const uint32_t low = __float_as_uint(z) & 0xFFFFu;
-  const int dist = static_cast<int>(low) - 0x8000;
-  if (dist > 128 || dist < -128) return __bfloat162float(__float2bfloat16_rn(z));
+// bfloat16 value of the float64 normal deviate BoxMuller(w0, w1), given its float32 evaluation
+// z, with the rounding decided exactly as float64 rounding would decide it.  The float32
+// evaluation is within 4 float32 ulp of the exact value (logf / log1pf <= 1 ulp, sqrtf exact,
+// sinpif / cospif <= 1 ulp, plus the roundings of their arguments and of the product); when it
+// lies further than kBf16Margin float32 ulp from a bfloat16 rounding midpoint its nearest-even
+// rounding equals that of the exact value, otherwise the float64 evaluation decides.
+constexpr int kBf16Margin = 16;
+
+__device__ __forceinline__ bool bf16_near_midpoint(float z) {
+  const int dist = static_cast<int>(__float_as_uint(z) & 0xFFFFu) - 0x8000;
+  return dist <= kBf16Margin && dist >= -kBf16Margin;
+}
+
+__device__ __forceinline__ float bf16_decide(float z, uint32_t w0, uint32_t w1) {
+  if (!bf16_near_midpoint(z)) return __bfloat162float(__float2bfloat16_rn(z));
   return bf16_round_f64(box_muller_f64(w0, w1));
 }
 
+__device__ __forceinline__ float gaussian_bf16_value(uint32_t w0, uint32_t w1) {
+  return bf16_decide(box_muller_f32(w0, w1), w0, w1);
+}
+
+// Gaussian sketch entries.  Four consecutive columns i = 4b..4b+3 of row j share the Philox
+// block (lo b, hi b, j, TAG_GAUSSIAN): columns 4b, 4b+1 are the cosine and sine normals of the
+// Box-Muller pair (w0, w1), columns 4b+2, 4b+3 those of (w2, w3).  sin(2 pi w 2^-32) is the
+// cosine of the word w - 2^30 (mod 2^32), which keeps the exact-argument evaluation.
+constexpr uint32_t kQuarterTurnWord = 0x40000000u;
+
 __device__ __forceinline__ float gaussian_entry(uint64_t seed, uint32_t row_j, uint64_t col_i) {
-  const U32x4 w = philox(static_cast<uint32_t>(col_i), static_cast<uint32_t>(col_i >> 32), row_j,
-                         TAG_GAUSSIAN, seed);
-  return gaussian_bf16_value(w.x, w.y);
+  const uint64_t blk = col_i >> 2;
+  const U32x4 w = philox(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), row_j, TAG_GAUSSIAN, seed);
+  const uint32_t r = static_cast<uint32_t>(col_i & 3u);
+  const uint32_t wa = r < 2 ? w.x : w.z;
+  uint32_t wb = r < 2 ? w.y : w.w;
+  if (r & 1u) wb -= kQuarterTurnWord;
+  return gaussian_bf16_value(wa, wb);
+}
+
+// float32 sqrt(-2 ln u1), u1 = (w+1) 2^-32 (log1p near 1, as in box_muller_f32).
+__device__ __forceinline__ float bm_radius_f32(uint32_t w) {
+  const float ln_u1 = (w >= 0x80000000u) ? log1pf(-static_cast<float>(0xFFFFFFFFu - w) * 0x1p-32f)
+                                         : logf((static_cast<float>(w) + 1.0f) * 0x1p-32f);
+  return sqrtf(-2.0f * ln_u1);
+}
+
+// Signed +-sin / +-cos of the reduced angle for octant o (same selection as box_muller_f32).
+__device__ __forceinline__ float bm_quarter(uint32_t oct, float sn, float cs) {
+  const bool odd = oct & 1u;
+  const uint32_t q = odd ? (oct + 1) >> 1 : oct >> 1;
+  switch (q) {
+    case 0: return cs;
+    case 1: return odd ? sn : -sn;
+    case 2: return -cs;
+    case 3: return odd ? -sn : sn;
+    default: return cs;
+  }
+}
+
+// float32 cos and sin of 2 pi w 2^-32 from one reduced argument: the word w - 2^30 has octant
+// o - 2 (mod 8) and the same fraction, hence the same sinpi/cospi values.
+__device__ __forceinline__ void bm_cos_sin_f32(uint32_t w, float& c, float& s) {
+  const uint32_t oct = w >> 29;
+  const uint32_t f = w & 0x1FFFFFFFu;
+  const uint32_t ci = (oct & 1u) ? (0x20000000u - f) : f;
+  float sn, cs;
+  sincospif(static_cast<float>(ci) * 0x1p-31f, &sn, &cs);
+  c = bm_quarter(oct, sn, cs);
+  s = bm_quarter((oct - 2u) & 7u, sn, cs);
+}
+
+// The four entries G[j, 4b..4b+3] in float32 (z) with the words each came from; the caller
+// rounds them with bf16_decide (or defers the entries with bf16_near_midpoint set).
+struct Gauss4 {
+  float z[4];
+  uint32_t w0[4], w1[4];
+};
+
+__device__ __forceinline__ Gauss4 gaussian_block4_f32(uint64_t seed, uint32_t row_j, uint64_t blk) {
+  const U32x4 w = philox(static_cast<uint32_t>(blk), static_cast<uint32_t>(blk >> 32), row_j, TAG_GAUSSIAN, seed);
+  const float ra = bm_radius_f32(w.x), rb = bm_radius_f32(w.z);
+  float ca, sa, cb, sb;
+  bm_cos_sin_f32(w.y, ca, sa);
+  bm_cos_sin_f32(w.w, cb, sb);
+  Gauss4 g;
+  g.z[0] = ra * ca;
+  g.z[1] = ra * sa;
+  g.z[2] = rb * cb;
+  g.z[3] = rb * sb;
+  g.w0[0] = g.w0[1] = w.x;
+  g.w0[2] = g.w0[3] = w.z;
+  g.w1[0] = w.y;
+  g.w1[1] = w.y - kQuarterTurnWord;
+  g.w1[2] = w.w;
+  g.w1[3] = w.w - kQuarterTurnWord;
+  return g;
 }
 
 // ------------------------------------------------------------------ small helpers
@@ -324,6 +402,10 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
 
 // score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
+// Tensor-core Gaussian sketch for float32 / bfloat16 X; *used = false when it does not apply
+// (float64 X or no tensor-map support), and the SIMT kernels run instead.
+slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
+                         int64_t s, uint64_t seed, double* SX, cudaStream_t st, bool* used);
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
                           cudaStream_t st);

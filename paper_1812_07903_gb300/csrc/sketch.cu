@@ -457,10 +457,14 @@ slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d
       if (xdt == SLSO_F32) return srht(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, SX, st);
       if (xdt == SLSO_BF16) return srht(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, SX, st);
       return srht(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, SX, st);
-    case SLSO_GAUSSIAN:
+    case SLSO_GAUSSIAN: {
+      bool used = false;
+      SLSO_TRY(run_gauss_tc(h, ar, X, n, d, ldx, xdt, s, seed, SX, st, &used));
+      if (used) return SLSO_OK;
       if (xdt == SLSO_F32) return gaussian(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, SX, st);
       if (xdt == SLSO_BF16) return gaussian(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, SX, st);
       return gaussian(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, SX, st);
+    }
     default:
       return fail(SLSO_ERR_INVALID_ARG, "unknown sketch kind %d", kind);
   }

@@ -73,17 +73,45 @@ def test_srht_matches_oracle(n, d, s, dtype):
     assert _rel_to_max(SX, want) < tol
 
 
-GAUSS_CASES = [(1, 2, 3), (100, 5, 64), (4096, 64, 256), (9000, 130, 200)]
+GAUSS_CASES = [(1, 2, 3), (100, 5, 64), (4096, 64, 256), (9000, 130, 200), (33000, 16, 130)]
 
 
 @pytest.mark.parametrize("n,d,s", GAUSS_CASES)
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64, torch.bfloat16])
 def test_gaussian_matches_oracle(n, d, s, dtype):
+    """float64 X: SIMT float64 sums.  float32 / bfloat16 X: tensor cores, exact bfloat16 products,
+    float32 accumulation over sub-chunks of at most 32 MMA steps (error <= ~32 * 2^-24 of the
+    partial sums), sub-chunk totals added in float32 and chunk totals in float64."""
     X = inputs.lognormal_rows(n, d, seed=7 * n + d, dtype=dtype)
     SX = api.sketch(_dev(X), "gaussian", s, 41).cpu().numpy()
     want = O.sketch(_np(X), "gaussian", s, 41)
     tol = 1e-12 if dtype == torch.float64 else 2e-6
     assert _rel_to_max(SX, want) < tol
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_gaussian_tensor_core_several_chunks_ragged_tiles(dtype):
+    """70001 rows = three chunks of 32768 rows (the last ragged), d = 300 (column tiles of 64 with a
+    ragged last tile), s = 333 (row tiles of 128 with a ragged last tile)."""
+    n, d, s = 70001, 300, 333
+    X = inputs.lognormal_rows(n, d, seed=7 * n + d, dtype=dtype)
+    SX = api.sketch(_dev(X), "gaussian", s, 41).cpu().numpy()
+    want = O.sketch(_np(X), "gaussian", s, 41)
+    assert _rel_to_max(SX, want) < 2e-6
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_gaussian_sketch_of_identity_is_the_oracle_g_bit_for_bit(dtype):
+    """X = I (4096 x 4096): SX = G / sqrt(s), one exact product per output, so every entry of G the
+    GPU generated (four per Philox block, the near-midpoint ones rounded from the float64
+    evaluation) must equal the oracle's bfloat16 G exactly; a one-ulp bfloat16 flip is a relative
+    change of 2^-8 and would show."""
+    n, s, seed = 4096, 1000, 41
+    X = torch.eye(n, dtype=dtype)
+    SX = api.sketch(_dev(X), "gaussian", s, seed).cpu().numpy()
+    G = O.gaussian_block(np.arange(s), np.arange(n), seed)
+    got = SX * math.sqrt(s)
+    assert np.max(np.abs(got - G) / np.maximum(np.abs(G), 1e-30)) < 1e-12
 
 
 # ------------------------------------------------------------------ small solve
