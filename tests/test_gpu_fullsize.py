@@ -1,0 +1,107 @@
+"""GPU parity at full size, in the launch configurations the benchmark times.
+
+At these sizes the oracle cannot redo every step, so each stage is checked on what the oracle
+can compute one by one, and the rest of the path is checked stage-wise (the oracle's solve
+applied to the GPU's own sketch, "Oracle C"):
+
+* 1,000,000 x 1024 float32, CountSketch s = 16384, k = 128 (the benchmark step): sampled rows
+  of SX summed exactly in float64 from the rows hashing to them; R, rank and M by the oracle from
+  the GPU's SX; float32 scores of sampled rows and of the top rows within 1e-4; the order equal
+  to a stable (score, index) sort of the GPU's scores; bfloat16 median error under 2%.
+* 60,000 x 784 image-like, CountSketch s = 8192 and SRHT s = 2048, k = 64: the whole oracle,
+  rank 716 (68 zero columns), every row's score within 1e-4.
+* 4,000,000 x 3072 bfloat16 with a 1% rank-16 outlier subspace, Gaussian s = 6144 on tensor
+  cores, k = 256: sampled entries of SX summed over all 4M rows in float64 (G regenerated by the
+  oracle), then the stage-wise check of the scores.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import slso_oracle as O
+from paper_1812_07903_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _max_rel(a, b):
+    mask = np.abs(b) > 0
+    return float(np.max(np.abs(a[mask] - b[mask]) / np.abs(b[mask])))
+
+
+def _stagewise_scores(SX_gpu, X_rows, k, seed_Pi):
+    """The oracle's solve on the GPU's sketch, then exact float64 scores of the given rows."""
+    d = SX_gpu.shape[1]
+    Pi = O.jl_matrix(d, k, seed_Pi) if k > 0 else None
+    sv = O.sketched_svd(SX_gpu, None, qr="lapack")
+    M = O.m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], Pi)
+    return O.row_scores(X_rows, M), sv
+
+
+def test_benchmark_workload_1m_x_1024_countsketch():
+    n, d, s, k, seed_S, seed_Pi = 1_000_000, 1024, 16384, 128, 2003, 3003
+    X = inputs.snr_student_t(n, d, seed=1003, device="cuda")
+    SX = api.sketch(X, "countsketch", s, seed_S).cpu().numpy()
+    sc, info = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="f32")
+    sc = sc.cpu().numpy()
+    order = api.order(torch.from_numpy(sc).cuda()).cpu().numpy()
+    Xh = X.cpu().numpy()
+
+    # sketch: sampled buckets summed exactly
+    bucket, sign = O.countsketch_hash(n, s, seed_S)
+    rng = np.random.default_rng(0)
+    for b in rng.choice(s, 24, replace=False):
+        rows = np.nonzero(bucket == b)[0]
+        want = (sign[rows][:, None] * Xh[rows].astype(np.float64)).sum(axis=0)
+        assert np.max(np.abs(SX[b] - want)) <= 1e-12 * max(np.max(np.abs(want)), 1e-300)
+
+    # solve and scores, stage-wise from the GPU's sketch
+    rows = np.unique(np.concatenate([rng.choice(n, 20000, replace=False), order[:200]]))
+    want, sv = _stagewise_scores(SX, Xh[rows], k, seed_Pi)
+    assert info["rank"] == sv["rank"] == d
+    assert _max_rel(sc[rows], want) < 1e-4
+
+    # order: bit-exact stable sort of the GPU's own scores
+    np.testing.assert_array_equal(order, O.order_dec(sc))
+
+    # bfloat16 scores (the metric's precision claim): median relative error < 2%
+    bf, _ = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="bf16")
+    rel = np.abs(bf.cpu().numpy()[rows] - want) / want
+    assert float(np.median(rel)) < 2e-2
+
+
+@pytest.mark.parametrize("kind,s", [("countsketch", 8192), ("srht", 2048)])
+def test_image_like_60000_x_784_full_oracle(kind, s):
+    X, zero_cols = inputs.image_like(n=60000, seed=1002)
+    k, seed_S, seed_Pi = 64, 2002, 3002
+    sc, info = api.leverage(X.cuda(), kind, s, k, seed_S, seed_Pi, compute="f32")
+    want, oinfo = O.sketched_leverage(X.double().numpy(), kind, s, k, seed_S, seed_Pi, qr="lapack")
+    assert info["rank"] == oinfo["rank"] == 716
+    assert _max_rel(sc.cpu().numpy(), want) < 1e-4
+
+
+def test_large_4m_x_3072_bf16_gaussian_tensor_cores():
+    n, d, s, k, seed_S, seed_Pi = 4_000_000, 3072, 6144, 256, 2005, 3005
+    X, out_rows = inputs.outlier_subspace(n, d, seed=1005, device="cuda", dtype=torch.bfloat16)
+    SXt = api.sketch(X, "gaussian", s, seed_S)
+    SX = SXt.cpu().numpy()
+    del SXt
+    # sketch: sampled entries summed over all rows in float64 with the oracle's G
+    rng = np.random.default_rng(1)
+    scale = 1.0 / math.sqrt(s)
+    for j, c in zip(rng.choice(s, 4, replace=False), rng.choice(d, 4, replace=False)):
+        col = X[:, int(c)].float().cpu().numpy().astype(np.float64)
+        g = O.gaussian_block(np.array([j]), np.arange(n), seed_S)[0]
+        want = float(np.dot(g, col)) * scale
+        # 123 chunks, each within ~1e-6 of its partial sums (sub-chunks of <= 32 MMA steps)
+        assert abs(SX[j, c] - want) <= 4e-6 * np.max(np.abs(SX))
+
+    sc, info = api.leverage(X, "gaussian", s, k, seed_S, seed_Pi, compute="f32")
+    sc = sc.cpu().numpy()
+    rows = np.unique(rng.choice(n, 4000, replace=False))
+    Xr = X[torch.from_numpy(rows).cuda()].float().cpu().numpy()
+    want, sv = _stagewise_scores(SX, Xr, k, seed_Pi)
+    assert info["rank"] == sv["rank"] == d
+    assert _max_rel(sc[rows], want) < 1e-4
