@@ -34,6 +34,10 @@ METRIC = "scored rows/s (BF16 vs FP32, ≤2% median rel err) + roofline %; p99 j
 WORKLOAD = dict(n=1_000_000, d=1024, s=16384, k=128, kind="countsketch", xseed=1003, seed_S=2003, seed_Pi=3003)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070 / 1e3  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3
+# DRAM bytes (read + write) of one qr_left_kernel<64> launch at s = 16384, d = 1024, from the ncu
+# capture summarised in profiles/qr_fp64_householder_s16384_d1024.md (496.4 MB + 130.2 MB).  Set
+# back to None whenever that kernel changes until it is captured again.
+QR_TRAFFIC_BYTES = 496_413_184 + 130_248_960
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 
 
@@ -238,6 +242,60 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
     }
 
 
+# ----------------------------------------------------------------------------- large workload
+LARGE = dict(n=4_000_000, d=3072, s=6144, k=256, kind="gaussian", xseed=1005, seed_S=2005, seed_Pi=3005)
+
+
+def large_bench(args):
+    """4M x 3072 bfloat16 rows (1% from a rank-16 subspace x 20), Gaussian sketch s = 6144 on tensor
+    cores, k = 256, scores in float32 / bfloat16 / FP8; one JSON line with stage times and the
+    sketch's tensor throughput."""
+    import torch
+
+    from paper_1812_07903_gb300 import api, inputs
+
+    L = dict(LARGE)
+    n = args.n if args.n != WORKLOAD["n"] else L["n"]
+    d, s, k = L["d"], L["s"], L["k"]
+    torch.cuda.set_device(0)
+    X, _ = inputs.outlier_subspace(n, d, seed=L["xseed"], device="cuda", dtype=torch.bfloat16)
+    h = api.Handle(0)
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    order = torch.empty(n, dtype=torch.int64, device="cuda")
+    peaks, peak_src = _peaks()
+    out = {"config": {"workload": f"outlier_subspace {n}x{d} bfloat16 (1% rank-16 rows x 20), gaussian s={s} "
+                                  f"(tensor cores), JL k={k}; leverage + dec order", "n": n, "d": d, "s": s, "k": k,
+                      "sketch": "gaussian", "l2": "X larger than L2; no flush"},
+           "metric": "scored rows/s", "unit": "rows/s", "steps": args.steps, "warmup": args.warmup}
+    for compute in ("f32", "bf16", "fp8"):
+        def step():
+            api.leverage(X, "gaussian", s, k, L["seed_S"], L["seed_Pi"], compute=compute, out=scores,
+                         want_info=False, handle=h)
+            api.order(scores, out=order, handle=h)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        api.profile(True, handle=h)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        stages, launches = api.profile_read(handle=h)
+        api.profile(False, handle=h)
+        per = {nm: v_ / max(c, 1) for nm, (v_, c) in stages.items() if c}
+        tf = 2.0 * s * n * d / (per["sketch"] / 1e3) / 1e12
+        out[compute] = {"value": n / (ms / 1e3), "ms_per_step": ms, "gpu_launches": int(launches),
+                        "stages_ms_per_step": {nm: round(v_, 3) for nm, v_ in per.items()},
+                        "sketch_tensor_tflops": tf,
+                        "sketch_frac_of_bf16_peak": tf / peaks["bf16_tflops_sustained"],
+                        "peak": {"bf16_tflops_sustained": peaks["bf16_tflops_sustained"], "source": peak_src}}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -250,9 +308,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=96, help="jobs in the serving trace (0 skips it)")
+    ap.add_argument("--config", default="benchmark", choices=["benchmark", "large"],
+                    help="large: the 4M x 3072 bfloat16 Gaussian-sketch workload (its own JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "large":
+        return large_bench(args)
 
     import numpy as np
     import torch
@@ -334,7 +396,8 @@ def main():
         flops = 2.0 * s * d * d - 2.0 * d ** 3 / 3.0
         ach = flops / (per["qr"] / 1e3) / 1e12
         roof = {"kernel": "qr_kernel (FP64 Householder, cooperative)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": QR_TRAFFIC_BYTES if (s, d) == (16384, 1024) else None,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.198)"}
     elif dom == "sketch":
         byts = n * d * 4.0 + s * d * 8.0
