@@ -34,9 +34,9 @@ METRIC = "scored rows/s (BF16 vs FP32, ≤2% median rel err) + roofline %; p99 j
 WORKLOAD = dict(n=1_000_000, d=1024, s=16384, k=128, kind="countsketch", xseed=1003, seed_S=2003, seed_Pi=3003)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070 / 1e3  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3
-# DRAM bytes (read + write) of one qr_left_kernel<64> launch at s = 16384, d = 1024, from the ncu
-# capture summarised in profiles/qr_fp64_householder_s16384_d1024.md (496.4 MB + 130.2 MB).  Set
-# back to None whenever that kernel changes until it is captured again.
+# DRAM bytes of one qr_left_kernel<64> launch at s = 16384, d = 1024 (dram__bytes_read.sum 496.4 MB
+# + dram__bytes_write.sum 130.2 MB from one ncu capture of the current kernel).  Set back to None
+# whenever that kernel changes, until it is captured again.
 QR_TRAFFIC_BYTES = 496_413_184 + 130_248_960
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 
