@@ -14,6 +14,8 @@
 //             (nearest-even), M = Mhi + Mlo likewise; D += Xhi Mhi + Xhi Mlo + Xlo Mhi (kind::tf32).
 //   BF16_CVT  float32 X rounded to bfloat16 in shared memory, M in bfloat16 (kind::f16).
 //   BF16      bfloat16 X loaded directly (kind::f16).
+//   BF16X3    bfloat16 X loaded directly, float32-accurate: M = M1 + M2 + M3 with each piece a
+//             bfloat16 (24 significant bits in all), D += X M1 + X M2 + X M3 (products exact).
 //   FP8_F32 / FP8_BF16  float32 or bfloat16 X scaled per column by c_j = 448 / max_i |x_ij| and
 //             rounded to e4m3 in shared memory; B = e4m3(e M^T diag(1/c)) with one scale e for
 //             M; the epilogue multiplies each row's sum of squares by 1/e^2 (kind::f8f6f4).
@@ -35,7 +37,15 @@ namespace {
 
 using namespace tc;
 
-enum Mode : int { MODE_TF32X3 = 0, MODE_BF16_CVT = 1, MODE_BF16 = 2, MODE_FP8_F32 = 3, MODE_FP8_BF16 = 4 };
+enum Mode : int { MODE_TF32X3 = 0, MODE_BF16_CVT = 1, MODE_BF16 = 2, MODE_FP8_F32 = 3, MODE_FP8_BF16 = 4,
+                  MODE_BF16X3 = 5 };
+
+// X tiles go straight from TMA into the operand stage (no converter pass).
+__host__ __device__ constexpr bool direct_x(int mode) { return mode == MODE_BF16 || mode == MODE_BF16X3; }
+// B = M^T tiles per operand stage.
+__host__ __device__ constexpr int b_tiles(int mode) {
+  return mode == MODE_TF32X3 ? 2 : (mode == MODE_BF16X3 ? 3 : 1);
+}
 
 constexpr int kConvThreads = 256;
 constexpr int kThreads = 192 + kConvThreads;
@@ -72,7 +82,8 @@ __device__ __forceinline__ void split_tf32(uint32_t x, uint32_t& hi, uint32_t& l
 
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB0,
-                    const __grid_constant__ CUtensorMap tmB1, const Layout L, int64_t n, int ntiles,
+                    const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
+                    const Layout L, int64_t n, int ntiles,
                     const float* __restrict__ cscale, const float* __restrict__ post_scale,
                     float* __restrict__ scores, DevState* __restrict__ state) {
   extern __shared__ unsigned char smem_dyn[];
@@ -89,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_abort;
   const volatile int* abort_flag = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool convert = L.mode != MODE_BF16;
+  const bool convert = !direct_x(L.mode);
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -126,10 +137,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(&op_empty[os], oph ^ 1u, abort_flag)) { ok = false; break; }
           unsigned char* op = smem + L.op_off + os * L.op_bytes;
           const int x = kb * L.kbe;
-          if (L.mode == MODE_BF16) {
-            mbar_arrive_expect_tx(&op_full[os], kXTileBytes + L.b_bytes);
+          if (direct_x(L.mode)) {
+            const int nb = b_tiles(L.mode);
+            mbar_arrive_expect_tx(&op_full[os], kXTileBytes + nb * L.b_bytes);
             tma_load_2d(op, &tmX, &op_full[os], x, y);
             tma_load_2d(op + kXTileBytes, &tmB0, &op_full[os], x, 0);
+            if (nb == 3) {
+              tma_load_2d(op + kXTileBytes + L.b_bytes, &tmB1, &op_full[os], x, 0);
+              tma_load_2d(op + kXTileBytes + 2 * L.b_bytes, &tmB2, &op_full[os], x, 0);
+            }
             continue;
           }
           const int rs = it % L.RS;
@@ -187,6 +203,17 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_tf32(d_tmem, ahi + o, bhi + o, id, (kb | ks) != 0);
               mma_tf32(d_tmem, ahi + o, blo + o, id, 1u);
               mma_tf32(d_tmem, alo + o, bhi + o, id, 1u);
+            }
+          } else if (L.mode == MODE_BF16X3) {
+            const uint64_t a = sdesc_sw128(op);
+            const uint64_t b0 = sdesc_sw128(op + kXTileBytes), b1 = sdesc_sw128(op + kXTileBytes + L.b_bytes);
+            const uint64_t b2 = sdesc_sw128(op + kXTileBytes + 2 * L.b_bytes);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t o = static_cast<uint64_t>(ks * 2);
+              mma_f16(d_tmem, a + o, b0 + o, id, (kb | ks) != 0);
+              mma_f16(d_tmem, a + o, b1 + o, id, 1u);
+              mma_f16(d_tmem, a + o, b2 + o, id, 1u);
             }
           } else {
             const uint64_t a = sdesc_sw128(op), b = sdesc_sw128(op + kXTileBytes);
@@ -371,6 +398,25 @@ __global__ void prep_b_bf16_kernel(const double* __restrict__ M, int64_t d, int6
   }
 }
 
+// M^T as three bfloat16 pieces: m = p1 + p2 + p3 (+ a remainder below 2^-24 |m|), each the
+// nearest bfloat16 to what is left.
+__global__ void prep_b_bf16x3_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
+                                     __nv_bfloat16* __restrict__ B0, __nv_bfloat16* __restrict__ B1,
+                                     __nv_bfloat16* __restrict__ B2) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < N * Kpad;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = e / Kpad, k = e % Kpad;
+    double m = (c < kk && k < d) ? M[k * kk + c] : 0.0;
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(static_cast<float>(m));
+    m -= static_cast<double>(__bfloat162float(p1));
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(static_cast<float>(m));
+    m -= static_cast<double>(__bfloat162float(p2));
+    B0[e] = p1;
+    B1[e] = p2;
+    B2[e] = __float2bfloat16_rn(static_cast<float>(m));
+  }
+}
+
 Layout make_layout(int mode, int64_t kk, int64_t d) {
   Layout L{};
   L.mode = mode;
@@ -379,13 +425,13 @@ Layout make_layout(int mode, int64_t kk, int64_t d) {
   L.kbe = (mode == MODE_TF32X3) ? 32 : (fp8 ? 128 : 64);  // one 128-byte operand row per K-block
   L.KB = static_cast<int>(ceil_div(d, L.kbe));
   L.b_bytes = static_cast<uint32_t>(L.N) * 128u;
-  L.box_cols = (mode == MODE_BF16 || mode == MODE_FP8_BF16) ? 64 : 32;
-  L.raw_boxes = (mode == MODE_BF16) ? 0 : L.kbe / L.box_cols;
+  L.box_cols = (direct_x(mode) || mode == MODE_FP8_BF16) ? 64 : 32;
+  L.raw_boxes = direct_x(mode) ? 0 : L.kbe / L.box_cols;
   L.x_op_bytes = (mode == MODE_TF32X3) ? 2 * kXTileBytes : kXTileBytes;
   const uint32_t budget = 226u * 1024u;  // + 1.5 KB barriers and alignment slack <= 227 KB
   L.raw_bytes = static_cast<uint32_t>(L.raw_boxes) * kXTileBytes;
-  L.op_bytes = L.x_op_bytes + (mode == MODE_TF32X3 ? 2 : 1) * L.b_bytes;
-  if (mode == MODE_BF16) {
+  L.op_bytes = L.x_op_bytes + static_cast<uint32_t>(b_tiles(mode)) * L.b_bytes;
+  if (direct_x(mode)) {
     L.OS = static_cast<int>(std::min<uint32_t>(kMaxStages, budget / L.op_bytes));
     L.RS = 1;
   } else {
@@ -394,7 +440,7 @@ Layout make_layout(int mode, int64_t kk, int64_t d) {
     L.RS = static_cast<int>(std::min<uint32_t>(4, (budget - L.OS * L.op_bytes) / L.raw_bytes));
   }
   L.raw_off = 0;
-  L.op_off = L.raw_bytes * static_cast<uint32_t>(mode == MODE_BF16 ? 0 : L.RS);
+  L.op_off = L.raw_bytes * static_cast<uint32_t>(direct_x(mode) ? 0 : L.RS);
   L.bar_off = L.op_off + L.op_bytes * static_cast<uint32_t>(L.OS);
   L.smem_bytes = L.bar_off + 64 * 8 + 1024;  // barriers + TMEM slot + alignment slack
   uint32_t cols = 32;
@@ -467,6 +513,7 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   if (xdt == SLSO_F32 && compute == SLSO_F32) mode = MODE_TF32X3;
   if (xdt == SLSO_F32 && compute == SLSO_BF16) mode = MODE_BF16_CVT;
   if (xdt == SLSO_BF16 && compute == SLSO_BF16) mode = MODE_BF16;
+  if (xdt == SLSO_BF16 && compute == SLSO_F32) mode = MODE_BF16X3;
   if (xdt == SLSO_F32 && compute == SLSO_FP8_E4M3) mode = MODE_FP8_F32;
   if (xdt == SLSO_BF16 && compute == SLSO_FP8_E4M3) mode = MODE_FP8_BF16;
   if (mode < 0 || kk > 256 || kk < 1) return SLSO_OK;
@@ -478,6 +525,7 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   const bool fp8 = mode == MODE_FP8_F32 || mode == MODE_FP8_BF16;
   void* B0 = nullptr;
   void* B1 = nullptr;
+  void* B2 = nullptr;
   unsigned int* colmax = nullptr;
   float* cscale = nullptr;
   float* escale = nullptr;
@@ -489,13 +537,17 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     colmax = ar.take<unsigned int>(d);
     cscale = ar.take<float>(Kpad);
     escale = ar.take<float>(2);
+  } else if (mode == MODE_BF16X3) {
+    B0 = ar.take<__nv_bfloat16>(static_cast<size_t>(L.N) * Kpad);
+    B1 = ar.take<__nv_bfloat16>(static_cast<size_t>(L.N) * Kpad);
+    B2 = ar.take<__nv_bfloat16>(static_cast<size_t>(L.N) * Kpad);
   } else {
     B0 = ar.take<__nv_bfloat16>(static_cast<size_t>(L.N) * Kpad);
   }
   *used = true;
   if (ar.measure()) return SLSO_OK;
   const int pg = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.N * Kpad, 256), 4LL * h.num_sms)));
-  CUtensorMap mX, mB0, mB1;
+  CUtensorMap mX, mB0, mB1, mB2;
   bool ok;
   const CUtensorMapDataType xdt_map = (xdt == SLSO_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   ok = make_map(&mX, xdt_map, X, d, n, ldx * esz, static_cast<uint32_t>(L.box_cols), kBM);
@@ -504,6 +556,7 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     SLSO_CHECK_LAUNCH();
     ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, 32, L.N) &&
          make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, 32, L.N);
+    mB2 = mB1;
   } else if (fp8) {
     SLSO_CHECK_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * d, st));
     const int64_t rows_per_cta = std::max<int64_t>(1024, ceil_div(n, 256));
@@ -520,19 +573,26 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                                           static_cast<__nv_fp8_storage_t*>(B0));
     SLSO_CHECK_LAUNCH();
     ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_UINT8, B0, Kpad, L.N, Kpad, 128, L.N);
-    mB1 = mB0;
+    mB1 = mB2 = mB0;
+  } else if (mode == MODE_BF16X3) {
+    prep_b_bf16x3_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<__nv_bfloat16*>(B0),
+                                             static_cast<__nv_bfloat16*>(B1), static_cast<__nv_bfloat16*>(B2));
+    SLSO_CHECK_LAUNCH();
+    ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B0, Kpad, L.N, Kpad * 2, 64, L.N) &&
+         make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B1, Kpad, L.N, Kpad * 2, 64, L.N) &&
+         make_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B2, Kpad, L.N, Kpad * 2, 64, L.N);
   } else {
     prep_b_bf16_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<__nv_bfloat16*>(B0));
     SLSO_CHECK_LAUNCH();
     ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B0, Kpad, L.N, Kpad * 2, 64, L.N);
-    mB1 = mB0;
+    mB1 = mB2 = mB0;
   }
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
   const int ntiles = static_cast<int>(ceil_div(n, kBM));
   const int grid = std::min(ntiles, h.num_sms);
   SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(L.smem_bytes)));
-  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, L, n, ntiles, cscale,
+  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, mB2, L, n, ntiles, cscale,
                                                         fp8 ? escale + 1 : nullptr, scores, h.state);
   SLSO_CHECK_LAUNCH();
   return SLSO_OK;

@@ -241,6 +241,19 @@ def test_tensor_core_float32_scores_match_oracle(n, d, k):
     assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
 
 
+@pytest.mark.parametrize("n,d,k", [(70, 16, 256), (1000, 100, 48), (12345, 320, 128), (4096, 1024, 16),
+                                   (20000, 3072, 256)])
+def test_tensor_core_float32_scores_of_bfloat16_x_match_oracle(n, d, k):
+    """bfloat16 X, float32-accurate scores: X loaded directly, M as three bfloat16 pieces (24
+    significant bits), exact products, float32 accumulation; same 1e-4 bound as the float32 path."""
+    X = inputs.lognormal_rows(n, d, seed=n + k, dtype=torch.bfloat16)
+    s = max(2 * d, 256)
+    sc, info = api.leverage(_dev(X), "countsketch", s, k, 5, 6, compute="f32")
+    want, oinfo = O.sketched_leverage(_np(X), "countsketch", s, k, 5, 6, qr="lapack")
+    assert info["rank"] == oinfo["rank"] == d
+    assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
+
+
 @pytest.mark.parametrize("xdtype", [torch.float32, torch.bfloat16])
 def test_tensor_core_bf16_scores_close_to_oracle(xdtype):
     """BF16 tensor-core paths (float32 X rounded in shared memory, or bfloat16 X loaded directly)."""
