@@ -273,47 +273,49 @@ __global__ void __launch_bounds__(kGenThreads) gauss_gen_kernel(uint64_t seed, i
     if (threadIdx.x == 0) q_len = 0;
     __syncthreads();
   };
-  const int64_t qn = Kc / 4;
-  const int64_t total = s * qn;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * kGenThreads;
-  for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * kGenThreads; t0 < total; t0 += stride) {  // block-uniform
-    const int64_t t = t0 + threadIdx.x;
-    if (t < total) {
-      const int64_t j = t / qn, q = t - j * qn;
-      const int64_t col = k0 + 4 * q;  // k0 is a multiple of 4
-      const int64_t at = j * Kc + 4 * q;
-      float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (col < n) {
-        const Gauss4 b = gaussian_block4_f32(seed, static_cast<uint32_t>(j), static_cast<uint64_t>(col) >> 2);
+  // grid: x over the Kc/4 Philox blocks of a row (grid-stride), y over rows of G (grid-stride);
+  // no 64-bit division per block
+  const int qn = static_cast<int>(Kc / 4);
+  const int qstride = gridDim.x * kGenThreads;
+  for (int64_t j = blockIdx.y; j < s; j += gridDim.y) {
+    for (int q0 = blockIdx.x * kGenThreads; q0 < qn; q0 += qstride) {  // block-uniform
+      const int q = q0 + threadIdx.x;
+      if (q < qn) {
+        const int64_t col = k0 + 4 * static_cast<int64_t>(q);  // k0 is a multiple of 4
+        const int64_t at = j * Kc + 4 * static_cast<int64_t>(q);
+        float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (col < n) {
+          const Gauss4 b = gaussian_block4_f32(seed, static_cast<uint32_t>(j), static_cast<uint64_t>(col) >> 2);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (col + e >= n) continue;
-          if (!bf16_near_midpoint(b.z[e])) {
-            g[e] = b.z[e];
-          } else {
-            const int slot = atomicAdd(&q_len, 1);
-            if (slot < kGenQueue) {
-              q_w0[slot] = b.w0[e];
-              q_w1[slot] = b.w1[e];
-              q_at[slot] = at + e;
+          for (int e = 0; e < 4; ++e) {
+            if (col + e >= n) continue;
+            if (!bf16_near_midpoint(b.z[e])) {
+              g[e] = b.z[e];
             } else {
-              g[e] = bf16_round_f64(box_muller_f64(b.w0[e], b.w1[e]));
+              const int slot = atomicAdd(&q_len, 1);
+              if (slot < kGenQueue) {
+                q_w0[slot] = b.w0[e];
+                q_w1[slot] = b.w1[e];
+                q_at[slot] = at + e;
+              } else {
+                g[e] = bf16_round_f64(box_muller_f64(b.w0[e], b.w1[e]));
+              }
             }
           }
         }
+        // queued entries are written here as 0 and overwritten by the drain (same block, after a barrier)
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(g[0], g[1]);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(g[2], g[3]);
+        uint2 o;
+        o.x = *reinterpret_cast<const uint32_t*>(&lo);
+        o.y = *reinterpret_cast<const uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(Gc + at) = o;
       }
-      // queued entries are written here as 0 and overwritten by the drain (same block, after a barrier)
-      const __nv_bfloat162 lo = __floats2bfloat162_rn(g[0], g[1]);
-      const __nv_bfloat162 hi = __floats2bfloat162_rn(g[2], g[3]);
-      uint2 o;
-      o.x = *reinterpret_cast<const uint32_t*>(&lo);
-      o.y = *reinterpret_cast<const uint32_t*>(&hi);
-      *reinterpret_cast<uint2*>(Gc + at) = o;
+      __syncthreads();
+      const int cnt = q_len < kGenQueue ? q_len : kGenQueue;
+      __syncthreads();  // every thread has read q_len before anyone appends again
+      if (cnt >= kGenThreads) drain(cnt);
     }
-    __syncthreads();
-    const int cnt = q_len < kGenQueue ? q_len : kGenQueue;
-    __syncthreads();  // every thread has read q_len before anyone appends again
-    if (cnt >= kGenThreads) drain(cnt);
   }
   __syncthreads();
   const int cnt = q_len < kGenQueue ? q_len : kGenQueue;
@@ -425,9 +427,11 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
   const double scale = 1.0 / std::sqrt(static_cast<double>(s));
   const dim3 grid_tc(static_cast<unsigned>(ceil_div(d, NT)), static_cast<unsigned>(ceil_div(s, kGBM)));
   const dim3 grid_xt(static_cast<unsigned>(ceil_div(d, 32)), static_cast<unsigned>(Kc / 32));
-  const int64_t gen_total = s * (Kc / 4);
-  const unsigned grid_gen =
-      static_cast<unsigned>(std::min<int64_t>(ceil_div(gen_total, kGenThreads), int64_t(h.num_sms) * 8));
+  // generator grid: enough blocks per row for the row's Kc/4 Philox blocks, rows spread over y
+  const unsigned gen_x = static_cast<unsigned>(ceil_div(Kc / 4, kGenThreads));
+  const unsigned gen_y = static_cast<unsigned>(std::max<int64_t>(
+      1, std::min<int64_t>(s, ceil_div(int64_t(h.num_sms) * 8, static_cast<int64_t>(gen_x)))));
+  const dim3 grid_gen(gen_x, gen_y);
   for (int64_t k0 = 0; k0 < n; k0 += Kc) {
     gauss_gen_kernel<<<grid_gen, kGenThreads, 0, st>>>(seed, s, n, k0, Kc, Gc);
     SLSO_CHECK_LAUNCH();

@@ -838,18 +838,23 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     void* fn = nullptr;
     int threads = kQrlThreads;
     int rpt = 0;  // rows per thread of the left-looking kernel (0: right-looking)
-    if (s <= 512) rpt = 2;
-    else if (s <= 1024) rpt = 4;
-    else if (s <= 2048) rpt = 8;
-    else if (s <= 4096) rpt = 16;
-    else if (s <= 8192) rpt = 32;
-    else if (s <= kQrlMaxS) rpt = 64;
+    // the smallest instantiated row count per thread that covers s (padding rows cost FMAs)
+    static const int kRpts[] = {2, 4, 8, 16, 24, 32, 40, 48, 56, 64};
+    for (int r : kRpts)
+      if (s <= static_cast<int64_t>(kQrlThreads) * r) {
+        rpt = r;
+        break;
+      }
     switch (rpt) {
       case 2: fn = reinterpret_cast<void*>(qr_left_kernel<2>); break;
       case 4: fn = reinterpret_cast<void*>(qr_left_kernel<4>); break;
       case 8: fn = reinterpret_cast<void*>(qr_left_kernel<8>); break;
       case 16: fn = reinterpret_cast<void*>(qr_left_kernel<16>); break;
+      case 24: fn = reinterpret_cast<void*>(qr_left_kernel<24>); break;
       case 32: fn = reinterpret_cast<void*>(qr_left_kernel<32>); break;
+      case 40: fn = reinterpret_cast<void*>(qr_left_kernel<40>); break;
+      case 48: fn = reinterpret_cast<void*>(qr_left_kernel<48>); break;
+      case 56: fn = reinterpret_cast<void*>(qr_left_kernel<56>); break;
       case 64: fn = reinterpret_cast<void*>(qr_left_kernel<64>); break;
       default: break;
     }

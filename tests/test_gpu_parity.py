@@ -115,8 +115,11 @@ def test_gaussian_sketch_of_identity_is_the_oracle_g_bit_for_bit(dtype):
 
 
 # ------------------------------------------------------------------ small solve
-@pytest.mark.parametrize("s,d", [(1, 1), (7, 3), (256, 64), (1000, 257), (4096, 700)])
+@pytest.mark.parametrize("s,d", [(1, 1), (7, 3), (256, 64), (1000, 257), (4096, 700), (6000, 300),
+                                 (9001, 200), (12000, 160), (14000, 96), (16384, 64)])
 def test_sketched_svd_matches_oracle(s, d):
+    """QR + SVD of SX; the s values cover every rows-per-thread instance of the left-looking QR
+    (256 threads x 2 .. 64 rows, odd s included)."""
     rng = np.random.default_rng(s + d)
     SX = rng.standard_normal((s, d)) * np.exp(rng.standard_normal(d))
     sigma, V, R, info = api.sketched_svd(torch.from_numpy(SX).cuda())
