@@ -20,8 +20,11 @@ generator independently.  Counter layouts (word 3 of the counter is a stream tag
   CountSketch row i      ctr=(lo(i), hi(i), 0, 1)  bucket=(w0*s)>>32, sign=1-2*(w1&1)
   SRHT sign of row i     ctr=(lo(i), hi(i), 0, 2)  D_i = 1-2*(w0&1)
   SRHT sample key of j   ctr=(lo(j), hi(j), 0, 3)  key_j = w0; keep the s smallest (key, j)
-  Gaussian entry (j, i)  ctr=(lo(i), hi(i), j, 4)  G_ji = bf16(BoxMuller(w0, w1))
+  Gaussian entry (j, i)  ctr=(lo(b), hi(b), j, 4), b = i // 4: i % 4 = 0, 1, 2, 3 give
+                         bf16 of BoxMuller(w0, w1), BoxMuller(w0, w1 - 2^30),
+                         BoxMuller(w2, w3), BoxMuller(w2, w3 - 2^30)  (cos, sin of each pair)
   JL entry (j, c)        ctr=(lo(c), hi(c), j, 5)  Pi_jc = BoxMuller(w0, w1) / sqrt(k)
+  sampling draw t        ctr=(lo(t), hi(t), 0, 6)  u_t = (m + 1/2) 2^-52, m = w0 2^20 + (w1 >> 12)
 
 with key = (lo(seed), hi(seed)), BoxMuller(w0, w1) = sqrt(-2 ln u1) cos(2 pi u2),
 u1 = (w0 + 1) 2^-32 in (0, 1], u2 = w1 2^-32 in [0, 1).
@@ -50,6 +53,7 @@ TAG_SRHT_SIGN = 2
 TAG_SRHT_SAMPLE = 3
 TAG_GAUSSIAN = 4
 TAG_JL = 5
+TAG_SAMPLE = 6
 
 
 def philox4x32_10(c0, c1, c2, c3, key):
@@ -458,3 +462,60 @@ def sampling_probabilities(scores):
     """Algorithm 4 step 3: P_i = l_i / sum_j l_j."""
     sc = np.asarray(scores, dtype=np.float64)
     return sc / np.sum(sc)
+
+
+def sample_uniforms(n, seed):
+    """Uniform u_t in (0, 1) for the draws t = 0..n-1 of a sampling policy.
+
+    52 bits m = w0 2^20 + (w1 >> 12) from the Philox block (lo t, hi t, 0, 6); u_t = (m + 1/2) 2^-52,
+    so 2m + 1 < 2^53 is exact in float64 and u_t is never 0 or 1.
+    """
+    lo, hi = _split64(np.arange(n, dtype=np.uint64))
+    w = philox4x32_10(lo, hi, 0, TAG_SAMPLE, seed)
+    m = (w[0] << np.uint64(20)) | (w[1] >> np.uint64(12))
+    return (m.astype(np.float64) + 0.5) * 2.0**-52
+
+
+def _sampling_weights(scores):
+    """Weights l_i for the sampling policies: non-finite or negative scores weigh 0 (never drawn)."""
+    sc = np.asarray(scores, dtype=np.float64)
+    return np.where(np.isfinite(sc) & (sc > 0.0), sc, 0.0)
+
+
+def order_swor_from_uniforms(scores, u):
+    """Policy "dec, swor" (Sec. 5.2; Algorithm 4 step 4): the order of n successive draws without
+    replacement, each draw picking one of the points not yet drawn with probability proportional to
+    its P_i = l_i / sum l (a weighted random permutation: the largest weights tend to come first).
+
+    The draw order is realised exactly in distribution by Efraimidis and Spirakis's keys: point i
+    gets u_i^(1 / P_i) and the points are taken by decreasing key.  Here log(u_i) / l_i stands for
+    the key (log is increasing and P_i is l_i times a positive constant, so the order is the same).
+    Points of weight 0 are never drawn: they follow all others, in increasing index; NaN scores
+    come last.
+    """
+    sc = np.asarray(scores, dtype=np.float64)
+    w = _sampling_weights(sc)
+    with np.errstate(divide="ignore"):
+        key = np.where(w > 0.0, np.log(u) / np.where(w > 0.0, w, 1.0), -np.inf)
+    key = np.where(np.isnan(sc), np.nan, key)
+    return order_dec(key)
+
+
+def order_swor(scores, seed):
+    """Policy "dec, swor" with the seeded uniforms of ``sample_uniforms``."""
+    return order_swor_from_uniforms(scores, sample_uniforms(np.asarray(scores).shape[0], seed))
+
+
+def order_swr_from_uniforms(scores, u):
+    """Policy "dec, swr" (Sec. 5.2; Algorithm 4 step 4): n successive draws with replacement from P,
+    in draw order (points can repeat; points of small P may never appear).  Draw t is the smallest
+    index i whose cumulative weight C_i = l_0 + ... + l_i exceeds u_t C_{n-1} (inverse CDF)."""
+    C = np.cumsum(_sampling_weights(scores))
+    if C.size == 0 or not C[-1] > 0.0:
+        raise ValueError("sampling with replacement needs a positive total score")
+    return np.searchsorted(C, np.asarray(u) * C[-1], side="right").astype(np.int64)
+
+
+def order_swr(scores, seed):
+    """Policy "dec, swr" with the seeded uniforms of ``sample_uniforms``."""
+    return order_swr_from_uniforms(scores, sample_uniforms(np.asarray(scores).shape[0], seed))
