@@ -453,9 +453,11 @@ def order_dec(scores):
     -0 and +0 compare equal.  A stable sort of the negated scores.
     """
     sc = np.asarray(scores, dtype=np.float64)
-    key = np.where(np.isnan(sc), np.inf, -sc)
+    nan = np.isnan(sc)
+    key = np.where(nan, 0.0, -sc)
     key = np.where(key == 0.0, 0.0, key)
-    return np.argsort(key, kind="stable").astype(np.int64)
+    # stable: NaN after every number (-inf included), then decreasing score, ties by index
+    return np.lexsort((key, nan)).astype(np.int64)
 
 
 def sampling_probabilities(scores):

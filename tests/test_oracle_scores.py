@@ -225,7 +225,8 @@ def test_jl_scores_are_unbiased():
 
 # ---------------------------------------------------------------- ordering
 def test_order_dec_matches_brute_force_sort():
-    vals = [0.5, 0.1, float("nan"), 0.5, -0.0, 0.0, 0.9, 0.1, float("nan"), 1e-30]
+    vals = [0.5, 0.1, float("nan"), 0.5, -0.0, 0.0, 0.9, 0.1, float("nan"), 1e-30, -math.inf, math.inf,
+            -math.inf]
     want = sorted(range(len(vals)), key=lambda i: (math.isnan(vals[i]), -vals[i] if not math.isnan(vals[i]) else 0, i))
     assert O.order_dec(np.array(vals)).tolist() == want
     assert O.order_dec(np.full(7, 0.25)).tolist() == list(range(7))
