@@ -61,6 +61,9 @@ typedef enum { SLSO_F64 = 0, SLSO_F32 = 1, SLSO_BF16 = 2, SLSO_FP8_E4M3 = 3 } sl
  *               rounding decided on the float64 value. */
 typedef enum { SLSO_COUNTSKETCH = 0, SLSO_SRHT = 1, SLSO_GAUSSIAN = 2 } slso_sketch_kind;
 
+/* Sampling policies of Algorithm 4 step 4 (Sec. 5.2) on P = scores / sum(scores). */
+typedef enum { SLSO_POLICY_DEC = 0, SLSO_POLICY_SWR = 1, SLSO_POLICY_SWOR = 2 } slso_policy;
+
 typedef struct slso_handle slso_handle;
 
 typedef struct {
@@ -135,6 +138,23 @@ slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t
  * LSD radix argsort on the 32-bit (F32 scores) or 64-bit (F64 scores) orderable key. */
 slso_status slso_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
                        int64_t* order, void* stream);
+
+/* Orderings of Algorithm 4 step 4 (Sec. 5.2) from the scores (device, F32 or F64, n of
+ * them) into order[0..n) (device, int64), on the given stream; seed selects the draws (one
+ * seed per training epoch).  Weights are the scores; NaN, infinite or negative scores weigh 0.
+ *   SLSO_POLICY_DEC   the "dec" order, exactly as slso_order (seed unused).
+ *   SLSO_POLICY_SWOR  "dec, swor": the order of n successive draws without replacement, each
+ *                     point drawn with probability proportional to its score among those not
+ *                     yet drawn (Efraimidis-Spirakis keys log(u_i)/l_i sorted decreasingly).
+ *                     Weight-0 points follow all others in increasing index, NaN scores last.
+ *   SLSO_POLICY_SWR   "dec, swr": n draws with replacement, in draw order: draw t is the
+ *                     smallest i whose cumulative score exceeds u_t times the total (points
+ *                     can repeat).  When no score is positive and finite every entry is -1.
+ * u_t = (m + 1/2) 2^-52, m = w0 2^20 + (w1 >> 12) from Philox4x32-10 at counter
+ * (lo t, hi t, 0, 6) with key seed.  Scratch from the handle's pool.
+ * Errors: INVALID_ARG (NULL pointers, unknown policy), SHAPE (n < 1 or n >= 2^31), DTYPE. */
+slso_status slso_sample_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
+                              int32_t policy, uint64_t seed, int64_t* order, void* stream);
 
 /* End-to-end call with HOST buffers: copies X_host (pinned or pageable) to the device,
  * runs slso_leverage + slso_order, copies scores (float32, or float64 for F64 compute)

@@ -15,13 +15,14 @@ STATUS_NAMES = {
 F64, F32, BF16, FP8_E4M3 = 0, 1, 2, 3
 COUNTSKETCH, SRHT, GAUSSIAN = 0, 1, 2
 KIND = {"countsketch": COUNTSKETCH, "srht": SRHT, "gaussian": GAUSSIAN}
+POLICY = {"dec": 0, "swr": 1, "swor": 2}
 DTYPE = {"f64": F64, "f32": F32, "bf16": BF16, "fp8": FP8_E4M3}
 
 # Every symbol include/slso.h declares.
 EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
     "slso_sketch", "slso_sketched_svd", "slso_leverage", "slso_order", "slso_rank_rows_host",
-    "slso_profile", "slso_profile_read", "slso_order_static",
+    "slso_profile", "slso_profile_read", "slso_order_static", "slso_sample_order",
     "slso_server_create", "slso_server_destroy", "slso_server_submit", "slso_server_poll", "slso_server_stats",
 )
 JOB_LEVERAGE, JOB_SKETCHED_SVD = 0, 1
@@ -87,6 +88,7 @@ def load():
         "slso_rank_rows_host": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), vp, vp,
                                  ctypes.POINTER(Info), vp], i32),
         "slso_order_static": ([vp, i32, i64, vp, vp], i32),
+        "slso_sample_order": ([vp, vp, i32, i64, i32, ctypes.c_uint64, vp, vp], i32),
         "slso_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], i32),
         "slso_server_destroy": ([vp], i32),
         "slso_server_submit": ([vp, ctypes.POINTER(Job), ctypes.POINTER(i64)], i32),

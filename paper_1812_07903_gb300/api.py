@@ -142,6 +142,22 @@ def order(scores, out=None, handle=None):
     return o
 
 
+def sample_order(scores, policy="swor", seed=0, out=None, handle=None):
+    """slso_sample_order: the "dec", "swr" or "swor" ordering (Algorithm 4 step 4) of a score vector."""
+    h = handle or default_handle()
+    _require_cuda(scores)
+    if scores.dtype not in (torch.float32, torch.float64) or not scores.is_contiguous():
+        raise TypeError("scores must be a contiguous float32/float64 CUDA tensor")
+    if policy not in L.POLICY:
+        raise ValueError(f"policy must be one of {sorted(L.POLICY)}")
+    n = scores.numel()
+    o = out if out is not None else torch.empty(n, dtype=torch.int64, device=scores.device)
+    sdt = L.F32 if scores.dtype == torch.float32 else L.F64
+    L.check(L.load().slso_sample_order(h.ptr, scores.data_ptr(), sdt, n, L.POLICY[policy], seed, o.data_ptr(),
+                                       _stream()))
+    return o
+
+
 def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
                    compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None):
     """slso_rank_rows_host: scores and order from a HOST matrix (copies inside the call)."""

@@ -193,6 +193,24 @@ extern "C" slso_status slso_order(slso_handle* handle, const void* scores, int32
   });
 }
 
+extern "C" slso_status slso_sample_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
+                                         int32_t policy, uint64_t seed, int64_t* order, void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (!scores || !order) return fail(SLSO_ERR_INVALID_ARG, "scores and order must be non-NULL");
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "need 1 <= n < 2^31");
+  if (sdt != SLSO_F32 && sdt != SLSO_F64) return fail(SLSO_ERR_DTYPE, "scores must be F32 or F64");
+  if (policy != SLSO_POLICY_DEC && policy != SLSO_POLICY_SWR && policy != SLSO_POLICY_SWOR)
+    return fail(SLSO_ERR_INVALID_ARG, "unknown sampling policy %d", policy);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return run_plan(*h, [&](Arena& ar) {
+    prof_begin(*h, ar, ST_ORDER, st);
+    SLSO_TRY(sample_order(*h, ar, scores, sdt, n, policy, seed, order, st));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  });
+}
+
 extern "C" slso_status slso_rank_rows_host(slso_handle* handle, const void* X_host, int64_t n, int64_t d,
                                            int64_t ldx, int32_t xdt, const slso_params* params,
                                            void* scores_host, int64_t* order_host, slso_info* info,
