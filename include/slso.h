@@ -139,6 +139,20 @@ slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t
 slso_status slso_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
                        int64_t* order, void* stream);
 
+/* The end-to-end call of slso_rank_rows_host for `count` host matrices of the same shape and
+ * type (X_host[i], scores_host[i], order_host[i]; info[i] when info is non-NULL), pipelined:
+ * item i+1's host-to-device copy and item i-1's device-to-host copies run on two internal
+ * streams while item i computes on `stream`, with two device buffers for X and for the
+ * outputs.  Every kernel runs on `stream`, in item order.  Synchronous: returns when every
+ * output is in host memory.  Host buffers should be pinned for the copies to overlap.
+ * Errors: as slso_rank_rows_host, checked for every item before anything is launched; a
+ * device-side condition (timeout, non-finite X) is reported for the first item it hit, after
+ * every item has run. */
+slso_status slso_rank_rows_host_batch(slso_handle* handle, int64_t count, const void* const* X_host,
+                                      int64_t n, int64_t d, int64_t ldx, int32_t xdt,
+                                      const slso_params* params, void* const* scores_host,
+                                      int64_t* const* order_host, slso_info* info, void* stream);
+
 /* Orderings of Algorithm 4 step 4 (Sec. 5.2) from the scores (device, F32 or F64, n of
  * them) into order[0..n) (device, int64), on the given stream; seed selects the draws (one
  * seed per training epoch).  Weights are the scores; NaN, infinite or negative scores weigh 0.

@@ -23,6 +23,7 @@ EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
     "slso_sketch", "slso_sketched_svd", "slso_leverage", "slso_order", "slso_rank_rows_host",
     "slso_profile", "slso_profile_read", "slso_order_static", "slso_sample_order",
+    "slso_rank_rows_host_batch",
     "slso_server_create", "slso_server_destroy", "slso_server_submit", "slso_server_poll", "slso_server_stats",
 )
 JOB_LEVERAGE, JOB_SKETCHED_SVD = 0, 1
@@ -89,6 +90,7 @@ def load():
                                  ctypes.POINTER(Info), vp], i32),
         "slso_order_static": ([vp, i32, i64, vp, vp], i32),
         "slso_sample_order": ([vp, vp, i32, i64, i32, ctypes.c_uint64, vp, vp], i32),
+        "slso_rank_rows_host_batch": ([vp, i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp], i32),
         "slso_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], i32),
         "slso_server_destroy": ([vp], i32),
         "slso_server_submit": ([vp, ctypes.POINTER(Job), ctypes.POINTER(i64)], i32),

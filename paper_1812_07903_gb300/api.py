@@ -176,6 +176,34 @@ def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0,
     return sc, od, info.as_dict()
 
 
+def rank_rows_host_batch(X_hosts, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
+                         compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None):
+    """slso_rank_rows_host_batch: rank_rows_host over a list of same-shaped HOST matrices, with the
+    copies of one item overlapped with the computation of its neighbours.  Returns lists of
+    (scores, order) host tensors and the per-item info dicts."""
+    h = handle or default_handle()
+    if not X_hosts:
+        raise ValueError("X_hosts must hold at least one matrix")
+    X0 = X_hosts[0]
+    for X in X_hosts:
+        if (X.is_cuda or X.dim() != 2 or X.dtype not in _XDT or X.stride(1) != 1 or X.shape != X0.shape
+                or X.dtype != X0.dtype or X.stride(0) != X0.stride(0)):
+            raise TypeError("X_hosts must be 2-D row-contiguous host tensors of one shape, dtype and row stride")
+    cnt = len(X_hosts)
+    n, d = X0.shape
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+    sdt = torch.float64 if compute == "f64" else torch.float32
+    sc = scores_out or [torch.empty(n, dtype=sdt) for _ in range(cnt)]
+    od = order_out or [torch.empty(n, dtype=torch.int64) for _ in range(cnt)]
+    xs = (ctypes.c_void_p * cnt)(*[X.data_ptr() for X in X_hosts])
+    ss = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in sc])
+    os_ = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in od])
+    infos = (L.Info * cnt)()
+    L.check(L.load().slso_rank_rows_host_batch(h.ptr, cnt, xs, n, d, X0.stride(0), _XDT[X0.dtype], ctypes.byref(p),
+                                               ss, os_, infos, _stream()))
+    return sc, od, [i.as_dict() for i in infos]
+
+
 def profile(enable=True, handle=None):
     """slso_profile: start (or stop) per-stage event timing on the handle."""
     h = handle or default_handle()

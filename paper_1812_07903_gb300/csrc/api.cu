@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <vector>
+
 #include "common.cuh"
 
 using namespace slso;
@@ -191,6 +193,137 @@ extern "C" slso_status slso_order(slso_handle* handle, const void* scores, int32
     prof_end(*h, ar, st);
     return SLSO_OK;
   });
+}
+
+extern "C" slso_status slso_rank_rows_host_batch(slso_handle* handle, int64_t count, const void* const* X_host,
+                                                 int64_t n, int64_t d, int64_t ldx, int32_t xdt,
+                                                 const slso_params* params, void* const* scores_host,
+                                                 int64_t* const* order_host, slso_info* info, void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (count < 1 || !X_host || !scores_host || !order_host)
+    return fail(SLSO_ERR_INVALID_ARG, "need count >= 1 and non-NULL pointer arrays");
+  for (int64_t i = 0; i < count; ++i) {
+    SLSO_TRY(check_x(X_host[i], n, d, ldx, xdt));
+    if (!scores_host[i] || !order_host[i]) return fail(SLSO_ERR_INVALID_ARG, "item %lld: NULL output", (long long)i);
+  }
+  SLSO_TRY(check_params(params, n, d));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t esz = dtype_size(xdt);
+  const int32_t sdt = params->compute == SLSO_F64 ? SLSO_F64 : SLSO_F32;
+  const size_t ssz = dtype_size(sdt);
+  const size_t xbytes = static_cast<size_t>(n) * d * esz;
+
+  // fixed buffers (two of each: item i uses set i % 2) and one scratch region reused per item
+  char* Xd[2] = {};
+  char* sc[2] = {};
+  int64_t* od[2] = {};
+  DevState* states = nullptr;
+  auto take_fixed = [&](Arena& ar) {
+    for (int b = 0; b < 2; ++b) {
+      Xd[b] = ar.take<char>(xbytes);
+      sc[b] = ar.take<char>(static_cast<size_t>(n) * ssz);
+      od[b] = ar.take<int64_t>(n);
+    }
+    states = ar.take<DevState>(count);
+  };
+  auto item = [&](Arena& ar, int b) -> slso_status {
+    SLSO_TRY(leverage_plan(*h, ar, Xd[b], n, d, d, xdt, params, sc[b], st));
+    prof_begin(*h, ar, ST_ORDER, st);
+    SLSO_TRY(order_scores(*h, ar, sc[b], sdt, n, od[b], st));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  };
+  Arena mf(nullptr, ~size_t(0), true);
+  take_fixed(mf);
+  const size_t scratch_off = (mf.used() + 255) & ~size_t(255);
+  Arena mi(nullptr, ~size_t(0), true);
+  SLSO_TRY(item(mi, 0));
+  SLSO_TRY(ensure_pool(*h, scratch_off + mi.used()));
+  Arena real(h->pool, h->pool_cap, false);
+  take_fixed(real);
+
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev[9] = {};  // start, xready[2], xfree[2], oready[2], ofree[2]
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (h2d) cudaStreamDestroy(h2d);
+    if (d2h) cudaStreamDestroy(d2h);
+  };
+  auto go = [&]() -> slso_status {
+    SLSO_CHECK_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
+    SLSO_CHECK_CUDA(cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : ev) SLSO_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t start = ev[0], *xready = ev + 1, *xfree = ev + 3, *oready = ev + 5, *ofree = ev + 7;
+    // the copies may not start before earlier work on the caller's stream (it may use the pool)
+    SLSO_CHECK_CUDA(cudaEventRecord(start, st));
+    SLSO_CHECK_CUDA(cudaStreamWaitEvent(h2d, start, 0));
+    SLSO_CHECK_CUDA(cudaStreamWaitEvent(d2h, start, 0));
+    auto copy_in = [&](int64_t i) -> slso_status {
+      const int b = static_cast<int>(i & 1);
+      if (ldx == d) SLSO_CHECK_CUDA(cudaMemcpyAsync(Xd[b], X_host[i], xbytes, cudaMemcpyHostToDevice, h2d));
+      else
+        SLSO_CHECK_CUDA(cudaMemcpy2DAsync(Xd[b], d * esz, X_host[i], ldx * esz, d * esz, n, cudaMemcpyHostToDevice, h2d));
+      SLSO_CHECK_CUDA(cudaEventRecord(xready[b], h2d));
+      return SLSO_OK;
+    };
+    SLSO_TRY(copy_in(0));
+    if (count > 1) SLSO_TRY(copy_in(1));
+    for (int64_t i = 0; i < count; ++i) {
+      const int b = static_cast<int>(i & 1);
+      SLSO_CHECK_CUDA(cudaStreamWaitEvent(st, xready[b], 0));
+      if (i >= 2) SLSO_CHECK_CUDA(cudaStreamWaitEvent(st, ofree[b], 0));
+      SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+      Arena sub(h->pool + scratch_off, h->pool_cap - scratch_off, false);
+      SLSO_TRY(item(sub, b));
+      if (sub.overflow()) return fail(SLSO_ERR_OOM, "internal: scratch plan overflowed the pool");
+      SLSO_CHECK_CUDA(cudaMemcpyAsync(states + i, h->state, sizeof(DevState), cudaMemcpyDeviceToDevice, st));
+      SLSO_CHECK_CUDA(cudaEventRecord(xfree[b], st));
+      SLSO_CHECK_CUDA(cudaEventRecord(oready[b], st));
+      if (i + 2 < count) {
+        SLSO_CHECK_CUDA(cudaStreamWaitEvent(h2d, xfree[b], 0));
+        SLSO_TRY(copy_in(i + 2));
+      }
+      SLSO_CHECK_CUDA(cudaStreamWaitEvent(d2h, oready[b], 0));
+      SLSO_CHECK_CUDA(cudaMemcpyAsync(scores_host[i], sc[b], static_cast<size_t>(n) * ssz, cudaMemcpyDeviceToHost, d2h));
+      SLSO_CHECK_CUDA(cudaMemcpyAsync(order_host[i], od[b], static_cast<size_t>(n) * sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, d2h));
+      SLSO_CHECK_CUDA(cudaEventRecord(ofree[b], d2h));
+    }
+    // the caller's stream completes after the last copy out
+    SLSO_CHECK_CUDA(cudaEventRecord(start, d2h));
+    SLSO_CHECK_CUDA(cudaStreamWaitEvent(st, start, 0));
+    SLSO_CHECK_CUDA(cudaStreamSynchronize(st));
+    std::vector<DevState> hs(static_cast<size_t>(count));
+    SLSO_CHECK_CUDA(cudaMemcpy(hs.data(), states, sizeof(DevState) * count, cudaMemcpyDeviceToHost));
+    slso_status first_err = SLSO_OK;
+    for (int64_t i = 0; i < count; ++i) {
+      const DevState& ds = hs[static_cast<size_t>(i)];
+      if (info) {
+        info[i].rank = ds.rank;
+        info[i].sigma_max = ds.sigma_max;
+        info[i].sigma_min_kept = ds.sigma_min_kept;
+        info[i].score_sum = ds.score_sum;
+        info[i].tau = ds.tau;
+        info[i].nonfinite = ds.nonfinite;
+        info[i].svd_route = ds.need_svd;
+      }
+      if (first_err == SLSO_OK && ds.timeout)
+        first_err = fail(SLSO_ERR_TIMEOUT, "item %lld: a bounded device wait gave up (kernel %d)", (long long)i, ds.timeout);
+      if (first_err == SLSO_OK && ds.nonfinite)
+        first_err = fail(SLSO_ERR_NONFINITE, "item %lld: X holds NaN or Inf", (long long)i);
+    }
+    return first_err;
+  };
+  const slso_status r = go();
+  if (r != SLSO_OK) {  // nothing issued may still use the pool, the host buffers or the events
+    cudaStreamSynchronize(st);
+    if (h2d) cudaStreamSynchronize(h2d);
+    if (d2h) cudaStreamSynchronize(d2h);
+  }
+  cleanup();
+  return r;
 }
 
 extern "C" slso_status slso_sample_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,

@@ -232,6 +232,21 @@ def test_host_entry_point_matches_device_entry_points():
     assert info["rank"] == 48
 
 
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_host_batch_entry_point_matches_item_by_item(count):
+    """The pipelined host batch gives, item by item, what the device entry points give (same
+    kernels on one stream), including a host row stride larger than d and per-item info."""
+    Xs = [inputs.lognormal_rows(3000, 50, seed=100 + i, dtype=torch.float32) for i in range(count)]
+    Xh = [X.pin_memory()[:, :47] for X in Xs]  # ldx = 50, d = 47
+    scs, ods, infos = api.rank_rows_host_batch(Xh, "countsketch", 512, 16, 7, 8, compute="f32")
+    for i in range(count):
+        sc_d, info = api.leverage(_dev(Xs[i])[:, :47], "countsketch", 512, 16, 7, 8, compute="f32")
+        assert torch.equal(scs[i], sc_d.cpu())
+        assert torch.equal(ods[i], api.order(sc_d).cpu())
+        assert infos[i]["rank"] == info["rank"] == 47
+        assert infos[i]["score_sum"] == info["score_sum"]
+
+
 # ------------------------------------------------------------------ tensor-core scores
 @pytest.mark.parametrize("n,d,k", [(70, 16, 256), (1000, 100, 48), (12345, 320, 128), (4096, 1024, 16)])
 def test_tensor_core_float32_scores_match_oracle(n, d, k):
