@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
   __shared__ double s_alpha;
   __shared__ double s_coef[2];  // g, 1/den of the staged reflector (written before arming full[0])
   __shared__ double s_scalar;   // warp 0's result of a reduction
+  __shared__ double s_form[2];  // den and R_cc of the reflector being formed
   __shared__ int s_abort;       // hint only: lets waits give up early once a wait or stage failed
   const int G = gridDim.x, tid = threadIdx.x, t2 = 2 * threadIdx.x, lane = threadIdx.x & 31;
   for (int i = lda + tid; i < VROWS; i += kQrlThreads) vsm[i] = 0.0;  // never written by a copy
@@ -416,45 +417,55 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       }
     }
     // reflector c: beta = -sign(alpha) ||(alpha, x)||, tau = (beta - alpha) / beta; no
-    // reflection when the subcolumn below the diagonal is exactly zero
+    // reflection when the subcolumn below the diagonal is exactly zero.  The vector's rows
+    // (zeros above row c, the subcolumn below it) do not depend on the scalars, so they are
+    // stored first; one thread forms the scalars (tau / den = -1 / beta, 1 / den, den) while
+    // the stores drain, and R's column is written after the announcement (it is read only
+    // after the kernel).
     red[tid] = x0 + x1;
-    __syncthreads();
-    if (tid < 32) {
-      const double xn2 = warp0_sum256(red);
-      if (lane == 0) s_scalar = xn2;
-    }
-    __syncthreads();
-    const double xn2 = s_scalar, alpha = s_alpha;
-    double g = 0.0, inv = 0.0, den = 0.0, rcc = alpha;
-    if (xn2 != 0.0) {
-      const double norm = sqrt(alpha * alpha + xn2);
-      const double beta = alpha >= 0.0 ? -norm : norm;
-      const double tau = (beta - alpha) / beta;
-      den = alpha - beta;
-      inv = 1.0 / den;
-      g = tau * inv;
-      rcc = beta;
-    }
-    double* rcol = Rc + static_cast<int64_t>(c) * d;
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int i = 2 * kQrlThreads * q + t2;
       if (i < lda) {
         double2 v;
-        v.x = (i < c) ? 0.0 : (i == c ? den : a[2 * q]);
-        v.y = (i + 1 < c) ? 0.0 : (i + 1 == c ? den : a[2 * q + 1]);
-        *reinterpret_cast<double2*>(col + i) = v;
-        if (i <= c) rcol[i] = (i == c) ? rcc : a[2 * q];
-        if (i + 1 <= c) rcol[i + 1] = (i + 1 == c) ? rcc : a[2 * q + 1];
+        v.x = (i < c) ? 0.0 : a[2 * q];
+        v.y = (i + 1 < c) ? 0.0 : a[2 * q + 1];
+        *reinterpret_cast<double2*>(col + i) = v;  // row c is rewritten with den below
       }
     }
-    if (tid == 0) {
-      coef[4 * c] = g;
-      coef[4 * c + 1] = inv;
+    __syncthreads();
+    if (tid < 32) {
+      const double xn2 = warp0_sum256(red);
+      if (lane == 0) {
+        const double alpha = s_alpha;
+        double g = 0.0, inv = 0.0, den = 0.0, rcc = alpha;
+        if (xn2 != 0.0) {
+          const double norm = sqrt(alpha * alpha + xn2);
+          const double beta = alpha >= 0.0 ? -norm : norm;
+          den = alpha - beta;
+          inv = 1.0 / den;
+          g = -1.0 / beta;
+          rcc = beta;
+        }
+        s_form[0] = den;
+        s_form[1] = rcc;
+        coef[4 * c] = g;
+        coef[4 * c + 1] = inv;
+      }
     }
+    __syncthreads();
+    if (t2 == (c & (2 * kQrlThreads - 1)) - (c & 1)) col[c] = s_form[0];  // the thread holding row c
     __threadfence();
     __syncthreads();
     if (tid == 0) atomicExch(&ready[c], 1);
+    double* rcol = Rc + static_cast<int64_t>(c) * d;
+    const double rcc = s_form[1];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int i = 2 * kQrlThreads * q + t2;
+      if (i <= c) rcol[i] = (i == c) ? rcc : a[2 * q];
+      if (i + 1 <= c) rcol[i + 1] = (i + 1 == c) ? rcc : a[2 * q + 1];
+    }
   }
 }
 
