@@ -260,7 +260,8 @@ __device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2,
 }
 
 // Per-column coefficients of the unscaled reflectors: coef[4c] = g = tau/den (0: H_c = I),
-// coef[4c+1] = 1/den.  Dynamic shared memory: 2 * kQrlThreads * (RPT/2) doubles.
+// coef[4c+1] = g/den, so that applying reflector j is x -= ((u_j^T x) g/den) u_j.
+// Dynamic shared memory: 2 * kQrlThreads * (RPT/2) doubles.
 template <int RPT>
 __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restrict__ A, int s, int lda, int d,
                                                                  double* __restrict__ Rc,
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
   __shared__ __align__(8) uint64_t full[2];
   __shared__ __align__(8) uint64_t empty[2];
   __shared__ double s_alpha;
-  __shared__ double s_coef[2];  // g, 1/den of the staged reflector (written before arming full[0])
+  __shared__ double s_coef[2];  // g, g/den of the staged reflector (written before arming full[0])
   __shared__ double s_scalar;   // warp 0's result of a reduction
   __shared__ double s_form[2];  // den and R_cc of the reflector being formed
   __shared__ int s_abort;       // hint only: lets waits give up early once a wait or stage failed
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
         *abort_flag = 1;
       }
       // the same bits in every thread: written once by thread 0 before it armed full[0]
-      const double g = s_coef[0], inv = s_coef[1];
+      const double g = s_coef[0], ginv = s_coef[1];
       double p0 = 0.0, p1 = 0.0;
       if (g != 0.0) dot_pairs<0, QA>(a, vsm, t2, p0, p1);
       if (!mbar_wait_bounded(&full[1], par, abort_flag)) {
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       if (g != 0.0) {
         if (tid < 32) {
           const double sum = warp0_sum256(red);
-          if (lane == 0) s_scalar = g * (sum * inv);
+          if (lane == 0) s_scalar = sum * ginv;
         }
         __syncthreads();
         const double tc = s_scalar;
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
         s_form[0] = den;
         s_form[1] = rcc;
         coef[4 * c] = g;
-        coef[4 * c + 1] = inv;
+        coef[4 * c + 1] = g * inv;
       }
     }
     __syncthreads();
