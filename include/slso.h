@@ -45,7 +45,8 @@ typedef enum {
   SLSO_ERR_NONFINITE = 6,   /* input held NaN or Inf (reported through slso_info)    */
   SLSO_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up                    */
   SLSO_ERR_BUSY = 8,        /* serving: no slot or memory free for the job           */
-  SLSO_ERR_NOT_FOUND = 9    /* serving: unknown ticket                               */
+  SLSO_ERR_NOT_FOUND = 9,   /* serving: unknown ticket                               */
+  SLSO_ERR_CANCELLED = 10   /* serving: the job was cancelled before it was admitted */
 } slso_status;
 
 typedef enum { SLSO_F64 = 0, SLSO_F32 = 1, SLSO_BF16 = 2, SLSO_FP8_E4M3 = 3 } slso_dtype;
@@ -215,6 +216,10 @@ slso_status slso_server_submit(slso_server* server, const slso_job* job, int64_t
  * A finished job is forgotten once polled. */
 slso_status slso_server_poll(slso_server* server, int64_t ticket, int timeout_ms, slso_status* job_status,
                              slso_info* info, double* times_ms);
+/* Cancels a job that is still queued (not yet admitted): it finishes with SLSO_ERR_CANCELLED,
+ * which slso_server_poll reports.  BUSY when the job is already running or finished,
+ * NOT_FOUND for an unknown or collected ticket. */
+slso_status slso_server_cancel(slso_server* server, int64_t ticket);
 /* counters[0..3] = {submitted, admitted, completed, queued}; bytes of scratch in use. */
 slso_status slso_server_stats(slso_server* server, int64_t* counters, size_t* mem_in_use);
 
@@ -232,6 +237,19 @@ slso_status slso_server_stats(slso_server* server, int64_t* counters, size_t* me
  * array, so calls that can overlap on the GPU (different streams, no ordering between them)
  * race and must be serialised by the caller; nothing in the array needs to start at zero. */
 slso_status slso_order_static(const void* scores, int32_t sdt, int64_t n, int64_t* order, void* stream);
+
+/* Caps the handle's device pool at `bytes` (0: no cap).  A call whose scratch would need more
+ * fails with SLSO_ERR_OOM before launching anything, as a real allocation failure does; lowering
+ * the cap below the current pool frees nothing until the pool next grows.  Used to give a
+ * caller a fixed footprint and to exercise allocation-failure paths. */
+slso_status slso_set_pool_limit(slso_handle* handle, size_t bytes);
+
+/* Self-test of the bounded device-side waits every kernel relies on (no GPU fault involved):
+ * what = 0 runs the ready-flag wait of the QR on a flag that nothing sets, what = 1 the
+ * mbarrier wait of the tensor-core kernels on a barrier that nothing completes, each limited to
+ * about limit_us microseconds (1 .. 10^7).  The expected outcome is SLSO_ERR_TIMEOUT after the
+ * limit, with the CUDA context still usable; SLSO_OK would mean the wait did not run out. */
+slso_status slso_selftest_wait(slso_handle* handle, int32_t what, int64_t limit_us, void* stream);
 
 /* Instrumentation (no counterpart in the paper).  slso_profile(h, 1) resets and starts
  * recording a CUDA event pair around every stage each call enqueues on its stream:

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libslso.so")
 SLSO_OK = 0
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "DTYPE", 4: "OOM", 5: "CUDA",
-    6: "NONFINITE", 7: "TIMEOUT", 8: "BUSY", 9: "NOT_FOUND",
+    6: "NONFINITE", 7: "TIMEOUT", 8: "BUSY", 9: "NOT_FOUND", 10: "CANCELLED",
 }
 F64, F32, BF16, FP8_E4M3 = 0, 1, 2, 3
 COUNTSKETCH, SRHT, GAUSSIAN = 0, 1, 2
@@ -23,7 +23,7 @@ EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
     "slso_sketch", "slso_sketched_svd", "slso_leverage", "slso_order", "slso_rank_rows_host",
     "slso_profile", "slso_profile_read", "slso_order_static", "slso_sample_order",
-    "slso_rank_rows_host_batch",
+    "slso_rank_rows_host_batch", "slso_set_pool_limit", "slso_selftest_wait", "slso_server_cancel",
     "slso_server_create", "slso_server_destroy", "slso_server_submit", "slso_server_poll", "slso_server_stats",
 )
 JOB_LEVERAGE, JOB_SKETCHED_SVD = 0, 1
@@ -91,6 +91,9 @@ def load():
         "slso_order_static": ([vp, i32, i64, vp, vp], i32),
         "slso_sample_order": ([vp, vp, i32, i64, i32, ctypes.c_uint64, vp, vp], i32),
         "slso_rank_rows_host_batch": ([vp, i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp], i32),
+        "slso_set_pool_limit": ([vp, ctypes.c_size_t], i32),
+        "slso_selftest_wait": ([vp, i32, i64, vp], i32),
+        "slso_server_cancel": ([vp, i64], i32),
         "slso_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], i32),
         "slso_server_destroy": ([vp], i32),
         "slso_server_submit": ([vp, ctypes.POINTER(Job), ctypes.POINTER(i64)], i32),

@@ -204,6 +204,19 @@ def rank_rows_host_batch(X_hosts, kind="countsketch", s=None, k=0, seed_S=0, see
     return sc, od, [i.as_dict() for i in infos]
 
 
+def set_pool_limit(nbytes, handle=None):
+    """slso_set_pool_limit: cap the handle's device pool (0: no cap); larger calls fail with OOM."""
+    h = handle or default_handle()
+    L.check(L.load().slso_set_pool_limit(h.ptr, int(nbytes)))
+
+
+def selftest_wait(what="flag", limit_us=2000, handle=None):
+    """slso_selftest_wait: run a bounded device wait that nothing signals; raises SlsoError(TIMEOUT)."""
+    h = handle or default_handle()
+    code = {"flag": 0, "mbarrier": 1}[what]
+    L.check(L.load().slso_selftest_wait(h.ptr, code, int(limit_us), _stream()))
+
+
 def profile(enable=True, handle=None):
     """slso_profile: start (or stop) per-stage event timing on the handle."""
     h = handle or default_handle()
@@ -273,6 +286,10 @@ class Server:
                                           ctypes.byref(info), times))
         outs = self._keep.pop(ticket)
         return st.value, info.as_dict(), list(times), outs[1:]
+
+    def cancel(self, ticket):
+        """slso_server_cancel: cancel a job still waiting for admission (poll then reports CANCELLED)."""
+        L.check(L.load().slso_server_cancel(self._s, int(ticket)))
 
     def stats(self):
         c = (ctypes.c_int64 * 4)()

@@ -94,6 +94,7 @@ struct Handle {
   int num_sms = 0;
   char* pool = nullptr;
   size_t pool_cap = 0;
+  size_t pool_limit = 0;           // 0: no cap (slso_set_pool_limit)
   DevState* state = nullptr;       // device
   DevState* state_host = nullptr;  // pinned mirror for info
   bool prof = false;

@@ -41,6 +41,8 @@ slso_status fail(slso_status st, const char* fmt, ...) {
 
 slso_status ensure_pool(Handle& h, size_t bytes) {
   if (bytes <= h.pool_cap) return SLSO_OK;
+  if (h.pool_limit && bytes > h.pool_limit)
+    return fail(SLSO_ERR_OOM, "scratch of %zu bytes exceeds the pool limit of %zu bytes", bytes, h.pool_limit);
   // Growing frees the old block; cudaFree waits for work in flight on the device.
   if (h.pool) {
     SLSO_CHECK_CUDA(cudaFree(h.pool));
@@ -116,6 +118,13 @@ extern "C" slso_status slso_destroy(slso_handle* handle) {
   if (h->state) cudaFree(h->state);
   if (h->state_host) cudaFreeHost(h->state_host);
   delete h;
+  return SLSO_OK;
+}
+
+extern "C" slso_status slso_set_pool_limit(slso_handle* handle, size_t bytes) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  h->pool_limit = bytes;
   return SLSO_OK;
 }
 

@@ -313,6 +313,26 @@ extern "C" slso_status slso_server_poll(slso_server* srv, int64_t ticket, int ti
   return SLSO_OK;
 }
 
+extern "C" slso_status slso_server_cancel(slso_server* srv, int64_t ticket) {
+  if (!srv) return fail(SLSO_ERR_INVALID_ARG, "server is NULL");
+  Server* s = reinterpret_cast<Server*>(srv);
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(ticket);
+  if (it == s->jobs.end()) return fail(SLSO_ERR_NOT_FOUND, "unknown ticket %lld", (long long)ticket);
+  Job* j = it->second;
+  for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+    if (*q != j) continue;
+    s->queue.erase(q);
+    j->status = SLSO_ERR_CANCELLED;
+    j->t_done = now_ms();
+    j->done = true;
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();  // the job behind it may now fit
+    return SLSO_OK;
+  }
+  return fail(SLSO_ERR_BUSY, "job %lld is already %s", (long long)ticket, j->done ? "finished" : "running");
+}
+
 extern "C" slso_status slso_server_stats(slso_server* srv, int64_t* counters, size_t* mem_in_use) {
   if (!srv || !counters) return fail(SLSO_ERR_INVALID_ARG, "server and counters must be non-NULL");
   Server* s = reinterpret_cast<Server*>(srv);
