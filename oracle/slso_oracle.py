@@ -410,6 +410,22 @@ def sketched_leverage(X, kind, s, k, seed_S, seed_Pi, tau=None, qr="loop"):
     return scores, info
 
 
+def approx_u_from_sketch(X, SX, tau=None, qr="loop"):
+    """Approximate left singular vectors (Algorithm 2 step 3; Algorithm 3 step 4 with the
+    transpose read as a typo) from a given sketch: SX = U' Sigma V^T, U = X V_r Sigma_r^-1 for the
+    r retained singular values (n x r).  Returns (U, info dict with rank, sigma, V, tau)."""
+    X = np.asarray(X, dtype=np.float64)
+    sv = sketched_svd(np.asarray(SX, dtype=np.float64), tau, qr)
+    r = sv["rank"]
+    U = X @ (sv["V"][:, :r] / sv["sigma"][:r])
+    return U, {"rank": r, "sigma": sv["sigma"], "V": sv["V"], "tau": sv["tau"]}
+
+
+def approx_u(X, kind, s, seed_S, tau=None, qr="loop"):
+    """``approx_u_from_sketch`` with the seeded sketch of ``sketch``."""
+    return approx_u_from_sketch(X, sketch(np.asarray(X, dtype=np.float64), kind, s, seed_S), tau, qr)
+
+
 def exact_leverage(X, tau=None):
     """Exact leverage scores (Sec. 2.2; Algorithm 1): l_i = ||U_i||^2 over the numerical rank.
 

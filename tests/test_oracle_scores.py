@@ -147,6 +147,32 @@ def test_identity_and_orthogonal_sketch_reproduce_exact_scores():
     np.testing.assert_allclose(sc, l, rtol=1e-9)
 
 
+def test_approx_u_with_identity_sketch_is_the_exact_left_singular_basis():
+    """S = I: U = X V Sigma^-1 are X's left singular vectors (numpy's SVD, up to column signs),
+    orthonormal, and U Sigma V^T = X; with zero columns only r = rank columns are kept."""
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((200, 7)) * np.exp(rng.standard_normal(7))
+    U, info = O.approx_u_from_sketch(X, X)
+    Uw, sw, _ = np.linalg.svd(X, full_matrices=False)
+    assert info["rank"] == 7
+    np.testing.assert_allclose(np.abs(np.sum(U * Uw, axis=0)), 1.0, atol=1e-10)
+    np.testing.assert_allclose(U.T @ U, np.eye(7), atol=1e-10)
+    np.testing.assert_allclose(U * info["sigma"] @ info["V"].T, X, atol=1e-10 * np.abs(X).max())
+    X[:, [1, 4]] = 0.0
+    U, info = O.approx_u_from_sketch(X, X)
+    assert info["rank"] == 5 and U.shape == (200, 5)
+    np.testing.assert_allclose(U.T @ U, np.eye(5), atol=1e-10)
+
+
+@pytest.mark.parametrize("kind", ["countsketch", "gaussian"])
+def test_approx_u_row_norms_are_the_sketched_scores(kind):
+    """||U_i||^2 equals Algorithm 3's score of row i (k = 0, same sketch)."""
+    X = np.random.default_rng(22).standard_normal((3000, 12))
+    U, info = O.approx_u(X, kind, 256, 9)
+    sc, _ = O.sketched_leverage(X, kind, 256, 0, 9, 0)
+    np.testing.assert_allclose(np.sum(U * U, axis=1), sc, rtol=1e-9)
+
+
 @pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian"])
 def test_sketch_of_identity_has_unit_columns_in_expectation(kind):
     n, s = 256, 64
