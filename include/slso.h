@@ -134,6 +134,17 @@ slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t
                           int32_t xdt, const slso_params* params, void* scores, slso_info* info,
                           void* stream);
 
+/* Approximate left singular vectors (Algorithm 2 step 3; Algorithm 3 step 4, read without
+ * the transpose): sketch SX = S X (params: kind, s, seed_S, tau; k, seed_Pi, compute and
+ * correct_frac are not used), sketched SVD SX = U' Sigma V^T (float64 QR + Jacobi SVD of R),
+ * r = #{sigma_j > tau sigma_1}, then U = X V_r Sigma_r^-1.  U is n x d row-major with leading
+ * dimension ldu >= d, float64 for F64 X, float32 otherwise; columns r .. d-1 are zero.  Column j
+ * is defined up to the sign of the singular vector v_j (as for any SVD).  ||U_i||^2 is row i's
+ * score of slso_leverage with k = 0.  Errors as slso_leverage, plus SHAPE for ldu < d. */
+slso_status slso_approx_u(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
+                          int32_t xdt, const slso_params* params, void* U, int64_t ldu, slso_info* info,
+                          void* stream);
+
 /* Policy "dec" of Sec. 5.2 (Algorithm 4 step 4): order[0..n) lists row indices by strictly
  * decreasing score; equal scores (with -0 == +0) by increasing index; NaN last.  A stable
  * LSD radix argsort on the 32-bit (F32 scores) or 64-bit (F64 scores) orderable key. */

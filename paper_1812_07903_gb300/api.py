@@ -129,6 +129,21 @@ def leverage(X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, 
     return scores, (info.as_dict() if want_info else None)
 
 
+def approx_u(X, kind="countsketch", s=None, seed_S=0, tau=-1.0, out=None, handle=None):
+    """slso_approx_u: U = X V_r Sigma_r^-1 from the sketched SVD (n x d; columns >= rank are zero)."""
+    h = handle or default_handle()
+    n, d, ldx, xdt = _x_args(X)
+    p = make_params(kind, s, 0, seed_S, 0, tau, "f32", 0.0)
+    udt = torch.float64 if X.dtype == torch.float64 else torch.float32
+    U = out if out is not None else torch.empty(n, d, dtype=udt, device=X.device)
+    if U.dtype != udt or U.dim() != 2 or U.shape != (n, d) or U.stride(1) != 1:
+        raise TypeError(f"out must be a row-contiguous {udt} tensor of shape ({n}, {d})")
+    info = L.Info()
+    L.check(L.load().slso_approx_u(h.ptr, X.data_ptr(), n, d, ldx, xdt, ctypes.byref(p), U.data_ptr(), U.stride(0),
+                                   ctypes.byref(info), _stream()))
+    return U, info.as_dict()
+
+
 def order(scores, out=None, handle=None):
     """slso_order: the "dec" ordering (int64 row indices) of a float32/float64 score vector."""
     h = handle or default_handle()

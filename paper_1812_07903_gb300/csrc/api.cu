@@ -179,6 +179,22 @@ extern "C" slso_status slso_leverage(slso_handle* handle, const void* X, int64_t
   return SLSO_OK;
 }
 
+extern "C" slso_status slso_approx_u(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
+                                     int32_t xdt, const slso_params* params, void* U, int64_t ldu, slso_info* info,
+                                     void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  SLSO_TRY(check_x(X, n, d, ldx, xdt));
+  SLSO_TRY(check_params(params, n, d));
+  if (!U) return fail(SLSO_ERR_INVALID_ARG, "U is NULL");
+  if (ldu < d) return fail(SLSO_ERR_SHAPE, "ldu=%lld must be >= d=%lld", (long long)ldu, (long long)d);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+  SLSO_TRY(run_plan(*h, [&](Arena& ar) { return approx_u_plan(*h, ar, X, n, d, ldx, xdt, params, U, ldu, st); }));
+  if (info) return fill_info(*h, st, info);
+  return SLSO_OK;
+}
+
 extern "C" slso_status slso_order(slso_handle* handle, const void* scores, int32_t sdt, int64_t n,
                                   int64_t* order, void* stream) {
   Handle* h = nullptr;

@@ -403,6 +403,9 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
 
 // score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
+// Approximate left singular vectors U = X V_r Sigma_r^-1 of the sketched SVD (basis.cu).
+slso_status approx_u_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
+                          const slso_params* p, void* U, int64_t ldu, cudaStream_t st);
 // Orderings of Algorithm 4 step 4 (policy dec, swr or swor) into order (int64, n).
 slso_status sample_order(Handle& h, Arena& ar, const void* scores, int32_t sdt, int64_t n, int32_t policy,
                          uint64_t seed, int64_t* order, cudaStream_t st);
