@@ -432,6 +432,26 @@ def main():
     }
     line["hbm_roofline_frac_whole_step"] = line["hbm_floor_ms"] / ms32
 
+    # ---- approximate left singular vectors (Algorithm 2 step 3) on the same matrix
+    if rank == 0:
+        U = torch.empty(n, d, dtype=torch.float32, device="cuda")
+        api.approx_u(X, kind, s, W["seed_S"], out=U, handle=h)
+        torch.cuda.synchronize()
+        api.profile(True, handle=h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            api.approx_u(X, kind, s, W["seed_S"], out=U, handle=h)
+        e1.record()
+        torch.cuda.synchronize()
+        st_u, _ = api.profile_read(handle=h)
+        api.profile(False, handle=h)
+        ms_u = e0.elapsed_time(e1) / 2
+        line["approx_u"] = {"value": n / (ms_u / 1e3), "unit": "rows/s", "ms_per_call": ms_u,
+                            "output": f"U {n}x{d} float32 ({n * d * 4 / 1e9:.1f} GB)",
+                            "stages_ms_per_call": {nm: round(v_ / 2, 3) for nm, (v_, c) in st_u.items() if c}}
+        del U
+
     # ---- end to end through the host-buffer entry points
     if not args.no_e2e:
         Xh = X.cpu().pin_memory()

@@ -88,6 +88,7 @@ typedef struct {
   double tau;            /* the threshold actually used                                       */
   int32_t nonfinite;     /* 1 if X held NaN or Inf                                            */
   int32_t svd_route;     /* 1: R^+ from the SVD of R; 0: rank d certified, R^+ = R^-1          */
+  int32_t svd_sweeps;    /* one-sided Jacobi sweeps the SVD of R took (0 when it did not run)   */
 } slso_info;
 
 /* Library / handle ------------------------------------------------------------------ */

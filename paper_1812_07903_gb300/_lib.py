@@ -43,7 +43,7 @@ class Info(ctypes.Structure):
     _fields_ = [
         ("rank", ctypes.c_int64), ("sigma_max", ctypes.c_double), ("sigma_min_kept", ctypes.c_double),
         ("score_sum", ctypes.c_double), ("tau", ctypes.c_double), ("nonfinite", ctypes.c_int32),
-        ("svd_route", ctypes.c_int32),
+        ("svd_route", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -84,6 +84,7 @@ slso_status fill_info(Handle& h, cudaStream_t st, slso_info* info) {
   info->tau = d.tau;
   info->nonfinite = d.nonfinite;
   info->svd_route = d.need_svd;
+  info->svd_sweeps = d.sweeps;
   if (d.timeout) return fail(SLSO_ERR_TIMEOUT, "a bounded device wait gave up (kernel %d)", d.timeout);
   if (d.nonfinite) return fail(SLSO_ERR_NONFINITE, "X holds NaN or Inf");
   return SLSO_OK;
@@ -324,6 +325,7 @@ extern "C" slso_status slso_rank_rows_host_batch(slso_handle* handle, int64_t co
         info[i].tau = ds.tau;
         info[i].nonfinite = ds.nonfinite;
         info[i].svd_route = ds.need_svd;
+        info[i].svd_sweeps = ds.sweeps;
       }
       if (first_err == SLSO_OK && ds.timeout)
         first_err = fail(SLSO_ERR_TIMEOUT, "item %lld: a bounded device wait gave up (kernel %d)", (long long)i, ds.timeout);

@@ -135,6 +135,7 @@ void finish_job(Server& s, Slot& sl) {
       j->info.score_sum = d.score_sum;
       j->info.tau = d.tau;
       j->info.nonfinite = d.nonfinite;
+      j->info.svd_sweeps = d.sweeps;
       j->info.svd_route = d.need_svd;
       if (d.timeout) j->status = SLSO_ERR_TIMEOUT;
       else if (d.nonfinite) j->status = SLSO_ERR_NONFINITE;

@@ -630,7 +630,12 @@ __device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, un
 }
 
 // W: dp x dp column-major (column p at W + p*dp), V likewise; dp even, column d.. are zero.
-__global__ void __launch_bounds__(256) jacobi_kernel(double* __restrict__ W, double* __restrict__ V,
+// Blocks of kJacobiThreads (two warps, one column pair per warp per round): the d/2 pairs of a
+// round spread over every SM (at most a few per SM), since a pair's float64 work is what bounds
+// a round.
+constexpr int kJacobiThreads = 64;
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double* __restrict__ W, double* __restrict__ V,
                                                      int d, int dp, int max_sweeps,
                                                      DevState* __restrict__ st,
                                                      unsigned int* bar, int* rot_count,
@@ -681,6 +686,101 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double* __restrict__ W, dou
             const double x = vp[i], y = vq[i];
             vp[i] = c * x - sn * y;
             vq[i] = sn * x + c * y;
+          }
+          ++local_rot;
+        }
+        __syncwarp();
+      }
+      if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+        if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+        return;
+      }
+    }
+    if (lane == 0 && local_rot) atomicAdd(rot_count + sweep, local_rot);
+    if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+      if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+      return;
+    }
+    const int total = *reinterpret_cast<volatile int*>(rot_count + sweep);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->sweeps = sweep + 1;
+    if (total == 0) break;
+  }
+}
+
+// The same sweeps for d <= 32 * CPL with each lane's share of a column pair held in registers
+// (CPL elements per column): one load and one store per column per round, with every load of a
+// column in flight at once, instead of two dependent passes over L2.  Same pairing, same
+// rotation formulas, same convergence test.
+template <int CPL>
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(double* __restrict__ W, double* __restrict__ V,
+                                                                    int d, int dp, int max_sweeps,
+                                                                    DevState* __restrict__ st, unsigned int* bar,
+                                                                    int* rot_count, int require_svd_flag) {
+  if (require_svd_flag && st->need_svd == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * wpb;
+  const double tol = sqrt(static_cast<double>(dp)) * 0x1p-53;
+  int* abort_flag = reinterpret_cast<int*>(bar + 2);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int local_rot = 0;
+    for (int r = 0; r < dp - 1; ++r) {
+      for (int kp = gw; kp < dp / 2; kp += nwarps) {
+        const int p = (kp == 0) ? 0 : ((r + kp - 1) % (dp - 1)) + 1;
+        const int t2 = dp - 1 - kp;
+        const int q = ((r + t2 - 1) % (dp - 1)) + 1;
+        if (p >= d || q >= d) continue;
+        double* wp = W + static_cast<int64_t>(p) * dp;
+        double* wq = W + static_cast<int64_t>(q) * dp;
+        double x[CPL], y[CPL];
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+          const int i = lane + 32 * e;
+          x[e] = (i < d) ? wp[i] : 0.0;
+          y[e] = (i < d) ? wq[i] : 0.0;
+        }
+        double a = 0.0, b = 0.0, g = 0.0;
+#pragma unroll
+        for (int e = 0; e < CPL; ++e) {
+          a = fma(x[e], x[e], a);
+          b = fma(y[e], y[e], b);
+          g = fma(x[e], y[e], g);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+          b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+          g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
+        }
+        if (g != 0.0 && fabs(g) > tol * sqrt(a * b)) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          const double sn = c * t;
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) {
+            const int i = lane + 32 * e;
+            if (i < d) {
+              wp[i] = c * x[e] - sn * y[e];
+              wq[i] = sn * x[e] + c * y[e];
+            }
+          }
+          double* vp = V + static_cast<int64_t>(p) * dp;
+          double* vq = V + static_cast<int64_t>(q) * dp;
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) {
+            const int i = lane + 32 * e;
+            x[e] = (i < d) ? vp[i] : 0.0;
+            y[e] = (i < d) ? vq[i] : 0.0;
+          }
+#pragma unroll
+          for (int e = 0; e < CPL; ++e) {
+            const int i = lane + 32 * e;
+            if (i < d) {
+              vp[i] = c * x[e] - sn * y[e];
+              vq[i] = sn * x[e] + c * y[e];
+            }
           }
           ++local_rot;
         }
@@ -932,16 +1032,19 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   SLSO_CHECK_CUDA(cudaMemsetAsync(rot, 0, sizeof(int) * 64, st));
   {
     int occ = 0;
-    SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, 256, 0));
+    void* jfn = reinterpret_cast<void*>(jacobi_kernel);
+    if (d <= 256) jfn = reinterpret_cast<void*>(jacobi_reg_kernel<8>);
+    else if (d <= 512) jfn = reinterpret_cast<void*>(jacobi_reg_kernel<16>);
+    else if (d <= 1024) jfn = reinterpret_cast<void*>(jacobi_reg_kernel<32>);
+    SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jfn, kJacobiThreads, 0));
     const int warps_needed = static_cast<int>(dp / 2);
-    int G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h.num_sms) * std::min(occ, 2),
-                                               ceil_div(warps_needed, 8)));
+    int G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h.num_sms) * occ,
+                                               ceil_div(warps_needed, kJacobiThreads / 32)));
     G = std::max(G, 1);
     int d_i = static_cast<int>(d), dp_i = static_cast<int>(dp), sweeps = 60, req = (mode == 0) ? 1 : 0;
     DevState* stp = h.state;
     void* args[] = {&W, &Vw, &d_i, &dp_i, &sweeps, &stp, &bar, &rot, &req};
-    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_kernel), dim3(G), dim3(256),
-                                                args, 0, st));
+    SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(jfn, dim3(G), dim3(kJacobiThreads), args, 0, st));
     note_launch();
   }
   const int32_t* guard = (mode == 0) ? need : nullptr;
