@@ -25,6 +25,7 @@ generator independently.  Counter layouts (word 3 of the counter is a stream tag
                          BoxMuller(w2, w3), BoxMuller(w2, w3 - 2^30)  (cos, sin of each pair)
   JL entry (j, c)        ctr=(lo(c), hi(c), j, 5)  Pi_jc = BoxMuller(w0, w1) / sqrt(k)
   sampling draw t        ctr=(lo(t), hi(t), 0, 6)  u_t = (m + 1/2) 2^-52, m = w0 2^20 + (w1 >> 12)
+  OSNAP row i, block b   ctr=(lo(i), hi(i), b, 7)  bucket = b s/z + ((w0 s/z) >> 32), sign = 1-2*(w1&1)
 
 with key = (lo(seed), hi(seed)), BoxMuller(w0, w1) = sqrt(-2 ln u1) cos(2 pi u2),
 u1 = (w0 + 1) 2^-32 in (0, 1], u2 = w1 2^-32 in [0, 1).
@@ -54,6 +55,8 @@ TAG_SRHT_SAMPLE = 3
 TAG_GAUSSIAN = 4
 TAG_JL = 5
 TAG_SAMPLE = 6
+TAG_OSNAP = 7
+OSNAP_DEFAULT_NNZ = 4
 
 
 def philox4x32_10(c0, c1, c2, c3, key):
@@ -234,6 +237,41 @@ def sketch_countsketch(X, s, seed):
     return SX
 
 
+def osnap_hash(n, s, z, seed):
+    """OSNAP (Nelson and Nguyen; the paper's variant of CountSketch, Sec. 3.1.2) in its block
+    form: the s rows of S are z blocks of s/z rows, and column i of S has one nonzero in each
+    block, +-1/sqrt(z) at row b s/z + h_b(i), with (h_b, sign_b) hashed like CountSketch from
+    the Philox block (lo i, hi i, b, 7).  Returns (bucket, sign) arrays of shape (z, n)."""
+    if s % z != 0:
+        raise ValueError("OSNAP needs s divisible by z")
+    m = s // z
+    lo, hi = _split64(np.arange(n, dtype=np.uint64))
+    buckets, signs = [], []
+    for b in range(z):
+        w = philox4x32_10(lo, hi, b, TAG_OSNAP, seed)
+        buckets.append(((w[0] * np.uint64(m)) >> _SH32).astype(np.int64) + b * m)
+        signs.append(1.0 - 2.0 * (w[1] & np.uint64(1)).astype(np.float64))
+    return np.stack(buckets), np.stack(signs)
+
+
+def sketch_osnap(X, s, seed, nnz=OSNAP_DEFAULT_NNZ):
+    """SX for OSNAP with nnz nonzeros per column of S: the sparse product S X, rows of S summing
+    their nonzeros in ascending i."""
+    import scipy.sparse as sp
+
+    n, d = X.shape
+    bucket, sign = osnap_hash(n, s, nnz, seed)
+    SX = np.zeros((s, d), dtype=np.float64)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        rows = bucket[:, a:b].ravel()
+        cols = np.tile(np.arange(b - a), nnz)
+        vals = sign[:, a:b].ravel() / math.sqrt(nnz)
+        S = sp.csr_matrix((vals, (rows, cols)), shape=(s, b - a))
+        SX += S @ np.asarray(X[a:b], dtype=np.float64)
+    return SX
+
+
 def sketch_srht(X, s, seed):
     """SX for the subsampled randomized Hadamard transform sqrt(n_pad/s) P (H/sqrt(n_pad)) D.
 
@@ -265,11 +303,14 @@ def sketch_gaussian(X, s, seed):
     return SX / math.sqrt(s)
 
 
-SKETCHES = {"countsketch": sketch_countsketch, "srht": sketch_srht, "gaussian": sketch_gaussian}
+SKETCHES = {"countsketch": sketch_countsketch, "srht": sketch_srht, "gaussian": sketch_gaussian,
+            "osnap": sketch_osnap}
 
 
-def sketch(X, kind, s, seed):
-    """Algorithm 2/3 step 1: the sketch SA of the data matrix."""
+def sketch(X, kind, s, seed, nnz=None):
+    """Algorithm 2/3 step 1: the sketch SA of the data matrix (nnz: OSNAP's nonzeros per column)."""
+    if kind == "osnap" and nnz:
+        return sketch_osnap(X, s, seed, nnz)
     return SKETCHES[kind](X, s, seed)
 
 

@@ -173,14 +173,15 @@ def test_approx_u_row_norms_are_the_sketched_scores(kind):
     np.testing.assert_allclose(np.sum(U * U, axis=1), sc, rtol=1e-9)
 
 
-@pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian"])
+@pytest.mark.parametrize("kind", ["countsketch", "srht", "gaussian", "osnap"])
 def test_sketch_of_identity_has_unit_columns_in_expectation(kind):
     n, s = 256, 64
     SI = O.sketch(np.eye(n), kind, s, 9)
     norms = np.sum(SI**2, axis=0)
     if kind == "gaussian":
         assert abs(norms.mean() - 1.0) < 5 * math.sqrt(2.0 / s) / math.sqrt(n)
-    else:  # one +-1 per column (CountSketch); (1/s) sum of s squared +-1 entries (SRHT)
+    else:  # one +-1 per column (CountSketch); (1/s) sum of s squared +-1 entries (SRHT);
+        # z entries +-1/sqrt(z) in z distinct rows (OSNAP)
         np.testing.assert_allclose(norms, 1.0, rtol=1e-14)
 
 
@@ -202,7 +203,29 @@ def test_collision_free_countsketch_is_an_isometry():
     np.testing.assert_allclose(SX.T @ SX, X.T @ X, rtol=1e-14)
 
 
-@pytest.mark.parametrize("kind,s", [("countsketch", 2048), ("srht", 512), ("gaussian", 256)])
+@pytest.mark.parametrize("z", [1, 2, 4, 8])
+def test_osnap_columns_have_one_entry_per_block(z):
+    """Column i of S: exactly z nonzeros, one in each block of s/z rows, each +-1/sqrt(z)."""
+    n, s = 300, 64
+    SI = O.sketch(np.eye(n), "osnap", s, 5, nnz=z)
+    m = s // z
+    for b in range(z):
+        blk = SI[b * m:(b + 1) * m]
+        np.testing.assert_array_equal(np.count_nonzero(blk, axis=0), np.ones(n))
+    np.testing.assert_allclose(np.abs(SI[SI != 0]), 1 / math.sqrt(z), rtol=1e-15)
+
+
+def test_collision_free_osnap_is_an_isometry():
+    n, s, z = 12, 1 << 24, 4
+    seed = next(sd for sd in range(100) if len(set(O.osnap_hash(n, s, z, sd)[0].ravel().tolist())) == n * z)
+    X = np.random.default_rng(9).standard_normal((n, 3))
+    SX = O.sketch_osnap(X, s, seed, z)
+    np.testing.assert_allclose(SX.T @ SX, X.T @ X, rtol=1e-13)
+    sc, _, _ = O.scores_from_sketch(X, SX)
+    np.testing.assert_allclose(sc, O.exact_leverage(X), rtol=1e-10)
+
+
+@pytest.mark.parametrize("kind,s", [("countsketch", 2048), ("srht", 512), ("gaussian", 256), ("osnap", 512)])
 def test_sketched_scores_lie_in_subspace_embedding_band(kind, s):
     """For Pi = I: l_i / sigma_max(SU)^2 <= l~_i <= l_i / sigma_min(SU)^2, U an orthonormal basis."""
     rng = np.random.default_rng(10)
