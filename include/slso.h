@@ -60,7 +60,10 @@ typedef enum { SLSO_F64 = 0, SLSO_F32 = 1, SLSO_BF16 = 2, SLSO_FP8_E4M3 = 3 } sl
  *  GAUSSIAN     (1/sqrt(s)) G, G_ji = bf16_rne(BoxMuller(w0, w1)) at counter (lo i, hi i, j, 4),
  *               BoxMuller(w0, w1) = sqrt(-2 ln((w0+1) 2^-32)) cos(2 pi w1 2^-32), the bf16
  *               rounding decided on the float64 value. */
-typedef enum { SLSO_COUNTSKETCH = 0, SLSO_SRHT = 1, SLSO_GAUSSIAN = 2 } slso_sketch_kind;
+/* OSNAP (Sec. 3.1.2, a variant of CountSketch): z blocks of s/z rows, one +-1/sqrt(z) per block in
+ * each column of S, bucket b s/z + ((w0 s/z) >> 32), sign 1 - 2 (w1 & 1) from Philox at counter
+ * (lo i, hi i, b, 7); z = slso_params.nnz (0: 4); slso_sketch uses z = 4. */
+typedef enum { SLSO_COUNTSKETCH = 0, SLSO_SRHT = 1, SLSO_GAUSSIAN = 2, SLSO_OSNAP = 3 } slso_sketch_kind;
 
 /* Sampling policies of Algorithm 4 step 4 (Sec. 5.2) on P = scores / sum(scores). */
 typedef enum { SLSO_POLICY_DEC = 0, SLSO_POLICY_SWR = 1, SLSO_POLICY_SWOR = 2 } slso_policy;
@@ -78,6 +81,7 @@ typedef struct {
   double tau;          /* relative rank threshold: keep sigma_j > tau sigma_1; < 0 selects
                           max(s, d) 2^-52 (float64 numerical rank)                            */
   double correct_frac; /* BF16/FP8 only: rescore the top ceil(frac n) rows in float32; 0 = off */
+  int32_t nnz;         /* OSNAP: nonzeros per column of S (1..64, s divisible by it); 0 = 4     */
 } slso_params;
 
 typedef struct {

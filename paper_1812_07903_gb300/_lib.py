@@ -13,8 +13,8 @@ STATUS_NAMES = {
     6: "NONFINITE", 7: "TIMEOUT", 8: "BUSY", 9: "NOT_FOUND", 10: "CANCELLED",
 }
 F64, F32, BF16, FP8_E4M3 = 0, 1, 2, 3
-COUNTSKETCH, SRHT, GAUSSIAN = 0, 1, 2
-KIND = {"countsketch": COUNTSKETCH, "srht": SRHT, "gaussian": GAUSSIAN}
+COUNTSKETCH, SRHT, GAUSSIAN, OSNAP = 0, 1, 2, 3
+KIND = {"countsketch": COUNTSKETCH, "srht": SRHT, "gaussian": GAUSSIAN, "osnap": OSNAP}
 POLICY = {"dec": 0, "swr": 1, "swor": 2}
 DTYPE = {"f64": F64, "f32": F32, "bf16": BF16, "fp8": FP8_E4M3}
 
@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
     _fields_ = [
         ("kind", ctypes.c_int32), ("compute", ctypes.c_int32), ("s", ctypes.c_int64),
         ("k", ctypes.c_int64), ("seed_S", ctypes.c_uint64), ("seed_Pi", ctypes.c_uint64),
-        ("tau", ctypes.c_double), ("correct_frac", ctypes.c_double),
+        ("tau", ctypes.c_double), ("correct_frac", ctypes.c_double), ("nnz", ctypes.c_int32),
     ]
 
 

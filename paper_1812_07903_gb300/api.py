@@ -101,7 +101,7 @@ def sketched_svd(SX, tau=-1.0, want_r=True, handle=None):
 
 
 def make_params(kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
-                correct_frac=0.0):
+                correct_frac=0.0, nnz=0):
     p = L.Params()
     p.kind = L.KIND[kind]
     p.compute = L.DTYPE[compute]
@@ -111,15 +111,17 @@ def make_params(kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, 
     p.seed_Pi = int(seed_Pi)
     p.tau = float(tau)
     p.correct_frac = float(correct_frac)
+    p.nnz = int(nnz)
     return p
 
 
 def leverage(X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
-             correct_frac=0.0, out=None, want_info=True, handle=None):
-    """slso_leverage: approximate leverage scores (float64 for compute='f64', else float32)."""
+             correct_frac=0.0, out=None, want_info=True, handle=None, nnz=0):
+    """slso_leverage: approximate leverage scores (float64 for compute='f64', else float32).
+    nnz: OSNAP nonzeros per column of S (0: the default 4)."""
     h = handle or default_handle()
     n, d, ldx, xdt = _x_args(X)
-    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac, nnz)
     sdt = torch.float64 if compute == "f64" else torch.float32
     scores = out if out is not None else torch.empty(n, dtype=sdt, device=X.device)
     info = L.Info()
@@ -129,11 +131,11 @@ def leverage(X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, 
     return scores, (info.as_dict() if want_info else None)
 
 
-def approx_u(X, kind="countsketch", s=None, seed_S=0, tau=-1.0, out=None, handle=None):
+def approx_u(X, kind="countsketch", s=None, seed_S=0, tau=-1.0, out=None, handle=None, nnz=0):
     """slso_approx_u: U = X V_r Sigma_r^-1 from the sketched SVD (n x d; columns >= rank are zero)."""
     h = handle or default_handle()
     n, d, ldx, xdt = _x_args(X)
-    p = make_params(kind, s, 0, seed_S, 0, tau, "f32", 0.0)
+    p = make_params(kind, s, 0, seed_S, 0, tau, "f32", 0.0, nnz)
     udt = torch.float64 if X.dtype == torch.float64 else torch.float32
     U = out if out is not None else torch.empty(n, d, dtype=udt, device=X.device)
     if U.dtype != udt or U.dim() != 2 or U.shape != (n, d) or U.stride(1) != 1:
@@ -174,13 +176,13 @@ def sample_order(scores, policy="swor", seed=0, out=None, handle=None):
 
 
 def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
-                   compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None):
+                   compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None, nnz=0):
     """slso_rank_rows_host: scores and order from a HOST matrix (copies inside the call)."""
     h = handle or default_handle()
     if X_host.is_cuda or X_host.dim() != 2 or X_host.dtype not in _XDT or X_host.stride(1) != 1:
         raise TypeError("X_host must be a 2-D row-contiguous host tensor (float64/float32/bfloat16)")
     n, d = X_host.shape
-    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac, nnz)
     sdt = torch.float64 if compute == "f64" else torch.float32
     sc = scores_out if scores_out is not None else torch.empty(n, dtype=sdt)
     od = order_out if order_out is not None else torch.empty(n, dtype=torch.int64)
@@ -192,7 +194,8 @@ def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0,
 
 
 def rank_rows_host_batch(X_hosts, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
-                         compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None):
+                         compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None,
+                         nnz=0):
     """slso_rank_rows_host_batch: rank_rows_host over a list of same-shaped HOST matrices, with the
     copies of one item overlapped with the computation of its neighbours.  Returns lists of
     (scores, order) host tensors and the per-item info dicts."""
@@ -206,7 +209,7 @@ def rank_rows_host_batch(X_hosts, kind="countsketch", s=None, k=0, seed_S=0, see
             raise TypeError("X_hosts must be 2-D row-contiguous host tensors of one shape, dtype and row stride")
     cnt = len(X_hosts)
     n, d = X0.shape
-    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac, nnz)
     sdt = torch.float64 if compute == "f64" else torch.float32
     sc = scores_out or [torch.empty(n, dtype=sdt) for _ in range(cnt)]
     od = order_out or [torch.empty(n, dtype=torch.int64) for _ in range(cnt)]
@@ -262,11 +265,11 @@ class Server:
         self._keep = {}
 
     def submit_leverage(self, X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
-                        compute="f32", correct_frac=0.0, with_order=True):
+                        compute="f32", correct_frac=0.0, with_order=True, nnz=0):
         n, d, ldx, xdt = _x_args(X)
         j = L.Job()
         j.job, j.xdt, j.X, j.n, j.d, j.ldx = L.JOB_LEVERAGE, xdt, X.data_ptr(), n, d, ldx
-        j.params = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac)
+        j.params = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac, nnz)
         sdt = torch.float64 if compute == "f64" else torch.float32
         scores = torch.empty(n, dtype=sdt, device=X.device)
         order = torch.empty(n, dtype=torch.int64, device=X.device) if with_order else None

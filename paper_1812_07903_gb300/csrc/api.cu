@@ -33,9 +33,15 @@ slso_status check_x(const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xd
   return SLSO_OK;
 }
 
-slso_status check_sketch(int32_t kind, int64_t n, int64_t d, int64_t s) {
-  if (kind != SLSO_COUNTSKETCH && kind != SLSO_SRHT && kind != SLSO_GAUSSIAN)
+slso_status check_sketch(int32_t kind, int64_t n, int64_t d, int64_t s, int32_t nnz) {
+  if (kind != SLSO_COUNTSKETCH && kind != SLSO_SRHT && kind != SLSO_GAUSSIAN && kind != SLSO_OSNAP)
     return fail(SLSO_ERR_INVALID_ARG, "unknown sketch kind %d", kind);
+  if (kind == SLSO_OSNAP) {
+    const int64_t z = nnz > 0 ? nnz : kOsnapDefaultNnz;
+    if (nnz < 0 || z > 64) return fail(SLSO_ERR_INVALID_ARG, "OSNAP nnz=%d must be in 0 .. 64", nnz);
+    if (s % z != 0) return fail(SLSO_ERR_SHAPE, "OSNAP needs s=%lld divisible by nnz=%lld", (long long)s, (long long)z);
+    if (n * z >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "OSNAP needs n * nnz < 2^31");
+  }
   if (s < 1) return fail(SLSO_ERR_SHAPE, "s=%lld must be >= 1", (long long)s);
   if (s >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "s=%lld must be < 2^31", (long long)s);
   if (kind == SLSO_SRHT && s > next_pow2(n))
@@ -46,7 +52,7 @@ slso_status check_sketch(int32_t kind, int64_t n, int64_t d, int64_t s) {
 
 slso_status check_params(const slso_params* p, int64_t n, int64_t d) {
   if (!p) return fail(SLSO_ERR_INVALID_ARG, "params is NULL");
-  SLSO_TRY(check_sketch(p->kind, n, d, p->s));
+  SLSO_TRY(check_sketch(p->kind, n, d, p->s, p->nnz));
   if (p->s < d) return fail(SLSO_ERR_SHAPE, "need s >= d for the d x d factor R (s=%lld, d=%lld)", (long long)p->s, (long long)d);
   if (p->k < 0 || p->k > 4096) return fail(SLSO_ERR_SHAPE, "k=%lld must be in [0, 4096]", (long long)p->k);
   if (p->compute != SLSO_F64 && p->compute != SLSO_F32 && p->compute != SLSO_BF16 && p->compute != SLSO_FP8_E4M3)
@@ -99,7 +105,7 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   const double tau = p->tau < 0 ? default_tau(p->s, d) : p->tau;
   double* SX = ar.take<double>(static_cast<size_t>(p->s) * d);
   prof_begin(h, ar, ST_SKETCH, st);
-  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, SX, st));
+  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, p->nnz, SX, st));
   prof_end(h, ar, st);
   SolveOut so;
   SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st));
@@ -132,13 +138,13 @@ extern "C" slso_status slso_sketch(slso_handle* handle, const void* X, int64_t n
   Handle* h = nullptr;
   SLSO_TRY(check_handle(handle, &h));
   SLSO_TRY(check_x(X, n, d, ldx, xdt));
-  SLSO_TRY(check_sketch(kind, n, d, s));
+  SLSO_TRY(check_sketch(kind, n, d, s, 0));
   if (!SX) return fail(SLSO_ERR_INVALID_ARG, "SX is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
   return run_plan(*h, [&](Arena& ar) {
     prof_begin(*h, ar, ST_SKETCH, st);
-    SLSO_TRY(run_sketch(*h, ar, X, n, d, ldx, xdt, kind, s, seed_S, SX, st));
+    SLSO_TRY(run_sketch(*h, ar, X, n, d, ldx, xdt, kind, s, seed_S, 0, SX, st));
     prof_end(*h, ar, st);
     return SLSO_OK;
   });

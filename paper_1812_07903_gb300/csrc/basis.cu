@@ -103,7 +103,7 @@ slso_status approx_u_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   const double tau = p->tau < 0 ? default_tau(s, d) : p->tau;
   double* SX = ar.take<double>(static_cast<size_t>(s) * d);
   prof_begin(h, ar, ST_SKETCH, st);
-  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, s, p->seed_S, SX, st));
+  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, s, p->seed_S, p->nnz, SX, st));
   prof_end(h, ar, st);
   SolveOut so;
   SLSO_TRY(run_solve(h, ar, SX, s, d, tau, 0, 0, 1, &so, st));

@@ -154,7 +154,8 @@ enum : uint32_t {
   TAG_SRHT_SIGN = 2,
   TAG_SRHT_SAMPLE = 3,
   TAG_GAUSSIAN = 4,
-  TAG_JL = 5
+  TAG_JL = 5,
+  TAG_OSNAP = 7
 };
 
 // ------------------------------------------------------------------ Box-Muller
@@ -379,8 +380,10 @@ slso_status order_scores(Handle& h, Arena& ar, const void* scores, int32_t sdt, 
                          int64_t* order, cudaStream_t st);
 
 // sketch.cu
+// nnz: OSNAP's nonzeros per column of S (ignored by the other kinds).
+constexpr int kOsnapDefaultNnz = 4;
 slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
-                       int32_t xdt, int32_t kind, int64_t s, uint64_t seed, double* SX,
+                       int32_t xdt, int32_t kind, int64_t s, uint64_t seed, int nnz, double* SX,
                        cudaStream_t st);
 
 // solve.cu

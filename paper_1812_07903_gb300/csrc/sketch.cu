@@ -23,14 +23,21 @@ namespace slso {
 namespace {
 
 // ---------------------------------------------------------------- CountSketch
-__global__ void cs_hash_kernel(int64_t n, uint32_t s, uint64_t seed, uint32_t* __restrict__ keys,
-                               uint32_t* __restrict__ vals) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const U32x4 w = philox(static_cast<uint32_t>(i), static_cast<uint32_t>(static_cast<uint64_t>(i) >> 32),
-                           0u, TAG_COUNTSKETCH, seed);
-    keys[i] = static_cast<uint32_t>((static_cast<uint64_t>(w.x) * s) >> 32);
-    vals[i] = static_cast<uint32_t>(i) | ((w.y & 1u) << 31);  // sign bit: 1 means -1
+// Hashes of CountSketch (z = 1, tag 1) and OSNAP (z blocks, tag 7): entry e = b n + i (block b,
+// row i) gets bucket b (s/z) + ((w0 (s/z)) >> 32) and sign 1 - 2 (w1 & 1) from Philox at counter
+// (lo i, hi i, b, tag).  Within a bucket (one block) the stable sort keeps rows ascending.
+__global__ void cs_hash_kernel(int64_t n, uint32_t s, int z, uint32_t tag, uint64_t seed,
+                               uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const uint32_t m = s / static_cast<uint32_t>(z);
+  const int64_t total = n * z;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t b = static_cast<uint32_t>(e / n);
+    const int64_t i = e - static_cast<int64_t>(b) * n;
+    const U32x4 w = philox(static_cast<uint32_t>(i), static_cast<uint32_t>(static_cast<uint64_t>(i) >> 32), b, tag,
+                           seed);
+    keys[e] = b * m + static_cast<uint32_t>((static_cast<uint64_t>(w.x) * m) >> 32);
+    vals[e] = static_cast<uint32_t>(i) | ((w.y & 1u) << 31);  // sign bit: 1 means -1
   }
 }
 
@@ -73,7 +80,7 @@ template <class T, int VEC, int UNROLL>
 __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X, int64_t d, int64_t ldx,
                                                         const uint32_t* __restrict__ rows,
                                                         const uint32_t* __restrict__ start,
-                                                        double* __restrict__ SX,
+                                                        double* __restrict__ SX, double scale,
                                                         DevState* __restrict__ state) {
   const uint32_t b = blockIdx.x;
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * VEC;
@@ -118,7 +125,8 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
   if (active) {
 #pragma unroll
     for (int v = 0; v < VEC; ++v)
-      if (c0 + v < d) SX[static_cast<int64_t>(b) * d + c0 + v] = static_cast<double>(hi[v]) + static_cast<double>(lo[v]);
+      if (c0 + v < d)
+        SX[static_cast<int64_t>(b) * d + c0 + v] = (static_cast<double>(hi[v]) + static_cast<double>(lo[v])) * scale;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&state->nonfinite, 1);
 }
@@ -127,7 +135,7 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
 __global__ void __launch_bounds__(256) cs_gather_f64_kernel(const double* __restrict__ X, int64_t d,
                                                             int64_t ldx, const uint32_t* __restrict__ rows,
                                                             const uint32_t* __restrict__ start,
-                                                            double* __restrict__ SX,
+                                                            double* __restrict__ SX, double scale,
                                                             DevState* __restrict__ state) {
   const uint32_t b = blockIdx.x;
   const int64_t c = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(256) cs_gather_f64_kernel(const double* __rest
       bad |= !isfinite(x);
       acc += (rv >> 31) ? -x : x;
     }
-    SX[static_cast<int64_t>(b) * d + c] = acc;
+    SX[static_cast<int64_t>(b) * d + c] = acc * scale;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&state->nonfinite, 1);
 }
@@ -339,27 +347,31 @@ int grid_for(int64_t n, const Handle& h) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 16LL * h.num_sms)));
 }
 
+// CountSketch (z = 1) and OSNAP (z blocks, entries +-1/sqrt(z)): hash, stable sort of the n z
+// entries by bucket, then the deterministic gather of each bucket's rows in ascending order.
 template <class T>
 slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx,
-                        int64_t s, uint64_t seed, double* SX, cudaStream_t st) {
-  uint32_t* keys = ar.take<uint32_t>(n);
-  uint32_t* vals = ar.take<uint32_t>(n);
+                        int64_t s, uint64_t seed, int z, uint32_t tag, double* SX, cudaStream_t st) {
+  const int64_t N = n * z;
+  uint32_t* keys = ar.take<uint32_t>(N);
+  uint32_t* vals = ar.take<uint32_t>(N);
   uint32_t* start = ar.take<uint32_t>(s + 1);
   int bits = 0;
   while ((int64_t(1) << bits) < s) ++bits;
   uint32_t* ks = keys;
   uint32_t* vs = vals;
   if (!ar.measure()) {
-    cs_hash_kernel<<<grid_for(n, h), 256, 0, st>>>(n, static_cast<uint32_t>(s), seed, keys, vals);
+    cs_hash_kernel<<<grid_for(N, h), 256, 0, st>>>(n, static_cast<uint32_t>(s), z, tag, seed, keys, vals);
     SLSO_CHECK_LAUNCH();
   }
-  if (bits > 0) SLSO_TRY(radix_sort_u32(ar, keys, vals, n, bits, st, &ks, &vs));
+  if (bits > 0) SLSO_TRY(radix_sort_u32(ar, keys, vals, N, bits, st, &ks, &vs));
   if (ar.measure()) return SLSO_OK;
-  bucket_start_kernel<<<grid_for(n + 1, h), 256, 0, st>>>(ks, n, static_cast<uint32_t>(s), start);
+  bucket_start_kernel<<<grid_for(N + 1, h), 256, 0, st>>>(ks, N, static_cast<uint32_t>(s), start);
   SLSO_CHECK_LAUNCH();
+  const double scale = (z == 1) ? 1.0 : 1.0 / std::sqrt(static_cast<double>(z));
   if constexpr (std::is_same<T, double>::value) {
     dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(d, 256)));
-    cs_gather_f64_kernel<<<grid, 256, 0, st>>>(X, d, ldx, vs, start, SX, h.state);
+    cs_gather_f64_kernel<<<grid, 256, 0, st>>>(X, d, ldx, vs, start, SX, scale, h.state);
   } else {
     const bool vec = (d % 4 == 0) && (ldx % 4 == 0) &&
                      (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(T)) == 0);
@@ -367,11 +379,11 @@ slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, 
       const int64_t thr_needed = ceil_div(d, 4);
       const int threads = static_cast<int>(std::min<int64_t>(256, ceil_div(thr_needed, 32) * 32));
       dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(thr_needed, threads)));
-      cs_gather_kernel<T, 4, 4><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, h.state);
+      cs_gather_kernel<T, 4, 4><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, h.state);
     } else {
       const int threads = static_cast<int>(std::min<int64_t>(256, ceil_div(d, 32) * 32));
       dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(d, threads)));
-      cs_gather_kernel<T, 1, 8><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, h.state);
+      cs_gather_kernel<T, 1, 8><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, h.state);
     }
   }
   SLSO_CHECK_LAUNCH();
@@ -446,13 +458,23 @@ slso_status gaussian(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int
 }  // namespace
 
 slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
-                       int32_t xdt, int32_t kind, int64_t s, uint64_t seed, double* SX,
+                       int32_t xdt, int32_t kind, int64_t s, uint64_t seed, int nnz, double* SX,
                        cudaStream_t st) {
   switch (kind) {
     case SLSO_COUNTSKETCH:
-      if (xdt == SLSO_F32) return countsketch(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, SX, st);
-      if (xdt == SLSO_BF16) return countsketch(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, SX, st);
-      return countsketch(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, SX, st);
+      if (xdt == SLSO_F32)
+        return countsketch(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, SX, st);
+      if (xdt == SLSO_BF16)
+        return countsketch(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, SX, st);
+      return countsketch(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, SX, st);
+    case SLSO_OSNAP: {
+      const int z = nnz > 0 ? nnz : kOsnapDefaultNnz;
+      if (xdt == SLSO_F32)
+        return countsketch(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, z, TAG_OSNAP, SX, st);
+      if (xdt == SLSO_BF16)
+        return countsketch(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, z, TAG_OSNAP, SX, st);
+      return countsketch(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, z, TAG_OSNAP, SX, st);
+    }
     case SLSO_SRHT:
       if (xdt == SLSO_F32) return srht(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, SX, st);
       if (xdt == SLSO_BF16) return srht(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, SX, st);
