@@ -170,6 +170,27 @@ slso_status slso_rank_rows_host_batch(slso_handle* handle, int64_t count, const 
                                       const slso_params* params, void* const* scores_host,
                                       int64_t* const* order_host, slso_info* info, void* stream);
 
+/* Out-of-core X: slso_rank_rows_host for a HOST matrix that need not fit in device memory.  X is
+ * streamed through the device twice in blocks of rows.  Pass 1 copies each block in and adds its
+ * sketch to SX; the hash, sign and Gaussian counters use the rows' indices in the whole X, so SX
+ * equals slso_sketch's up to the float64 rounding of the block sums.  The solve runs once.  Pass 2
+ * copies the blocks in again, last block first (the two blocks still on the device are not copied
+ * again), and scores them.  Copies run on a stream of the call's own, overlapped with the compute
+ * of the neighbouring block.
+ *   X_host       n x d host matrix, row stride ldx (pinned memory lets the copies overlap compute)
+ *   block_rows   rows per block: at least 65536, rounded down to a power of two (0: 262144)
+ *   scores_host  n scores, F64 when params->compute == SLSO_F64, else F32; order_host n int64
+ * Device memory: two blocks (block_rows x d elements each), SX, and O(n) for the scores and the
+ * order, plus scratch; independent of n x d.
+ * params->correct_frac must be 0 (a correction pass would need a third pass over X).  With compute
+ * FP8 the per-column scales are taken per block.
+ * Errors: as slso_rank_rows_host; INVALID_ARG for correct_frac != 0 or block_rows < 0.
+ * Synchronous: returns after the copies out have finished. */
+slso_status slso_rank_rows_streamed(slso_handle* handle, const void* X_host, int64_t n, int64_t d,
+                                    int64_t ldx, int32_t xdt, const slso_params* params,
+                                    int64_t block_rows, void* scores_host, int64_t* order_host,
+                                    slso_info* info, void* stream);
+
 /* Orderings of Algorithm 4 step 4 (Sec. 5.2) from the scores (device, F32 or F64, n of
  * them) into order[0..n) (device, int64), on the given stream; seed selects the draws (one
  * seed per training epoch).  Weights are the scores; NaN, infinite or negative scores weigh 0.

@@ -193,6 +193,25 @@ def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0,
     return sc, od, info.as_dict()
 
 
+def rank_rows_streamed(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
+                       block_rows=0, scores_out=None, order_out=None, handle=None, nnz=0):
+    """slso_rank_rows_streamed: scores and order of a HOST matrix streamed through the device in
+    blocks of rows (out-of-core X: device memory independent of n x d)."""
+    h = handle or default_handle()
+    if X_host.is_cuda or X_host.dim() != 2 or X_host.dtype not in _XDT or X_host.stride(1) != 1:
+        raise TypeError("X_host must be a 2-D row-contiguous host tensor (float64/float32/bfloat16)")
+    n, d = X_host.shape
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, 0.0, nnz)
+    sdt = torch.float64 if compute == "f64" else torch.float32
+    sc = scores_out if scores_out is not None else torch.empty(n, dtype=sdt)
+    od = order_out if order_out is not None else torch.empty(n, dtype=torch.int64)
+    info = L.Info()
+    L.check(L.load().slso_rank_rows_streamed(h.ptr, X_host.data_ptr(), n, d, X_host.stride(0), _XDT[X_host.dtype],
+                                             ctypes.byref(p), int(block_rows), sc.data_ptr(), od.data_ptr(),
+                                             ctypes.byref(info), _stream()))
+    return sc, od, info.as_dict()
+
+
 def rank_rows_host_batch(X_hosts, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0,
                          compute="f32", correct_frac=0.0, scores_out=None, order_out=None, handle=None,
                          nnz=0):

@@ -15,6 +15,11 @@ using namespace slso;
 
 namespace slso {
 
+// Streamed entry point: rows per block (a power of two; a multiple of SRHT's 8192-row chunks and of
+// the Gaussian generator's 4-column Philox blocks).
+constexpr int64_t kStreamMinBlock = 65536;
+constexpr int64_t kStreamDefaultBlock = 262144;
+
 double default_tau(int64_t s, int64_t d) { return static_cast<double>(std::max(s, d)) * std::ldexp(1.0, -52); }
 
 int64_t next_pow2(int64_t n) {
@@ -347,6 +352,197 @@ extern "C" slso_status slso_rank_rows_host_batch(slso_handle* handle, int64_t co
     if (d2h) cudaStreamSynchronize(d2h);
   }
   cleanup();
+  return r;
+}
+
+// Out-of-core X: two passes over blocks of rows copied from the host (see include/slso.h).
+// Device layout: fixed buffers (two blocks, SX, the SRHT sample, scores and order of all n rows),
+// then one scratch region R reused by every phase: the SRHT sample draw, each block's sketch, the
+// solve (whose M stays at the start of R during pass 2), each block's scores after it, and the
+// final score sum and ordering.
+extern "C" slso_status slso_rank_rows_streamed(slso_handle* handle, const void* X_host, int64_t n, int64_t d,
+                                               int64_t ldx, int32_t xdt, const slso_params* params,
+                                               int64_t block_rows, void* scores_host, int64_t* order_host,
+                                               slso_info* info, void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  SLSO_TRY(check_x(X_host, n, d, ldx, xdt));
+  SLSO_TRY(check_params(params, n, d));
+  if (!scores_host || !order_host) return fail(SLSO_ERR_INVALID_ARG, "scores_host and order_host must be non-NULL");
+  if (params->correct_frac != 0.0)
+    return fail(SLSO_ERR_INVALID_ARG, "correct_frac must be 0 for the streamed entry point");
+  if (block_rows < 0) return fail(SLSO_ERR_INVALID_ARG, "block_rows must be >= 0");
+  int64_t B = block_rows > 0 ? std::max<int64_t>(block_rows, kStreamMinBlock) : kStreamDefaultBlock;
+  while (B & (B - 1)) B &= B - 1;  // round down to a power of two
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nb = ceil_div(n, B);
+  const int64_t Bm = std::min(B, n);
+  const size_t esz = dtype_size(xdt);
+  const int32_t sdt = params->compute == SLSO_F64 ? SLSO_F64 : SLSO_F32;
+  const size_t ssz = dtype_size(sdt);
+  const size_t xbytes = static_cast<size_t>(Bm) * d * esz;
+  const double tau = params->tau < 0 ? default_tau(params->s, d) : params->tau;
+  const int64_t kk = params->k > 0 ? params->k : d;
+  auto rows_of = [&](int64_t b) { return std::min(B, n - b * B); };
+
+  char* Xb[2] = {};
+  double* SX = nullptr;
+  uint32_t* sample = nullptr;
+  char* scd = nullptr;
+  int64_t* odd = nullptr;
+  auto take_fixed = [&](Arena& ar) {
+    Xb[0] = ar.take<char>(xbytes);
+    Xb[1] = nb > 1 ? ar.take<char>(xbytes) : nullptr;
+    SX = ar.take<double>(static_cast<size_t>(params->s) * d);
+    sample = params->kind == SLSO_SRHT ? ar.take<uint32_t>(params->s) : nullptr;
+    scd = ar.take<char>(static_cast<size_t>(n) * ssz);
+    odd = ar.take<int64_t>(n);
+  };
+  SketchBlock blk{};
+  blk.n_total = n;
+  SolveOut so;
+  auto draw_sample = [&](Arena& ar) -> slso_status {
+    if (params->kind != SLSO_SRHT) return SLSO_OK;
+    const uint32_t* rows = nullptr;
+    SLSO_TRY(srht_sample_rows(*h, ar, n, params->s, params->seed_S, &rows, st));
+    if (!ar.measure())
+      SLSO_CHECK_CUDA(cudaMemcpyAsync(sample, rows, sizeof(uint32_t) * params->s, cudaMemcpyDeviceToDevice, st));
+    return SLSO_OK;
+  };
+  auto sketch_block = [&](Arena& ar, int64_t b) -> slso_status {
+    blk.row0 = b * B;
+    blk.accumulate = b > 0;
+    blk.srht_rows = sample;
+    prof_begin(*h, ar, ST_SKETCH, st);
+    SLSO_TRY(run_sketch(*h, ar, Xb[b & 1], rows_of(b), d, d, xdt, params->kind, params->s, params->seed_S,
+                        params->nnz, SX, st, &blk));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  };
+  auto solve = [&](Arena& ar) {
+    return run_solve(*h, ar, SX, params->s, d, tau, params->k, params->seed_Pi, 0, &so, st);
+  };
+  auto score_block = [&](Arena& ar, int64_t b) -> slso_status {
+    prof_begin(*h, ar, ST_SCORES, st);
+    SLSO_TRY(run_scores(*h, ar, Xb[b & 1], rows_of(b), d, d, xdt, so.M, kk, params->compute,
+                        scd + static_cast<size_t>(b * B) * ssz, 0.0, st));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  };
+  auto finish = [&](Arena& ar) -> slso_status {
+    SLSO_TRY(score_sum(*h, ar, scd, sdt, n, st));
+    prof_begin(*h, ar, ST_ORDER, st);
+    SLSO_TRY(order_scores(*h, ar, scd, sdt, n, odd, st));
+    prof_end(*h, ar, st);
+    return SLSO_OK;
+  };
+
+  // footprint: fixed + max(sample, block sketch, solve + block scores, finish), blocks of Bm rows
+  auto aligned = [](size_t v) { return (v + 255) & ~size_t(255); };
+  Arena mf(nullptr, ~size_t(0), true);
+  take_fixed(mf);
+  const size_t off_R = aligned(mf.used());
+  size_t need = 0, solve_used = 0;
+  {
+    Arena m0(nullptr, ~size_t(0), true);
+    SLSO_TRY(draw_sample(m0));
+    need = std::max(need, m0.used());
+    Arena m1(nullptr, ~size_t(0), true);
+    SLSO_TRY(sketch_block(m1, 0));
+    need = std::max(need, m1.used());
+    Arena m2(nullptr, ~size_t(0), true);
+    SLSO_TRY(solve(m2));
+    solve_used = aligned(m2.used());
+    Arena m3(nullptr, ~size_t(0), true);
+    SLSO_TRY(score_block(m3, 0));
+    need = std::max(need, solve_used + m3.used());
+    Arena m4(nullptr, ~size_t(0), true);
+    SLSO_TRY(finish(m4));
+    need = std::max(need, m4.used());
+  }
+  SLSO_TRY(ensure_pool(*h, off_R + need));
+  Arena real(h->pool, h->pool_cap, false);
+  take_fixed(real);
+  auto region = [&](size_t off) { return Arena(h->pool + off_R + off, h->pool_cap - off_R - off, false); };
+
+  // steps: pass 1 over blocks 0 .. nb-1, pass 2 over nb-1 .. 0; block b lives in buffer b & 1, so
+  // pass 2's first two blocks are still on the device
+  struct Step { int pass; int64_t b; };
+  std::vector<Step> steps;
+  for (int64_t b = 0; b < nb; ++b) steps.push_back({1, b});
+  for (int64_t b = nb - 1; b >= 0; --b) steps.push_back({2, b});
+  auto needs_load = [&](size_t j) { return steps[j].pass == 1 || steps[j].b < nb - 2; };
+
+  cudaStream_t h2d = nullptr;
+  cudaEvent_t ev[5] = {};  // start, xready[2], xfree[2]
+  auto go = [&]() -> slso_status {
+    SLSO_CHECK_CUDA(cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : ev) SLSO_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t start = ev[0], *xready = ev + 1, *xfree = ev + 3;
+    SLSO_CHECK_CUDA(cudaMemsetAsync(h->state, 0, sizeof(DevState), st));
+    SLSO_CHECK_CUDA(cudaEventRecord(start, st));
+    SLSO_CHECK_CUDA(cudaStreamWaitEvent(h2d, start, 0));
+    auto copy_in = [&](size_t j) -> slso_status {
+      const int64_t b = steps[j].b;
+      const char* src = static_cast<const char*>(X_host) + static_cast<size_t>(b * B) * ldx * esz;
+      if (ldx == d)
+        SLSO_CHECK_CUDA(cudaMemcpyAsync(Xb[b & 1], src, static_cast<size_t>(rows_of(b)) * d * esz,
+                                        cudaMemcpyHostToDevice, h2d));
+      else
+        SLSO_CHECK_CUDA(cudaMemcpy2DAsync(Xb[b & 1], d * esz, src, ldx * esz, d * esz, rows_of(b),
+                                          cudaMemcpyHostToDevice, h2d));
+      SLSO_CHECK_CUDA(cudaEventRecord(xready[b & 1], h2d));
+      return SLSO_OK;
+    };
+    {
+      Arena r = region(0);
+      SLSO_TRY(draw_sample(r));
+    }
+    for (size_t j = 0; j < 2 && j < steps.size(); ++j)
+      if (needs_load(j)) SLSO_TRY(copy_in(j));
+    for (size_t j = 0; j < steps.size(); ++j) {
+      const int64_t b = steps[j].b;
+      if (needs_load(j)) SLSO_CHECK_CUDA(cudaStreamWaitEvent(st, xready[b & 1], 0));
+      if (steps[j].pass == 1) {
+        Arena r = region(0);
+        SLSO_TRY(sketch_block(r, b));
+        if (r.overflow()) return fail(SLSO_ERR_OOM, "internal: scratch plan overflowed the pool");
+      } else {
+        if (j == static_cast<size_t>(nb)) {
+          Arena r = region(0);
+          SLSO_TRY(solve(r));
+          if (r.overflow()) return fail(SLSO_ERR_OOM, "internal: scratch plan overflowed the pool");
+        }
+        Arena r = region(solve_used);
+        SLSO_TRY(score_block(r, b));
+        if (r.overflow()) return fail(SLSO_ERR_OOM, "internal: scratch plan overflowed the pool");
+      }
+      SLSO_CHECK_CUDA(cudaEventRecord(xfree[b & 1], st));
+      if (j + 2 < steps.size() && needs_load(j + 2)) {
+        SLSO_CHECK_CUDA(cudaStreamWaitEvent(h2d, xfree[steps[j + 2].b & 1], 0));
+        SLSO_TRY(copy_in(j + 2));
+      }
+    }
+    {
+      Arena r = region(0);
+      SLSO_TRY(finish(r));
+      if (r.overflow()) return fail(SLSO_ERR_OOM, "internal: scratch plan overflowed the pool");
+    }
+    prof_begin(*h, real, ST_COPY, st);
+    SLSO_CHECK_CUDA(cudaMemcpyAsync(scores_host, scd, static_cast<size_t>(n) * ssz, cudaMemcpyDeviceToHost, st));
+    SLSO_CHECK_CUDA(cudaMemcpyAsync(order_host, odd, static_cast<size_t>(n) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    prof_end(*h, real, st);
+    slso_info tmp{};
+    return fill_info(*h, st, info ? info : &tmp);
+  };
+  const slso_status r = go();
+  if (r != SLSO_OK) {  // nothing issued may still use the pool, the host buffer or the events
+    cudaStreamSynchronize(st);
+    if (h2d) cudaStreamSynchronize(h2d);
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  if (h2d) cudaStreamDestroy(h2d);
   return r;
 }
 

@@ -382,9 +382,21 @@ slso_status order_scores(Handle& h, Arena& ar, const void* scores, int32_t sdt, 
 // sketch.cu
 // nnz: OSNAP's nonzeros per column of S (ignored by the other kinds).
 constexpr int kOsnapDefaultNnz = 4;
+// A block of rows of a larger X (the streamed entry point): the block is rows row0 .. row0 + n - 1
+// of an X with n_total rows (the sketch's hash, sign and Gaussian counters use those global
+// indices), and with accumulate its sketch is added to SX.  SRHT needs row0 to be a multiple of
+// 8192 and the sampled rows of H drawn once for n_total (srht_sample_rows).
+struct SketchBlock {
+  int64_t row0 = 0;
+  int64_t n_total = 0;  // 0: the block is the whole X
+  bool accumulate = false;
+  const uint32_t* srht_rows = nullptr;
+};
 slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, int32_t kind, int64_t s, uint64_t seed, int nnz, double* SX,
-                       cudaStream_t st);
+                       cudaStream_t st, const SketchBlock* blk = nullptr);
+slso_status srht_sample_rows(Handle& h, Arena& ar, int64_t n_total, int64_t s, uint64_t seed,
+                             const uint32_t** rows, cudaStream_t st);
 
 // solve.cu
 struct SolveOut {
@@ -405,7 +417,6 @@ slso_status check_params(const slso_params* p, int64_t n, int64_t d);
 slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
 
-// score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
 // Approximate left singular vectors U = X V_r Sigma_r^-1 of the sketched SVD (basis.cu).
 slso_status approx_u_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const slso_params* p, void* U, int64_t ldu, cudaStream_t st);
@@ -414,13 +425,18 @@ slso_status sample_order(Handle& h, Arena& ar, const void* scores, int32_t sdt, 
                          uint64_t seed, int64_t* order, cudaStream_t st);
 // Tensor-core Gaussian sketch for float32 / bfloat16 X; *used = false when it does not apply
 // (float64 X or no tensor-map support), and the SIMT kernels run instead.
+// row0: the first row's index in the whole X (a multiple of 4); accumulate adds to SX.
 slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
-                         int64_t s, uint64_t seed, double* SX, cudaStream_t st, bool* used);
+                         int64_t s, uint64_t seed, int64_t row0, bool accumulate, double* SX, cudaStream_t st,
+                         bool* used);
+// score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
                           cudaStream_t st);
 
 // score.cu
+// state->score_sum = the sum of n scores (F32 or F64), in a fixed order.
+slso_status score_sum(Handle& h, Arena& ar, const void* scores, int32_t sdt, int64_t n, cudaStream_t st);
 slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, const double* M, int64_t kk, int32_t compute, void* scores,
                        double correct_frac, cudaStream_t st);

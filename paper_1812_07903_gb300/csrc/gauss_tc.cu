@@ -259,8 +259,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
 constexpr int kGenThreads = 256;
 constexpr int kGenQueue = 2048;  // > kGenThreads - 1 + 4 * kGenThreads: one pass never overflows
 
-__global__ void __launch_bounds__(kGenThreads) gauss_gen_kernel(uint64_t seed, int64_t s, int64_t n, int64_t k0,
-                                                                int64_t Kc, __nv_bfloat16* __restrict__ Gc) {
+__global__ void __launch_bounds__(kGenThreads) gauss_gen_kernel(uint64_t seed, int64_t s, int64_t n, int64_t row0,
+                                                                int64_t k0, int64_t Kc,
+                                                                __nv_bfloat16* __restrict__ Gc) {
   __shared__ uint32_t q_w0[kGenQueue], q_w1[kGenQueue];
   __shared__ int64_t q_at[kGenQueue];
   __shared__ int q_len;
@@ -285,7 +286,8 @@ __global__ void __launch_bounds__(kGenThreads) gauss_gen_kernel(uint64_t seed, i
         const int64_t at = j * Kc + 4 * static_cast<int64_t>(q);
         float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (col < n) {
-          const Gauss4 b = gaussian_block4_f32(seed, static_cast<uint32_t>(j), static_cast<uint64_t>(col) >> 2);
+          // column row0 + col of G (row0 a multiple of 4): the block's row in the whole X
+          const Gauss4 b = gaussian_block4_f32(seed, static_cast<uint32_t>(j), static_cast<uint64_t>(row0 + col) >> 2);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             if (col + e >= n) continue;
@@ -404,10 +406,11 @@ slso_status launch_gauss_tc(const dim3& grid, const GLayout& L, const CUtensorMa
 }  // namespace
 
 slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
-                         int64_t s, uint64_t seed, double* SX, cudaStream_t st, bool* used) {
+                         int64_t s, uint64_t seed, int64_t row0, bool accumulate, double* SX, cudaStream_t st,
+                         bool* used) {
   *used = false;
   if (xdt != SLSO_F32 && xdt != SLSO_BF16) return SLSO_OK;
-  if (!encode_fn()) return SLSO_OK;
+  if (row0 % 4 != 0 || !encode_fn()) return SLSO_OK;
   const int P = (xdt == SLSO_BF16) ? 1 : 3;
   const int NT = choose_nt(d, P);
   const int64_t Kc = std::min<int64_t>(kChunkRows, ceil_div(n, kGKB) * kGKB);
@@ -433,7 +436,7 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
       1, std::min<int64_t>(s, ceil_div(int64_t(h.num_sms) * 8, static_cast<int64_t>(gen_x)))));
   const dim3 grid_gen(gen_x, gen_y);
   for (int64_t k0 = 0; k0 < n; k0 += Kc) {
-    gauss_gen_kernel<<<grid_gen, kGenThreads, 0, st>>>(seed, s, n, k0, Kc, Gc);
+    gauss_gen_kernel<<<grid_gen, kGenThreads, 0, st>>>(seed, s, n, row0, k0, Kc, Gc);
     SLSO_CHECK_LAUNCH();
     if (xdt == SLSO_F32)
       xt_split_kernel<float><<<grid_xt, dim3(32, 8), 0, st>>>(static_cast<const float*>(X), n, d, ldx, k0, Kc, P,
@@ -442,7 +445,7 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
       xt_split_kernel<__nv_bfloat16><<<grid_xt, dim3(32, 8), 0, st>>>(static_cast<const __nv_bfloat16*>(X), n, d,
                                                                       ldx, k0, Kc, P, XT, h.state);
     SLSO_CHECK_LAUNCH();
-    const int first = (k0 == 0) ? 1 : 0;
+    const int first = (k0 == 0 && !accumulate) ? 1 : 0;
     switch (NT) {
       case 256: SLSO_TRY(launch_gauss_tc<256>(grid_tc, L, mA, mB, s, d, scale, first, SX, h.state, st)); break;
       case 128: SLSO_TRY(launch_gauss_tc<128>(grid_tc, L, mA, mB, s, d, scale, first, SX, h.state, st)); break;

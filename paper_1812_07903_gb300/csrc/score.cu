@@ -292,3 +292,14 @@ slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d
 }
 
 }  // namespace slso
+
+namespace slso {
+
+slso_status score_sum(Handle& h, Arena& ar, const void* scores, int32_t sdt, int64_t n, cudaStream_t st) {
+  double* sums = ar.take<double>(kSumBlocks);
+  if (ar.measure()) return SLSO_OK;
+  if (sdt == SLSO_F64) return launch_score_sum<double>(h, static_cast<const double*>(scores), n, sums, st);
+  return launch_score_sum<float>(h, static_cast<const float*>(scores), n, sums, st);
+}
+
+}  // namespace slso

@@ -26,7 +26,7 @@ namespace {
 // Hashes of CountSketch (z = 1, tag 1) and OSNAP (z blocks, tag 7): entry e = b n + i (block b,
 // row i) gets bucket b (s/z) + ((w0 (s/z)) >> 32) and sign 1 - 2 (w1 & 1) from Philox at counter
 // (lo i, hi i, b, tag).  Within a bucket (one block) the stable sort keeps rows ascending.
-__global__ void cs_hash_kernel(int64_t n, uint32_t s, int z, uint32_t tag, uint64_t seed,
+__global__ void cs_hash_kernel(int64_t n, int64_t row0, uint32_t s, int z, uint32_t tag, uint64_t seed,
                                uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const uint32_t m = s / static_cast<uint32_t>(z);
   const int64_t total = n * z;
@@ -34,8 +34,8 @@ __global__ void cs_hash_kernel(int64_t n, uint32_t s, int z, uint32_t tag, uint6
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const uint32_t b = static_cast<uint32_t>(e / n);
     const int64_t i = e - static_cast<int64_t>(b) * n;
-    const U32x4 w = philox(static_cast<uint32_t>(i), static_cast<uint32_t>(static_cast<uint64_t>(i) >> 32), b, tag,
-                           seed);
+    const uint64_t ig = static_cast<uint64_t>(row0 + i);  // row of the whole X: the hash's counter
+    const U32x4 w = philox(static_cast<uint32_t>(ig), static_cast<uint32_t>(ig >> 32), b, tag, seed);
     keys[e] = b * m + static_cast<uint32_t>((static_cast<uint64_t>(w.x) * m) >> 32);
     vals[e] = static_cast<uint32_t>(i) | ((w.y & 1u) << 31);  // sign bit: 1 means -1
   }
@@ -80,7 +80,7 @@ template <class T, int VEC, int UNROLL>
 __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X, int64_t d, int64_t ldx,
                                                         const uint32_t* __restrict__ rows,
                                                         const uint32_t* __restrict__ start,
-                                                        double* __restrict__ SX, double scale,
+                                                        double* __restrict__ SX, double scale, int acc,
                                                         DevState* __restrict__ state) {
   const uint32_t b = blockIdx.x;
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * VEC;
@@ -125,8 +125,11 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
   if (active) {
 #pragma unroll
     for (int v = 0; v < VEC; ++v)
-      if (c0 + v < d)
-        SX[static_cast<int64_t>(b) * d + c0 + v] = (static_cast<double>(hi[v]) + static_cast<double>(lo[v])) * scale;
+      if (c0 + v < d) {
+        double* o = SX + static_cast<int64_t>(b) * d + c0 + v;
+        const double t = (static_cast<double>(hi[v]) + static_cast<double>(lo[v])) * scale;
+        *o = acc ? *o + t : t;
+      }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&state->nonfinite, 1);
 }
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
 __global__ void __launch_bounds__(256) cs_gather_f64_kernel(const double* __restrict__ X, int64_t d,
                                                             int64_t ldx, const uint32_t* __restrict__ rows,
                                                             const uint32_t* __restrict__ start,
-                                                            double* __restrict__ SX, double scale,
+                                                            double* __restrict__ SX, double scale, int accum,
                                                             DevState* __restrict__ state) {
   const uint32_t b = blockIdx.x;
   const int64_t c = static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x;
@@ -148,7 +151,8 @@ __global__ void __launch_bounds__(256) cs_gather_f64_kernel(const double* __rest
       bad |= !isfinite(x);
       acc += (rv >> 31) ? -x : x;
     }
-    SX[static_cast<int64_t>(b) * d + c] = acc * scale;
+    double* o = SX + static_cast<int64_t>(b) * d + c;
+    *o = accum ? *o + acc * scale : acc * scale;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&state->nonfinite, 1);
 }
@@ -180,7 +184,7 @@ constexpr int kSrhtThreads = 512;
 // CTA (i1, slab): chunk i1 of n2 rows, columns [c0, c0 + 4).  Acc = float (F32/BF16 X) or double.
 template <class T, class Acc>
 __global__ void __launch_bounds__(kSrhtThreads) srht_chunk_kernel(
-    const T* __restrict__ X, int64_t n, int64_t d, int64_t ldx, int log2_n2, uint64_t seed,
+    const T* __restrict__ X, int64_t n, int64_t d, int64_t ldx, int64_t row0, int log2_n2, uint64_t seed,
     const uint32_t* __restrict__ sample, int64_t s, Acc* __restrict__ P, DevState* __restrict__ state) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* T_s = reinterpret_cast<Acc*>(smem_raw);  // [n2][kSrhtSlab]
@@ -189,11 +193,11 @@ __global__ void __launch_bounds__(kSrhtThreads) srht_chunk_kernel(
   const int64_t c0 = static_cast<int64_t>(blockIdx.y) * kSrhtSlab;
   bool bad = false;
   for (int64_t r = threadIdx.x; r < n2; r += kSrhtThreads) {
-    const int64_t i = i1 * n2 + r;
+    const int64_t i = i1 * n2 + r;  // row of this block; row0 + i of the whole X
     Acc v[kSrhtSlab];
     if (i < n) {
-      const U32x4 w = philox(static_cast<uint32_t>(i), static_cast<uint32_t>(static_cast<uint64_t>(i) >> 32),
-                             0u, TAG_SRHT_SIGN, seed);
+      const uint64_t ig = static_cast<uint64_t>(row0 + i);
+      const U32x4 w = philox(static_cast<uint32_t>(ig), static_cast<uint32_t>(ig >> 32), 0u, TAG_SRHT_SIGN, seed);
       const bool neg = w.x & 1u;
 #pragma unroll
       for (int c = 0; c < kSrhtSlab; ++c) {
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(kSrhtThreads) srht_chunk_kernel(
   for (int64_t q = threadIdx.x; q < s; q += kSrhtThreads) {
     const uint32_t j = sample[q];
     const uint32_t j1 = j >> log2_n2, j2 = j & static_cast<uint32_t>(n2 - 1);
-    const bool neg = __popc(static_cast<uint32_t>(i1) & j1) & 1;
+    const bool neg = __popc(static_cast<uint32_t>((row0 >> log2_n2) + i1) & j1) & 1;  // row0: multiple of n2
 #pragma unroll
     for (int c = 0; c < kSrhtSlab; ++c) {
       if (c0 + c < d) {
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(kSrhtThreads) srht_chunk_kernel(
 
 // SX[q][c] = (sum_i1 P[(i1*d + c)*s + q]) / sqrt(s), float64, ascending i1; 32x32 tile transpose.
 template <class Acc>
-__global__ void srht_combine_kernel(const Acc* __restrict__ P, int64_t n1, int64_t d, int64_t s,
+__global__ void srht_combine_kernel(const Acc* __restrict__ P, int64_t n1, int64_t d, int64_t s, int accum,
                                     double* __restrict__ SX) {
   __shared__ double tile[32][33];
   const int64_t q0 = static_cast<int64_t>(blockIdx.x) * 32, c0 = static_cast<int64_t>(blockIdx.y) * 32;
@@ -253,7 +257,7 @@ __global__ void srht_combine_kernel(const Acc* __restrict__ P, int64_t n1, int64
   __syncthreads();
   for (int qq = threadIdx.y; qq < 32; qq += blockDim.y) {
     const int64_t q = q0 + qq, c = c0 + threadIdx.x;
-    if (q < s && c < d) SX[q * d + c] = tile[threadIdx.x][qq];
+    if (q < s && c < d) SX[q * d + c] = accum ? SX[q * d + c] + tile[threadIdx.x][qq] : tile[threadIdx.x][qq];
   }
 }
 
@@ -265,7 +269,7 @@ constexpr int kGbm = 64, kGbn = 64, kGbk = 16;
 // (hi, lo) pair (float32 data) or a float64 sum (float64 data).
 template <class T, class Acc>
 __global__ void __launch_bounds__(256) gauss_tile_kernel(const T* __restrict__ X, int64_t n, int64_t d,
-                                                         int64_t ldx, int64_t s, uint64_t seed,
+                                                         int64_t ldx, int64_t row0, int64_t s, uint64_t seed,
                                                          int64_t kc, Acc* __restrict__ P,
                                                          DevState* __restrict__ state) {
   __shared__ Acc Gs[kGbk][kGbm + 1];
@@ -284,7 +288,8 @@ __global__ void __launch_bounds__(256) gauss_tile_kernel(const T* __restrict__ X
     for (int t = threadIdx.x; t < kGbk * kGbm; t += 256) {
       const int kk = t / kGbm, jj = t % kGbm;
       const int64_t i = k0 + kk, j = j0 + jj;
-      Gs[kk][jj] = (i < r1 && j < s) ? static_cast<Acc>(gaussian_entry(seed, static_cast<uint32_t>(j), i)) : Acc(0);
+      Gs[kk][jj] = (i < r1 && j < s) ? static_cast<Acc>(gaussian_entry(seed, static_cast<uint32_t>(j), row0 + i))
+                                     : Acc(0);
     }
     for (int t = threadIdx.x; t < kGbk * kGbn; t += 256) {
       const int kk = t / kGbn, cc = t % kGbn;
@@ -332,14 +337,14 @@ __global__ void __launch_bounds__(256) gauss_tile_kernel(const T* __restrict__ X
 }
 
 template <class Acc>
-__global__ void gauss_combine_kernel(const Acc* __restrict__ P, int64_t nz, int64_t sd, int64_t s,
+__global__ void gauss_combine_kernel(const Acc* __restrict__ P, int64_t nz, int64_t sd, int64_t s, int accum,
                                      double* __restrict__ SX) {
   const double inv = sqrt(static_cast<double>(s));
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < sd;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     double acc = 0.0;
     for (int64_t z = 0; z < nz; ++z) acc += static_cast<double>(P[z * sd + e]);
-    SX[e] = acc / inv;
+    SX[e] = accum ? SX[e] + acc / inv : acc / inv;
   }
 }
 
@@ -349,9 +354,12 @@ int grid_for(int64_t n, const Handle& h) {
 
 // CountSketch (z = 1) and OSNAP (z blocks, entries +-1/sqrt(z)): hash, stable sort of the n z
 // entries by bucket, then the deterministic gather of each bucket's rows in ascending order.
+// The rows are rows row0 .. row0 + n - 1 of the whole X (their hash counters); acc adds the
+// block's sketch to SX.
 template <class T>
 slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx,
-                        int64_t s, uint64_t seed, int z, uint32_t tag, double* SX, cudaStream_t st) {
+                        int64_t s, uint64_t seed, int z, uint32_t tag, int64_t row0, int acc, double* SX,
+                        cudaStream_t st) {
   const int64_t N = n * z;
   uint32_t* keys = ar.take<uint32_t>(N);
   uint32_t* vals = ar.take<uint32_t>(N);
@@ -361,7 +369,7 @@ slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, 
   uint32_t* ks = keys;
   uint32_t* vs = vals;
   if (!ar.measure()) {
-    cs_hash_kernel<<<grid_for(N, h), 256, 0, st>>>(n, static_cast<uint32_t>(s), z, tag, seed, keys, vals);
+    cs_hash_kernel<<<grid_for(N, h), 256, 0, st>>>(n, row0, static_cast<uint32_t>(s), z, tag, seed, keys, vals);
     SLSO_CHECK_LAUNCH();
   }
   if (bits > 0) SLSO_TRY(radix_sort_u32(ar, keys, vals, N, bits, st, &ks, &vs));
@@ -371,7 +379,7 @@ slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, 
   const double scale = (z == 1) ? 1.0 : 1.0 / std::sqrt(static_cast<double>(z));
   if constexpr (std::is_same<T, double>::value) {
     dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(d, 256)));
-    cs_gather_f64_kernel<<<grid, 256, 0, st>>>(X, d, ldx, vs, start, SX, scale, h.state);
+    cs_gather_f64_kernel<<<grid, 256, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state);
   } else {
     const bool vec = (d % 4 == 0) && (ldx % 4 == 0) &&
                      (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(T)) == 0);
@@ -379,32 +387,102 @@ slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, 
       const int64_t thr_needed = ceil_div(d, 4);
       const int threads = static_cast<int>(std::min<int64_t>(256, ceil_div(thr_needed, 32) * 32));
       dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(thr_needed, threads)));
-      cs_gather_kernel<T, 4, 4><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, h.state);
+      cs_gather_kernel<T, 4, 4><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state);
     } else {
       const int threads = static_cast<int>(std::min<int64_t>(256, ceil_div(d, 32) * 32));
       dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(d, threads)));
-      cs_gather_kernel<T, 1, 8><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, h.state);
+      cs_gather_kernel<T, 1, 8><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state);
     }
   }
   SLSO_CHECK_LAUNCH();
   return SLSO_OK;
 }
 
-template <class T>
-slso_status srht(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx, int64_t s,
-                 uint64_t seed, double* SX, cudaStream_t st) {
-  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+int log2_ceil(int64_t n) {
   int m = 0;
   while ((int64_t(1) << m) < n) ++m;
+  return m;
+}
+
+template <class T>
+int srht_log2_n2(int64_t n_total) {
+  const int log2_n2_max = std::is_same<T, double>::value ? 12 : 13;  // 128 KB of shared memory
+  return std::min(log2_ceil(n_total), log2_n2_max);
+}
+
+// Rows n .. n_pad - 1 of the padded X are zero, so only the ceil(n / n2) chunks holding rows of
+// this block are transformed; the whole X has n_total rows and the block starts at row row0 (a
+// multiple of n2).
+template <class T>
+slso_status srht(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx, int64_t s,
+                 uint64_t seed, const uint32_t* sample, int64_t row0, int64_t n_total, int acc, double* SX,
+                 cudaStream_t st) {
+  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  const int log2_n2 = srht_log2_n2<T>(n_total);
+  const int64_t n1 = ceil_div(n, int64_t(1) << log2_n2);
+  if (sample == nullptr) SLSO_TRY(srht_sample_rows(h, ar, n_total, s, seed, &sample, st));
+  Acc* P = ar.take<Acc>(static_cast<size_t>(n1) * d * s);
+  if (ar.measure()) return SLSO_OK;
+  const size_t smem = (size_t(1) << log2_n2) * kSrhtSlab * sizeof(Acc);
+  SLSO_CHECK_CUDA(cudaFuncSetAttribute(srht_chunk_kernel<T, Acc>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  dim3 g1(static_cast<unsigned>(n1), static_cast<unsigned>(ceil_div(d, kSrhtSlab)));
+  srht_chunk_kernel<T, Acc><<<g1, kSrhtThreads, smem, st>>>(X, n, d, ldx, row0, log2_n2, seed, sample, s, P,
+                                                            h.state);
+  SLSO_CHECK_LAUNCH();
+  dim3 g2(static_cast<unsigned>(ceil_div(s, 32)), static_cast<unsigned>(ceil_div(d, 32)));
+  srht_combine_kernel<Acc><<<g2, dim3(32, 8), 0, st>>>(P, n1, d, s, acc, SX);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
+template <class T>
+slso_status gaussian(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx, int64_t s,
+                     uint64_t seed, int64_t row0, int acc, double* SX, cudaStream_t st) {
+  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  // chunks of >= 2048 rows, at most 32 of them
+  const int64_t kc = std::max<int64_t>(2048, ceil_div(ceil_div(n, 32), kGbk) * kGbk);
+  const int64_t nz = ceil_div(n, kc);
+  Acc* P = ar.take<Acc>(static_cast<size_t>(nz) * s * d);
+  if (ar.measure()) return SLSO_OK;
+  dim3 g1(static_cast<unsigned>(ceil_div(s, kGbm)), static_cast<unsigned>(ceil_div(d, kGbn)),
+          static_cast<unsigned>(nz));
+  gauss_tile_kernel<T, Acc><<<g1, 256, 0, st>>>(X, n, d, ldx, row0, s, seed, kc, P, h.state);
+  SLSO_CHECK_LAUNCH();
+  gauss_combine_kernel<Acc><<<grid_for(s * d, h), 256, 0, st>>>(P, nz, s * d, s, acc, SX);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
+template <class T>
+slso_status sketch_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx, int32_t kind,
+                         int64_t s, uint64_t seed, int nnz, const SketchBlock& b, double* SX, cudaStream_t st) {
+  const int acc = b.accumulate ? 1 : 0;
+  switch (kind) {
+    case SLSO_COUNTSKETCH:
+      return countsketch(h, ar, X, n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, b.row0, acc, SX, st);
+    case SLSO_OSNAP:
+      return countsketch(h, ar, X, n, d, ldx, s, seed, nnz > 0 ? nnz : kOsnapDefaultNnz, TAG_OSNAP, b.row0, acc,
+                         SX, st);
+    case SLSO_SRHT:
+      return srht(h, ar, X, n, d, ldx, s, seed, b.srht_rows, b.row0, b.n_total > 0 ? b.n_total : n, acc, SX, st);
+    default:
+      return gaussian(h, ar, X, n, d, ldx, s, seed, b.row0, acc, SX, st);
+  }
+}
+
+}  // namespace
+
+// The s sampled rows of H for an X of n_total rows: the s smallest (Philox key, index) among the
+// n_pad = 2^ceil(log2 n_total) rows, then sorted ascending.
+slso_status srht_sample_rows(Handle& h, Arena& ar, int64_t n_total, int64_t s, uint64_t seed,
+                             const uint32_t** rows, cudaStream_t st) {
+  const int m = log2_ceil(n_total);
   const int64_t n_pad = int64_t(1) << m;
-  const int log2_n2_max = std::is_same<Acc, double>::value ? 12 : 13;  // 128 KB of shared memory
-  const int log2_n2 = std::min(m, log2_n2_max);
-  const int64_t n1 = n_pad >> log2_n2;
   uint32_t* keys = ar.take<uint32_t>(n_pad);
   uint32_t* vals = ar.take<uint32_t>(n_pad);
   uint32_t* skeys = ar.take<uint32_t>(s);
   uint32_t* svals = ar.take<uint32_t>(s);
-  Acc* P = ar.take<Acc>(static_cast<size_t>(n1) * d * s);
   uint32_t* ks = nullptr;
   uint32_t* vs = nullptr;
   if (!ar.measure()) {
@@ -417,78 +495,32 @@ slso_status srht(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t
     copy_u32_kernel<<<grid_for(s, h), 256, 0, st>>>(vs, s, skeys, svals);
     SLSO_CHECK_LAUNCH();
   }
-  uint32_t* sk = nullptr;
+  uint32_t* sk = skeys;
   uint32_t* sv = nullptr;
-  if (m > 0) {
-    SLSO_TRY(radix_sort_u32(ar, skeys, svals, s, m, st, &sk, &sv));
-  } else {
-    sk = skeys;
-  }
-  if (ar.measure()) return SLSO_OK;
-  const size_t smem = (size_t(1) << log2_n2) * kSrhtSlab * sizeof(Acc);
-  SLSO_CHECK_CUDA(cudaFuncSetAttribute(srht_chunk_kernel<T, Acc>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  dim3 g1(static_cast<unsigned>(n1), static_cast<unsigned>(ceil_div(d, kSrhtSlab)));
-  srht_chunk_kernel<T, Acc><<<g1, kSrhtThreads, smem, st>>>(X, n, d, ldx, log2_n2, seed, sk, s, P, h.state);
-  SLSO_CHECK_LAUNCH();
-  dim3 g2(static_cast<unsigned>(ceil_div(s, 32)), static_cast<unsigned>(ceil_div(d, 32)));
-  srht_combine_kernel<Acc><<<g2, dim3(32, 8), 0, st>>>(P, n1, d, s, SX);
-  SLSO_CHECK_LAUNCH();
+  if (m > 0) SLSO_TRY(radix_sort_u32(ar, skeys, svals, s, m, st, &sk, &sv));
+  *rows = sk;
   return SLSO_OK;
 }
-
-template <class T>
-slso_status gaussian(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx, int64_t s,
-                     uint64_t seed, double* SX, cudaStream_t st) {
-  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
-  // chunks of >= 2048 rows, at most 32 of them
-  const int64_t kc = std::max<int64_t>(2048, ceil_div(ceil_div(n, 32), kGbk) * kGbk);
-  const int64_t nz = ceil_div(n, kc);
-  Acc* P = ar.take<Acc>(static_cast<size_t>(nz) * s * d);
-  if (ar.measure()) return SLSO_OK;
-  dim3 g1(static_cast<unsigned>(ceil_div(s, kGbm)), static_cast<unsigned>(ceil_div(d, kGbn)),
-          static_cast<unsigned>(nz));
-  gauss_tile_kernel<T, Acc><<<g1, 256, 0, st>>>(X, n, d, ldx, s, seed, kc, P, h.state);
-  SLSO_CHECK_LAUNCH();
-  gauss_combine_kernel<Acc><<<grid_for(s * d, h), 256, 0, st>>>(P, nz, s * d, s, SX);
-  SLSO_CHECK_LAUNCH();
-  return SLSO_OK;
-}
-
-}  // namespace
 
 slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, int32_t kind, int64_t s, uint64_t seed, int nnz, double* SX,
-                       cudaStream_t st) {
-  switch (kind) {
-    case SLSO_COUNTSKETCH:
-      if (xdt == SLSO_F32)
-        return countsketch(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, SX, st);
-      if (xdt == SLSO_BF16)
-        return countsketch(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, SX, st);
-      return countsketch(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, SX, st);
-    case SLSO_OSNAP: {
-      const int z = nnz > 0 ? nnz : kOsnapDefaultNnz;
-      if (xdt == SLSO_F32)
-        return countsketch(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, z, TAG_OSNAP, SX, st);
-      if (xdt == SLSO_BF16)
-        return countsketch(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, z, TAG_OSNAP, SX, st);
-      return countsketch(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, z, TAG_OSNAP, SX, st);
-    }
-    case SLSO_SRHT:
-      if (xdt == SLSO_F32) return srht(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, SX, st);
-      if (xdt == SLSO_BF16) return srht(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, SX, st);
-      return srht(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, SX, st);
-    case SLSO_GAUSSIAN: {
-      bool used = false;
-      SLSO_TRY(run_gauss_tc(h, ar, X, n, d, ldx, xdt, s, seed, SX, st, &used));
-      if (used) return SLSO_OK;
-      if (xdt == SLSO_F32) return gaussian(h, ar, static_cast<const float*>(X), n, d, ldx, s, seed, SX, st);
-      if (xdt == SLSO_BF16) return gaussian(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, s, seed, SX, st);
-      return gaussian(h, ar, static_cast<const double*>(X), n, d, ldx, s, seed, SX, st);
-    }
+                       cudaStream_t st, const SketchBlock* blk) {
+  const SketchBlock whole{};
+  const SketchBlock& b = blk ? *blk : whole;
+  if (kind != SLSO_COUNTSKETCH && kind != SLSO_OSNAP && kind != SLSO_SRHT && kind != SLSO_GAUSSIAN)
+    return fail(SLSO_ERR_INVALID_ARG, "unknown sketch kind %d", kind);
+  if (kind == SLSO_GAUSSIAN) {
+    bool used = false;
+    SLSO_TRY(run_gauss_tc(h, ar, X, n, d, ldx, xdt, s, seed, b.row0, b.accumulate, SX, st, &used));
+    if (used) return SLSO_OK;
+  }
+  switch (xdt) {
+    case SLSO_F32:
+      return sketch_typed(h, ar, static_cast<const float*>(X), n, d, ldx, kind, s, seed, nnz, b, SX, st);
+    case SLSO_BF16:
+      return sketch_typed(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, kind, s, seed, nnz, b, SX, st);
     default:
-      return fail(SLSO_ERR_INVALID_ARG, "unknown sketch kind %d", kind);
+      return sketch_typed(h, ar, static_cast<const double*>(X), n, d, ldx, kind, s, seed, nnz, b, SX, st);
   }
 }
 
