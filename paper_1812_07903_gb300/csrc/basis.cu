@@ -1,9 +1,12 @@
 // Approximate left singular vectors U = X V_r Sigma_r^-1 (Algorithm 2 step 3; Algorithm 3
 // step 4): the sketch SX, its sketched SVD (Householder QR + one-sided Jacobi SVD of R, float64,
 // rank r = #{sigma_j > tau sigma_1} on the device), M = V diag(1/sigma) with columns >= r zero,
-// then the product X M written tile by tile (CTA tile 64 rows x 64 columns, K-steps of 16 through
-// shared memory, 4 x 4 outputs per thread): float64 for float64 X, float32 otherwise.
+// then the product X M.  For float32 / bfloat16 X it runs on the tensor cores (the score kernel
+// with a write-out epilogue, 256-column blocks of M, float32-accurate 3xTF32 / BF16X3 operands);
+// for float64 X it is written tile by tile in float64 (CTA tile 64 rows x 64 columns, K-steps of
+// 16 through shared memory, 4 x 4 outputs per thread).
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -85,6 +88,18 @@ __global__ void __launch_bounds__(256) basis_tile_kernel(const T* __restrict__ X
 template <class T, class Acc>
 slso_status basis_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx, const SolveOut& so,
                         Acc* U, int64_t ldu, cudaStream_t st) {
+  if constexpr (!std::is_same<T, double>::value) {
+    // float32 / bfloat16 X: the product on the tensor cores (float32-accurate split operands)
+    double* M64 = ar.take<double>(static_cast<size_t>(d) * d);
+    if (!ar.measure()) {
+      basis_m_kernel<double><<<blocks_for(d * d, h), 256, 0, st>>>(so.sigma, so.V, d, h.state, M64);
+      SLSO_CHECK_LAUNCH();
+    }
+    bool used = false;
+    SLSO_TRY(run_product_tc(h, ar, X, n, d, ldx, std::is_same<T, float>::value ? SLSO_F32 : SLSO_BF16, M64, d, U,
+                            ldu, &used, st));
+    if (used) return SLSO_OK;
+  }
   Acc* M = ar.take<Acc>(static_cast<size_t>(d) * d);
   if (ar.measure()) return SLSO_OK;
   basis_m_kernel<Acc><<<blocks_for(d * d, h), 256, 0, st>>>(so.sigma, so.V, d, h.state, M);

@@ -434,6 +434,11 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
                           cudaStream_t st);
 
+// Y = X M (M d x kk row-major float64) written to U (float32, row stride ldu) on the tensor cores
+// for float32 / bfloat16 X (score_tc.cu); *used = false when the SIMT kernel must run instead.
+slso_status run_product_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
+                           const double* M, int64_t kk, float* U, int64_t ldu, bool* used, cudaStream_t st);
+
 // score.cu
 // state->score_sum = the sum of n scores (F32 or F64), in a fixed order.
 slso_status score_sum(Handle& h, Arena& ar, const void* scores, int32_t sdt, int64_t n, cudaStream_t st);

@@ -83,9 +83,10 @@ __device__ __forceinline__ void split_tf32(uint32_t x, uint32_t& hi, uint32_t& l
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB0,
                     const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
-                    const Layout L, int64_t n, int ntiles,
+                    const Layout L, int64_t n, int ntiles, int ncb,
                     const float* __restrict__ cscale, const float* __restrict__ post_scale,
-                    float* __restrict__ scores, DevState* __restrict__ state) {
+                    float* __restrict__ scores, float* __restrict__ U, int64_t ldu, int64_t ucols,
+                    DevState* __restrict__ state) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const volatile int* abort_flag = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool convert = !direct_x(L.mode);
+  const int nwork = ntiles * ncb;  // (row tile, column block) work items, row tile major
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -129,8 +131,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int y = tile * kBM;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        const int y = (w / ncb) * kBM;
+        const int yb = (w % ncb) * L.N;  // rows of B = M^T: this work item's column block
         for (int kb = 0; kb < L.KB; ++kb, ++it) {
           const int os = it % L.OS;
           const uint32_t oph = (it / L.OS) & 1u;
@@ -141,10 +144,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nb = b_tiles(L.mode);
             mbar_arrive_expect_tx(&op_full[os], kXTileBytes + nb * L.b_bytes);
             tma_load_2d(op, &tmX, &op_full[os], x, y);
-            tma_load_2d(op + kXTileBytes, &tmB0, &op_full[os], x, 0);
+            tma_load_2d(op + kXTileBytes, &tmB0, &op_full[os], x, yb);
             if (nb == 3) {
-              tma_load_2d(op + kXTileBytes + L.b_bytes, &tmB1, &op_full[os], x, 0);
-              tma_load_2d(op + kXTileBytes + 2 * L.b_bytes, &tmB2, &op_full[os], x, 0);
+              tma_load_2d(op + kXTileBytes + L.b_bytes, &tmB1, &op_full[os], x, yb);
+              tma_load_2d(op + kXTileBytes + 2 * L.b_bytes, &tmB2, &op_full[os], x, yb);
             }
             continue;
           }
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           unsigned char* raw = smem + L.raw_off + rs * L.raw_bytes;
           const int nb = (L.mode == MODE_TF32X3) ? 2 : 1;  // B tiles per stage
           mbar_arrive_expect_tx(&op_full[os], nb * L.b_bytes);
-          tma_load_2d(op + L.x_op_bytes, &tmB0, &op_full[os], x, 0);
-          if (nb == 2) tma_load_2d(op + L.x_op_bytes + L.b_bytes, &tmB1, &op_full[os], x, 0);
+          tma_load_2d(op + L.x_op_bytes, &tmB0, &op_full[os], x, yb);
+          if (nb == 2) tma_load_2d(op + L.x_op_bytes + L.b_bytes, &tmB1, &op_full[os], x, yb);
           mbar_arrive_expect_tx(&raw_full[rs], L.raw_boxes * kXTileBytes);
           for (int b = 0; b < L.raw_boxes; ++b)
             tma_load_2d(raw + b * kXTileBytes, &tmX, &raw_full[rs], x + b * L.box_cols, y);
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                   : idesc(FMT_BF16, FMT_BF16, kBM, L.N);
       int it = 0, tcount = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++tcount) {
         const int ab = tcount & 1;
         const uint32_t aph = (tcount >> 1) & 1u;
         if (!mbar_wait(&acc_empty[ab], aph ^ 1u, abort_flag)) { ok = false; break; }
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int ct = threadIdx.x - kWarpConvert0 * 32;  // 0 .. kConvThreads-1
       int it = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
         for (int kb = 0; kb < L.KB; ++kb, ++it) {
           const int rs = it % L.RS, os = it % L.OS;
           if (!mbar_wait(&raw_full[rs], (it / L.RS) & 1u, abort_flag)) { ok = false; break; }
@@ -340,7 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float post = post_scale ? *post_scale : 1.0f;
     int tcount = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++tcount) {
+      const int tile = w / ncb;
       const int ab = tcount & 1;
       const uint32_t aph = (tcount >> 1) & 1u;
       int got = 0;
@@ -349,6 +353,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!got) { ok = false; break; }
       tc_fence_after();
       const uint32_t taddr = tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(ab * L.N);
+      const int64_t row = static_cast<int64_t>(tile) * kBM + warp * 32 + lane;
+      if (U) {  // Y = X M written out: this thread's row, columns of block w % ncb
+        const int64_t col_base = static_cast<int64_t>(w % ncb) * L.N;
+        float* urow = U + row * ldu + col_base;
+        const bool vec = (ldu % 4 == 0) && ((reinterpret_cast<uintptr_t>(U) & 15u) == 0);
+        for (int c0 = 0; c0 < L.N && col_base + c0 < ucols; c0 += 32) {
+          float v[32];
+          tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c0), v);
+          if (row >= n) continue;
+          if (vec && col_base + c0 + 32 <= ucols) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(urow + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (col_base + c0 + i < ucols) urow[c0 + i] = v[i];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[ab]);
+        continue;
+      }
       float sum = 0.0f;
       for (int c0 = 0; c0 < L.N; c0 += 32) {
         float v[32];
@@ -358,7 +385,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[ab]);
-      const int64_t row = static_cast<int64_t>(tile) * kBM + warp * 32 + lane;
       if (row < n) scores[row] = sum * post;
     }
     if (!ok && lane == 0) {
@@ -592,8 +618,67 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   const int grid = std::min(ntiles, h.num_sms);
   SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(L.smem_bytes)));
-  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, mB2, L, n, ntiles, cscale,
-                                                        fp8 ? escale + 1 : nullptr, scores, h.state);
+  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, mB2, L, n, ntiles, 1, cscale,
+                                                        fp8 ? escale + 1 : nullptr, scores, nullptr, 0, 0,
+                                                        h.state);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
+
+// Y = X M written to U (float32, n x ucols, row stride ldu) on the tensor cores, for M d x kk
+// (row-major float64) with kk columns taken in blocks of 256: float32 X as 3xTF32, bfloat16 X
+// as BF16X3 (both float32-accurate).  *used = false when the shapes need the SIMT kernel.
+slso_status run_product_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
+                           const double* M, int64_t kk, float* U, int64_t ldu, bool* used, cudaStream_t st) {
+  *used = false;
+  const int mode = (xdt == SLSO_F32) ? MODE_TF32X3 : (xdt == SLSO_BF16 ? MODE_BF16X3 : -1);
+  if (mode < 0 || kk < 1) return SLSO_OK;
+  const size_t esz = dtype_size(xdt);
+  if (reinterpret_cast<uintptr_t>(X) % 16 != 0 || (ldx * esz) % 16 != 0) return SLSO_OK;
+  if (!encode_fn()) return SLSO_OK;
+  const Layout L = make_layout(mode, std::min<int64_t>(kk, 256), d);
+  const int ncb = static_cast<int>(ceil_div(kk, L.N));
+  const int64_t NB = static_cast<int64_t>(ncb) * L.N;  // rows of B = M^T, zero beyond kk
+  const int64_t Kpad = static_cast<int64_t>(L.KB) * L.kbe;
+  void* B0 = nullptr;
+  void* B1 = nullptr;
+  void* B2 = nullptr;
+  if (mode == MODE_TF32X3) {
+    B0 = ar.take<float>(static_cast<size_t>(NB) * Kpad);
+    B1 = ar.take<float>(static_cast<size_t>(NB) * Kpad);
+  } else {
+    B0 = ar.take<__nv_bfloat16>(static_cast<size_t>(NB) * Kpad);
+    B1 = ar.take<__nv_bfloat16>(static_cast<size_t>(NB) * Kpad);
+    B2 = ar.take<__nv_bfloat16>(static_cast<size_t>(NB) * Kpad);
+  }
+  *used = true;
+  if (ar.measure()) return SLSO_OK;
+  const int pg = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(NB * Kpad, 256), 4LL * h.num_sms)));
+  CUtensorMap mX, mB0, mB1, mB2;
+  const CUtensorMapDataType xdt_map = (xdt == SLSO_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  bool ok = make_map(&mX, xdt_map, X, d, n, ldx * esz, static_cast<uint32_t>(L.box_cols), kBM);
+  if (mode == MODE_TF32X3) {
+    prep_b_tf32_kernel<<<pg, 256, 0, st>>>(M, d, kk, NB, Kpad, static_cast<float*>(B0), static_cast<float*>(B1));
+    SLSO_CHECK_LAUNCH();
+    ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, NB, Kpad * 4, 32, L.N) &&
+         make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, NB, Kpad * 4, 32, L.N);
+    mB2 = mB1;
+  } else {
+    prep_b_bf16x3_kernel<<<pg, 256, 0, st>>>(M, d, kk, NB, Kpad, static_cast<__nv_bfloat16*>(B0),
+                                             static_cast<__nv_bfloat16*>(B1), static_cast<__nv_bfloat16*>(B2));
+    SLSO_CHECK_LAUNCH();
+    ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B0, Kpad, NB, Kpad * 2, 64, L.N) &&
+         make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B1, Kpad, NB, Kpad * 2, 64, L.N) &&
+         make_map(&mB2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B2, Kpad, NB, Kpad * 2, 64, L.N);
+  }
+  if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a product operand layout");
+  const int ntiles = static_cast<int>(ceil_div(n, kBM));
+  const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(ntiles) * ncb, h.num_sms));
+  SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(L.smem_bytes)));
+  score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, mB2, L, n, ntiles, ncb, nullptr, nullptr,
+                                                        nullptr, U, ldu, kk, h.state);
   SLSO_CHECK_LAUNCH();
   return SLSO_OK;
 }

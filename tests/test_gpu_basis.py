@@ -50,3 +50,17 @@ def test_approx_u_rank_deficient_image_like():
     Uo, oinfo = O.approx_u(X.double().numpy(), "countsketch", 2048, 5, qr="lapack")
     assert info["rank"] == oinfo["rank"] == 716
     _check(U.cpu().numpy().astype(np.float64), Uo, 716, 1e-4)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_approx_u_tensor_core_column_blocks_and_strides(dtype):
+    """d = 300: two 256-column blocks of M (the second ragged); X and U with row strides != d."""
+    n, d, s = 9001, 300, 1024
+    Xw = inputs.lognormal_rows(n, d + 4, seed=31, dtype=dtype)
+    X = Xw[:, :d]
+    Ubuf = torch.full((n, d + 3), 7.0, dtype=torch.float32, device="cuda")
+    U, info = api.approx_u(Xw.cuda()[:, :d], "countsketch", s, 23, out=Ubuf[:, :d])
+    Uo, oinfo = O.approx_u(_np(X), "countsketch", s, 23, qr="lapack")
+    assert info["rank"] == oinfo["rank"] == d
+    _check(U.cpu().numpy().astype(np.float64), Uo, d, 1e-4)
+    assert torch.all(Ubuf[:, d:] == 7.0)  # nothing written past column d
