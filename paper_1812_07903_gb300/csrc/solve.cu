@@ -634,8 +634,21 @@ __device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, un
 // round spread over every SM (at most a few per SM), since a pair's float64 work is what bounds
 // a round.
 constexpr int kJacobiThreads = 64;
+// d from which the float64 sweeps start from a float32-preconditioned basis, and the float32
+// sweep limit (float32 sweeps cost a fraction of float64 ones on this part's narrow FP64 pipe).
+constexpr int64_t kJacobiPrecondMin = 64;
+constexpr int kJacobiF32Sweeps = 30;
 
-__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double* __restrict__ W, double* __restrict__ V,
+// Rotation test threshold: |w_p . w_q| > tol sqrt(|w_p|^2 |w_q|^2) with tol = sqrt(dp) u.  Float64:
+// u = 2^-53, the convergence test of the result.  Float32 (preconditioning only): u = 2^-21, above
+// the rounding noise of a float32 dot product, so the float32 sweeps stop once the columns are
+// orthogonal to about float32 accuracy instead of rotating on noise.
+template <class T> __device__ __forceinline__ T jacobi_tol(int dp);
+template <> __device__ __forceinline__ double jacobi_tol<double>(int dp) { return sqrt(static_cast<double>(dp)) * 0x1p-53; }
+template <> __device__ __forceinline__ float jacobi_tol<float>(int dp) { return sqrtf(static_cast<float>(dp)) * 0x1p-21f; }
+
+template <class T>
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(T* __restrict__ W, T* __restrict__ V, T* nrm,
                                                      int d, int dp, int max_sweeps,
                                                      DevState* __restrict__ st,
                                                      unsigned int* bar, int* rot_count,
@@ -645,8 +658,20 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double* __restri
   const int wpb = blockDim.x >> 5;
   const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * wpb;
-  const double tol = sqrt(static_cast<double>(dp)) * 0x1p-53;
+  const T tol = jacobi_tol<T>(dp);
   int* abort_flag = reinterpret_cast<int*>(bar + 2);
+  for (int p = gw; p < d; p += nwarps) {  // squared column norms, kept exact below
+    const T* wp = W + static_cast<int64_t>(p) * dp;
+    T a = 0;
+    for (int i = lane; i < d; i += 32) a = fma(wp[i], wp[i], a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if (lane == 0) nrm[p] = a;
+  }
+  if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+    if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+    return;
+  }
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int local_rot = 0;
     for (int r = 0; r < dp - 1; ++r) {
@@ -655,35 +680,40 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double* __restri
         const int t2 = dp - 1 - kp;
         const int q = ((r + t2 - 1) % (dp - 1)) + 1;
         if (p >= d || q >= d) continue;
-        double* wp = W + static_cast<int64_t>(p) * dp;
-        double* wq = W + static_cast<int64_t>(q) * dp;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = lane; i < d; i += 32) {
-          const double x = wp[i], y = wq[i];
-          a = fma(x, x, a);
-          b = fma(y, y, b);
-          g = fma(x, y, g);
-        }
+        T* wp = W + static_cast<int64_t>(p) * dp;
+        T* wq = W + static_cast<int64_t>(q) * dp;
+        T g = 0;
+        for (int i = lane; i < d; i += 32) g = fma(wp[i], wq[i], g);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-          b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-          g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
-        }
-        if (g != 0.0 && fabs(g) > tol * sqrt(a * b)) {
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double sn = c * t;
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
+        const T a = nrm[p], b = nrm[q];
+        if (g != T(0) && fabs(g) > tol * sqrt(a * b)) {
+          const T zeta = (b - a) / (T(2) * g);
+          const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + t * t);
+          const T sn = c * t;
+          T na = 0, nb = 0;  // norms of the rotated columns, from the stored values
           for (int i = lane; i < d; i += 32) {
-            const double x = wp[i], y = wq[i];
-            wp[i] = c * x - sn * y;
-            wq[i] = sn * x + c * y;
+            const T x = wp[i], y = wq[i];
+            const T xn = c * x - sn * y, yn = sn * x + c * y;
+            wp[i] = xn;
+            wq[i] = yn;
+            na = fma(xn, xn, na);
+            nb = fma(yn, yn, nb);
           }
-          double* vp = V + static_cast<int64_t>(p) * dp;
-          double* vq = V + static_cast<int64_t>(q) * dp;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            na += __shfl_xor_sync(0xFFFFFFFFu, na, o);
+            nb += __shfl_xor_sync(0xFFFFFFFFu, nb, o);
+          }
+          if (lane == 0) {
+            nrm[p] = na;
+            nrm[q] = nb;
+          }
+          T* vp = V + static_cast<int64_t>(p) * dp;
+          T* vq = V + static_cast<int64_t>(q) * dp;
           for (int i = lane; i < d; i += 32) {
-            const double x = vp[i], y = vq[i];
+            const T x = vp[i], y = vq[i];
             vp[i] = c * x - sn * y;
             vq[i] = sn * x + c * y;
           }
@@ -711,8 +741,8 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(double* __restri
 // (CPL elements per column): one load and one store per column per round, with every load of a
 // column in flight at once, instead of two dependent passes over L2.  Same pairing, same
 // rotation formulas, same convergence test.
-template <int CPL>
-__global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(double* __restrict__ W, double* __restrict__ V,
+template <class T, int CPL>
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(T* __restrict__ W, T* __restrict__ V, T* nrm,
                                                                     int d, int dp, int max_sweeps,
                                                                     DevState* __restrict__ st, unsigned int* bar,
                                                                     int* rot_count, int require_svd_flag) {
@@ -721,8 +751,25 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(double* __re
   const int wpb = blockDim.x >> 5;
   const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * wpb;
-  const double tol = sqrt(static_cast<double>(dp)) * 0x1p-53;
+  const T tol = jacobi_tol<T>(dp);
   int* abort_flag = reinterpret_cast<int*>(bar + 2);
+  for (int p = gw; p < d; p += nwarps) {  // squared column norms, kept exact below
+    const T* wp = W + static_cast<int64_t>(p) * dp;
+    T a = 0;
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+      const int i = lane + 32 * e;
+      const T x = (i < d) ? wp[i] : T(0);
+      a = fma(x, x, a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if (lane == 0) nrm[p] = a;
+  }
+  if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+    if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+    return;
+  }
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int local_rot = 0;
     for (int r = 0; r < dp - 1; ++r) {
@@ -731,48 +778,54 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(double* __re
         const int t2 = dp - 1 - kp;
         const int q = ((r + t2 - 1) % (dp - 1)) + 1;
         if (p >= d || q >= d) continue;
-        double* wp = W + static_cast<int64_t>(p) * dp;
-        double* wq = W + static_cast<int64_t>(q) * dp;
-        double x[CPL], y[CPL];
+        T* wp = W + static_cast<int64_t>(p) * dp;
+        T* wq = W + static_cast<int64_t>(q) * dp;
+        T x[CPL], y[CPL];
 #pragma unroll
         for (int e = 0; e < CPL; ++e) {
           const int i = lane + 32 * e;
-          x[e] = (i < d) ? wp[i] : 0.0;
-          y[e] = (i < d) ? wq[i] : 0.0;
+          x[e] = (i < d) ? wp[i] : T(0);
+          y[e] = (i < d) ? wq[i] : T(0);
         }
-        double a = 0.0, b = 0.0, g = 0.0;
+        T g = 0;
 #pragma unroll
-        for (int e = 0; e < CPL; ++e) {
-          a = fma(x[e], x[e], a);
-          b = fma(y[e], y[e], b);
-          g = fma(x[e], y[e], g);
-        }
+        for (int e = 0; e < CPL; ++e) g = fma(x[e], y[e], g);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-          b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-          g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
-        }
-        if (g != 0.0 && fabs(g) > tol * sqrt(a * b)) {
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double sn = c * t;
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
+        const T a = nrm[p], b = nrm[q];
+        if (g != T(0) && fabs(g) > tol * sqrt(a * b)) {
+          const T zeta = (b - a) / (T(2) * g);
+          const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + t * t);
+          const T sn = c * t;
+          T na = 0, nb = 0;  // norms of the rotated columns, from the stored values
 #pragma unroll
           for (int e = 0; e < CPL; ++e) {
             const int i = lane + 32 * e;
+            const T xn = c * x[e] - sn * y[e], yn = sn * x[e] + c * y[e];
             if (i < d) {
-              wp[i] = c * x[e] - sn * y[e];
-              wq[i] = sn * x[e] + c * y[e];
+              wp[i] = xn;
+              wq[i] = yn;
             }
+            na = fma(xn, xn, na);  // padding lanes hold zeros: xn = yn = 0 there
+            nb = fma(yn, yn, nb);
           }
-          double* vp = V + static_cast<int64_t>(p) * dp;
-          double* vq = V + static_cast<int64_t>(q) * dp;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            na += __shfl_xor_sync(0xFFFFFFFFu, na, o);
+            nb += __shfl_xor_sync(0xFFFFFFFFu, nb, o);
+          }
+          if (lane == 0) {
+            nrm[p] = na;
+            nrm[q] = nb;
+          }
+          T* vp = V + static_cast<int64_t>(p) * dp;
+          T* vq = V + static_cast<int64_t>(q) * dp;
 #pragma unroll
           for (int e = 0; e < CPL; ++e) {
             const int i = lane + 32 * e;
-            x[e] = (i < d) ? vp[i] : 0.0;
-            y[e] = (i < d) ? vq[i] : 0.0;
+            x[e] = (i < d) ? vp[i] : T(0);
+            y[e] = (i < d) ? vq[i] : T(0);
           }
 #pragma unroll
           for (int e = 0; e < CPL; ++e) {
@@ -809,6 +862,58 @@ __global__ void jacobi_init_kernel(const double* __restrict__ R, int64_t d, int6
     const int64_t col = e / dp, row = e % dp;
     W[e] = (row < d && col < d) ? R[row * d + col] : 0.0;
     V[e] = (row == col) ? 1.0 : 0.0;
+  }
+}
+
+// float32 preconditioning of the Jacobi SVD: W32 = float32(R) (column-major dp x dp), V32 = I.
+__global__ void jacobi_init_f32_kernel(const double* __restrict__ R, int64_t d, int64_t dp,
+                                       float* __restrict__ W, float* __restrict__ V, const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < dp * dp;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t col = e / dp, row = e % dp;
+    W[e] = (row < d && col < d) ? static_cast<float>(R[row * d + col]) : 0.0f;
+    V[e] = (row == col) ? 1.0f : 0.0f;
+  }
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ a, int64_t n, double* __restrict__ b,
+                                  const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    b[e] = static_cast<double>(a[e]);
+}
+
+// E = G - I in place (G = V0^T V0, d x d row-major).
+__global__ void sub_identity_kernel(double* __restrict__ G, int64_t d, const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * d;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    if (e / d == e % d) G[e] -= 1.0;
+}
+
+// P = (I + E)^(-1/2) to third order: I - E/2 + 3/8 E^2 - 5/16 E^3, written over E2 (with
+// ||E|| ~ 1e-5 the next term is below 1e-19).
+__global__ void inv_sqrt_series_kernel(const double* __restrict__ E, double* __restrict__ E2P,
+                                       const double* __restrict__ E3, int64_t d, const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * d;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    E2P[e] = ((e / d == e % d) ? 1.0 : 0.0) - 0.5 * E[e] + 0.375 * E2P[e] - 0.3125 * E3[e];
+}
+
+// W = W0, V = Q (both d x d row-major) into the column-major dp x dp Jacobi storage.
+__global__ void jacobi_init_from_kernel(const double* __restrict__ W0, const double* __restrict__ Q, int64_t d,
+                                        int64_t dp, double* __restrict__ W, double* __restrict__ V,
+                                        const int32_t* guard) {
+  if (guard && *guard == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < dp * dp;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t col = e / dp, row = e % dp;
+    const bool in = row < d && col < d;
+    W[e] = in ? W0[row * d + col] : 0.0;
+    V[e] = in ? Q[row * d + col] : ((row == col) ? 1.0 : 0.0);
   }
 }
 
@@ -898,6 +1003,14 @@ int grid1d(int64_t n, const Handle& h) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8LL * h.num_sms)));
 }
 
+template <class T>
+void* jacobi_fn(int64_t d) {
+  if (d <= 256) return reinterpret_cast<void*>(jacobi_reg_kernel<T, 8>);
+  if (d <= 512) return reinterpret_cast<void*>(jacobi_reg_kernel<T, 16>);
+  if (d <= 1024) return reinterpret_cast<void*>(jacobi_reg_kernel<T, 32>);
+  return reinterpret_cast<void*>(jacobi_kernel<T>);
+}
+
 slso_status launch_gemm(int64_t m, int64_t n, int64_t K, const double* A, int64_t ars, int64_t acs,
                         const double* B, int64_t brs, int64_t bcs, double* C, const int32_t* guard,
                         int want, cudaStream_t st) {
@@ -928,6 +1041,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* sig = ar.take<double>(d);
   int* perm = ar.take<int>(d);
   unsigned int* bar = ar.take<unsigned int>(4);
+  double* nrm = ar.take<double>(dp);  // Jacobi squared column norms (float32 phase uses the first half)
   int* rot = ar.take<int>(64);
   double* Vs = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* Ur = (mode == 0 && k > 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
@@ -935,6 +1049,13 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* M = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * kk) : nullptr;
   double* sigma_out = (mode == 1) ? ar.take<double>(d) : nullptr;
   double* Vout = (mode == 1) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  const bool precond = d >= kJacobiPrecondMin;
+  float* W32 = precond ? ar.take<float>(static_cast<size_t>(dp) * dp) : nullptr;
+  float* V32 = precond ? ar.take<float>(static_cast<size_t>(dp) * dp) : nullptr;
+  double* Gm = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  double* E2 = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  double* Qm = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  double* W0m = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   if (ar.measure()) return SLSO_OK;
 
   // ---- QR
@@ -1026,28 +1147,51 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   }
 
   // ---- SVD route (always for mode 1)
-  jacobi_init_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(R, d, dp, W, Vw);
-  SLSO_CHECK_LAUNCH();
-  SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 4, st));
-  SLSO_CHECK_CUDA(cudaMemsetAsync(rot, 0, sizeof(int) * 64, st));
-  {
+  const int32_t* guard = (mode == 0) ? need : nullptr;
+  auto launch_jacobi = [&](void* jfn, void* Wp, void* Vp, int max_sweeps) -> slso_status {
+    void* np_ = nrm;
+    SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 4, st));
+    SLSO_CHECK_CUDA(cudaMemsetAsync(rot, 0, sizeof(int) * 64, st));
     int occ = 0;
-    void* jfn = reinterpret_cast<void*>(jacobi_kernel);
-    if (d <= 256) jfn = reinterpret_cast<void*>(jacobi_reg_kernel<8>);
-    else if (d <= 512) jfn = reinterpret_cast<void*>(jacobi_reg_kernel<16>);
-    else if (d <= 1024) jfn = reinterpret_cast<void*>(jacobi_reg_kernel<32>);
     SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jfn, kJacobiThreads, 0));
     const int warps_needed = static_cast<int>(dp / 2);
     int G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h.num_sms) * occ,
                                                ceil_div(warps_needed, kJacobiThreads / 32)));
     G = std::max(G, 1);
-    int d_i = static_cast<int>(d), dp_i = static_cast<int>(dp), sweeps = 60, req = (mode == 0) ? 1 : 0;
+    int d_i = static_cast<int>(d), dp_i = static_cast<int>(dp), sweeps = max_sweeps, req = (mode == 0) ? 1 : 0;
     DevState* stp = h.state;
-    void* args[] = {&W, &Vw, &d_i, &dp_i, &sweeps, &stp, &bar, &rot, &req};
+    void* args[] = {&Wp, &Vp, &np_, &d_i, &dp_i, &sweeps, &stp, &bar, &rot, &req};
     SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(jfn, dim3(G), dim3(kJacobiThreads), args, 0, st));
     note_launch();
+    return SLSO_OK;
+  };
+  if (precond) {
+    // float32 sweeps from R give V32 (orthogonal to ~1e-6); V0 = float64(V32) made orthogonal in
+    // float64, Q = V0 (V0^T V0)^(-1/2) by the third-order series; the float64 sweeps then start
+    // from W0 = R Q, V = Q, whose columns are already orthogonal to float32 accuracy.
+    jacobi_init_f32_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(R, d, dp, W32, V32, guard);
+    SLSO_CHECK_LAUNCH();
+    SLSO_TRY(launch_jacobi(jacobi_fn<float>(d), W32, V32, kJacobiF32Sweeps));
+    double* V0 = W;  // dp x dp column-major; W is rewritten below
+    f32_to_f64_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(V32, dp * dp, V0, guard);
+    SLSO_CHECK_LAUNCH();
+    const int want = 1;
+    SLSO_TRY(launch_gemm(d, d, d, V0, dp, 1, V0, 1, dp, Gm, guard, want, st));  // G = V0^T V0
+    sub_identity_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Gm, d, guard);
+    SLSO_CHECK_LAUNCH();
+    SLSO_TRY(launch_gemm(d, d, d, Gm, d, 1, Gm, d, 1, E2, guard, want, st));  // E^2
+    SLSO_TRY(launch_gemm(d, d, d, E2, d, 1, Gm, d, 1, Qm, guard, want, st));  // E^3 (in Q's buffer)
+    inv_sqrt_series_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Gm, E2, Qm, d, guard);
+    SLSO_CHECK_LAUNCH();
+    SLSO_TRY(launch_gemm(d, d, d, V0, 1, dp, E2, d, 1, Qm, guard, want, st));  // Q = V0 P
+    SLSO_TRY(launch_gemm(d, d, d, R, d, 1, Qm, d, 1, W0m, guard, want, st));   // W0 = R Q
+    jacobi_init_from_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(W0m, Qm, d, dp, W, Vw, guard);
+    SLSO_CHECK_LAUNCH();
+  } else {
+    jacobi_init_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(R, d, dp, W, Vw);
+    SLSO_CHECK_LAUNCH();
   }
-  const int32_t* guard = (mode == 0) ? need : nullptr;
+  SLSO_TRY(launch_jacobi(jacobi_fn<double>(d), W, Vw, 60));
   colnorm_kernel<<<static_cast<unsigned>(ceil_div(d * 32, 256)), 256, 0, st>>>(W, d, dp, sig, guard);
   SLSO_CHECK_LAUNCH();
   svd_finalize_kernel<<<1, 1024, 0, st>>>(W, Vw, sig, d, dp, tau, sigma_out, Vout, Vs, Ur, perm, h.state, guard);
