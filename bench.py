@@ -231,6 +231,7 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
         bad += st != 0
         lat.append(times[2])
     makespan = time.perf_counter() - start
+    counters = srv.counters()
     srv.close()
     lat.sort()
     pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]  # noqa: E731
@@ -241,7 +242,36 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
         "slots": slots, "jobs": n_jobs, "failed": bad, "calibrated_service_ms": service_s * 1e3,
         "arrival_rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
         "makespan_s": makespan, "jobs_per_s": n_jobs / makespan, "rows_per_s": rows / makespan,
+        "graphs": {k: counters[k] for k in ("graphs_new", "graphs_updated", "direct")},
+        "repeated_shape": repeated_shape_latency(api, inputs, torch),
     }
+
+
+def repeated_shape_latency(api, inputs, torch, n=65536, d=256, jobs=24):
+    """Latency of back-to-back jobs of one shape through a 1-slot server: the first runs direct,
+    the second is captured into a CUDA graph, the rest replay it (arguments updated in place)."""
+    X = [inputs.gaussian_mixture(n, d, seed=500 + i, device="cuda") for i in range(4)]
+    srv = api.Server(slots=1, mem_budget_bytes=4 << 30)
+    lat = []
+    for i in range(jobs):
+        t = srv.submit_leverage(X[i % 4], "countsketch", 4096, 64, 9, 10)
+        st, info, times, _ = srv.poll(t, timeout_ms=600000)
+        lat.append(times[2])
+    c = srv.counters()
+    srv.close()
+    direct = []  # the same jobs through the direct entry points, one at a time
+    for i in range(jobs):
+        t0 = time.perf_counter()
+        sc, _ = api.leverage(X[i % 4], "countsketch", 4096, 64, 9, 10, want_info=False)
+        api.order(sc)
+        torch.cuda.synchronize()
+        direct.append((time.perf_counter() - t0) * 1e3)
+    rest = sorted(lat[2:])
+    direct = sorted(direct[2:])
+    return {"workload": f"{jobs} sequential jobs, n={n}, d={d}, CountSketch s=4096, k=64, 1 slot",
+            "first_ms": lat[0], "captured_ms": lat[1], "replay_p50_ms": rest[len(rest) // 2],
+            "direct_call_p50_ms": direct[len(direct) // 2],
+            "graphs": {k: c[k] for k in ("graphs_new", "graphs_updated", "direct")}}
 
 
 # ----------------------------------------------------------------------------- large workload

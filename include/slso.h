@@ -259,6 +259,13 @@ slso_status slso_server_poll(slso_server* server, int64_t ticket, int timeout_ms
 slso_status slso_server_cancel(slso_server* server, int64_t ticket);
 /* counters[0..3] = {submitted, admitted, completed, queued}; bytes of scratch in use. */
 slso_status slso_server_stats(slso_server* server, int64_t* counters, size_t* mem_in_use);
+/* The first `count` of {submitted, admitted, completed, queued, scratch bytes in use, graphs
+ * instantiated, graphs updated in place, leverage jobs run without a graph} (zeros beyond).
+ * From the second job of a shape (n, d, ldx, dtype, params, order or not) on, leverage jobs are
+ * recorded into CUDA graphs by stream capture; each slot keeps the graphs of its 8 most recent
+ * shapes with their workspace, within a quarter of the memory budget, and a job of a cached
+ * shape updates that graph's arguments in place and replays it. */
+slso_status slso_server_counters(slso_server* server, int64_t* counters, int32_t count);
 
 /* Ordering that allocates nothing (the paper has no counterpart; this exists for callers).
  * Some callers cannot call cudaMalloc where they need an ordering: a process whose device

@@ -26,6 +26,7 @@ EXPORTS = (
     "slso_rank_rows_host_batch", "slso_set_pool_limit", "slso_selftest_wait", "slso_server_cancel",
     "slso_approx_u", "slso_rank_rows_streamed",
     "slso_server_create", "slso_server_destroy", "slso_server_submit", "slso_server_poll", "slso_server_stats",
+    "slso_server_counters",
 )
 JOB_LEVERAGE, JOB_SKETCHED_SVD = 0, 1
 STAGES = ("sketch", "qr", "solve", "scores", "order", "copy")
@@ -100,6 +101,7 @@ def load():
         "slso_server_cancel": ([vp, i64], i32),
         "slso_server_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], i32),
         "slso_server_destroy": ([vp], i32),
+        "slso_server_counters": ([vp, ctypes.POINTER(i64), i32], i32),
         "slso_server_submit": ([vp, ctypes.POINTER(Job), ctypes.POINTER(i64)], i32),
         "slso_server_poll": ([vp, i64, ctypes.c_int, ctypes.POINTER(i32), ctypes.POINTER(Info),
                               ctypes.POINTER(ctypes.c_double)], i32),

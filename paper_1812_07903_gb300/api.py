@@ -334,6 +334,14 @@ class Server:
         L.check(L.load().slso_server_stats(self._s, c, ctypes.byref(mem)))
         return {"submitted": c[0], "admitted": c[1], "completed": c[2], "queued": c[3], "mem_in_use": mem.value}
 
+    def counters(self):
+        """slso_server_counters: job counts, scratch in use and the graph-capture counters."""
+        names = ("submitted", "admitted", "completed", "queued", "mem_in_use", "graphs_new", "graphs_updated",
+                 "direct")
+        c = (ctypes.c_int64 * len(names))()
+        L.check(L.load().slso_server_counters(self._s, c, len(names)))
+        return dict(zip(names, list(c)))
+
     def close(self):
         if self._s:
             L.load().slso_server_destroy(self._s)

@@ -9,8 +9,18 @@
 // allocated stream-ordered (cudaMallocAsync / cudaFreeAsync on the slot's stream), which never
 // synchronises the device.  Every kernel on the path is deterministic, so a job's result is
 // the same alone and in any mix.
+//
+// Captured graphs: from the second job of a shape on (n, d, ldx, dtype, parameters, with or
+// without the order), a leverage job's launches are recorded by stream capture into a CUDA graph
+// and replayed with one cudaGraphLaunch.  Each slot keeps the instantiated graphs of recent job
+// shapes together with their workspace, so a later job of the same shape only re-records its
+// launches against that workspace and updates the instantiated graph in place
+// (cudaGraphExecUpdate: new X, scores and order pointers) instead of instantiating again.  Cached workspaces count against a quarter of
+// the memory budget (least recently used shapes are dropped); a job whose launches cannot be
+// captured runs them directly.
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -18,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tmap.cuh"
 
 namespace slso {
 namespace {
@@ -37,13 +48,26 @@ struct Job {
   bool done = false;
 };
 
+// An instantiated graph of one job shape and the workspace its launches were recorded against.
+struct GraphEntry {
+  std::vector<int64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  void* ws = nullptr;
+  size_t bytes = 0;
+  uint64_t last_use = 0;
+};
+
 struct Slot {
   Handle h;
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
   Job* job = nullptr;
   void* ws = nullptr;
+  std::vector<GraphEntry> graphs;
 };
+
+constexpr size_t kGraphsPerSlot = 8;
+constexpr size_t kSeenShapes = 256;
 
 }  // namespace
 
@@ -55,6 +79,12 @@ struct Server {
   std::unordered_map<int64_t, Job*> jobs;
   int64_t next_ticket = 1;
   int64_t n_submitted = 0, n_admitted = 0, n_completed = 0;
+  // graph statistics: new instantiations, in-place updates, direct (uncaptured) leverage runs
+  int64_t n_graph_new = 0, n_graph_update = 0, n_graph_direct = 0;
+  size_t graph_bytes = 0;  // workspaces held by cached graphs (all slots)
+  uint64_t use_clock = 0;
+  bool capture_ok = true;  // cleared if the driver refuses to capture the launches
+  std::deque<std::vector<int64_t>> seen;  // recent leverage shapes (a shape's first job runs direct)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::thread worker;
@@ -102,8 +132,129 @@ slso_status check_job(const slso_job* j) {
   return fail(SLSO_ERR_INVALID_ARG, "unknown job kind %d", j->job);
 }
 
+// Shape key of a leverage job: everything the launch sequence depends on except the X, scores
+// and order addresses (an X address of different alignment may change it; then the update is
+// refused and the graph instantiated again).
+std::vector<int64_t> graph_key(const slso_job& d) {
+  const slso_params& p = d.params;
+  int64_t tau_bits = 0, frac_bits = 0;
+  std::memcpy(&tau_bits, &p.tau, sizeof(double));
+  std::memcpy(&frac_bits, &p.correct_frac, sizeof(double));
+  return {d.n, d.d, d.ldx, d.xdt, p.kind, p.s, p.k, static_cast<int64_t>(p.seed_S), static_cast<int64_t>(p.seed_Pi),
+          tau_bits, p.compute, frac_bits, p.nnz, d.order ? 1 : 0};
+}
+
+// Record the job's launches on the slot's stream into a graph against workspace ws.
+slso_status capture_job(Slot& sl, const Job* j, void* ws, cudaGraph_t* g) {
+  *g = nullptr;
+  SLSO_CHECK_CUDA(cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeThreadLocal));
+  Arena ar(static_cast<char*>(ws), j->bytes + 256, false);
+  const slso_status stt = job_plan(sl.h, ar, j->desc, sl.st);
+  const cudaError_t e = cudaStreamEndCapture(sl.st, g);  // always ends the capture
+  cudaGetLastError();
+  if (stt != SLSO_OK || e != cudaSuccess) {
+    if (*g) cudaGraphDestroy(*g);
+    *g = nullptr;
+    return stt != SLSO_OK ? stt : fail(SLSO_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+  }
+  return SLSO_OK;
+}
+
+// Run a leverage job through the slot's graph cache (worker thread only: the slots' graph lists,
+// graph_bytes and capture_ok are touched by no other thread).  Returns 0 when the job must run
+// uncaptured (nothing was enqueued), 1 after a new instantiation, 2 after an in-place update.
+int start_job_graph(Server& s, Slot& sl, Job* j) {
+  if (!s.capture_ok || j->desc.job != SLSO_JOB_LEVERAGE) return 0;
+  const std::vector<int64_t> key = graph_key(j->desc);
+  int outcome = 0;
+  GraphEntry* e = nullptr;
+  for (GraphEntry& g : sl.graphs)
+    if (g.key == key) e = &g;
+  if (!e) {
+    // a shape's first job runs direct: instantiating a graph costs more than launching once
+    bool seen = false;
+    for (const auto& k : s.seen) seen |= k == key;
+    if (!seen) {
+      s.seen.push_back(key);
+      if (s.seen.size() > kSeenShapes) s.seen.pop_front();
+      return 0;
+    }
+    // room for one more cached workspace: drop least recently used entries of this slot
+    const size_t cap = s.budget / 4;
+    while (!sl.graphs.empty() && (sl.graphs.size() >= kGraphsPerSlot || s.graph_bytes + j->bytes + 256 > cap)) {
+      size_t lru = 0;
+      for (size_t i = 1; i < sl.graphs.size(); ++i)
+        if (sl.graphs[i].last_use < sl.graphs[lru].last_use) lru = i;
+      GraphEntry& v = sl.graphs[lru];
+      cudaGraphExecDestroy(v.exec);
+      cudaFreeAsync(v.ws, sl.st);
+      s.graph_bytes -= v.bytes + 256;
+      sl.graphs.erase(sl.graphs.begin() + static_cast<std::ptrdiff_t>(lru));
+    }
+    if (s.graph_bytes + j->bytes + 256 > cap) return 0;
+    GraphEntry ne;
+    ne.key = key;
+    ne.bytes = j->bytes;
+    if (cudaMallocAsync(&ne.ws, j->bytes + 256, sl.st) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaGraph_t g = nullptr;
+    if (capture_job(sl, j, ne.ws, &g) != SLSO_OK || cudaGraphInstantiate(&ne.exec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      cudaFreeAsync(ne.ws, sl.st);
+      s.capture_ok = false;  // the plan is the same kind of launch sequence for every job: stop trying
+      return 0;
+    }
+    cudaGraphDestroy(g);
+    s.graph_bytes += ne.bytes + 256;
+    sl.graphs.push_back(ne);
+    e = &sl.graphs.back();
+    outcome = 1;
+  } else {
+    cudaGraph_t g = nullptr;
+    if (capture_job(sl, j, e->ws, &g) != SLSO_OK) return 0;
+    cudaGraphExecUpdateResultInfo res{};
+    if (cudaGraphExecUpdate(e->exec, g, &res) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(e->exec);
+      e->exec = nullptr;
+      if (cudaGraphInstantiate(&e->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        cudaFreeAsync(e->ws, sl.st);
+        s.graph_bytes -= e->bytes + 256;
+        sl.graphs.erase(sl.graphs.begin() + (e - sl.graphs.data()));
+        return 0;
+      }
+      outcome = 1;
+    } else {
+      outcome = 2;
+    }
+    cudaGraphDestroy(g);
+  }
+  e->last_use = ++s.use_clock;
+  j->status = SLSO_OK;
+  if (cudaMemsetAsync(sl.h.state, 0, sizeof(DevState), sl.st) != cudaSuccess ||
+      cudaGraphLaunch(e->exec, sl.st) != cudaSuccess) {
+    cudaGetLastError();
+    j->status = SLSO_ERR_CUDA;
+  }
+  cudaEventRecord(sl.done, sl.st);
+  return outcome;
+}
+
 // Enqueue a job's work on its slot (worker thread, lock not held).
-void start_job(Slot& sl, Job* j) {
+void start_job(Server& srv, Slot& sl, Job* j) {
+  const int outcome = start_job_graph(srv, sl, j);
+  {
+    std::lock_guard<std::mutex> lk(srv.mu);
+    if (outcome == 1) ++srv.n_graph_new;
+    else if (outcome == 2) ++srv.n_graph_update;
+    else if (j->desc.job == SLSO_JOB_LEVERAGE) ++srv.n_graph_direct;
+  }
+  if (outcome) return;
   slso_status stt = SLSO_OK;
   if (cudaMemsetAsync(sl.h.state, 0, sizeof(DevState), sl.st) != cudaSuccess) stt = SLSO_ERR_CUDA;
   if (stt == SLSO_OK && cudaMallocAsync(&sl.ws, j->bytes + 256, sl.st) != cudaSuccess) {
@@ -177,7 +328,7 @@ void worker_main(Server* s) {
       ++s->n_admitted;
       free_slot->job = j;
       lk.unlock();
-      start_job(*free_slot, j);
+      start_job(*s, *free_slot, j);
       lk.lock();
       progressed = true;
     }
@@ -226,6 +377,7 @@ extern "C" slso_status slso_server_create(slso_server** out, int device, int nsl
       return fail(SLSO_ERR_CUDA, "slso_server_create: %s", cudaGetErrorString(e));
     }
   }
+  encode_fn();  // resolve the driver entry point now, not while a capture is recording
   s->worker = std::thread(worker_main, s);
   *out = reinterpret_cast<slso_server*>(s);
   return SLSO_OK;
@@ -248,6 +400,11 @@ extern "C" slso_status slso_server_destroy(slso_server* srv) {
   cudaSetDevice(s->device);
   for (Slot& sl : s->slots) {
     cudaStreamSynchronize(sl.st);
+    for (GraphEntry& g : sl.graphs) {
+      cudaGraphExecDestroy(g.exec);
+      cudaFree(g.ws);
+    }
+    sl.graphs.clear();
     cudaStreamDestroy(sl.st);
     cudaEventDestroy(sl.done);
     cudaFree(sl.h.state);
@@ -332,6 +489,16 @@ extern "C" slso_status slso_server_cancel(slso_server* srv, int64_t ticket) {
     return SLSO_OK;
   }
   return fail(SLSO_ERR_BUSY, "job %lld is already %s", (long long)ticket, j->done ? "finished" : "running");
+}
+
+extern "C" slso_status slso_server_counters(slso_server* srv, int64_t* counters, int32_t count) {
+  if (!srv || !counters || count < 0) return fail(SLSO_ERR_INVALID_ARG, "server and counters must be non-NULL");
+  Server* s = reinterpret_cast<Server*>(srv);
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int64_t v[] = {s->n_submitted, s->n_admitted, s->n_completed, static_cast<int64_t>(s->queue.size()),
+                       static_cast<int64_t>(s->in_use), s->n_graph_new, s->n_graph_update, s->n_graph_direct};
+  for (int32_t i = 0; i < count; ++i) counters[i] = i < static_cast<int32_t>(sizeof(v) / sizeof(v[0])) ? v[i] : 0;
+  return SLSO_OK;
 }
 
 extern "C" slso_status slso_server_stats(slso_server* srv, int64_t* counters, size_t* mem_in_use) {

@@ -74,3 +74,24 @@ def test_invalid_job_is_rejected_at_submit():
     with pytest.raises(RuntimeError, match="SHAPE"):
         srv.submit_leverage(X, "countsketch", 32, 16, 1, 2)  # s < d
     srv.close()
+
+
+def test_repeated_shapes_replay_captured_graphs():
+    """A shape's first job runs direct, its second is captured into a graph, later ones replay
+    that graph with their own X, scores and order (updated in place); results equal the direct
+    entry points bit for bit."""
+    shapes = [(20000, 64, "countsketch", 1024, 32), (9000, 100, "srht", 512, 0), (12000, 48, "gaussian", 256, 16)]
+    srv = api.Server(slots=1, mem_budget_bytes=1 << 30)
+    want, tickets = [], []
+    for rep in range(3):
+        for i, (n, d, kind, s, k) in enumerate(shapes):
+            X = inputs.gaussian_mixture(n, d, seed=100 * rep + i, device="cuda")
+            sc, _ = api.leverage(X, kind, s, k, 7, 8)
+            want.append((sc.clone(), api.order(sc).clone()))
+            tickets.append(srv.submit_leverage(X, kind, s, k, 7, 8))
+    for t, (sc0, o0) in zip(tickets, want):
+        st, info, times, (sc, o) = srv.poll(t)
+        assert st == 0 and torch.equal(sc, sc0) and torch.equal(o, o0)
+    c = srv.counters()
+    srv.close()
+    assert c["direct"] == len(shapes) and c["graphs_new"] == len(shapes) and c["graphs_updated"] == len(shapes)
