@@ -92,7 +92,8 @@ typedef struct {
   double tau;            /* the threshold actually used                                       */
   int32_t nonfinite;     /* 1 if X held NaN or Inf                                            */
   int32_t svd_route;     /* 1: R^+ from the SVD of R; 0: rank d certified, R^+ = R^-1          */
-  int32_t svd_sweeps;    /* one-sided Jacobi sweeps the SVD of R took (0 when it did not run)   */
+  int32_t svd_sweeps;    /* float64 one-sided Jacobi sweeps of the SVD of R (after the float32
+                            preconditioning sweeps when d >= 64); 0 when it did not run          */
 } slso_info;
 
 /* Library / handle ------------------------------------------------------------------ */
@@ -108,13 +109,16 @@ slso_status slso_workspace_size(const slso_params* params, int64_t n, int64_t d,
  * CountSketch sums each bucket's rows in ascending row order with compensated float32
  * (float64 for F64 X); SRHT and Gaussian accumulate partial sums in float32 (float64
  * for F64 X) merged in float64 in a fixed order, so the result is deterministic.
- * Errors: SHAPE if n < 1, d < 1, s < 1, ldx < d, or (SRHT) s > n_pad. */
+ * Errors: SHAPE if n < 1, d < 1, s < 1, ldx < d, (SRHT) s > n_pad, or (OSNAP, z = 4) s not a
+ * multiple of 4. */
 slso_status slso_sketch(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
                         int32_t xdt, int32_t kind, int64_t s, uint64_t seed_S, double* SX,
                         void* stream);
 
 /* Sketched SVD (title; Algorithm 2/3 steps 2-3): unpivoted Householder QR of SX (s x d,
- * float64, s >= d) with R_jj >= 0, then the SVD of R (one-sided Jacobi, float64):
+ * float64, s >= d) with R_jj >= 0, then the SVD of R by one-sided Jacobi.  For d >= 64 float32
+ * sweeps on float32(R) first give a basis V32; Q = V32 (V32^T V32)^(-1/2) (series, float64) and
+ * the float64 sweeps run on R Q with V starting at Q, so the result is float64-accurate:
  * sigma (d, descending) are the singular values of SX and V (d x d, row-major, column j
  * the j-th right singular vector) its right singular vectors.  R (d x d) is written when
  * non-NULL.  rank = #{sigma_j > tau sigma_1} (tau < 0: max(s, d) 2^-52) goes to info.
@@ -142,7 +146,8 @@ slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t
 /* Approximate left singular vectors (Algorithm 2 step 3; Algorithm 3 step 4, read without
  * the transpose): sketch SX = S X (params: kind, s, seed_S, tau; k, seed_Pi, compute and
  * correct_frac are not used), sketched SVD SX = U' Sigma V^T (float64 QR + Jacobi SVD of R),
- * r = #{sigma_j > tau sigma_1}, then U = X V_r Sigma_r^-1.  U is n x d row-major with leading
+ * r = #{sigma_j > tau sigma_1}, then U = X V_r Sigma_r^-1 (tensor cores, float32-accurate split
+ * operands, for F32 / BF16 X; float64 for F64 X).  U is n x d row-major with leading
  * dimension ldu >= d, float64 for F64 X, float32 otherwise; columns r .. d-1 are zero.  Column j
  * is defined up to the sign of the singular vector v_j (as for any SVD).  ||U_i||^2 is row i's
  * score of slso_leverage with k = 0.  Errors as slso_leverage, plus SHAPE for ldu < d. */
