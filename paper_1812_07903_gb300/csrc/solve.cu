@@ -781,11 +781,21 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(T* __restric
         T* wp = W + static_cast<int64_t>(p) * dp;
         T* wq = W + static_cast<int64_t>(q) * dp;
         T x[CPL], y[CPL];
+        T* vp = V + static_cast<int64_t>(p) * dp;
+        T* vq = V + static_cast<int64_t>(q) * dp;
+        // V's columns are fetched with W's when they fit in registers beside them (float32, or
+        // float64 with CPL <= 16), so a rotation does not wait for a second round trip to L2
+        constexpr bool kPrefetchV = sizeof(T) == 4 || CPL <= 16;
+        T u[kPrefetchV ? CPL : 1], v[kPrefetchV ? CPL : 1];
 #pragma unroll
         for (int e = 0; e < CPL; ++e) {
           const int i = lane + 32 * e;
           x[e] = (i < d) ? wp[i] : T(0);
           y[e] = (i < d) ? wq[i] : T(0);
+          if constexpr (kPrefetchV) {
+            u[e] = (i < d) ? vp[i] : T(0);
+            v[e] = (i < d) ? vq[i] : T(0);
+          }
         }
         T g = 0;
 #pragma unroll
@@ -819,20 +829,29 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(T* __restric
             nrm[p] = na;
             nrm[q] = nb;
           }
-          T* vp = V + static_cast<int64_t>(p) * dp;
-          T* vq = V + static_cast<int64_t>(q) * dp;
+          if constexpr (kPrefetchV) {
 #pragma unroll
-          for (int e = 0; e < CPL; ++e) {
-            const int i = lane + 32 * e;
-            x[e] = (i < d) ? vp[i] : T(0);
-            y[e] = (i < d) ? vq[i] : T(0);
-          }
+            for (int e = 0; e < CPL; ++e) {
+              const int i = lane + 32 * e;
+              if (i < d) {
+                vp[i] = c * u[e] - sn * v[e];
+                vq[i] = sn * u[e] + c * v[e];
+              }
+            }
+          } else {
 #pragma unroll
-          for (int e = 0; e < CPL; ++e) {
-            const int i = lane + 32 * e;
-            if (i < d) {
-              vp[i] = c * x[e] - sn * y[e];
-              vq[i] = sn * x[e] + c * y[e];
+            for (int e = 0; e < CPL; ++e) {
+              const int i = lane + 32 * e;
+              x[e] = (i < d) ? vp[i] : T(0);
+              y[e] = (i < d) ? vq[i] : T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+              const int i = lane + 32 * e;
+              if (i < d) {
+                vp[i] = c * x[e] - sn * y[e];
+                vq[i] = sn * x[e] + c * y[e];
+              }
             }
           }
           ++local_rot;
