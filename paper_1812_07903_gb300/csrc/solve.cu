@@ -874,6 +874,197 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(T* __restric
   }
 }
 
+// Block one-sided Jacobi for the float32 preconditioning sweeps (d <= 1024): the columns are split
+// into nb blocks of kJacobiKB, block pairs follow the same round-robin tournament as columns do,
+// and a CTA of 8 warps loads its block pair's W and V columns (2 * kJacobiKB of each) into shared
+// memory, rotates every cross pair there (kJacobiKB sub-rounds of kJacobiKB disjoint pairs, one
+// pair per warp, __syncthreads between them; in a sweep's first round also the pairs inside each
+// block), and writes the columns back.  One grid barrier per block round: nb - 1 per sweep instead
+// of dp - 1.  The rotation formulas, norm bookkeeping and convergence test are those of
+// jacobi_reg_kernel.
+constexpr int kJacobiKB = 8;
+constexpr int kJacobiBlockThreads = 256;
+constexpr int kCopyCols = 4, kCopyRows = 4;  // 16 loads of each of W and V in flight per thread
+
+// One column pair of a block round, by one warp, on the shared-memory copies: each lane holds its
+// CPL elements of both columns in registers (all loads in flight at once, four partial sums),
+// as jacobi_reg_kernel does with global memory.
+template <int CPL>
+__device__ __forceinline__ void jacobi_smem_pair(float* __restrict__ Ws, float* __restrict__ Vs, float* nrm_s,
+                                                 int a, int b, int d, float tol, int lane, int* rot) {
+  float* wa = Ws + a * d;
+  float* wb = Ws + b * d;
+  float x[CPL], y[CPL];
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+    const int i = lane + 32 * e;
+    x[e] = (i < d) ? wa[i] : 0.0f;
+    y[e] = (i < d) ? wb[i] : 0.0f;
+  }
+  float gp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) gp[e & 3] = fmaf(x[e], y[e], gp[e & 3]);
+  float g = (gp[0] + gp[1]) + (gp[2] + gp[3]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xFFFFFFFFu, g, o);
+  const float x2 = nrm_s[a], y2 = nrm_s[b];
+  if (!(g != 0.0f && fabsf(g) > tol * sqrtf(x2 * y2))) return;
+  const float zeta = (y2 - x2) / (2.0f * g);
+  const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+  const float c = 1.0f / sqrtf(1.0f + t * t);
+  const float sn = c * t;
+  float na[2] = {0.0f, 0.0f}, nb[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+    const int i = lane + 32 * e;
+    const float xn = c * x[e] - sn * y[e], yn = sn * x[e] + c * y[e];
+    if (i < d) {
+      wa[i] = xn;
+      wb[i] = yn;
+    }
+    na[e & 1] = fmaf(xn, xn, na[e & 1]);  // padding elements are zero
+    nb[e & 1] = fmaf(yn, yn, nb[e & 1]);
+  }
+  float va_[CPL], vb_[CPL];
+  float* va = Vs + a * d;
+  float* vb = Vs + b * d;
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+    const int i = lane + 32 * e;
+    va_[e] = (i < d) ? va[i] : 0.0f;
+    vb_[e] = (i < d) ? vb[i] : 0.0f;
+  }
+#pragma unroll
+  for (int e = 0; e < CPL; ++e) {
+    const int i = lane + 32 * e;
+    if (i < d) {
+      va[i] = c * va_[e] - sn * vb_[e];
+      vb[i] = sn * va_[e] + c * vb_[e];
+    }
+  }
+  float sa = na[0] + na[1], sb = nb[0] + nb[1];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xFFFFFFFFu, sa, o);
+    sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    nrm_s[a] = sa;
+    nrm_s[b] = sb;
+    ++*rot;
+  }
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(kJacobiBlockThreads) jacobi_block_f32_kernel(
+    float* __restrict__ W, float* __restrict__ V, float* nrm, int d, int dp, int nb, int max_sweeps,
+    DevState* __restrict__ st, unsigned int* bar, int* rot_count, int require_svd_flag) {
+  if (require_svd_flag && st->need_svd == 0) return;
+  extern __shared__ __align__(16) float jsm[];
+  float* Ws = jsm;                                  // [2 kJacobiKB][d]
+  float* Vs = jsm + 2 * kJacobiKB * d;              // [2 kJacobiKB][d]
+  __shared__ float nrm_s[2 * kJacobiKB];
+  __shared__ int gcol[2 * kJacobiKB];               // global column of each local column, -1: padding
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float tol = jacobi_tol<float>(dp);
+  int* abort_flag = reinterpret_cast<int*>(bar + 2);
+  // squared column norms, kept exact below
+  for (int p = blockIdx.x * (kJacobiBlockThreads / 32) + warp; p < d; p += gridDim.x * (kJacobiBlockThreads / 32)) {
+    float a = 0.0f;
+    for (int i = lane; i < d; i += 32) a = fmaf(W[static_cast<int64_t>(p) * dp + i], W[static_cast<int64_t>(p) * dp + i], a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if (lane == 0) nrm[p] = a;
+  }
+  if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+    if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+    return;
+  }
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int local_rot = 0;
+    for (int r = 0; r < nb - 1; ++r) {
+      for (int kp = blockIdx.x; kp < nb / 2; kp += gridDim.x) {
+        const int P = (kp == 0) ? 0 : ((r + kp - 1) % (nb - 1)) + 1;
+        const int Q = ((r + (nb - 1 - kp) - 1) % (nb - 1)) + 1;
+        if (threadIdx.x < 2 * kJacobiKB) {
+          const int lc = threadIdx.x;
+          const int gc = (lc < kJacobiKB ? P : Q) * kJacobiKB + (lc % kJacobiKB);
+          gcol[lc] = gc < d ? gc : -1;
+          nrm_s[lc] = gc < d ? nrm[gc] : 0.0f;
+        }
+        __syncthreads();
+        // copy in: batches of kCopyBatch independent loads per thread, then their stores
+        for (int lc0 = 0; lc0 < 2 * kJacobiKB; lc0 += kCopyCols) {
+          for (int i0 = threadIdx.x; i0 < d; i0 += kJacobiBlockThreads * kCopyRows) {
+            float wv[kCopyCols][kCopyRows], vv[kCopyCols][kCopyRows];
+#pragma unroll
+            for (int cc = 0; cc < kCopyCols; ++cc) {
+              const int gc = gcol[lc0 + cc];
+#pragma unroll
+              for (int rr = 0; rr < kCopyRows; ++rr) {
+                const int i = i0 + rr * kJacobiBlockThreads;
+                const bool ok = gc >= 0 && i < d;
+                wv[cc][rr] = ok ? W[static_cast<int64_t>(gc) * dp + i] : 0.0f;
+                vv[cc][rr] = ok ? V[static_cast<int64_t>(gc) * dp + i] : 0.0f;
+              }
+            }
+#pragma unroll
+            for (int cc = 0; cc < kCopyCols; ++cc)
+#pragma unroll
+              for (int rr = 0; rr < kCopyRows; ++rr) {
+                const int i = i0 + rr * kJacobiBlockThreads;
+                if (i < d) {
+                  Ws[(lc0 + cc) * d + i] = wv[cc][rr];
+                  Vs[(lc0 + cc) * d + i] = vv[cc][rr];
+                }
+              }
+          }
+        }
+        __syncthreads();
+        if (r == 0) {
+          // pairs inside each block: kJacobiKB - 1 sub-rounds of kJacobiKB / 2 pairs per block
+          for (int t = 0; t < kJacobiKB - 1; ++t) {
+            const int blk = warp / (kJacobiKB / 2), k = warp % (kJacobiKB / 2);
+            const int u = (k == 0) ? 0 : ((t + k - 1) % (kJacobiKB - 1)) + 1;
+            const int v = ((t + (kJacobiKB - 1 - k) - 1) % (kJacobiKB - 1)) + 1;
+            const int a = blk * kJacobiKB + u, b = blk * kJacobiKB + v;
+            if (gcol[a] >= 0 && gcol[b] >= 0) jacobi_smem_pair<CPL>(Ws, Vs, nrm_s, a, b, d, tol, lane, &local_rot);
+            __syncthreads();
+          }
+        }
+        for (int t = 0; t < kJacobiKB; ++t) {  // cross pairs (P_i, Q_(i+t) mod KB), one per warp
+          const int a = warp, b = kJacobiKB + (warp + t) % kJacobiKB;
+          if (gcol[a] >= 0 && gcol[b] >= 0) jacobi_smem_pair<CPL>(Ws, Vs, nrm_s, a, b, d, tol, lane, &local_rot);
+          __syncthreads();
+        }
+        for (int lc = 0; lc < 2 * kJacobiKB; ++lc) {
+          const int gc = gcol[lc];
+          if (gc < 0) continue;
+          for (int i = threadIdx.x; i < d; i += kJacobiBlockThreads) {
+            W[static_cast<int64_t>(gc) * dp + i] = Ws[lc * d + i];
+            V[static_cast<int64_t>(gc) * dp + i] = Vs[lc * d + i];
+          }
+        }
+        if (threadIdx.x < 2 * kJacobiKB && gcol[threadIdx.x] >= 0) nrm[gcol[threadIdx.x]] = nrm_s[threadIdx.x];
+        __syncthreads();
+      }
+      if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+        if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+        return;
+      }
+    }
+    if (lane == 0 && local_rot) atomicAdd(rot_count + sweep, local_rot);
+    if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+      if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+      return;
+    }
+    const int total = *reinterpret_cast<volatile int*>(rot_count + sweep);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->sweeps = sweep + 1;
+    if (total == 0) break;
+  }
+}
+
 __global__ void jacobi_init_kernel(const double* __restrict__ R, int64_t d, int64_t dp,
                                    double* __restrict__ W, double* __restrict__ V) {
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < dp * dp;
@@ -1190,7 +1381,32 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     // from W0 = R Q, V = Q, whose columns are already orthogonal to float32 accuracy.
     jacobi_init_f32_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(R, d, dp, W32, V32, guard);
     SLSO_CHECK_LAUNCH();
-    SLSO_TRY(launch_jacobi(jacobi_fn<float>(d), W32, V32, kJacobiF32Sweeps));
+    if (d <= 1024) {
+      // block sweeps: one grid barrier per block round
+      SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 4, st));
+      SLSO_CHECK_CUDA(cudaMemsetAsync(rot, 0, sizeof(int) * 64, st));
+      int nb = static_cast<int>(ceil_div(d, kJacobiKB));
+      nb += nb & 1;
+      const size_t smem = sizeof(float) * 2 * 2 * kJacobiKB * static_cast<size_t>(d);
+      void* fn = d <= 256 ? reinterpret_cast<void*>(jacobi_block_f32_kernel<8>)
+                 : d <= 512 ? reinterpret_cast<void*>(jacobi_block_f32_kernel<16>)
+                            : reinterpret_cast<void*>(jacobi_block_f32_kernel<32>);
+      SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+      int occ = 0;
+      SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kJacobiBlockThreads, smem));
+      if (occ < 1) return fail(SLSO_ERR_CUDA, "block Jacobi kernel cannot be resident (smem %zu)", smem);
+      int G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h.num_sms) * occ, nb / 2));
+      G = std::max(G, 1);
+      float* nrm32 = reinterpret_cast<float*>(nrm);
+      int d_i = static_cast<int>(d), dp_i = static_cast<int>(dp), sweeps = kJacobiF32Sweeps,
+          req = (mode == 0) ? 1 : 0;
+      DevState* stp = h.state;
+      void* args[] = {&W32, &V32, &nrm32, &d_i, &dp_i, &nb, &sweeps, &stp, &bar, &rot, &req};
+      SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kJacobiBlockThreads), args, smem, st));
+      note_launch();
+    } else {
+      SLSO_TRY(launch_jacobi(jacobi_fn<float>(d), W32, V32, kJacobiF32Sweeps));
+    }
     double* V0 = W;  // dp x dp column-major; W is rewritten below
     f32_to_f64_kernel<<<grid1d(dp * dp, h), 256, 0, st>>>(V32, dp * dp, V0, guard);
     SLSO_CHECK_LAUNCH();
