@@ -753,24 +753,25 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(T* __restric
   const int nwarps = gridDim.x * wpb;
   const T tol = jacobi_tol<T>(dp);
   int* abort_flag = reinterpret_cast<int*>(bar + 2);
-  for (int p = gw; p < d; p += nwarps) {  // squared column norms, kept exact below
-    const T* wp = W + static_cast<int64_t>(p) * dp;
-    T a = 0;
-#pragma unroll
-    for (int e = 0; e < CPL; ++e) {
-      const int i = lane + 32 * e;
-      const T x = (i < d) ? wp[i] : T(0);
-      a = fma(x, x, a);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-    if (lane == 0) nrm[p] = a;
-  }
-  if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
-    if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
-    return;
-  }
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // squared column norms, recomputed exactly at every sweep's start (the sweep updates them)
+    for (int p = gw; p < d; p += nwarps) {
+      const T* wp = W + static_cast<int64_t>(p) * dp;
+      T a = 0;
+#pragma unroll
+      for (int e = 0; e < CPL; ++e) {
+        const int i = lane + 32 * e;
+        const T x = (i < d) ? wp[i] : T(0);
+        a = fma(x, x, a);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+      if (lane == 0) nrm[p] = a;
+    }
+    if (!grid_barrier(bar, bar + 1, gridDim.x, abort_flag)) {
+      if (threadIdx.x == 0) atomicExch(&st->timeout, 2);
+      return;
+    }
     int local_rot = 0;
     for (int r = 0; r < dp - 1; ++r) {
       for (int kp = gw; kp < dp / 2; kp += nwarps) {
@@ -808,26 +809,45 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_reg_kernel(T* __restric
           const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
           const T c = T(1) / sqrt(T(1) + t * t);
           const T sn = c * t;
-          T na = 0, nb = 0;  // norms of the rotated columns, from the stored values
+          // new squared norms: a - t g and b + t g exactly in real arithmetic; taken so when the
+          // change is at most half of either norm (no cancellation: a few roundings), else
+          // recomputed from the rotated values
+          const T tg = t * g;
+          if (fabs(tg) <= T(0.5) * fmin(a, b)) {
 #pragma unroll
-          for (int e = 0; e < CPL; ++e) {
-            const int i = lane + 32 * e;
-            const T xn = c * x[e] - sn * y[e], yn = sn * x[e] + c * y[e];
-            if (i < d) {
-              wp[i] = xn;
-              wq[i] = yn;
+            for (int e = 0; e < CPL; ++e) {
+              const int i = lane + 32 * e;
+              if (i < d) {
+                wp[i] = c * x[e] - sn * y[e];
+                wq[i] = sn * x[e] + c * y[e];
+              }
             }
-            na = fma(xn, xn, na);  // padding lanes hold zeros: xn = yn = 0 there
-            nb = fma(yn, yn, nb);
-          }
+            if (lane == 0) {
+              nrm[p] = a - tg;
+              nrm[q] = b + tg;
+            }
+          } else {
+            T na = 0, nb = 0;  // norms of the rotated columns, from the stored values
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            na += __shfl_xor_sync(0xFFFFFFFFu, na, o);
-            nb += __shfl_xor_sync(0xFFFFFFFFu, nb, o);
-          }
-          if (lane == 0) {
-            nrm[p] = na;
-            nrm[q] = nb;
+            for (int e = 0; e < CPL; ++e) {
+              const int i = lane + 32 * e;
+              const T xn = c * x[e] - sn * y[e], yn = sn * x[e] + c * y[e];
+              if (i < d) {
+                wp[i] = xn;
+                wq[i] = yn;
+              }
+              na = fma(xn, xn, na);  // padding lanes hold zeros: xn = yn = 0 there
+              nb = fma(yn, yn, nb);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              na += __shfl_xor_sync(0xFFFFFFFFu, na, o);
+              nb += __shfl_xor_sync(0xFFFFFFFFu, nb, o);
+            }
+            if (lane == 0) {
+              nrm[p] = na;
+              nrm[q] = nb;
+            }
           }
           if constexpr (kPrefetchV) {
 #pragma unroll
