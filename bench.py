@@ -329,6 +329,24 @@ def large_bench(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every rank of an N-rank run gets the same value (weak scaling times
+    the whole job by its slowest replica)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rows_per_s(n_per_rank, world, ms):
+    """Whole-job throughput: every rank scores its own n rows per step, the step takes ms."""
+    return world * n_per_rank / (ms / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,10 +420,7 @@ def main():
         stages, launches = api.profile_read(handle=h)
         api.profile(False, handle=h)
         clk = sampler.stop() if sampler else None
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), stages, launches, clk
+        return max_over_ranks(ms, world, "cuda"), stages, launches, clk
 
     ms32, stages32, launches32, clk = timed("f32", scores, args.steps, clocks=True)
     ms16, stages16, _, _ = timed("bf16", scores_bf, args.steps)
@@ -417,8 +432,8 @@ def main():
     ms8c, stages8c, _, _ = timed("fp8", scores_f8c, args.steps, correct=CORRECT_FRAC)
     _, info = api.leverage(X, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", out=scores, handle=h)
 
-    value = world * n / (ms32 / 1e3)
-    value16 = world * n / (ms16 / 1e3)
+    value = job_rows_per_s(n, world, ms32)
+    value16 = job_rows_per_s(n, world, ms16)
     peaks, peak_src = _peaks()
 
     # ---- roofline of the dominant stage's kernel
@@ -450,12 +465,12 @@ def main():
         "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages32.items() if c},
         "bf16": {"value": value16, "unit": "rows/s", "ms_per_step": ms16,
                  "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages16.items() if c}},
-        "bf16_corrected": {"value": world * n / (msbc / 1e3), "unit": "rows/s", "ms_per_step": msbc,
+        "bf16_corrected": {"value": job_rows_per_s(n, world, msbc), "unit": "rows/s", "ms_per_step": msbc,
                            "correct_frac": CORRECT_FRAC,
                            "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stagesbc.items() if c}},
-        "fp8": {"value": world * n / (ms8 / 1e3), "unit": "rows/s", "ms_per_step": ms8,
+        "fp8": {"value": job_rows_per_s(n, world, ms8), "unit": "rows/s", "ms_per_step": ms8,
                 "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages8.items() if c}},
-        "fp8_corrected": {"value": world * n / (ms8c / 1e3), "unit": "rows/s", "ms_per_step": ms8c,
+        "fp8_corrected": {"value": job_rows_per_s(n, world, ms8c), "unit": "rows/s", "ms_per_step": ms8c,
                           "correct_frac": CORRECT_FRAC,
                           "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages8c.items() if c}},
         "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"]},
@@ -526,10 +541,7 @@ def main():
             fn()
             e1.record(st)
             torch.cuda.synchronize()
-            t = torch.tensor([e0.elapsed_time(e1) / ke], device="cuda", dtype=torch.float64)
-            if world > 1:
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
+            return max_over_ranks(e0.elapsed_time(e1) / ke, world, "cuda")
 
         def single_calls():
             for i in range(ke):
@@ -553,18 +565,18 @@ def main():
         nblk = -(-n // STREAM_BLOCK)
         reloads = max(0, nblk - 2)  # the second pass finds the last two blocks still on the device
         line["out_of_core"] = {
-            "value": world * n / (ms_stream / 1e3), "unit": "rows/s", "ms_per_step": ms_stream,
+            "value": job_rows_per_s(n, world, ms_stream), "unit": "rows/s", "ms_per_step": ms_stream,
             "api": "slso_rank_rows_streamed: X stays in pinned host memory and is streamed through the device "
                    "twice in blocks (sketch pass, then score pass); device memory independent of n x d",
             "block_rows": STREAM_BLOCK, "blocks": nblk,
             "h2d_bytes_per_step": (n + reloads * STREAM_BLOCK) * d * 4,
             "d2h_bytes_per_step": n * (4 + 8)}
-        line["e2e"] = {"value": world * n / (ms_e / 1e3), "unit": "rows/s", "ms_per_step": ms_e,
+        line["e2e"] = {"value": job_rows_per_s(n, world, ms_e), "unit": "rows/s", "ms_per_step": ms_e,
                        "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * (4 + 8),
                        "api": f"slso_rank_rows_host_batch over {ke} host matrices (pinned): each step copies its X "
                               "in and its scores + order out; copies overlap the neighbouring steps' compute",
                        "single_call_ms_per_step": ms_single,
-                       "single_call_value": world * n / (ms_single / 1e3)}
+                       "single_call_value": job_rows_per_s(n, world, ms_single)}
         del Xh
 
     # ---- precision against the FP64 oracle, and the oracle's own throughput (rank 0, N = 1)
