@@ -215,25 +215,30 @@ __device__ __forceinline__ void bulk_stage(double* buf, const double* col, int l
       : "memory");
 }
 
-// Sum of the 256 values in red (warp 0 only; every lane returns the same bits): lane l adds
-// red[l + 32 m] for m = 0..7 in a fixed tree, then a 5-level butterfly.
-__device__ __forceinline__ double warp0_sum256(const double* red) {
+// Sum of the NT values in red (warp 0 only; every lane returns the same bits): lane l adds
+// red[l + 32 m] for m = 0..NT/32-1 in a fixed pairwise tree, then a 5-level butterfly.
+template <int NT>
+__device__ __forceinline__ double warp0_sum(const double* red) {
+  constexpr int NW = NT / 32;
+  static_assert(NW == 4 || NW == 8, "4 or 8 warps");
   const int lane = threadIdx.x & 31;
-  double v[kQrlWarps];
+  double v[NW];
 #pragma unroll
-  for (int m = 0; m < kQrlWarps; ++m) v[m] = red[lane + 32 * m];
-  double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+  for (int m = 0; m < NW; ++m) v[m] = red[lane + 32 * m];
+  double t;
+  if constexpr (NW == 8) t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+  else t = (v[0] + v[1]) + (v[2] + v[3]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
   return t;
 }
 
 // Dot of the staged vector with pairs [Q0, Q1) of the column: two chains (even, odd rows).
-template <int Q0, int Q1>
+template <int NT, int Q0, int Q1>
 __device__ __forceinline__ void dot_pairs(const double* a, const double* vsm, int t2, double& p0, double& p1) {
 #pragma unroll
   for (int q = Q0; q < Q1; ++q) {
-    const double2 w = *reinterpret_cast<const double2*>(vsm + 2 * kQrlThreads * q + t2);
+    const double2 w = *reinterpret_cast<const double2*>(vsm + 2 * NT * q + t2);
     p0 = fma(w.x, a[2 * q], p0);
     p1 = fma(w.y, a[2 * q + 1], p1);
   }
@@ -241,12 +246,12 @@ __device__ __forceinline__ void dot_pairs(const double* a, const double* vsm, in
 
 // a -= tc * u over pairs [Q0, Q1); with NORM also the squared norm of rows > c (x0, x1) and the
 // element at row c (to *alpha) of the updated column.
-template <int Q0, int Q1, bool NORM>
+template <int NT, int Q0, int Q1, bool NORM>
 __device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2, double tc, int c, int s,
                                            double& x0, double& x1, double* alpha) {
 #pragma unroll
   for (int q = Q0; q < Q1; ++q) {
-    const int i = 2 * kQrlThreads * q + t2;
+    const int i = 2 * NT * q + t2;
     const double2 w = *reinterpret_cast<const double2*>(vsm + i);
     a[2 * q] = fma(-tc, w.x, a[2 * q]);
     a[2 * q + 1] = fma(-tc, w.y, a[2 * q + 1]);
@@ -261,9 +266,10 @@ __device__ __forceinline__ void axpy_pairs(double* a, const double* vsm, int t2,
 
 // Per-column coefficients of the unscaled reflectors: coef[4c] = g = tau/den (0: H_c = I),
 // coef[4c+1] = g/den, so that applying reflector j is x -= ((u_j^T x) g/den) u_j.
-// Dynamic shared memory: 2 * kQrlThreads * (RPT/2) doubles.
-template <int RPT>
-__global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restrict__ A, int s, int lda, int d,
+// Dynamic shared memory: 2 * NT * (RPT/2) doubles.  NT = 256 threads (one CTA per SM), or 128 with
+// two CTAs per SM so that one CTA's reductions overlap the other's FMAs (s <= 8192).
+template <int RPT, int NT>
+__global__ void __launch_bounds__(NT, 256 / NT) qr_left_kernel(double* __restrict__ A, int s, int lda, int d,
                                                                  double* __restrict__ Rc,
                                                                  int* __restrict__ ready,
                                                                  double* __restrict__ coef,
@@ -271,10 +277,10 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
   static_assert(RPT % 2 == 0, "rows are held in pairs");
   constexpr int P = RPT / 2;                    // row pairs per thread
   constexpr int QA = P / 2;                     // pairs in staging half A
-  constexpr int HA = 2 * kQrlThreads * QA;      // rows in staging half A
-  constexpr int VROWS = 2 * kQrlThreads * P;    // rows of the staging buffer (>= lda)
+  constexpr int HA = 2 * NT * QA;      // rows in staging half A
+  constexpr int VROWS = 2 * NT * P;    // rows of the staging buffer (>= lda)
   extern __shared__ __align__(128) double vsm[];
-  __shared__ double red[kQrlThreads];
+  __shared__ double red[NT];
   __shared__ __align__(8) uint64_t full[2];
   __shared__ __align__(8) uint64_t empty[2];
   __shared__ double s_alpha;
@@ -283,13 +289,13 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
   __shared__ double s_form[2];  // den and R_cc of the reflector being formed
   __shared__ int s_abort;       // hint only: lets waits give up early once a wait or stage failed
   const int G = gridDim.x, tid = threadIdx.x, t2 = 2 * threadIdx.x, lane = threadIdx.x & 31;
-  for (int i = lda + tid; i < VROWS; i += kQrlThreads) vsm[i] = 0.0;  // never written by a copy
+  for (int i = lda + tid; i < VROWS; i += NT) vsm[i] = 0.0;  // never written by a copy
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[1])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[0])), "r"(kQrlWarps));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[1])), "r"(kQrlWarps));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[0])), "r"((NT / 32)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[1])), "r"((NT / 32)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
     double a[RPT];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      const int i = 2 * kQrlThreads * q + t2;
+      const int i = 2 * NT * q + t2;
       double2 v = make_double2(0.0, 0.0);
       if (i < lda) v = __ldcg(reinterpret_cast<const double2*>(col + i));
       a[2 * q] = i < s ? v.x : 0.0;
@@ -361,13 +367,13 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       // the same bits in every thread: written once by thread 0 before it armed full[0]
       const double g = s_coef[0], ginv = s_coef[1];
       double p0 = 0.0, p1 = 0.0;
-      if (g != 0.0) dot_pairs<0, QA>(a, vsm, t2, p0, p1);
+      if (g != 0.0) dot_pairs<NT, 0, QA>(a, vsm, t2, p0, p1);
       if (!mbar_wait_bounded(&full[1], par, abort_flag)) {
         bad = true;
         *abort_flag = 1;
       }
       if (g != 0.0) {
-        dot_pairs<QA, P>(a, vsm, t2, p0, p1);
+        dot_pairs<NT, QA, P>(a, vsm, t2, p0, p1);
         red[tid] = p0 + p1;
       }
       // any failed wait or stage so far ends the kernel (uniformly)
@@ -381,18 +387,18 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       const bool last = (j + 1 == c) && g != 0.0;
       if (g != 0.0) {
         if (tid < 32) {
-          const double sum = warp0_sum256(red);
+          const double sum = warp0_sum<NT>(red);
           if (lane == 0) s_scalar = sum * ginv;
         }
         __syncthreads();
         const double tc = s_scalar;
-        if (last) axpy_pairs<0, QA, true>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
-        else axpy_pairs<0, QA, false>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        if (last) axpy_pairs<NT, 0, QA, true>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        else axpy_pairs<NT, 0, QA, false>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[0]);
         if (tid == 0 && j + 1 < c) stage_half(j + 1, 0);
-        if (last) axpy_pairs<QA, P, true>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
-        else axpy_pairs<QA, P, false>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        if (last) axpy_pairs<NT, QA, P, true>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
+        else axpy_pairs<NT, QA, P, false>(a, vsm, t2, tc, c, s, x0, x1, &s_alpha);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[1]);
       } else {
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
     if (!fused) {
 #pragma unroll
       for (int q = 0; q < P; ++q) {
-        const int i = 2 * kQrlThreads * q + t2;
+        const int i = 2 * NT * q + t2;
         if (i > c && i < s) x0 = fma(a[2 * q], a[2 * q], x0);
         if (i + 1 > c && i + 1 < s) x1 = fma(a[2 * q + 1], a[2 * q + 1], x1);
         if (i == c) s_alpha = a[2 * q];
@@ -426,7 +432,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
     red[tid] = x0 + x1;
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      const int i = 2 * kQrlThreads * q + t2;
+      const int i = 2 * NT * q + t2;
       if (i < lda) {
         double2 v;
         v.x = (i < c) ? 0.0 : a[2 * q];
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
     }
     __syncthreads();
     if (tid < 32) {
-      const double xn2 = warp0_sum256(red);
+      const double xn2 = warp0_sum<NT>(red);
       if (lane == 0) {
         const double alpha = s_alpha;
         double g = 0.0, inv = 0.0, den = 0.0, rcc = alpha;
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
       }
     }
     __syncthreads();
-    if (t2 == (c & (2 * kQrlThreads - 1)) - (c & 1)) col[c] = s_form[0];  // the thread holding row c
+    if (t2 == (c & (2 * NT - 1)) - (c & 1)) col[c] = s_form[0];  // the thread holding row c
     __threadfence();
     __syncthreads();
     if (tid == 0) atomicExch(&ready[c], 1);
@@ -463,7 +469,7 @@ __global__ void __launch_bounds__(kQrlThreads, 1) qr_left_kernel(double* __restr
     const double rcc = s_form[1];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-      const int i = 2 * kQrlThreads * q + t2;
+      const int i = 2 * NT * q + t2;
       if (i <= c) rcol[i] = (i == c) ? rcc : a[2 * q];
       if (i + 1 <= c) rcol[i + 1] = (i + 1 == c) ? rcc : a[2 * q + 1];
     }
@@ -1301,27 +1307,47 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     void* fn = nullptr;
     int threads = kQrlThreads;
     int rpt = 0;  // rows per thread of the left-looking kernel (0: right-looking)
-    // the smallest instantiated row count per thread that covers s (padding rows cost FMAs)
-    static const int kRpts[] = {2, 4, 8, 16, 24, 32, 40, 48, 56, 64};
-    for (int r : kRpts)
-      if (s <= static_cast<int64_t>(kQrlThreads) * r) {
-        rpt = r;
-        break;
+    // the smallest instantiated row count per thread that covers s (padding rows cost FMAs).  For
+    // 2048 < s <= 8192, CTAs of 128 threads (twice the rows per thread) run two per SM, so that one
+    // CTA's reductions and barriers overlap the other's FMAs; otherwise one 256-thread CTA per SM.
+    if (s > 2048 && s <= 8192) {
+      static const int kRpts128[] = {24, 32, 40, 48, 56, 64};
+      for (int r : kRpts128)
+        if (s <= static_cast<int64_t>(128) * r) {
+          rpt = r;
+          break;
+        }
+      threads = 128;
+      switch (rpt) {
+        case 24: fn = reinterpret_cast<void*>(qr_left_kernel<24, 128>); break;
+        case 32: fn = reinterpret_cast<void*>(qr_left_kernel<32, 128>); break;
+        case 40: fn = reinterpret_cast<void*>(qr_left_kernel<40, 128>); break;
+        case 48: fn = reinterpret_cast<void*>(qr_left_kernel<48, 128>); break;
+        case 56: fn = reinterpret_cast<void*>(qr_left_kernel<56, 128>); break;
+        default: fn = reinterpret_cast<void*>(qr_left_kernel<64, 128>); break;
       }
-    switch (rpt) {
-      case 2: fn = reinterpret_cast<void*>(qr_left_kernel<2>); break;
-      case 4: fn = reinterpret_cast<void*>(qr_left_kernel<4>); break;
-      case 8: fn = reinterpret_cast<void*>(qr_left_kernel<8>); break;
-      case 16: fn = reinterpret_cast<void*>(qr_left_kernel<16>); break;
-      case 24: fn = reinterpret_cast<void*>(qr_left_kernel<24>); break;
-      case 32: fn = reinterpret_cast<void*>(qr_left_kernel<32>); break;
-      case 40: fn = reinterpret_cast<void*>(qr_left_kernel<40>); break;
-      case 48: fn = reinterpret_cast<void*>(qr_left_kernel<48>); break;
-      case 56: fn = reinterpret_cast<void*>(qr_left_kernel<56>); break;
-      case 64: fn = reinterpret_cast<void*>(qr_left_kernel<64>); break;
-      default: break;
+    } else {
+      static const int kRpts[] = {2, 4, 8, 16, 24, 32, 40, 48, 56, 64};
+      for (int r : kRpts)
+        if (s <= static_cast<int64_t>(kQrlThreads) * r) {
+          rpt = r;
+          break;
+        }
+      switch (rpt) {
+        case 2: fn = reinterpret_cast<void*>(qr_left_kernel<2, 256>); break;
+        case 4: fn = reinterpret_cast<void*>(qr_left_kernel<4, 256>); break;
+        case 8: fn = reinterpret_cast<void*>(qr_left_kernel<8, 256>); break;
+        case 16: fn = reinterpret_cast<void*>(qr_left_kernel<16, 256>); break;
+        case 24: fn = reinterpret_cast<void*>(qr_left_kernel<24, 256>); break;
+        case 32: fn = reinterpret_cast<void*>(qr_left_kernel<32, 256>); break;
+        case 40: fn = reinterpret_cast<void*>(qr_left_kernel<40, 256>); break;
+        case 48: fn = reinterpret_cast<void*>(qr_left_kernel<48, 256>); break;
+        case 56: fn = reinterpret_cast<void*>(qr_left_kernel<56, 256>); break;
+        case 64: fn = reinterpret_cast<void*>(qr_left_kernel<64, 256>); break;
+        default: break;
+      }
     }
-    size_t smem = sizeof(double) * kQrlThreads * rpt;  // staging buffer of the left-looking kernel
+    size_t smem = sizeof(double) * threads * rpt;  // staging buffer of the left-looking kernel
     if (rpt == 0) {
       const bool vsm = s <= 24576;
       smem = vsm ? sizeof(double) * s : 0;
@@ -1332,7 +1358,8 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     int occ = 0;
     SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
     if (occ < 1) return fail(SLSO_ERR_CUDA, "QR kernel cannot be resident (smem %zu)", smem);
-    int G = static_cast<int>(std::min<int64_t>(h.num_sms, d));
+    int G = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(h.num_sms) * (rpt ? std::min(occ, 256 / threads) : 1),
+                                               d));
     int s_i = static_cast<int>(s), lda_i = static_cast<int>(lda), d_i = static_cast<int>(d);
     void* args_left[] = {&A, &s_i, &lda_i, &d_i, &Rc, &ready, &taus, &h.state};
     void* args_right[] = {&A, &s_i, &lda_i, &d_i, &ready, &taus, &h.state};
