@@ -1308,9 +1308,12 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     int threads = kQrlThreads;
     int rpt = 0;  // rows per thread of the left-looking kernel (0: right-looking)
     // the smallest instantiated row count per thread that covers s (padding rows cost FMAs).  For
-    // 2048 < s <= 8192, CTAs of 128 threads (twice the rows per thread) run two per SM, so that one
-    // CTA's reductions and barriers overlap the other's FMAs; otherwise one 256-thread CTA per SM.
-    if (s > 2048 && s <= 8192) {
+    // 2048 < s <= 8192 and at least 4 columns per SM, CTAs of 128 threads (twice the rows per
+    // thread) run two per SM, so that one CTA's reductions and barriers overlap the other's FMAs
+    // (measured: 6144 x 3072 141 -> 117 ms, 4096 x 1024 14.6 -> 12.4 ms); with fewer columns the
+    // reflector chain dominates and sharing an SM slows it (8192 x 128 1.5 -> 1.9 ms), so one
+    // 256-thread CTA per SM is used.
+    if (s > 2048 && s <= 8192 && d >= 4 * static_cast<int64_t>(h.num_sms)) {
       static const int kRpts128[] = {24, 32, 40, 48, 56, 64};
       for (int r : kRpts128)
         if (s <= static_cast<int64_t>(128) * r) {
