@@ -83,7 +83,7 @@ struct Server {
   int64_t n_graph_new = 0, n_graph_update = 0, n_graph_direct = 0;
   size_t graph_bytes = 0;  // workspaces held by cached graphs (all slots)
   uint64_t use_clock = 0;
-  bool capture_ok = true;  // cleared if the driver refuses to capture the launches
+  bool capture_ok = true;  // cleared if the CUDA driver refuses to capture the launches
   std::deque<std::vector<int64_t>> seen;  // recent leverage shapes (a shape's first job runs direct)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -377,7 +377,7 @@ extern "C" slso_status slso_server_create(slso_server** out, int device, int nsl
       return fail(SLSO_ERR_CUDA, "slso_server_create: %s", cudaGetErrorString(e));
     }
   }
-  encode_fn();  // resolve the driver entry point now, not while a capture is recording
+  encode_fn();  // resolve the CUDA driver entry point now, not while a capture is recording
   s->worker = std::thread(worker_main, s);
   *out = reinterpret_cast<slso_server*>(s);
   return SLSO_OK;

@@ -1,4 +1,4 @@
-// Host helpers for TMA tensor maps: the driver's cuTensorMapEncodeTiled through the runtime's
+// Host helpers for TMA tensor maps: the CUDA driver's cuTensorMapEncodeTiled through the runtime's
 // entry-point query (no libcuda link), and 2-D row-major maps with 128-byte swizzle.
 #pragma once
 
