@@ -401,6 +401,204 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Two-tile form of the float32-accurate (3xTF32) scores for k <= 128: a work item is two
+// 128-row tiles of X that share every K-block of B = M^T, so B's hi and lo tiles (the larger part
+// of what each SM reads from L2 in the one-tile form) are read once per 256 rows.  X is converted
+// in place: the TMA writes the float32 tile, the converters overwrite it with its tf32 high part
+// and write the remainder beside it.  Stage layout (1024-byte aligned pieces): XA, XB (tiles 0, 1:
+// float32, then hi), LA, LB (lo), BH, BL.  TMEM: two accumulator pairs (tiles 0, 1) of N columns,
+// double-buffered across work items (4N <= 512 columns).  Warps 0-3 epilogue, 4 TMA producer,
+// 5 TMEM owner and MMA issuer, 6-13 converters.  Every wait is bounded.  KBE float32 elements per
+// K-block: 32 (128-byte rows, 128B swizzle) or 16 (64-byte rows, 64B swizzle: half the bytes per
+// stage, so twice the stages fit and more copies are in flight).
+struct Layout2T {
+  int N, KB, S;
+  uint32_t b_bytes, stage_bytes, bar_off, smem_bytes, tmem_cols;
+};
+
+constexpr int kMaxStages2T = 4;
+
+template <int KBE>
+__global__ void __launch_bounds__(kThreads, 1)
+    score_tc2_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBh,
+                     const __grid_constant__ CUtensorMap tmBl, const Layout2T L, int64_t n, int nwork,
+                     float* __restrict__ scores, DevState* __restrict__ state) {
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);  // TMA bytes landed
+  uint64_t* cvt = full + kMaxStages2T;                               // converters done
+  uint64_t* empty = cvt + kMaxStages2T;                              // MMAs reading the stage done
+  uint64_t* acc_full = empty + kMaxStages2T;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ int s_abort;
+  const volatile int* abort_flag = &s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t kX = kBM * KBE * 4;  // one 128-row x KBE-float tile
+  constexpr int kSteps = KBE / 8;         // tf32 MMAs take K = 8
+  auto sdesc = [](const void* t) { return KBE == 32 ? sdesc_sw128(t) : sdesc_sw64(t); };
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int i = 0; i < L.S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&cvt[i], kConvThreads);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 128);
+    }
+    fence_mbar_init();
+  }
+  if (warp == kWarpMma) tmem_alloc(tmem_slot, L.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == kWarpProducer) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        const int y0 = w * 2 * kBM;
+        for (int kb = 0; kb < L.KB; ++kb, ++it) {
+          const int st = it % L.S;
+          if (!mbar_wait(&empty[st], ((it / L.S) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
+          const int x = kb * KBE;
+          mbar_arrive_expect_tx(&full[st], 2 * kX + 2 * L.b_bytes);
+          tma_load_2d(stage, &tmX, &full[st], x, y0);
+          tma_load_2d(stage + kX, &tmX, &full[st], x, y0 + kBM);
+          tma_load_2d(stage + 4 * kX, &tmBh, &full[st], x, 0);
+          tma_load_2d(stage + 4 * kX + L.b_bytes, &tmBl, &full[st], x, 0);
+        }
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(&state->timeout, 3);
+        for (int j = (it > L.S ? it - L.S : 0); j < it; ++j)  // let issued copies land (bounded)
+          mbar_wait(&full[j % L.S], (j / L.S) & 1u, nullptr, 50000000ull);
+      }
+    }
+  } else if (warp == kWarpMma) {
+    if (lane == 0) {
+      const uint32_t id = idesc(FMT_TF32, FMT_TF32, kBM, static_cast<uint32_t>(L.N));
+      int it = 0, tcount = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++tcount) {
+        const int ab = tcount & 1;
+        if (!mbar_wait(&acc_empty[ab], ((tcount >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d0 = tmem_base + static_cast<uint32_t>(ab * 2 * L.N);
+        const uint32_t d1 = d0 + static_cast<uint32_t>(L.N);
+        for (int kb = 0; kb < L.KB; ++kb, ++it) {
+          const int st = it % L.S;
+          if (!mbar_wait(&cvt[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
+          const uint64_t ha = sdesc(stage), hb = sdesc(stage + kX);
+          const uint64_t la = sdesc(stage + 2 * kX), lb = sdesc(stage + 3 * kX);
+          const uint64_t bh = sdesc(stage + 4 * kX), bl = sdesc(stage + 4 * kX + L.b_bytes);
+#pragma unroll
+          for (int ks = 0; ks < kSteps; ++ks) {
+            const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
+            const uint32_t first = (kb | ks) != 0;
+            mma_tf32(d0, ha + o, bh + o, id, first);
+            mma_tf32(d0, ha + o, bl + o, id, 1u);
+            mma_tf32(d0, la + o, bh + o, id, 1u);
+            mma_tf32(d1, hb + o, bh + o, id, first);
+            mma_tf32(d1, hb + o, bl + o, id, 1u);
+            mma_tf32(d1, lb + o, bh + o, id, 1u);
+          }
+          mma_commit(&empty[st]);
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[ab]);
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(&state->timeout, 3);
+      }
+      // all MMAs issued by this thread have completed before TMEM is released
+      if (it > 0) mbar_wait(&empty[(it - 1) % L.S], ((it - 1) / L.S) & 1u, nullptr, 50000000ull);
+    }
+  } else if (warp >= kWarpConvert0) {
+    const int ct = threadIdx.x - kWarpConvert0 * 32;
+    int it = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+      for (int kb = 0; kb < L.KB; ++kb, ++it) {
+        const int st = it % L.S;
+        if (!mbar_wait(&full[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
+        unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
+        // both tiles: chunk q of XA|XB (float32, the TMA's swizzled layout) -> hi in place and
+        // lo at the same chunk of LA|LB (same element size and layout)
+        uint4* xs = reinterpret_cast<uint4*>(stage);
+        uint4* ls = reinterpret_cast<uint4*>(stage + 2 * kX);
+#pragma unroll 4
+        for (int q = ct; q < static_cast<int>(2 * kX / 16); q += kConvThreads) {
+          const uint4 v = xs[q];
+          uint4 h, l;
+          split_tf32(v.x, h.x, l.x);
+          split_tf32(v.y, h.y, l.y);
+          split_tf32(v.z, h.z, l.z);
+          split_tf32(v.w, h.w, l.w);
+          xs[q] = h;
+          ls[q] = l;
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&cvt[st]);
+      }
+    }
+    if (!ok) {
+      atomicExch(&s_abort, 1);
+      atomicExch(&state->timeout, 3);
+    }
+  } else {  // warps 0-3: epilogue; warp w reads TMEM lanes 32w..32w+31 = tile rows 32w..32w+31
+    int tcount = 0;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++tcount) {
+      const int ab = tcount & 1;
+      int got = 0;
+      if (lane == 0) got = mbar_wait(&acc_full[ab], (tcount >> 1) & 1u, abort_flag) ? 1 : 0;
+      got = __shfl_sync(0xFFFFFFFFu, got, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
+      if (!got) {
+        if (lane == 0) {
+          atomicExch(&s_abort, 1);
+          atomicExch(&state->timeout, 3);
+        }
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(warp * 32) << 16) +
+                               static_cast<uint32_t>(ab * 2 * L.N + u * L.N);
+        float sum = 0.0f;
+        for (int c0 = 0; c0 < L.N; c0 += 32) {
+          float v[32];
+          tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c0), v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) sum = fmaf(v[i], v[i], sum);
+        }
+        const int64_t row = (static_cast<int64_t>(w) * 2 + u) * kBM + warp * 32 + lane;
+        if (row < n) scores[row] = sum;
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[ab]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kWarpMma) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, L.tmem_cols);
+  }
+}
+
 // B = M^T (N x Kpad, K contiguous) split into tf32-exact high parts and float32 remainders.
 __global__ void prep_b_tf32_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
                                    float* __restrict__ Bhi, float* __restrict__ Blo) {
@@ -615,6 +813,38 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   }
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
   const int ntiles = static_cast<int>(ceil_div(n, kBM));
+  if (mode == MODE_TF32X3 && L.N <= 128) {
+    // two 128-row tiles per work item share each B K-block
+    // K-blocks of 16 floats (64-byte rows, 64B swizzle): 4 stages of 48 KB at k = 128
+    constexpr int kbe = 16;
+    CUtensorMap mX16, mBh16, mBl16;
+    const bool ok16 = make_map(&mX16, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * esz, kbe, kBM,
+                               CU_TENSOR_MAP_SWIZZLE_64B) &&
+                      make_map(&mBh16, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, kbe, L.N,
+                               CU_TENSOR_MAP_SWIZZLE_64B) &&
+                      make_map(&mBl16, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, kbe, L.N,
+                               CU_TENSOR_MAP_SWIZZLE_64B);
+    if (!ok16) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
+    Layout2T L2{};
+    L2.N = L.N;
+    L2.KB = static_cast<int>(Kpad / kbe);
+    L2.b_bytes = static_cast<uint32_t>(L.N) * kbe * 4u;
+    L2.stage_bytes = 4 * (kBM * kbe * 4u) + 2 * L2.b_bytes;
+    L2.S = static_cast<int>(std::min<uint32_t>(kMaxStages2T, (226u * 1024u) / L2.stage_bytes));
+    L2.bar_off = static_cast<uint32_t>(L2.S) * L2.stage_bytes;
+    L2.smem_bytes = L2.bar_off + (3 * kMaxStages2T + 4) * 8 + 8 + 1024;
+    uint32_t cols = 32;
+    while (cols < static_cast<uint32_t>(4 * L.N)) cols <<= 1;
+    L2.tmem_cols = cols;
+    const int nwork = (ntiles + 1) / 2;
+    const int grid2 = std::min(nwork, h.num_sms);
+    SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc2_kernel<kbe>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(L2.smem_bytes)));
+    score_tc2_kernel<16><<<grid2, kThreads, L2.smem_bytes, st>>>(mX16, mBh16, mBl16, L2, n, nwork, scores,
+                                                                h.state);
+    SLSO_CHECK_LAUNCH();
+    return SLSO_OK;
+  }
   const int grid = std::min(ntiles, h.num_sms);
   SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(L.smem_bytes)));

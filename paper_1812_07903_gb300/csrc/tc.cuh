@@ -128,6 +128,19 @@ __device__ __forceinline__ uint64_t sdesc_sw128(const void* tile) {
   return d;
 }
 
+// The same for the 64-byte swizzle layout (rows of 64 bytes, 8-row atoms of 512 bytes): stride
+// byte offset 512 >> 4, swizzle mode 4 (64B).
+__device__ __forceinline__ uint64_t sdesc_sw64(const void* tile) {
+  const uint32_t a = smem_u32(tile);
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((a & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;
+  return d;
+}
+
 // Instruction descriptor (kind::f16 / kind::tf32 / kind::f8f6f4): D float32 (bits 4-5 = 1),
 // A and B formats in bits 7-9 / 10-12, both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
 enum : uint32_t { FMT_F16 = 0, FMT_BF16 = 1, FMT_TF32 = 2, FMT_E4M3 = 0 };
