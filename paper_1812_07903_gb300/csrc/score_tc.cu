@@ -413,12 +413,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 // stage, so twice the stages fit and more copies are in flight).
 struct Layout2T {
   int N, KB, S;
+  int nbuf;  // accumulator sets in TMEM: 2 (the epilogue of one work item overlaps the next) or 1
   uint32_t b_bytes, stage_bytes, bar_off, smem_bytes, tmem_cols;
 };
 
 constexpr int kMaxStages2T = 4;
 
-template <int KBE>
+template <int KBE, int T>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc2_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBh,
                      const __grid_constant__ CUtensorMap tmBl, const Layout2T L, int64_t n, int nwork,
@@ -463,17 +464,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-        const int y0 = w * 2 * kBM;
+        const int y0 = w * T * kBM;
         for (int kb = 0; kb < L.KB; ++kb, ++it) {
           const int st = it % L.S;
           if (!mbar_wait(&empty[st], ((it / L.S) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
           unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
           const int x = kb * KBE;
-          mbar_arrive_expect_tx(&full[st], 2 * kX + 2 * L.b_bytes);
-          tma_load_2d(stage, &tmX, &full[st], x, y0);
-          tma_load_2d(stage + kX, &tmX, &full[st], x, y0 + kBM);
-          tma_load_2d(stage + 4 * kX, &tmBh, &full[st], x, 0);
-          tma_load_2d(stage + 4 * kX + L.b_bytes, &tmBl, &full[st], x, 0);
+          mbar_arrive_expect_tx(&full[st], T * kX + 2 * L.b_bytes);
+#pragma unroll
+          for (int u = 0; u < T; ++u) tma_load_2d(stage + u * kX, &tmX, &full[st], x, y0 + u * kBM);
+          tma_load_2d(stage + 2 * T * kX, &tmBh, &full[st], x, 0);
+          tma_load_2d(stage + 2 * T * kX + L.b_bytes, &tmBl, &full[st], x, 0);
         }
       }
       if (!ok) {
@@ -489,29 +490,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       int it = 0, tcount = 0;
       bool ok = true;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++tcount) {
-        const int ab = tcount & 1;
-        if (!mbar_wait(&acc_empty[ab], ((tcount >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        const int ab = tcount % L.nbuf;
+        if (!mbar_wait(&acc_empty[ab], ((tcount / L.nbuf) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d0 = tmem_base + static_cast<uint32_t>(ab * 2 * L.N);
-        const uint32_t d1 = d0 + static_cast<uint32_t>(L.N);
+        const uint32_t dbase = tmem_base + static_cast<uint32_t>(ab * T * L.N);
         for (int kb = 0; kb < L.KB; ++kb, ++it) {
           const int st = it % L.S;
           if (!mbar_wait(&cvt[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
           unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
-          const uint64_t ha = sdesc(stage), hb = sdesc(stage + kX);
-          const uint64_t la = sdesc(stage + 2 * kX), lb = sdesc(stage + 3 * kX);
-          const uint64_t bh = sdesc(stage + 4 * kX), bl = sdesc(stage + 4 * kX + L.b_bytes);
+          const uint64_t bh = sdesc(stage + 2 * T * kX), bl = sdesc(stage + 2 * T * kX + L.b_bytes);
 #pragma unroll
           for (int ks = 0; ks < kSteps; ++ks) {
             const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
             const uint32_t first = (kb | ks) != 0;
-            mma_tf32(d0, ha + o, bh + o, id, first);
-            mma_tf32(d0, ha + o, bl + o, id, 1u);
-            mma_tf32(d0, la + o, bh + o, id, 1u);
-            mma_tf32(d1, hb + o, bh + o, id, first);
-            mma_tf32(d1, hb + o, bl + o, id, 1u);
-            mma_tf32(d1, lb + o, bh + o, id, 1u);
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+              const uint32_t du = dbase + static_cast<uint32_t>(u * L.N);
+              const uint64_t hu = sdesc(stage + u * kX), lu = sdesc(stage + (T + u) * kX);
+              mma_tf32(du, hu + o, bh + o, id, first);
+              mma_tf32(du, hu + o, bl + o, id, 1u);
+              mma_tf32(du, lu + o, bh + o, id, 1u);
+            }
           }
           mma_commit(&empty[st]);
         }
@@ -534,12 +534,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int st = it % L.S;
         if (!mbar_wait(&full[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
         unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
-        // both tiles: chunk q of XA|XB (float32, the TMA's swizzled layout) -> hi in place and
-        // lo at the same chunk of LA|LB (same element size and layout)
+        // all tiles: chunk q of the X tiles (float32, the TMA's swizzled layout) -> hi in place and
+        // lo at the same chunk of the lo tiles (same element size and layout)
         uint4* xs = reinterpret_cast<uint4*>(stage);
-        uint4* ls = reinterpret_cast<uint4*>(stage + 2 * kX);
+        uint4* ls = reinterpret_cast<uint4*>(stage + T * kX);
 #pragma unroll 4
-        for (int q = ct; q < static_cast<int>(2 * kX / 16); q += kConvThreads) {
+        for (int q = ct; q < static_cast<int>(T * kX / 16); q += kConvThreads) {
           const uint4 v = xs[q];
           uint4 h, l;
           split_tf32(v.x, h.x, l.x);
@@ -560,9 +560,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {  // warps 0-3: epilogue; warp w reads TMEM lanes 32w..32w+31 = tile rows 32w..32w+31
     int tcount = 0;
     for (int w = blockIdx.x; w < nwork; w += gridDim.x, ++tcount) {
-      const int ab = tcount & 1;
+      const int ab = tcount % L.nbuf;
       int got = 0;
-      if (lane == 0) got = mbar_wait(&acc_full[ab], (tcount >> 1) & 1u, abort_flag) ? 1 : 0;
+      if (lane == 0) got = mbar_wait(&acc_full[ab], (tcount / L.nbuf) & 1u, abort_flag) ? 1 : 0;
       got = __shfl_sync(0xFFFFFFFFu, got, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
       if (!got) {
         if (lane == 0) {
@@ -573,9 +573,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_after();
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < T; ++u) {
         const uint32_t taddr = tmem_base + (static_cast<uint32_t>(warp * 32) << 16) +
-                               static_cast<uint32_t>(ab * 2 * L.N + u * L.N);
+                               static_cast<uint32_t>(ab * T * L.N + u * L.N);
         float sum = 0.0f;
         for (int c0 = 0; c0 < L.N; c0 += 32) {
           float v[32];
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 32; ++i) sum = fmaf(v[i], v[i], sum);
         }
-        const int64_t row = (static_cast<int64_t>(w) * 2 + u) * kBM + warp * 32 + lane;
+        const int64_t row = (static_cast<int64_t>(w) * T + u) * kBM + warp * 32 + lane;
         if (row < n) scores[row] = sum;
       }
       tc_fence_before();
@@ -825,23 +825,27 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                       make_map(&mBl16, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, kbe, L.N,
                                CU_TENSOR_MAP_SWIZZLE_64B);
     if (!ok16) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
+    // row tiles per work item: B's hi and lo parts are read once per 256 rows (measured on 1M x 1024:
+    // 2 tiles 1.27 ms, 4 tiles 1.29 ms: shared-memory bandwidth, not L2 ingress, bounds the kernel)
+    constexpr int kT = 2;
     Layout2T L2{};
     L2.N = L.N;
     L2.KB = static_cast<int>(Kpad / kbe);
     L2.b_bytes = static_cast<uint32_t>(L.N) * kbe * 4u;
-    L2.stage_bytes = 4 * (kBM * kbe * 4u) + 2 * L2.b_bytes;
+    L2.stage_bytes = 2 * kT * (kBM * kbe * 4u) + 2 * L2.b_bytes;
+    L2.nbuf = (2 * kT * L.N <= 512) ? 2 : 1;
     L2.S = static_cast<int>(std::min<uint32_t>(kMaxStages2T, (226u * 1024u) / L2.stage_bytes));
     L2.bar_off = static_cast<uint32_t>(L2.S) * L2.stage_bytes;
     L2.smem_bytes = L2.bar_off + (3 * kMaxStages2T + 4) * 8 + 8 + 1024;
     uint32_t cols = 32;
-    while (cols < static_cast<uint32_t>(4 * L.N)) cols <<= 1;
+    while (cols < static_cast<uint32_t>(L2.nbuf * kT * L.N)) cols <<= 1;
     L2.tmem_cols = cols;
-    const int nwork = (ntiles + 1) / 2;
+    const int nwork = (ntiles + kT - 1) / kT;
     const int grid2 = std::min(nwork, h.num_sms);
-    SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc2_kernel<kbe>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc2_kernel<kbe, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L2.smem_bytes)));
-    score_tc2_kernel<16><<<grid2, kThreads, L2.smem_bytes, st>>>(mX16, mBh16, mBl16, L2, n, nwork, scores,
-                                                                h.state);
+    score_tc2_kernel<kbe, kT><<<grid2, kThreads, L2.smem_bytes, st>>>(mX16, mBh16, mBl16, L2, n, nwork, scores,
+                                                                     h.state);
     SLSO_CHECK_LAUNCH();
     return SLSO_OK;
   }
