@@ -34,10 +34,11 @@ METRIC = "scored rows/s (BF16 vs FP32, ≤2% median rel err) + roofline %; p99 j
 WORKLOAD = dict(n=1_000_000, d=1024, s=16384, k=128, kind="countsketch", xseed=1003, seed_S=2003, seed_Pi=3003)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070 / 1e3  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3
-# DRAM bytes of one qr_left_kernel<64> launch at s = 16384, d = 1024 (dram__bytes_read.sum 496.4 MB
-# + dram__bytes_write.sum 130.2 MB from one ncu capture of the current kernel).  Set back to None
-# whenever that kernel changes, until it is captured again.
-QR_TRAFFIC_BYTES = 496_413_184 + 130_248_960
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the named kernel at
+# s = 16384, d = 1024 from one ncu capture of its current source; None whenever the kernel changed
+# since, until it is captured again.
+QR_TRAFFIC_BYTES = None  # qr_left_kernel<64, 256>
+SYRK_TRAFFIC_BYTES = None  # gram_syrk_kernel
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point
@@ -318,7 +319,7 @@ def large_bench(args):
         ms = e0.elapsed_time(e1) / args.steps
         stages, launches = api.profile_read(handle=h)
         api.profile(False, handle=h)
-        per = {nm: v_ / max(c, 1) for nm, (v_, c) in stages.items() if c}
+        per = {nm: v_ / args.steps for nm, (v_, c) in stages.items() if c}
         tf = 2.0 * s * n * d / (per["sketch"] / 1e3) / 1e12
         out[compute] = {"value": n / (ms / 1e3), "ms_per_step": ms, "gpu_launches": int(launches),
                         "stages_ms_per_step": {nm: round(v_, 3) for nm, v_ in per.items()},
@@ -437,9 +438,16 @@ def main():
     peaks, peak_src = _peaks()
 
     # ---- roofline of the dominant stage's kernel
-    per = {name: ms_ / max(c, 1) for name, (ms_, c) in stages32.items() if c}
+    per = {name: ms_ / args.steps for name, (ms_, c) in stages32.items() if c}
     dom = max(per, key=per.get)
-    if dom == "qr":
+    if dom == "syrk":
+        flops = float(s) * d * (d + 1)  # 2 flops per FMA, s d (d + 1) / 2 FMAs (lower triangle of G)
+        ach = flops / (per["syrk"] / 1e3) / 1e12
+        roof = {"kernel": "gram_syrk_kernel (FP64 SYRK G = SX^T SX)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": SYRK_TRAFFIC_BYTES if (s, d) == (16384, 1024) else None,
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.198)"}
+    elif dom == "qr":
         flops = 2.0 * s * d * d - 2.0 * d ** 3 / 3.0
         ach = flops / (per["qr"] / 1e3) / 1e12
         roof = {"kernel": "qr_kernel (FP64 Householder, cooperative)", "bound": "alu", "achieved": ach,
@@ -462,18 +470,19 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(n, d, s, k, kind),
         "roofline": roof, "gpu_launches": int(launches32),
-        "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages32.items() if c},
+        "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages32.items() if c},
         "bf16": {"value": value16, "unit": "rows/s", "ms_per_step": ms16,
-                 "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages16.items() if c}},
+                 "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages16.items() if c}},
         "bf16_corrected": {"value": job_rows_per_s(n, world, msbc), "unit": "rows/s", "ms_per_step": msbc,
                            "correct_frac": CORRECT_FRAC,
-                           "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stagesbc.items() if c}},
+                           "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stagesbc.items() if c}},
         "fp8": {"value": job_rows_per_s(n, world, ms8), "unit": "rows/s", "ms_per_step": ms8,
-                "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages8.items() if c}},
+                "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages8.items() if c}},
         "fp8_corrected": {"value": job_rows_per_s(n, world, ms8c), "unit": "rows/s", "ms_per_step": ms8c,
                           "correct_frac": CORRECT_FRAC,
-                          "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in stages8c.items() if c}},
-        "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"]},
+                          "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages8c.items() if c}},
+        "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"],
+                      "gram_route": info["gram_route"], "gram_resid": info["gram_resid"]},
         "clocks": clk,
         "hbm_floor_ms": (2 * n * d * 4 + n * 12) / (peaks["hbm_gbs"] * 1e6),
     }
@@ -521,7 +530,7 @@ def main():
         api.profile(False, handle=h)
         ms_o = e0.elapsed_time(e1) / args.steps
         line["osnap"] = {"value": n / (ms_o / 1e3), "unit": "rows/s", "ms_per_step": ms_o, "nnz": OSNAP_NNZ,
-                         "stages_ms_per_step": {nm: round(v_ / max(c, 1), 4) for nm, (v_, c) in st_o.items() if c}}
+                         "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in st_o.items() if c}}
         del scores_os
 
     # ---- end to end through the host-buffer entry points

@@ -68,6 +68,17 @@ typedef enum { SLSO_COUNTSKETCH = 0, SLSO_SRHT = 1, SLSO_GAUSSIAN = 2, SLSO_OSNA
 /* Sampling policies of Algorithm 4 step 4 (Sec. 5.2) on P = scores / sum(scores). */
 typedef enum { SLSO_POLICY_DEC = 0, SLSO_POLICY_SWR = 1, SLSO_POLICY_SWOR = 2 } slso_policy;
 
+/* The factor R of SX (Algorithm 2/3 step 2).  With R_jj > 0 and SX of full column rank R is unique,
+ * so both give the same R up to rounding.
+ *  HOUSEHOLDER  unpivoted Householder QR of SX, float64 (orthogonality error ~ kappa(SX) u).
+ *  AUTO         for compute != F64: the Gram route first, R = chol(SX^T SX) (float64 SYRK and
+ *               blocked Cholesky, half the FMAs of Householder), kept only when a check with 4
+ *               seeded Gaussian probes z (Philox at counter (lo c, hi c, q, 8)) estimates
+ *               ||R^-T SX^T SX R^-1 - I||_F <= 1e-8 (its error grows like kappa(SX)^2 u; the
+ *               relative error of every score is at most that norm); otherwise, and always for
+ *               compute = F64, Householder.  Decided on the device; slso_info reports it. */
+typedef enum { SLSO_FACTOR_AUTO = 0, SLSO_FACTOR_HOUSEHOLDER = 1 } slso_factor;
+
 typedef struct slso_handle slso_handle;
 
 typedef struct {
@@ -82,6 +93,7 @@ typedef struct {
                           max(s, d) 2^-52 (float64 numerical rank)                            */
   double correct_frac; /* BF16/FP8 only: rescore the top ceil(frac n) rows in float32; 0 = off */
   int32_t nnz;         /* OSNAP: nonzeros per column of S (1..64, s divisible by it); 0 = 4     */
+  int32_t factor;      /* how R of SX is formed: SLSO_FACTOR_AUTO or SLSO_FACTOR_HOUSEHOLDER    */
 } slso_params;
 
 typedef struct {
@@ -94,6 +106,9 @@ typedef struct {
   int32_t svd_route;     /* 1: R^+ from the SVD of R; 0: rank d certified, R^+ = R^-1          */
   int32_t svd_sweeps;    /* float64 one-sided Jacobi sweeps of the SVD of R (after the float32
                             preconditioning sweeps when d >= 64); 0 when it did not run          */
+  int32_t gram_route;    /* 1: R from the Gram route; 0: Householder QR                          */
+  double gram_resid;     /* the Gram route's probe estimate of ||R^-T SX^T SX R^-1 - I||_F; NaN
+                            when its Cholesky broke down or the route was not tried              */
 } slso_info;
 
 /* Library / handle ------------------------------------------------------------------ */
@@ -303,11 +318,13 @@ slso_status slso_selftest_wait(slso_handle* handle, int32_t what, int64_t limit_
 /* Instrumentation (no counterpart in the paper).  slso_profile(h, 1) resets and starts
  * recording a CUDA event pair around every stage each call enqueues on its stream:
  * 0 sketch, 1 Householder QR, 2 rest of the small solve (certificate, R^-1 or SVD, M),
- * 3 scores (X.M + row norms), 4 ordering, 5 host<->device copies.  slso_profile_read
- * waits for the recorded events and returns per-stage milliseconds and call counts
- * (arrays of SLSO_STAGES) and the number of kernels this library launched (in this process)
- * since slso_profile was called.  Recording stops after 4096 stages. */
-#define SLSO_STAGES 6
+ * 3 scores (X.M + row norms), 4 ordering, 5 host<->device copies, 6 the Gram route's SYRK
+ * (G = SX^T SX), 7 the rest of the Gram route (Cholesky, R^-1, probe check).  A stage may be
+ * recorded more than once per call (calls counts records, not calls of the API).
+ * slso_profile_read waits for the recorded events and returns per-stage milliseconds and record
+ * counts (arrays of SLSO_STAGES) and the number of kernels this library launched (in this
+ * process) since slso_profile was called.  Recording stops after 4096 stages. */
+#define SLSO_STAGES 8
 slso_status slso_profile(slso_handle* handle, int enable);
 slso_status slso_profile_read(slso_handle* handle, double* stage_ms, int64_t* stage_calls,
                               int64_t* launches);

@@ -29,7 +29,7 @@ EXPORTS = (
     "slso_server_counters",
 )
 JOB_LEVERAGE, JOB_SKETCHED_SVD = 0, 1
-STAGES = ("sketch", "qr", "solve", "scores", "order", "copy")
+STAGES = ("sketch", "qr", "solve", "scores", "order", "copy", "syrk", "chol")
 
 
 class Params(ctypes.Structure):
@@ -37,6 +37,7 @@ class Params(ctypes.Structure):
         ("kind", ctypes.c_int32), ("compute", ctypes.c_int32), ("s", ctypes.c_int64),
         ("k", ctypes.c_int64), ("seed_S", ctypes.c_uint64), ("seed_Pi", ctypes.c_uint64),
         ("tau", ctypes.c_double), ("correct_frac", ctypes.c_double), ("nnz", ctypes.c_int32),
+        ("factor", ctypes.c_int32),
     ]
 
 
@@ -44,7 +45,8 @@ class Info(ctypes.Structure):
     _fields_ = [
         ("rank", ctypes.c_int64), ("sigma_max", ctypes.c_double), ("sigma_min_kept", ctypes.c_double),
         ("score_sum", ctypes.c_double), ("tau", ctypes.c_double), ("nonfinite", ctypes.c_int32),
-        ("svd_route", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32),
+        ("svd_route", ctypes.c_int32), ("svd_sweeps", ctypes.c_int32), ("gram_route", ctypes.c_int32),
+        ("gram_resid", ctypes.c_double),
     ]
 
     def as_dict(self):

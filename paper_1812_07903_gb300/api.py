@@ -100,8 +100,13 @@ def sketched_svd(SX, tau=-1.0, want_r=True, handle=None):
     return sigma, V, R, info.as_dict()
 
 
+FACTOR = {"auto": 0, "householder": 1}
+
+
 def make_params(kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
-                correct_frac=0.0, nnz=0):
+                correct_frac=0.0, nnz=0, factor="auto"):
+    """factor: how R of SX is formed; 'auto' tries the probe-checked Gram route (R = chol(SX^T SX))
+    when compute != 'f64', 'householder' always takes Householder QR."""
     p = L.Params()
     p.kind = L.KIND[kind]
     p.compute = L.DTYPE[compute]
@@ -112,16 +117,17 @@ def make_params(kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, 
     p.tau = float(tau)
     p.correct_frac = float(correct_frac)
     p.nnz = int(nnz)
+    p.factor = FACTOR[factor]
     return p
 
 
 def leverage(X, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
-             correct_frac=0.0, out=None, want_info=True, handle=None, nnz=0):
+             correct_frac=0.0, out=None, want_info=True, handle=None, nnz=0, factor="auto"):
     """slso_leverage: approximate leverage scores (float64 for compute='f64', else float32).
-    nnz: OSNAP nonzeros per column of S (0: the default 4)."""
+    nnz: OSNAP nonzeros per column of S (0: the default 4); factor: see make_params."""
     h = handle or default_handle()
     n, d, ldx, xdt = _x_args(X)
-    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac, nnz)
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, correct_frac, nnz, factor)
     sdt = torch.float64 if compute == "f64" else torch.float32
     scores = out if out is not None else torch.empty(n, dtype=sdt, device=X.device)
     info = L.Info()
@@ -194,14 +200,14 @@ def rank_rows_host(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0,
 
 
 def rank_rows_streamed(X_host, kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, compute="f32",
-                       block_rows=0, scores_out=None, order_out=None, handle=None, nnz=0):
+                       block_rows=0, scores_out=None, order_out=None, handle=None, nnz=0, factor="auto"):
     """slso_rank_rows_streamed: scores and order of a HOST matrix streamed through the device in
     blocks of rows (out-of-core X: device memory independent of n x d)."""
     h = handle or default_handle()
     if X_host.is_cuda or X_host.dim() != 2 or X_host.dtype not in _XDT or X_host.stride(1) != 1:
         raise TypeError("X_host must be a 2-D row-contiguous host tensor (float64/float32/bfloat16)")
     n, d = X_host.shape
-    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, 0.0, nnz)
+    p = make_params(kind, s, k, seed_S, seed_Pi, tau, compute, 0.0, nnz, factor)
     sdt = torch.float64 if compute == "f64" else torch.float32
     sc = scores_out if scores_out is not None else torch.empty(n, dtype=sdt)
     od = order_out if order_out is not None else torch.empty(n, dtype=torch.int64)

@@ -66,8 +66,12 @@ slso_status check_params(const slso_params* p, int64_t n, int64_t d) {
     return fail(SLSO_ERR_INVALID_ARG, "correct_frac must be in [0, 1]");
   if (std::isnan(p->tau)) return fail(SLSO_ERR_INVALID_ARG, "tau is NaN");
   if (d > 8192) return fail(SLSO_ERR_SHAPE, "d=%lld exceeds 8192", (long long)d);
+  if (p->factor != SLSO_FACTOR_AUTO && p->factor != SLSO_FACTOR_HOUSEHOLDER)
+    return fail(SLSO_ERR_INVALID_ARG, "unknown factor %d", p->factor);
   return SLSO_OK;
 }
+
+bool use_gram(const slso_params* p) { return p->factor == SLSO_FACTOR_AUTO && p->compute != SLSO_F64; }
 
 }  // namespace slso
 
@@ -96,6 +100,8 @@ slso_status fill_info(Handle& h, cudaStream_t st, slso_info* info) {
   info->nonfinite = d.nonfinite;
   info->svd_route = d.need_svd;
   info->svd_sweeps = d.sweeps;
+  info->gram_route = d.gram_ok;
+  info->gram_resid = d.gram_tried ? d.gram_resid : std::nan("");
   if (d.timeout) return fail(SLSO_ERR_TIMEOUT, "a bounded device wait gave up (kernel %d)", d.timeout);
   if (d.nonfinite) return fail(SLSO_ERR_NONFINITE, "X holds NaN or Inf");
   return SLSO_OK;
@@ -113,7 +119,7 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, p->nnz, SX, st));
   prof_end(h, ar, st);
   SolveOut so;
-  SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st));
+  SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st, use_gram(p)));
   const int64_t kk = p->k > 0 ? p->k : d;
   prof_begin(h, ar, ST_SCORES, st);
   SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, so.M, kk, p->compute, scores, p->correct_frac, st));
@@ -420,7 +426,7 @@ extern "C" slso_status slso_rank_rows_streamed(slso_handle* handle, const void* 
     return SLSO_OK;
   };
   auto solve = [&](Arena& ar) {
-    return run_solve(*h, ar, SX, params->s, d, tau, params->k, params->seed_Pi, 0, &so, st);
+    return run_solve(*h, ar, SX, params->s, d, tau, params->k, params->seed_Pi, 0, &so, st, use_gram(params));
   };
   auto score_block = [&](Arena& ar, int64_t b) -> slso_status {
     prof_begin(*h, ar, ST_SCORES, st);

@@ -47,13 +47,15 @@ struct DevState {
   int32_t rank;          // numerical rank r
   int32_t rotations;     // Jacobi: rotations applied in the current sweep
   int32_t sweeps;        // Jacobi: sweeps run
-  int32_t pad0, pad1;
+  int32_t gram_ok;       // Gram route: 1 while its factor stands (the Householder kernels then return)
+  int32_t gram_tried;    // Gram route attempted
   double sigma_max;      // sigma_1 (SVD route)
   double sigma_min_kept; // sigma_r (SVD route)
   double score_sum;
   double tau;
   double fro_r;          // ||R||_F
   double fro_rinv;       // ||R^-1||_F
+  double gram_resid;     // Gram route: probe estimate of ||R^-T SX^T SX R^-1 - I||_F (NaN: breakdown)
 };
 
 // ------------------------------------------------------------------ scratch arena
@@ -82,7 +84,10 @@ class Arena {
 
 // Stage timing for slso_profile / slso_profile_read: event pairs recorded on the caller's
 // stream around each stage, summed when read.
-enum Stage { ST_SKETCH = 0, ST_QR = 1, ST_SOLVE = 2, ST_SCORES = 3, ST_ORDER = 4, ST_COPY = 5, ST_COUNT = 6 };
+enum Stage {
+  ST_SKETCH = 0, ST_QR = 1, ST_SOLVE = 2, ST_SCORES = 3, ST_ORDER = 4, ST_COPY = 5, ST_SYRK = 6, ST_CHOL = 7,
+  ST_COUNT = 8
+};
 
 struct ProfRecord {
   int stage;
@@ -155,7 +160,8 @@ enum : uint32_t {
   TAG_SRHT_SAMPLE = 3,
   TAG_GAUSSIAN = 4,
   TAG_JL = 5,
-  TAG_OSNAP = 7
+  TAG_OSNAP = 7,
+  TAG_PROBE = 8
 };
 
 // ------------------------------------------------------------------ Box-Muller
@@ -407,13 +413,45 @@ struct SolveOut {
   int64_t kk = 0;
 };
 // mode 0: leverage (certified inverse or SVD); mode 1: sketched SVD only (always SVD).
+// gram (mode 0 only): try the Gram route for R first (gram.cu), Householder when it fails.
 slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t d, double tau,
-                      int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st);
+                      int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st,
+                      bool gram = false);
+
+// gram.cu: R of SX from the Cholesky factor of G = SX^T SX, with a probe check.
+// gram_take takes the buffers (call before the arena's measuring return); run_gram_factor writes
+// L = R^T (d x d row-major lower triangle, i.e. R column-major) into L and sets state->gram_ok;
+// run_gram_check (after R^-1, column-major, is in Rinv) clears gram_ok when the probe estimate
+// of ||R^-T SX^T SX R^-1 - I||_F exceeds kGramTol.
+constexpr double kGramTol = 1e-8;
+struct GramWork {
+  double* part = nullptr;   // split-K partial tiles of the Gram matrix
+  double* Z = nullptr;      // d x P probes
+  double* Y = nullptr;      // d x P
+  double* W = nullptr;      // s x P
+  double* vpart = nullptr;  // row-chunk partials of SX^T W
+  double* V = nullptr;      // d x P
+  double* eres = nullptr;   // d per-row squared residuals
+  double* ldiag = nullptr;  // the factored 32 x 32 diagonal blocks of the Cholesky factor
+  unsigned long long* colmax = nullptr;  // per column max |SX| (float64 bits)
+  int* cexp = nullptr;      // per column scale exponent e_j
+  double* cscale = nullptr; // 2^-e_j
+  float* xh = nullptr;      // SX 2^-e_j split into float32 parts xh + xl (s x d row-major)
+  float* xl = nullptr;
+  int splits = 1, tiles = 0, vchunks = 1;
+  int64_t kc = 0;
+};
+GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d);
+slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
+                            int64_t d, double* L, cudaStream_t st);
+slso_status run_gram_check(Handle& h, const GramWork& g, const double* SX, int64_t s, int64_t d,
+                           const double* Rinv, cudaStream_t st);
 
 // api.cu: argument checks and the leverage plan shared with the server
 double default_tau(int64_t s, int64_t d);
 slso_status check_x(const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt);
 slso_status check_params(const slso_params* p, int64_t n, int64_t d);
+bool use_gram(const slso_params* p);  // the Gram route is tried for this leverage call
 slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
 

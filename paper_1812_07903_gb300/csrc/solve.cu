@@ -56,8 +56,10 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void transpose_kernel(const double* __restrict__ in, int64_t rows, int64_t cols,
-                                 double* __restrict__ out, int64_t ldo) {
-  // in: rows x cols row-major; out: cols x rows with row stride ldo (= in column-major)
+                                 double* __restrict__ out, int64_t ldo, const int32_t* skip) {
+  // in: rows x cols row-major; out: cols x rows with row stride ldo (= in column-major).
+  // Returns at once when skip is set (the Gram route's factor stands).
+  if (skip && *skip) return;
   __shared__ double tile[32][33];
   const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32, c0 = static_cast<int64_t>(blockIdx.x) * 32;
   for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) qr_kernel(double* __restrict__ 
                                                            int* __restrict__ ready,
                                                            double* __restrict__ taus,
                                                            DevState* __restrict__ state) {
+  if (state->gram_ok) return;  // the Gram route's factor stands
   extern __shared__ double vs[];
   __shared__ double red[33];
   __shared__ int s_abort;
@@ -275,6 +278,7 @@ __global__ void __launch_bounds__(NT, 256 / NT) qr_left_kernel(double* __restric
                                                                  double* __restrict__ coef,
                                                                  DevState* __restrict__ state) {
   static_assert(RPT % 2 == 0, "rows are held in pairs");
+  if (state->gram_ok) return;  // the Gram route's factor stands
   constexpr int P = RPT / 2;                    // row pairs per thread
   constexpr int QA = P / 2;                     // pairs in staging half A
   constexpr int HA = 2 * NT * QA;      // rows in staging half A
@@ -488,6 +492,18 @@ __global__ void r_extract_kernel(const double* __restrict__ A, int64_t lda, int6
   }
 }
 
+// The upper triangle of R from the right-looking kernel's storage A into Rc (column-major, leading
+// dimension d), where the Gram route leaves its factor; only when *guard == 0 (Householder ran).
+__global__ void r_to_rc_kernel(const double* __restrict__ A, int64_t lda, int64_t d, double* __restrict__ Rc,
+                               const int32_t* guard) {
+  if (*guard) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < d * d;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t l = e / d, i = e % d;
+    if (i <= l) Rc[l * d + i] = A[l * lda + i];
+  }
+}
+
 // Sum of squares in two fixed-order stages: block b of kSumBlocks sums a contiguous chunk into
 // part[b]; the consumer (certify_kernel) adds the kSumBlocks partials in order.
 constexpr int kSumBlocks = 64;
@@ -505,9 +521,13 @@ __global__ void sumsq_partial_kernel(const double* __restrict__ x, int64_t n, do
 // Column c of R^-1 (column-major, d x d): back substitution R x = e_c in 32-row blocks from the
 // bottom.  One warp solves each 32 x 32 diagonal block with shuffles; then all threads subtract
 // that block's contribution from the rows above (a GEMV over column-major R).  R_ik is
-// sgn_i * A[k*lda + i].
+// sgn_i * A[k*lda + i] (sgn NULL: all +1); invd[k] = 1 / R_kk (inv_diag_kernel), so that the
+// chain of the diagonal solve holds a multiply where a float64 division would cost ten times as
+// many instructions.  Runs only when guard == nullptr or *guard == want.
 __global__ void __launch_bounds__(256) trinv_kernel(const double* __restrict__ A, int64_t lda, int64_t d,
-                                                    const double* __restrict__ sgn, double* __restrict__ Rinv) {
+                                                    const double* __restrict__ sgn, const double* __restrict__ invd,
+                                                    double* __restrict__ Rinv, const int32_t* guard, int want) {
+  if (guard && *guard != want) return;
   extern __shared__ double b[];
   const int c = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -518,11 +538,10 @@ __global__ void __launch_bounds__(256) trinv_kernel(const double* __restrict__ A
     if (warp == 0) {
       const int row = lo + lane;
       double y = (row <= hi) ? b[row] : 0.0;
-      const double sr = (row <= hi) ? sgn[row] : 0.0;
+      const double sr = (row <= hi) ? (sgn ? sgn[row] : 1.0) : 0.0;
       for (int k = hi; k >= lo; --k) {
         const int o = k - lo;
-        const double rkk = sgn[k] * A[static_cast<int64_t>(k) * lda + k];
-        const double xk = __shfl_sync(0xFFFFFFFFu, y, o) / rkk;
+        const double xk = __shfl_sync(0xFFFFFFFFu, y, o) * invd[k];
         if (lane == o) y = xk;
         else if (lane < o) y -= sr * A[static_cast<int64_t>(k) * lda + row] * xk;
       }
@@ -531,13 +550,21 @@ __global__ void __launch_bounds__(256) trinv_kernel(const double* __restrict__ A
     __syncthreads();
     for (int i = threadIdx.x; i < lo; i += blockDim.x) {
       double acc = b[i];
-      const double si = sgn[i];
+      const double si = sgn ? sgn[i] : 1.0;
       for (int k = lo; k <= hi; ++k) acc -= si * A[static_cast<int64_t>(k) * lda + i] * b[k];
       b[i] = acc;
     }
     __syncthreads();
   }
   for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Rinv[static_cast<int64_t>(c) * d + i] = (i <= c) ? b[i] : 0.0;
+}
+
+// invd[k] = 1 / (sgn_k A[k*lda + k]) (sgn NULL: +1); only when guard == nullptr or *guard == want.
+__global__ void inv_diag_kernel(const double* __restrict__ A, int64_t lda, int64_t d, const double* __restrict__ sgn,
+                                double* __restrict__ invd, const int32_t* guard, int want) {
+  if (guard && *guard != want) return;
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k < d) invd[k] = 1.0 / ((sgn ? sgn[k] : 1.0) * A[k * lda + k]);
 }
 
 __global__ void certify_kernel(DevState* __restrict__ st, const double* __restrict__ fro2,
@@ -1259,7 +1286,8 @@ slso_status launch_gemm(int64_t m, int64_t n, int64_t K, const double* A, int64_
 }  // namespace
 
 slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t d, double tau,
-                      int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st) {
+                      int64_t k, uint64_t seed_pi, int mode, SolveOut* out, cudaStream_t st, bool gram) {
+  gram = gram && mode == 0;
   const int64_t dp = d + (d & 1);
   const int64_t kk = (k > 0) ? k : d;
   const int64_t lda = s + (s & 1);  // even: 16-byte aligned columns for the bulk copies
@@ -1269,6 +1297,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* Rc = ar.take<double>(static_cast<size_t>(d) * d);  // qr_left_kernel: R column-major
   double* R = ar.take<double>(static_cast<size_t>(d) * d);
   double* sgn = ar.take<double>(d);
+  double* invd = ar.take<double>(d);  // 1 / R_kk for trinv_kernel
   double* fro2 = ar.take<double>(2 * kSumBlocks);
   double* Rinv = (mode == 0) ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* Pi = (k > 0) ? ar.take<double>(static_cast<size_t>(d) * k) : nullptr;
@@ -1292,13 +1321,32 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* E2 = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* Qm = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* W0m = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
+  const GramWork gw = gram ? gram_take(h, ar, s, d) : GramWork{};
   if (ar.measure()) return SLSO_OK;
+
+  // ---- Gram route (leverage only): R = chol(SX^T SX) into Rc, R^-1, probe check.  gram_ok
+  // stays 1 when it stands; the Householder kernels below then return at once.
+  int32_t* gram_ok = &h.state->gram_ok;
+  // trinv_kernel keeps one column of R^-1 in shared memory: d doubles, above 48 KB for d > 6144
+  SLSO_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(trinv_kernel),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sizeof(double) * d)));
+  if (gram) {
+    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, st));
+    prof_begin(h, ar, ST_CHOL, st);
+    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, nullptr, invd, gram_ok, 1);
+    SLSO_CHECK_LAUNCH();
+    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rc, d, d, nullptr, invd, Rinv, gram_ok, 1);
+    SLSO_CHECK_LAUNCH();
+    SLSO_TRY(run_gram_check(h, gw, SX, s, d, Rinv, st));
+    prof_end(h, ar, st);
+  }
 
   // ---- QR
   prof_begin(h, ar, ST_SOLVE, st);
   {
     dim3 g(static_cast<unsigned>(ceil_div(d, 32)), static_cast<unsigned>(ceil_div(s, 32)));
-    transpose_kernel<<<g, dim3(32, 8), 0, st>>>(SX, s, d, A, lda);
+    transpose_kernel<<<g, dim3(32, 8), 0, st>>>(SX, s, d, A, lda, gram ? gram_ok : nullptr);
     SLSO_CHECK_LAUNCH();
   }
   SLSO_CHECK_CUDA(cudaMemsetAsync(ready, 0, sizeof(int) * d, st));
@@ -1373,10 +1421,15 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
     prof_end(h, ar, st);
     prof_begin(h, ar, ST_SOLVE, st);
   }
-  // the upper triangle of R: Rc (leading dimension d) from the left-looking kernel, else in A
+  // the upper triangle of R: Rc (leading dimension d) from the left-looking kernel or the Gram
+  // route, else in A
   const bool left = s <= kQrlMaxS;
-  const double* Rsrc = left ? Rc : A;
-  const int64_t ldr = left ? d : lda;
+  if (gram && !left) {
+    r_to_rc_kernel<<<grid1d(d * d, h), 256, 0, st>>>(A, lda, d, Rc, gram_ok);
+    SLSO_CHECK_LAUNCH();
+  }
+  const double* Rsrc = (left || gram) ? Rc : A;
+  const int64_t ldr = (left || gram) ? d : lda;
   r_extract_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Rsrc, ldr, d, R, sgn);
   SLSO_CHECK_LAUNCH();
   sumsq_partial_kernel<<<kSumBlocks, 256, 0, st>>>(R, d * d, fro2);
@@ -1384,7 +1437,12 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
 
   // ---- certified route: R^-1
   if (mode == 0) {
-    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rsrc, ldr, d, sgn, Rinv);
+    // on the Gram route R^-1 is already in Rinv (computed for the probe check)
+    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rsrc, ldr, d, sgn, invd,
+                                                                             gram ? gram_ok : nullptr, 0);
+    SLSO_CHECK_LAUNCH();
+    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rsrc, ldr, d, sgn, invd, Rinv,
+                                                                            gram ? gram_ok : nullptr, 0);
     SLSO_CHECK_LAUNCH();
     sumsq_partial_kernel<<<kSumBlocks, 256, 0, st>>>(Rinv, d * d, fro2 + kSumBlocks);
     SLSO_CHECK_LAUNCH();
