@@ -34,11 +34,14 @@ METRIC = "scored rows/s (BF16 vs FP32, ≤2% median rel err) + roofline %; p99 j
 WORKLOAD = dict(n=1_000_000, d=1024, s=16384, k=128, kind="countsketch", xseed=1003, seed_S=2003, seed_Pi=3003)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070 / 1e3  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3
+# float-float multiply-add (TwoProd by FMA with the split operand's cross terms, TwoSum): 12 float32
+# instructions, so the float32 pipe's issue rate bounds the Gram SYRK at this many TFLOP/s
+FF_SYRK_PEAK_TFLOPS = 152 * 128 * 2.070 / 12 * 2 / 1e3
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the named kernel at
 # s = 16384, d = 1024 from one ncu capture of its current source; None whenever the kernel changed
 # since, until it is captured again.
 QR_TRAFFIC_BYTES = None  # qr_left_kernel<64, 256>
-SYRK_TRAFFIC_BYTES = None  # gram_syrk_kernel
+SYRK_TRAFFIC_BYTES = 158_031_616 + 8_353_792  # gram_syrk_kernel
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point
@@ -56,7 +59,8 @@ def _config(n, d, s, k, kind):
     return {
         "workload": f"snr_student_t {n}x{d} float32 (rank-200 + SNR 10 noise, t(3) rows), "
                     f"{kind} s={s}, JL k={k}; leverage + dec order",
-        "n": n, "d": d, "s": s, "k": k, "sketch": kind, "solve": "fp64 Householder QR, certified R^-1",
+        "n": n, "d": d, "s": s, "k": k, "sketch": kind, "solve": "R = chol(SX^T SX) (float-float SYRK, fp64 Cholesky) kept by a 4-probe "
+                 "orthogonality check (else fp64 Householder QR); certified R^-1",
         "l2": "inputs larger than L2 (X is 4.1 GB > 129 MB); no flush",
     }
 
@@ -440,13 +444,16 @@ def main():
     # ---- roofline of the dominant stage's kernel
     per = {name: ms_ / args.steps for name, (ms_, c) in stages32.items() if c}
     dom = max(per, key=per.get)
-    if dom == "syrk":
-        flops = float(s) * d * (d + 1)  # 2 flops per FMA, s d (d + 1) / 2 FMAs (lower triangle of G)
+    if "syrk" in per and per["syrk"] >= per.get("qr", 0.0):
+        # the Gram route's SYRK (float-float on the float32 pipe): s d (d + 1) / 2 multiply-adds of
+        # float64-class accuracy, 2 flops each, against 12 float32 instructions per multiply-add
+        flops = float(s) * d * (d + 1)
         ach = flops / (per["syrk"] / 1e3) / 1e12
-        roof = {"kernel": "gram_syrk_kernel (FP64 SYRK G = SX^T SX)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+        roof = {"kernel": "gram_syrk_kernel (float-float SYRK G = SX^T SX)", "bound": "alu", "achieved": ach,
+                "peak": FF_SYRK_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FF_SYRK_PEAK_TFLOPS,
                 "traffic": SYRK_TRAFFIC_BYTES if (s, d) == (16384, 1024) else None,
-                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.198)"}
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2.07 GHz / 12 instructions per float-float "
+                               "multiply-add x 2 flops"}
     elif dom == "qr":
         flops = 2.0 * s * d * d - 2.0 * d ** 3 / 3.0
         ach = flops / (per["qr"] / 1e3) / 1e12
