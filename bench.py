@@ -41,7 +41,7 @@ FF_SYRK_PEAK_TFLOPS = 152 * 128 * 2.070 / 12 * 2 / 1e3
 # s = 16384, d = 1024 from one ncu capture of its current source; None whenever the kernel changed
 # since, until it is captured again.
 QR_TRAFFIC_BYTES = None  # qr_left_kernel<64, 256>
-SYRK_TRAFFIC_BYTES = 158_031_616 + 8_353_792  # gram_syrk_kernel
+SYRK_TRAFFIC_BYTES = 177_818_112 + 8_952_320  # gram_syrk_kernel<true>
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point

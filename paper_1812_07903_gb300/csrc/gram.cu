@@ -122,20 +122,38 @@ __device__ __forceinline__ void ff_fold(float& S, float& C, float& St, float& Ct
   C = 0.0f;
 }
 
+// 4-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0), and its group fences.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+// 16-byte form (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // part[(q T + t) 1024 + a 32 + b] = sum over rows r of split q of x[r, 32 I + a] x[r, 32 J + b] for
 // the scaled columns x = xh + xl, in float-float; float64 out.  128 threads, each a 2 x 4 block of
-// the tile (rows 2 ty.., columns tx + 8 c).  The float32 pipe's instruction issue bounds it: a
-// 4 x 4 block per thread (a quarter of the shared loads) measured slower, 4.96 ms against 4.73 ms
-// at s = 16384, d = 1024.  Work item blockIdx.x = q T + t, so that the items running together read
-// the same rows.
+// the tile (rows 2 ty.., columns tx + 8 c).  The next 16 rows are copied into the second half of a
+// double buffer (cp.async) while these 16 rows are summed; 16 KB of shared memory and at most 64
+// registers keep 8 CTAs per SM, so the 1056 items of the d = 1024 sketch run in one wave.  The float32 pipe's instruction
+// issue bounds the kernel: a 4 x 4 block per thread (a quarter of the shared loads) measured slower,
+// 4.96 ms against 4.73 ms at s = 16384, d = 1024.  Work item blockIdx.x = q T + t, so that the items
+// running together read the same rows.
 constexpr int kSyrkThreads = 128;
-__global__ void __launch_bounds__(kSyrkThreads) gram_syrk_kernel(const float* __restrict__ xh,
+constexpr int kSyrkRows = 16;  // rows per copy stage; the float-float pair is folded every 2 stages
+// V16: d % 4 == 0, so every 4-float chunk of a row starts 16-byte aligned and lies wholly inside or
+// outside the matrix; the stage then copies 16 bytes per instruction.
+template <bool V16>
+__global__ void __launch_bounds__(kSyrkThreads, 8) gram_syrk_kernel(const float* __restrict__ xh,
                                                                  const float* __restrict__ xl, int64_t s, int d,
                                                                  int T, int64_t kc, double* __restrict__ part) {
-  __shared__ __align__(16) float sah[kGt][kGt];
-  __shared__ __align__(16) float sal[kGt][kGt];
-  __shared__ __align__(16) float sbh[kGt][kGt];
-  __shared__ __align__(16) float sbl[kGt][kGt];
+  __shared__ __align__(16) float sm[2][4][kSyrkRows][kGt];  // [buffer][ah, al, bh, bl][row][column]
   const int q = blockIdx.x / T, t = blockIdx.x % T;
   int I, J;
   tri_index(t, I, J);
@@ -143,25 +161,51 @@ __global__ void __launch_bounds__(kSyrkThreads) gram_syrk_kernel(const float* __
   const int64_t r1 = r0 + kc < s ? r0 + kc : s;
   const int ci = I * kGt, cj = J * kGt;
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  auto stage = [&](int buf, int64_t rb) {
+    if constexpr (V16) {
+      for (int e = tid; e < kSyrkRows * (kGt / 4); e += kSyrkThreads) {
+        const int rr = e >> 3, c = (e & 7) * 4;
+        const int64_t r = rb + rr;
+        const bool ok = r < r1;
+        const bool oi = ok && ci + c < d, oj = ok && cj + c < d;
+        cp_async16(&sm[buf][0][rr][c], oi ? xh + r * d + ci + c : xh, oi ? 16 : 0);
+        cp_async16(&sm[buf][1][rr][c], oi ? xl + r * d + ci + c : xl, oi ? 16 : 0);
+        cp_async16(&sm[buf][2][rr][c], oj ? xh + r * d + cj + c : xh, oj ? 16 : 0);
+        cp_async16(&sm[buf][3][rr][c], oj ? xl + r * d + cj + c : xl, oj ? 16 : 0);
+      }
+    } else {
+      for (int e = tid; e < kSyrkRows * kGt; e += kSyrkThreads) {
+        const int rr = e >> 5, c = e & 31;
+        const int64_t r = rb + rr;
+        const bool ok = r < r1;
+        const bool oi = ok && ci + c < d, oj = ok && cj + c < d;
+        // out of range: zero-filled, the (unread) source pointed at the array's start
+        cp_async4(&sm[buf][0][rr][c], oi ? xh + r * d + ci + c : xh, oi ? 4 : 0);
+        cp_async4(&sm[buf][1][rr][c], oi ? xl + r * d + ci + c : xl, oi ? 4 : 0);
+        cp_async4(&sm[buf][2][rr][c], oj ? xh + r * d + cj + c : xh, oj ? 4 : 0);
+        cp_async4(&sm[buf][3][rr][c], oj ? xl + r * d + cj + c : xl, oj ? 4 : 0);
+      }
+    }
+    cp_async_commit();
+  };
   float S[2][4], C[2][4], St[2][4], Ct[2][4];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) S[a][c] = C[a][c] = St[a][c] = Ct[a][c] = 0.0f;
-  for (int64_t rb = r0; rb < r1; rb += kGt) {
-    for (int e = tid; e < kGt * kGt; e += kSyrkThreads) {
-      const int rr = e >> 5, c = e & 31;
-      const int64_t r = rb + rr;
-      const bool ok = r < r1;
-      const bool oi = ok && ci + c < d, oj = ok && cj + c < d;
-      sah[rr][c] = oi ? xh[r * d + ci + c] : 0.0f;
-      sal[rr][c] = oi ? xl[r * d + ci + c] : 0.0f;
-      sbh[rr][c] = oj ? xh[r * d + cj + c] : 0.0f;
-      sbl[rr][c] = oj ? xl[r * d + cj + c] : 0.0f;
-    }
+  if (r0 < r1) stage(0, r0);
+  int cur = 0;
+  for (int64_t rb = r0; rb < r1; rb += kSyrkRows, cur ^= 1) {
+    if (rb + kSyrkRows < r1) stage(cur ^ 1, rb + kSyrkRows);
+    else cp_async_commit();  // an empty group keeps "all but the newest group done" meaning this block
+    cp_async_wait_one();
     __syncthreads();
+    float(*sah)[kGt] = sm[cur][0];
+    float(*sal)[kGt] = sm[cur][1];
+    float(*sbh)[kGt] = sm[cur][2];
+    float(*sbl)[kGt] = sm[cur][3];
 #pragma unroll 4
-    for (int kk = 0; kk < kGt; ++kk) {
+    for (int kk = 0; kk < kSyrkRows; ++kk) {
       const float2 ah = *reinterpret_cast<const float2*>(&sah[kk][2 * ty]);
       const float2 al = *reinterpret_cast<const float2*>(&sal[kk][2 * ty]);
 #pragma unroll
@@ -171,11 +215,13 @@ __global__ void __launch_bounds__(kSyrkThreads) gram_syrk_kernel(const float* __
         ff_term(ah.y, al.y, bh, bl, S[1][c], C[1][c]);
       }
     }
+    if (((rb - r0) / kSyrkRows) % 2 == 1 || rb + kSyrkRows >= r1) {  // every 32 rows, and at the end
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) ff_fold(S[a][c], C[a][c], St[a][c], Ct[a][c]);
-    __syncthreads();
+        for (int c = 0; c < 4; ++c) ff_fold(S[a][c], C[a][c], St[a][c], Ct[a][c]);
+    }
+    __syncthreads();  // every warp is done with this buffer before the copy into it is issued
   }
   double* out = part + (static_cast<int64_t>(q) * T + t) * (kGt * kGt);
 #pragma unroll
@@ -538,8 +584,12 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
   SLSO_CHECK_LAUNCH();
   prof_end(h, ar, st);
   prof_begin(h, ar, ST_SYRK, st);
-  gram_syrk_kernel<<<static_cast<unsigned>(g.tiles) * g.splits, kSyrkThreads, 0, st>>>(g.xh, g.xl, s, d_i, g.tiles,
-                                                                                      g.kc, g.part);
+  if (d % 4 == 0)
+    gram_syrk_kernel<true><<<static_cast<unsigned>(g.tiles) * g.splits, kSyrkThreads, 0, st>>>(g.xh, g.xl, s, d_i,
+                                                                                              g.tiles, g.kc, g.part);
+  else
+    gram_syrk_kernel<false><<<static_cast<unsigned>(g.tiles) * g.splits, kSyrkThreads, 0, st>>>(g.xh, g.xl, s, d_i,
+                                                                                               g.tiles, g.kc, g.part);
   SLSO_CHECK_LAUNCH();
   prof_end(h, ar, st);
   prof_begin(h, ar, ST_CHOL, st);

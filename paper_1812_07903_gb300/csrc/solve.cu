@@ -518,12 +518,14 @@ __global__ void sumsq_partial_kernel(const double* __restrict__ x, int64_t n, do
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// Column c of R^-1 (column-major, d x d): back substitution R x = e_c in 32-row blocks from the
-// bottom.  One warp solves each 32 x 32 diagonal block with shuffles; then all threads subtract
-// that block's contribution from the rows above (a GEMV over column-major R).  R_ik is
-// sgn_i * A[k*lda + i] (sgn NULL: all +1); invd[k] = 1 / R_kk (inv_diag_kernel), so that the
-// chain of the diagonal solve holds a multiply where a float64 division would cost ten times as
-// many instructions.  Runs only when guard == nullptr or *guard == want.
+// Column c of R^-1 (column-major, d x d).  The storage holds R = diag(sgn) Rs with Rs_ik =
+// A[k*lda + i] (sgn NULL: all +1), so R^-1 = Rs^-1 diag(sgn) and column c is sgn_c times the
+// solution of Rs x = e_c: the back substitution carries no signs, and every inner step is one
+// float64 FMA.  It runs in 32-row blocks from the bottom.  One warp solves each 32 x 32 diagonal
+// block with shuffles; then all threads subtract that block's contribution from the rows above (a
+// GEMV over column-major Rs).  invd[k] = 1 / Rs_kk (inv_diag_kernel), so that the chain of the
+// diagonal solve holds a multiply where a float64 division would cost ten times as many
+// instructions.  Runs only when guard == nullptr or *guard == want.
 __global__ void __launch_bounds__(256) trinv_kernel(const double* __restrict__ A, int64_t lda, int64_t d,
                                                     const double* __restrict__ sgn, const double* __restrict__ invd,
                                                     double* __restrict__ Rinv, const int32_t* guard, int want) {
@@ -538,33 +540,32 @@ __global__ void __launch_bounds__(256) trinv_kernel(const double* __restrict__ A
     if (warp == 0) {
       const int row = lo + lane;
       double y = (row <= hi) ? b[row] : 0.0;
-      const double sr = (row <= hi) ? (sgn ? sgn[row] : 1.0) : 0.0;
       for (int k = hi; k >= lo; --k) {
         const int o = k - lo;
         const double xk = __shfl_sync(0xFFFFFFFFu, y, o) * invd[k];
         if (lane == o) y = xk;
-        else if (lane < o) y -= sr * A[static_cast<int64_t>(k) * lda + row] * xk;
+        else if (lane < o) y = fma(-A[static_cast<int64_t>(k) * lda + row], xk, y);
       }
       if (row <= hi) b[row] = y;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < lo; i += blockDim.x) {
       double acc = b[i];
-      const double si = sgn ? sgn[i] : 1.0;
-      for (int k = lo; k <= hi; ++k) acc -= si * A[static_cast<int64_t>(k) * lda + i] * b[k];
+      for (int k = lo; k <= hi; ++k) acc = fma(-A[static_cast<int64_t>(k) * lda + i], b[k], acc);
       b[i] = acc;
     }
     __syncthreads();
   }
-  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Rinv[static_cast<int64_t>(c) * d + i] = (i <= c) ? b[i] : 0.0;
+  const double sc = sgn ? sgn[c] : 1.0;
+  for (int64_t i = threadIdx.x; i < d; i += blockDim.x) Rinv[static_cast<int64_t>(c) * d + i] = (i <= c) ? sc * b[i] : 0.0;
 }
 
-// invd[k] = 1 / (sgn_k A[k*lda + k]) (sgn NULL: +1); only when guard == nullptr or *guard == want.
-__global__ void inv_diag_kernel(const double* __restrict__ A, int64_t lda, int64_t d, const double* __restrict__ sgn,
-                                double* __restrict__ invd, const int32_t* guard, int want) {
+// invd[k] = 1 / A[k*lda + k] (the unsigned diagonal); only when guard == nullptr or *guard == want.
+__global__ void inv_diag_kernel(const double* __restrict__ A, int64_t lda, int64_t d, double* __restrict__ invd,
+                                const int32_t* guard, int want) {
   if (guard && *guard != want) return;
   const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (k < d) invd[k] = 1.0 / ((sgn ? sgn[k] : 1.0) * A[k * lda + k]);
+  if (k < d) invd[k] = 1.0 / A[k * lda + k];
 }
 
 __global__ void certify_kernel(DevState* __restrict__ st, const double* __restrict__ fro2,
@@ -1334,7 +1335,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   if (gram) {
     SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, st));
     prof_begin(h, ar, ST_CHOL, st);
-    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, nullptr, invd, gram_ok, 1);
+    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, invd, gram_ok, 1);
     SLSO_CHECK_LAUNCH();
     trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rc, d, d, nullptr, invd, Rinv, gram_ok, 1);
     SLSO_CHECK_LAUNCH();
@@ -1438,7 +1439,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   // ---- certified route: R^-1
   if (mode == 0) {
     // on the Gram route R^-1 is already in Rinv (computed for the probe check)
-    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rsrc, ldr, d, sgn, invd,
+    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rsrc, ldr, d, invd,
                                                                              gram ? gram_ok : nullptr, 0);
     SLSO_CHECK_LAUNCH();
     trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rsrc, ldr, d, sgn, invd, Rinv,
