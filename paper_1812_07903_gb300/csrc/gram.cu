@@ -258,8 +258,8 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int T, int S
 // memory; block 0 stores it in ldiag (not in L, where the other blocks are still reading G_kk),
 // block b > 0 solves row block I = k + b: L_Ik = G_Ik L_kk^-T.  A pivot that is not positive and
 // finite ends the route.  On this part's narrow float64 pipe the cost is the number of warp
-// instructions on the chain: one lane forms sqrt(pivot) and its reciprocal (the column is scaled
-// by a multiply), and the trailing update of step j walks only its (31 - j)(32 - j) / 2 live
+// instructions on the chain: one lane forms rsqrt(pivot), which gives both L_jj = pivot rsqrt and
+// its reciprocal (the column is scaled by a multiply), and the trailing update of step j walks only its (31 - j)(32 - j) / 2 live
 // entries, listed by decreasing column so that they are a prefix of one table.
 __global__ void __launch_bounds__(kGramThreads) chol_panel_kernel(double* __restrict__ L, int d, int k,
                                                                   double* __restrict__ ldiag,
@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(kGramThreads) chol_panel_kernel(double* __rest
       if (!(piv > 0.0) || !isfinite(piv)) {
         s_bad = 1;
       } else {
-        const double l = sqrt(piv);
-        D[j][j] = l;
-        rl[j] = 1.0 / l;
+        const double r = rsqrt(piv);  // one float64 chain for both: L_jj = piv r, 1 / L_jj = r
+        D[j][j] = piv * r;
+        rl[j] = r;
       }
     }
     __syncthreads();

@@ -104,6 +104,42 @@ def test_householder_r_against_lapack_and_gram():
     np.testing.assert_allclose(R.T @ R, A.T @ A, rtol=1e-11, atol=1e-11 * np.abs(A.T @ A).max())
 
 
+def test_cholesky_of_gram_is_the_householder_r_and_gives_the_same_m():
+    # With R_jj > 0 and full column rank, R is unique: the Cholesky factor of A^T A is the oracle's
+    # Householder R, so R^-1 Pi (JL included) is the oracle's SVD-route M.  The GPU's Gram route
+    # for R rests on this.
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((300, 40)) * np.exp(rng.standard_normal(40))
+    R = O.householder_r(A)
+    C = np.linalg.cholesky(A.T @ A).T
+    np.testing.assert_allclose(C, R, rtol=1e-9, atol=1e-12 * np.abs(R).max())
+    Pi = O.jl_matrix(40, 16, 5)
+    sv = O.sketched_svd(A)
+    M = O.m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], Pi)
+    M_chol = np.linalg.solve(C, Pi)
+    np.testing.assert_allclose(M_chol, M, rtol=1e-8, atol=1e-10 * np.abs(M).max())
+
+
+def test_rank_deficient_r_is_not_unique_and_only_jl_scores_notice():
+    # A repeated column: R_77 = 0 and a rotation of rows 7 and 8 gives another R with the same
+    # R^T R.  The k = 0 scores (x R^+) do not change; R^+ Pi does.
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((60, 10))
+    A[:, 7] = A[:, 2]
+    R1 = O.householder_r(A)
+    assert abs(R1[7, 7]) < 1e-12 * abs(R1).max()
+    R1[7, 7] = 0.0
+    G = np.eye(10)
+    c, s_ = np.cos(0.7), np.sin(0.7)
+    G[7, 7], G[7, 8], G[8, 7], G[8, 8] = c, s_, -s_, c
+    R2 = G @ R1
+    np.testing.assert_allclose(R2.T @ R2, R1.T @ R1, atol=1e-12 * np.abs(A.T @ A).max())
+    P1, P2 = np.linalg.pinv(R1, rcond=1e-10), np.linalg.pinv(R2, rcond=1e-10)
+    np.testing.assert_allclose(((A @ P1) ** 2).sum(1), ((A @ P2) ** 2).sum(1), rtol=1e-9)
+    Pi = O.jl_matrix(10, 6, 3)
+    assert np.max(np.abs((A @ P1 @ Pi) ** 2 - (A @ P2 @ Pi) ** 2).sum(1)) > 1e-3
+
+
 def test_householder_r_exact_integer_gram():
     A = np.array([[2, 1, 0], [1, 3, 1], [0, 1, 4], [1, 0, 1], [2, 2, 2]], dtype=float)
     R = O.householder_r(A)
