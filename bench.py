@@ -59,8 +59,7 @@ def _config(n, d, s, k, kind):
     return {
         "workload": f"snr_student_t {n}x{d} float32 (rank-200 + SNR 10 noise, t(3) rows), "
                     f"{kind} s={s}, JL k={k}; leverage + dec order",
-        "n": n, "d": d, "s": s, "k": k, "sketch": kind, "solve": "R = chol(SX^T SX) (float-float SYRK, fp64 Cholesky) kept by a 4-probe "
-                 "orthogonality check (else fp64 Householder QR); certified R^-1",
+        "n": n, "d": d, "s": s, "k": k, "sketch": kind,
         "l2": "inputs larger than L2 (X is 4.1 GB > 129 MB); no flush",
     }
 
@@ -488,6 +487,8 @@ def main():
         "fp8_corrected": {"value": job_rows_per_s(n, world, ms8c), "unit": "rows/s", "ms_per_step": ms8c,
                           "correct_frac": CORRECT_FRAC,
                           "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages8c.items() if c}},
+        "solve": "R = chol(SX^T SX) (float-float SYRK, fp64 Cholesky) kept by a 4-probe orthogonality check "
+                 "(else fp64 Householder QR); certified R^-1",
         "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"],
                       "gram_route": info["gram_route"], "gram_resid": info["gram_resid"]},
         "clocks": clk,

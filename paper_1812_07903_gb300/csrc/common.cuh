@@ -115,6 +115,16 @@ void prof_begin(Handle& h, const Arena& ar, int stage, cudaStream_t st);
 void prof_end(Handle& h, const Arena& ar, cudaStream_t st);
 
 slso_status ensure_pool(Handle& h, size_t bytes);
+
+// Raise fn's dynamic shared-memory limit on the current device to at least `bytes`, never lowering
+// it.  The limit belongs to the function, not to a launch: every call, host thread and captured
+// graph shares it, so setting it to one call's size would make a concurrent or later launch with
+// more shared memory fail.
+slso_status raise_smem_limit(const void* fn, size_t bytes);
+template <class F>
+slso_status raise_smem_limit(F* fn, size_t bytes) {
+  return raise_smem_limit(reinterpret_cast<const void*>(fn), bytes);
+}
 slso_status check_handle(slso_handle* hp, Handle** out);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -395,8 +395,7 @@ template <int NT>
 slso_status launch_gauss_tc(const dim3& grid, const GLayout& L, const CUtensorMap& mA, const CUtensorMap* mB,
                             int64_t s, int64_t d, double scale, int first, double* SX, DevState* state,
                             cudaStream_t st) {
-  SLSO_CHECK_CUDA(cudaFuncSetAttribute(gauss_tc_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(L.smem_bytes)));
+  SLSO_TRY(raise_smem_limit(gauss_tc_kernel<NT>, L.smem_bytes));
   gauss_tc_kernel<NT><<<grid, kGThreads, L.smem_bytes, st>>>(mA, mB[0], mB[1], mB[2], L, s, d, scale, first, SX,
                                                              state);
   SLSO_CHECK_LAUNCH();

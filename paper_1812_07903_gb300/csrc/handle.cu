@@ -1,5 +1,8 @@
 // Handle, device pool and error reporting of libslso.
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -37,6 +40,20 @@ slso_status fail(slso_status st, const char* fmt, ...) {
   vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
   va_end(ap);
   return st;
+}
+
+slso_status raise_smem_limit(const void* fn, size_t bytes) {
+  constexpr size_t kDefault = 48 * 1024;  // the limit a function starts with
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limits;
+  int dev = 0;
+  SLSO_CHECK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limits.try_emplace(std::make_pair(dev, fn), kDefault).first->second;
+  if (bytes <= cur) return SLSO_OK;
+  SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+  cur = bytes;
+  return SLSO_OK;
 }
 
 slso_status ensure_pool(Handle& h, size_t bytes) {

@@ -842,16 +842,14 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     L2.tmem_cols = cols;
     const int nwork = (ntiles + kT - 1) / kT;
     const int grid2 = std::min(nwork, h.num_sms);
-    SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc2_kernel<kbe, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(L2.smem_bytes)));
+    SLSO_TRY(raise_smem_limit(score_tc2_kernel<kbe, kT>, L2.smem_bytes));
     score_tc2_kernel<kbe, kT><<<grid2, kThreads, L2.smem_bytes, st>>>(mX16, mBh16, mBl16, L2, n, nwork, scores,
                                                                      h.state);
     SLSO_CHECK_LAUNCH();
     return SLSO_OK;
   }
   const int grid = std::min(ntiles, h.num_sms);
-  SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(L.smem_bytes)));
+  SLSO_TRY(raise_smem_limit(score_tc_kernel, L.smem_bytes));
   score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, mB2, L, n, ntiles, 1, cscale,
                                                         fp8 ? escale + 1 : nullptr, scores, nullptr, 0, 0,
                                                         h.state);
@@ -909,8 +907,7 @@ slso_status run_product_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a product operand layout");
   const int ntiles = static_cast<int>(ceil_div(n, kBM));
   const int grid = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(ntiles) * ncb, h.num_sms));
-  SLSO_CHECK_CUDA(cudaFuncSetAttribute(score_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(L.smem_bytes)));
+  SLSO_TRY(raise_smem_limit(score_tc_kernel, L.smem_bytes));
   score_tc_kernel<<<grid, kThreads, L.smem_bytes, st>>>(mX, mB0, mB1, mB2, L, n, ntiles, ncb, nullptr, nullptr,
                                                         nullptr, U, ldu, kk, h.state);
   SLSO_CHECK_LAUNCH();

@@ -424,8 +424,7 @@ slso_status srht(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t
   Acc* P = ar.take<Acc>(static_cast<size_t>(n1) * d * s);
   if (ar.measure()) return SLSO_OK;
   const size_t smem = (size_t(1) << log2_n2) * kSrhtSlab * sizeof(Acc);
-  SLSO_CHECK_CUDA(cudaFuncSetAttribute(srht_chunk_kernel<T, Acc>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  SLSO_TRY(raise_smem_limit(srht_chunk_kernel<T, Acc>, smem));
   dim3 g1(static_cast<unsigned>(n1), static_cast<unsigned>(ceil_div(d, kSrhtSlab)));
   srht_chunk_kernel<T, Acc><<<g1, kSrhtThreads, smem, st>>>(X, n, d, ldx, row0, log2_n2, seed, sample, s, P,
                                                             h.state);

@@ -1329,9 +1329,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   // stays 1 when it stands; the Householder kernels below then return at once.
   int32_t* gram_ok = &h.state->gram_ok;
   // trinv_kernel keeps one column of R^-1 in shared memory: d doubles, above 48 KB for d > 6144
-  SLSO_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(trinv_kernel),
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sizeof(double) * d)));
+  SLSO_TRY(raise_smem_limit(trinv_kernel, sizeof(double) * d));
   if (gram) {
     SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, st));
     prof_begin(h, ar, ST_CHOL, st);
@@ -1406,7 +1404,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
       fn = vsm ? reinterpret_cast<void*>(qr_kernel<true>) : reinterpret_cast<void*>(qr_kernel<false>);
       threads = kQrThreads;
     }
-    SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    SLSO_TRY(raise_smem_limit(fn, smem));
     int occ = 0;
     SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
     if (occ < 1) return fail(SLSO_ERR_CUDA, "QR kernel cannot be resident (smem %zu)", smem);
@@ -1500,7 +1498,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
       void* fn = d <= 256 ? reinterpret_cast<void*>(jacobi_block_f32_kernel<8>)
                  : d <= 512 ? reinterpret_cast<void*>(jacobi_block_f32_kernel<16>)
                             : reinterpret_cast<void*>(jacobi_block_f32_kernel<32>);
-      SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+      SLSO_TRY(raise_smem_limit(fn, smem));
       int occ = 0;
       SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kJacobiBlockThreads, smem));
       if (occ < 1) return fail(SLSO_ERR_CUDA, "block Jacobi kernel cannot be resident (smem %zu)", smem);
