@@ -147,13 +147,17 @@ slso_status slso_sketched_svd(slso_handle* handle, const double* SX, int64_t s, 
  *   SX = S X;  R = householder_R(SX);  r = #{sigma_j(R) > tau sigma_1};
  *   M = R^+_tau Pi = V_r Sigma_r^-1 U_R,r^T Pi  (Pi = I when k = 0);
  *   scores_i = ||x_i M||^2.
+ * With params->factor = SLSO_FACTOR_AUTO and compute != F64, R is first taken as the Cholesky
+ * factor of SX^T SX (the same R at full column rank); it stands only when its probe check
+ * passes, else the Householder R is computed instead (slso_factor; info->gram_route and
+ * info->gram_resid report which).
  * When ||R||_F ||R^-1||_F < 1e-3 / tau the rank is certified to be d and R^+_tau = R^-1
  * exactly, so the SVD is skipped (info->svd_route = 0).  scores: n values, float64 when
  * compute == F64, else float32.  compute F32 evaluates X.M to float32 accuracy on the
  * tensor cores (three TF32 products); BF16 and FP8 round X and M (FP8 with per-column
  * scales of X folded into M) and accumulate in float32.
  * Errors: SHAPE as for slso_sketch plus k > 4096 or s < d; DTYPE for an unsupported
- * (xdt, compute) pair. */
+ * (xdt, compute) pair; INVALID_ARG for an unknown factor. */
 slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
                           int32_t xdt, const slso_params* params, void* scores, slso_info* info,
                           void* stream);

@@ -43,8 +43,27 @@ def test_version_and_workspace_sizing_without_gpu(lib):
     p = L.Params(kind=L.COUNTSKETCH, compute=L.F32, s=16384, k=128, seed_S=1, seed_Pi=2, tau=-1.0, correct_frac=0.0)
     nbytes = ctypes.c_size_t(0)
     assert lib.slso_workspace_size(ctypes.byref(p), 1_000_000, 1024, ctypes.byref(nbytes)) == L.SLSO_OK
-    # dominated by SX (s x d float64) and the QR copy of it
-    assert 2 * 16384 * 1024 * 8 <= nbytes.value < 4 * 16384 * 1024 * 8 + 200 * 2**20
+    # dominated by SX (s x d float64), the QR copy of it and the Gram route's float32 split of it
+    assert 3 * 16384 * 1024 * 8 <= nbytes.value < 4 * 16384 * 1024 * 8 + 200 * 2**20
+
+
+def test_factor_choice_sizes_the_gram_route_and_rejects_unknown_values(lib):
+    from paper_1812_07903_gb300 import _lib as L
+    def size(compute, factor):
+        p = L.Params(kind=L.COUNTSKETCH, compute=compute, s=4096, k=64, seed_S=1, seed_Pi=2, tau=-1.0,
+                     correct_frac=0.0, nnz=0, factor=factor)
+        nbytes = ctypes.c_size_t(0)
+        st = lib.slso_workspace_size(ctypes.byref(p), 100_000, 256, ctypes.byref(nbytes))
+        return st, nbytes.value
+    st_auto, auto = size(L.F32, 0)
+    st_hh, hh = size(L.F32, 1)
+    assert st_auto == st_hh == L.SLSO_OK
+    # the Gram route's buffers: the split SX (2 x s x d float32) at least
+    assert auto - hh >= 2 * 4096 * 256 * 4
+    # compute = F64 never tries the Gram route
+    assert size(L.F64, 0) == size(L.F64, 1)
+    st, _ = size(L.F32, 2)
+    assert st == 1 and b"factor" in lib.slso_last_error()  # INVALID_ARG
 
 
 def test_shape_errors_are_reported_before_any_device_work(lib):
