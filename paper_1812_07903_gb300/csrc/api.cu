@@ -73,6 +73,19 @@ slso_status check_params(const slso_params* p, int64_t n, int64_t d) {
 
 bool use_gram(const slso_params* p) { return p->factor == SLSO_FACTOR_AUTO && p->compute != SLSO_F64; }
 
+void info_from_state(const DevState& d, slso_info* info) {
+  info->rank = d.rank;
+  info->sigma_max = d.sigma_max;
+  info->sigma_min_kept = d.sigma_min_kept;
+  info->score_sum = d.score_sum;
+  info->tau = d.tau;
+  info->nonfinite = d.nonfinite;
+  info->svd_route = d.need_svd;
+  info->svd_sweeps = d.sweeps;
+  info->gram_route = d.gram_ok;
+  info->gram_resid = d.gram_tried ? d.gram_resid : std::nan("");
+}
+
 }  // namespace slso
 
 namespace {
@@ -92,16 +105,7 @@ slso_status fill_info(Handle& h, cudaStream_t st, slso_info* info) {
   SLSO_CHECK_CUDA(cudaMemcpyAsync(h.state_host, h.state, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   SLSO_CHECK_CUDA(cudaStreamSynchronize(st));
   const DevState& d = *h.state_host;
-  info->rank = d.rank;
-  info->sigma_max = d.sigma_max;
-  info->sigma_min_kept = d.sigma_min_kept;
-  info->score_sum = d.score_sum;
-  info->tau = d.tau;
-  info->nonfinite = d.nonfinite;
-  info->svd_route = d.need_svd;
-  info->svd_sweeps = d.sweeps;
-  info->gram_route = d.gram_ok;
-  info->gram_resid = d.gram_tried ? d.gram_resid : std::nan("");
+  info_from_state(d, info);
   if (d.timeout) return fail(SLSO_ERR_TIMEOUT, "a bounded device wait gave up (kernel %d)", d.timeout);
   if (d.nonfinite) return fail(SLSO_ERR_NONFINITE, "X holds NaN or Inf");
   return SLSO_OK;
@@ -334,16 +338,7 @@ extern "C" slso_status slso_rank_rows_host_batch(slso_handle* handle, int64_t co
     slso_status first_err = SLSO_OK;
     for (int64_t i = 0; i < count; ++i) {
       const DevState& ds = hs[static_cast<size_t>(i)];
-      if (info) {
-        info[i].rank = ds.rank;
-        info[i].sigma_max = ds.sigma_max;
-        info[i].sigma_min_kept = ds.sigma_min_kept;
-        info[i].score_sum = ds.score_sum;
-        info[i].tau = ds.tau;
-        info[i].nonfinite = ds.nonfinite;
-        info[i].svd_route = ds.need_svd;
-        info[i].svd_sweeps = ds.sweeps;
-      }
+      if (info) info_from_state(ds, info + i);
       if (first_err == SLSO_OK && ds.timeout)
         first_err = fail(SLSO_ERR_TIMEOUT, "item %lld: a bounded device wait gave up (kernel %d)", (long long)i, ds.timeout);
       if (first_err == SLSO_OK && ds.nonfinite)

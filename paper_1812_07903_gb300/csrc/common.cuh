@@ -462,6 +462,8 @@ double default_tau(int64_t s, int64_t d);
 slso_status check_x(const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt);
 slso_status check_params(const slso_params* p, int64_t n, int64_t d);
 bool use_gram(const slso_params* p);  // the Gram route is tried for this leverage call
+// Every slso_info field from a call's device status words.
+void info_from_state(const DevState& d, slso_info* info);
 slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
 

@@ -16,6 +16,7 @@
 // Layout: the Gram matrix and its factor share L (d x d, row-major); only the lower triangle is
 // written and read.  Its lower triangle L_ij = R_ji is R stored column-major, the layout the
 // Householder kernel leaves R in.
+#include <algorithm>
 #include <cmath>
 
 #include <math_constants.h>

@@ -280,14 +280,7 @@ void finish_job(Server& s, Slot& sl) {
       j->status = SLSO_ERR_CUDA;
     } else {
       const DevState& d = *sl.h.state_host;
-      j->info.rank = d.rank;
-      j->info.sigma_max = d.sigma_max;
-      j->info.sigma_min_kept = d.sigma_min_kept;
-      j->info.score_sum = d.score_sum;
-      j->info.tau = d.tau;
-      j->info.nonfinite = d.nonfinite;
-      j->info.svd_sweeps = d.sweeps;
-      j->info.svd_route = d.need_svd;
+      info_from_state(d, &j->info);
       if (d.timeout) j->status = SLSO_ERR_TIMEOUT;
       else if (d.nonfinite) j->status = SLSO_ERR_NONFINITE;
     }
