@@ -7,7 +7,9 @@ applied to the GPU's own sketch, "Oracle C"):
 * 1,000,000 x 1024 float32, CountSketch s = 16384, k = 128 (the benchmark step): sampled rows
   of SX summed exactly in float64 from the rows hashing to them; R, rank and M by the oracle from
   the GPU's SX; float32 scores of sampled rows and of the top rows within 1e-4; the order equal
-  to a stable (score, index) sort of the GPU's scores; bfloat16 median error under 2%.
+  to a stable (score, index) sort of the GPU's scores; bfloat16 median error under 2%.  R comes
+  from the Gram route (probe residual under 1e-10), and every score is within 1e-6 of the scores
+  with the Householder R (factor='householder').
 * 60,000 x 784 image-like, CountSketch s = 8192 and SRHT s = 2048, k = 64: the whole oracle,
   rank 716 (68 zero columns), every row's score within 1e-4.
 * 4,000,000 x 3072 bfloat16 with a 1% rank-16 outlier subspace, Gaussian s = 6144 on tensor
@@ -65,6 +67,12 @@ def test_benchmark_workload_1m_x_1024_countsketch():
 
     # order: bit-exact stable sort of the GPU's own scores
     np.testing.assert_array_equal(order, O.order_dec(sc))
+
+    # the float32 path's R came from the Gram route, and agrees with the Householder R
+    assert info["gram_route"] == 1 and info["gram_resid"] < 1e-10
+    hh, hinfo = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="f32", factor="householder")
+    assert hinfo["gram_route"] == 0
+    assert _max_rel(sc, hh.cpu().numpy()) < 1e-6
 
     # bfloat16 scores (the metric's precision claim): median relative error < 2%
     bf, _ = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="bf16")
