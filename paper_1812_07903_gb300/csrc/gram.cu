@@ -3,9 +3,10 @@
 // When SX has full column rank, its QR factor R with a positive diagonal is unique, and it is the
 // Cholesky factor of G = SX^T SX (R^T R = G).  The Gram route forms G with a SYRK (s d (d+1)/2
 // multiply-adds, against about s d^2 for Householder QR) in float-float arithmetic on the float32
-// pipe, whose rate is 64 times the float64 pipe's here: each column of SX is scaled by a power of
-// two and split into two float32 parts, and every product and sum keeps its rounding error (about
-// 2^-46 relative).  The factorisation (d^3/6 multiply-adds) runs in float64.  The
+// pipe, whose rate is 64 times the float64 pipe's on GB300: each column of SX is scaled by a power
+// of two and split into two float32 parts, and every product and sum keeps its rounding error
+// (about 2^-47 of sum |a||b| with the running pair folded every 32 rows).  The factorisation
+// (d^3/6 multiply-adds) runs in float64.  The
 // computed factor then carries an orthogonality error F = R^-T SX^T SX R^-1 - I whose size grows
 // like kappa(SX)^2 u, where Householder's grows like kappa u.  Since every score (and every JL
 // score) is then off by at most ||F||_2 relative, the route is checked a posteriori: for P seeded
