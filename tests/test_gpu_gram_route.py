@@ -11,7 +11,8 @@ oracle and against the Householder route.
   break down, fall back to Householder, and then return bit-for-bit the scores of
   factor='householder';
 * compute='f64' never takes the Gram route;
-* d > 6144 (R^-1 columns above 48 KB of shared memory) on both routes.
+* d > 6144 (R^-1 columns above 48 KB of shared memory) on both routes, and s > 16384 (the
+  right-looking Householder kernel as the fallback).
 """
 import math
 
@@ -58,6 +59,19 @@ def test_gram_route_matches_oracle(kind, n, d, s, k, nnz):
     hh, hinfo = api.leverage(X.cuda(), kind, s, k, 11, 12, compute="f32", nnz=nnz, factor="householder")
     assert hinfo["gram_route"] == 0 and math.isnan(hinfo["gram_resid"])
     assert _rel(sc.cpu().numpy(), hh.cpu().numpy()) < 1e-6
+
+
+def test_sketch_taller_than_the_left_looking_qr():
+    # s > 16384: the Householder fallback is the right-looking kernel, whose R is copied into the
+    # buffer the Gram route writes only when that kernel ran
+    n, d, s = 200000, 64, 20000
+    X = inputs.lognormal_rows(n, d, seed=82, dtype=torch.float32)
+    want, rank = _oracle(X.double().numpy(), "countsketch", s, 16, 13, 14)
+    assert rank == d
+    for factor, route in (("auto", 1), ("householder", 0)):
+        sc, info = api.leverage(X.cuda(), "countsketch", s, 16, 13, 14, compute="f32", factor=factor)
+        assert info["gram_route"] == route and info["rank"] == d
+        assert _rel(sc.cpu().numpy(), want) < 1e-4
 
 
 def test_gram_route_bf16_x_and_bf16_compute():
