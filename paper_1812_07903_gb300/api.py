@@ -117,6 +117,8 @@ def make_params(kind="countsketch", s=None, k=0, seed_S=0, seed_Pi=0, tau=-1.0, 
     p.tau = float(tau)
     p.correct_frac = float(correct_frac)
     p.nnz = int(nnz)
+    if factor not in FACTOR:
+        raise ValueError(f"factor must be one of {sorted(FACTOR)}, not {factor!r}")
     p.factor = FACTOR[factor]
     return p
 

@@ -84,3 +84,11 @@ def test_handle_calls_reject_null_handle(lib):
     from paper_1812_07903_gb300 import _lib as L
     assert lib.slso_order(None, None, L.F32, 10, None, None) == 1  # INVALID_ARG: NULL handle
     assert lib.slso_destroy(None) == L.SLSO_OK
+
+
+def test_binding_maps_the_factor_choice():
+    from paper_1812_07903_gb300 import api
+    assert api.make_params(s=64, factor="auto").factor == 0
+    assert api.make_params(s=64, factor="householder").factor == 1
+    with pytest.raises(ValueError, match="factor"):
+        api.make_params(s=64, factor="cholesky")
