@@ -76,7 +76,9 @@ typedef enum { SLSO_POLICY_DEC = 0, SLSO_POLICY_SWR = 1, SLSO_POLICY_SWOR = 2 } 
  *               seeded Gaussian probes z (Philox at counter (lo c, hi c, q, 8)) estimates
  *               ||R^-T SX^T SX R^-1 - I||_F <= 1e-8 (its error grows like kappa(SX)^2 u; the
  *               relative error of every score is at most that norm); otherwise, and always for
- *               compute = F64, Householder.  Decided on the device; slso_info reports it. */
+ *               compute = F64, Householder.  Decided on the device; slso_info reports it.
+ *               Its scratch (the float32 split of SX, 8 s d bytes, plus O(d^2)) is taken
+ *               whether or not the route stands; slso_workspace_size includes it. */
 typedef enum { SLSO_FACTOR_AUTO = 0, SLSO_FACTOR_HOUSEHOLDER = 1 } slso_factor;
 
 typedef struct slso_handle slso_handle;
