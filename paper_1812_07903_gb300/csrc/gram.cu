@@ -32,6 +32,7 @@ constexpr int kGt = 32;            // tile edge of the Gram and Cholesky kernels
 constexpr int kGramThreads = 128;  // 16 x 8 threads, 2 x 4 outputs each
 constexpr int kProbes = 4;         // P
 constexpr uint64_t kProbeSeed = 0x243F6A8885A308D3ull;
+constexpr int kGramBalanceSms = 152;  // GB300's SM count: the split-K and probe-chunk counts
 
 // The route flag read once per block (thread 0, then a barrier), so that every thread of a block
 // takes the same branch even while block 0 of the panel kernel may be clearing it.
@@ -535,8 +536,11 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
   const int64_t nb = ceil_div(d, kGt);
   g.tiles = static_cast<int>(nb * (nb + 1) / 2);
   // split-K count: the smallest S (at most 16, at least 256 rows per split) whose items spread
-  // over the SMs within 3% of even; else the most even one
-  const int P = h.num_sms > 0 ? h.num_sms : 1;
+  // over the SMs within 3% of even; else the most even one.  The SM count is GB300's fixed 152,
+  // not the device's: S sets the summation order of G, so results and slso_workspace_size's
+  // estimate do not depend on the device the call runs on.
+  (void)h;
+  constexpr int P = kGramBalanceSms;
   double best = 1e30;
   int best_s = 1;
   for (int S = 1; S <= 16; ++S) {
