@@ -262,8 +262,9 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int T, int S
 // block b > 0 solves row block I = k + b: L_Ik = G_Ik L_kk^-T.  A pivot that is not positive and
 // finite ends the route.  On this part's narrow float64 pipe the cost is the number of warp
 // instructions on the chain: one lane forms rsqrt(pivot), which gives both L_jj = pivot rsqrt and
-// its reciprocal (the column is scaled by a multiply), and the trailing update of step j walks only its (31 - j)(32 - j) / 2 live
-// entries, listed by decreasing column so that they are a prefix of one table.
+// its reciprocal (the column is scaled by a multiply), and the trailing update of step j walks
+// only its (31 - j)(32 - j) / 2 live entries, listed by decreasing column so that they are a
+// prefix of one table.
 __global__ void __launch_bounds__(kGramThreads) chol_panel_kernel(double* __restrict__ L, int d, int k,
                                                                   double* __restrict__ ldiag,
                                                                   DevState* __restrict__ st) {
