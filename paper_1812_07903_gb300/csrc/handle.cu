@@ -43,13 +43,21 @@ slso_status fail(slso_status st, const char* fmt, ...) {
 }
 
 slso_status raise_smem_limit(const void* fn, size_t bytes) {
-  constexpr size_t kDefault = 48 * 1024;  // the limit a function starts with
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> limits;
   int dev = 0;
   SLSO_CHECK_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
-  size_t& cur = limits.try_emplace(std::make_pair(dev, fn), kDefault).first->second;
+  auto key = std::make_pair(dev, fn);
+  auto it = limits.find(key);
+  if (it == limits.end()) {
+    // A function starts with a dynamic limit of 48 KB minus its own static __shared__ bytes, so
+    // the starting value is read from the function, not assumed.
+    cudaFuncAttributes a{};
+    SLSO_CHECK_CUDA(cudaFuncGetAttributes(&a, fn));
+    it = limits.emplace(key, static_cast<size_t>(a.maxDynamicSharedSizeBytes)).first;
+  }
+  size_t& cur = it->second;
   if (bytes <= cur) return SLSO_OK;
   SLSO_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
   cur = bytes;

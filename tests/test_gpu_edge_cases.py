@@ -97,3 +97,27 @@ def test_equal_rows_share_the_mass_and_zero_row_scores_zero():
     od = api.order(sc).cpu().numpy()
     np.testing.assert_array_equal(od, O.order_dec(sc.cpu().numpy()))
     assert od[-1] == 777  # the only zero score comes last
+
+
+def test_qr_two_ctas_per_sm_at_s_6144():
+    # s = 6144 with d >= 4 x 152 columns takes the QR kernel with two 128-thread CTAs per SM and 48
+    # rows per thread: 48 KB of dynamic shared memory on top of the kernel's static arrays
+    n, d, s = 8192, 640, 6144
+    X = inputs.lognormal_rows(n, d, seed=45, dtype=torch.float64)
+    sc, info = api.leverage(X.cuda(), "countsketch", s, 16, 11, 12, compute="f64")
+    want, rank = _oracle(X.numpy(), "countsketch", s, 16, 11, 12)
+    assert info["rank"] == rank == d
+    assert _rel(sc.cpu().numpy(), want) < 1e-9
+
+
+def test_block_jacobi_at_48_kb_of_shared_memory():
+    # d = 384: the float32 block sweeps of the sketched SVD ask for exactly 48 KB of dynamic shared
+    # memory, which with the kernel's static arrays is above a function's starting limit
+    s, d = 1024, 384
+    X = inputs.lognormal_rows(4096, d, seed=46, dtype=torch.float64)
+    SX = api.sketch(X.cuda(), "countsketch", s, 13)
+    sigma, V, R, info = api.sketched_svd(SX)
+    sv = O.sketched_svd(SX.cpu().numpy(), qr="lapack")
+    got = sigma.cpu().numpy()
+    assert info["rank"] == sv["rank"] == d
+    assert float(np.max(np.abs(got - sv["sigma"]))) < 1e-10 * float(sv["sigma"][0])

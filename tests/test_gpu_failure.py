@@ -62,6 +62,11 @@ def test_cancel_a_queued_serving_job():
     t_mid = srv.submit_leverage(small, "countsketch", 512, 16, 3, 4)
     t_cut = srv.submit_leverage(small, "countsketch", 512, 16, 5, 6)
     srv.cancel(t_cut)  # one slot: the big job runs, the other two wait
+    # submit returns before the worker admits the big job; cancel it only once it has left the queue
+    deadline = time.perf_counter() + 30.0
+    while srv.counters()["admitted"] < 1 and time.perf_counter() < deadline:
+        time.sleep(0.001)
+    assert srv.counters()["admitted"] >= 1
     with pytest.raises(L.SlsoError) as e:
         srv.cancel(t_big)
     assert e.value.status == 8  # BUSY: already running
