@@ -145,6 +145,18 @@ slso_status slso_sketched_svd(slso_handle* handle, const double* SX, int64_t s, 
                               double tau, double* sigma, double* V, double* R, slso_info* info,
                               void* stream);
 
+/* Gram matrix G = SX^T SX (d x d float64, row-major, symmetric) as the float32 compute path's
+ * Gram route forms it for R (R^T R = G at full column rank; Algorithm 2/3 step 2).  Each column j
+ * of SX (s x d float64, row-major, s >= 1) is scaled by 2^-e_j, its largest entry then in [1/2, 1),
+ * rounded to 47 fractional bits and cut into six signed 8-bit digits; the digit products of order
+ * <= 5 run on the tensor cores (bfloat16, float32 accumulation) in 256-row windows where every
+ * partial sum of orders 0-2 is an exact integer, and the windows are added as exact int64 sums,
+ * so G is deterministic and, for integer-valued columns with at most 47 significant bits below
+ * their scale, exact.  Where the tensor route does not apply (s >= 2^25) a float-float SYRK on the
+ * float32 pipe forms G instead.  SX, G: caller-owned device memory; asynchronous on stream.
+ * Errors: SHAPE unless 1 <= d <= 8192 and 1 <= s < 2^31; INVALID_ARG for NULL pointers. */
+slso_status slso_gram(slso_handle* handle, const double* SX, int64_t s, int64_t d, double* G, void* stream);
+
 /* Approximate leverage scores (Algorithm 3 with the JL projection Pi):
  *   SX = S X;  R = householder_R(SX);  r = #{sigma_j(R) > tau sigma_1};
  *   M = R^+_tau Pi = V_r Sigma_r^-1 U_R,r^T Pi  (Pi = I when k = 0);

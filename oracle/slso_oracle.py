@@ -36,6 +36,7 @@ pinned by a test in ``tests/test_oracle_*.py`` to something other than itself.
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 
 import numpy as np
 
@@ -352,6 +353,59 @@ def householder_r(A, steps=None):
     neg = np.diag(R) < 0.0
     R[neg, :] *= -1.0
     return R
+
+
+def gram(SX):
+    """G = SX^T SX with every entry the float64 rounding of its exact value (the Gram matrix whose
+    Cholesky factor is the R of Algorithm 2/3 step 2 at full column rank).
+
+    Exact arithmetic by integer pieces: column j is scaled by 2^-k_j (k_j from frexp of its
+    largest magnitude, so the scaled entries lie in (-1, 1)) and cut into five 17-bit integer
+    pieces, a' 2^85 = sum_p P_p 2^(17 (4 - p)) + rem with |rem| < 1.  Float64 matrix products of
+    pieces, and the up to five of them of equal order t = p + q, are exact in any summation order
+    while s < 2^16 (every partial sum is an integer below 5 s 2^34 < 2^53); they are combined as Python
+    integers V = sum_t 2^(17 (8 - t)) C_t, and G_ij = V_ij 2^(k_i + k_j - 170) is rounded once.
+    Exact whenever every entry's bits lie within 85 bits of its column's largest magnitude
+    (always for entries at least 2^-32 of it); below that, within 2^-85 of it.
+    """
+    A = np.asarray(SX, dtype=np.float64)
+    s, d = A.shape
+    if s >= 1 << 16:
+        raise ValueError("gram: s must be below 2^16 for exact piece products")
+    if not np.all(np.isfinite(A)):
+        raise ValueError("gram: SX must be finite")
+    colmax = np.max(np.abs(A), axis=0) if s else np.zeros(d)
+    k = np.zeros(d, dtype=np.int64)
+    nz = colmax > 0
+    k[nz] = np.frexp(colmax[nz])[1]
+    a = np.ldexp(A, -k[None, :])  # exact: scaling by a power of two
+    pieces = []
+    for _ in range(5):
+        a = a * 131072.0  # 2^17, exact
+        P = np.trunc(a)
+        a = a - P  # exact: the remainder has fewer bits than a
+        pieces.append(P)
+    V = np.zeros((d, d), dtype=object)
+    for t in range(9):
+        C = np.zeros((d, d))
+        for p in range(5):
+            q = t - p
+            if 0 <= q < 5:
+                C += pieces[p].T @ pieces[q]  # integers below 2^53: exact
+        V = V + np.vectorize(int, otypes=[object])(C) * (1 << (17 * (8 - t)))
+    G = np.empty((d, d))
+    for i in range(d):
+        for j in range(d):
+            v, e = int(V[i, j]), int(k[i] + k[j]) - 170
+            if v == 0:
+                G[i, j] = 0.0
+            elif v.bit_length() + e > 1024:
+                G[i, j] = math.copysign(math.inf, v)
+            elif v.bit_length() + e < -1020:  # subnormal range: round the exact rational once
+                G[i, j] = float(Fraction(v) * Fraction(2) ** e)
+            else:
+                G[i, j] = math.ldexp(float(v), e)  # float(v) rounds once; the scaling is exact
+    return G
 
 
 def householder_r_lapack(A):

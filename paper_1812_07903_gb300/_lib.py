@@ -21,7 +21,7 @@ DTYPE = {"f64": F64, "f32": F32, "bf16": BF16, "fp8": FP8_E4M3}
 # Every symbol include/slso.h declares.
 EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
-    "slso_sketch", "slso_sketched_svd", "slso_leverage", "slso_order", "slso_rank_rows_host",
+    "slso_sketch", "slso_sketched_svd", "slso_gram", "slso_leverage", "slso_order", "slso_rank_rows_host",
     "slso_profile", "slso_profile_read", "slso_order_static", "slso_sample_order",
     "slso_rank_rows_host_batch", "slso_set_pool_limit", "slso_selftest_wait", "slso_server_cancel",
     "slso_approx_u", "slso_rank_rows_streamed",
@@ -88,6 +88,7 @@ def load():
         "slso_workspace_size": ([ctypes.POINTER(Params), i64, i64, ctypes.POINTER(ctypes.c_size_t)], i32),
         "slso_sketch": ([vp, vp, i64, i64, i64, i32, i32, i64, u64, vp, vp], i32),
         "slso_sketched_svd": ([vp, vp, i64, i64, dbl, vp, vp, vp, ctypes.POINTER(Info), vp], i32),
+        "slso_gram": ([vp, vp, i64, i64, vp, vp], i32),
         "slso_leverage": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), vp, ctypes.POINTER(Info), vp], i32),
         "slso_order": ([vp, vp, i32, i64, vp, vp], i32),
         "slso_rank_rows_host": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), vp, vp,

@@ -100,6 +100,18 @@ def sketched_svd(SX, tau=-1.0, want_r=True, handle=None):
     return sigma, V, R, info.as_dict()
 
 
+def gram(SX, handle=None):
+    """slso_gram: G = SX^T SX (d x d float64) as the float32 path's Gram route forms it."""
+    h = handle or default_handle()
+    _require_cuda(SX)
+    if SX.dtype != torch.float64 or not SX.is_contiguous():
+        raise TypeError("SX must be a contiguous float64 CUDA tensor")
+    s, d = SX.shape
+    G = torch.empty(d, d, dtype=torch.float64, device=SX.device)
+    L.check(L.load().slso_gram(h.ptr, SX.data_ptr(), s, d, G.data_ptr(), _stream()))
+    return G
+
+
 FACTOR = {"auto": 0, "householder": 1}
 
 

@@ -186,6 +186,22 @@ extern "C" slso_status slso_sketched_svd(slso_handle* handle, const double* SX, 
   return SLSO_OK;
 }
 
+extern "C" slso_status slso_gram(slso_handle* handle, const double* SX, int64_t s, int64_t d, double* G,
+                                 void* stream) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (!SX || !G) return fail(SLSO_ERR_INVALID_ARG, "SX and G must be non-NULL");
+  if (d < 1 || d > 8192 || s < 1 || s >= (int64_t(1) << 31))
+    return fail(SLSO_ERR_SHAPE, "need 1 <= d <= 8192 and 1 <= s < 2^31 (s=%lld, d=%lld)", (long long)s, (long long)d);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return run_plan(*h, [&](Arena& ar) {
+    GramWork g = gram_take(*h, ar, s, d);
+    double* L = ar.take<double>(static_cast<size_t>(d) * d);
+    if (ar.measure()) return SLSO_OK;
+    return run_gram_full(*h, ar, g, SX, s, d, L, G, st);
+  });
+}
+
 extern "C" slso_status slso_leverage(slso_handle* handle, const void* X, int64_t n, int64_t d, int64_t ldx,
                                      int32_t xdt, const slso_params* params, void* scores, slso_info* info,
                                      void* stream) {

@@ -434,6 +434,19 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
 // run_gram_check (after R^-1, column-major, is in Rinv) clears gram_ok when the probe estimate
 // of ||R^-T SX^T SX R^-1 - I||_F exceeds kGramTol.
 constexpr double kGramTol = 1e-8;
+// gram_tc.cu: G = SX^T SX on the tensor cores from six exact bfloat16 digit slices of the scaled
+// columns (float64-class accuracy), written like the float-float SYRK's reduction into L.
+struct GramTcWork {
+  __nv_bfloat16* E = nullptr;  // 6 dpad x sp slices, K (rows of SX) contiguous
+  long long* part = nullptr;   // split partial tiles (128 x 64 int64 sums)
+  int* bad = nullptr;          // a non-finite SX entry was met
+  int dpad = 0, nbJ = 0, tiles = 0, splits = 1;
+  int64_t sp = 0, kc = 0;
+};
+bool gram_tc_applies(int64_t s, int64_t d);
+void gram_tc_take(Arena& ar, int64_t s, int64_t d, GramTcWork* w);
+slso_status run_gram_tc(Handle& h, const GramTcWork& w, const double* SX, int64_t s, int64_t d, const int* cexp,
+                        double* L, cudaStream_t st);
 struct GramWork {
   double* part = nullptr;   // split-K partial tiles of the Gram matrix
   double* Z = nullptr;      // d x P probes
@@ -448,12 +461,20 @@ struct GramWork {
   double* cscale = nullptr; // 2^-e_j
   float* xh = nullptr;      // SX 2^-e_j split into float32 parts xh + xl (s x d row-major)
   float* xl = nullptr;
+  bool use_tc = false;      // G from the tensor-core route (gram_tc.cu) instead of the float-float SYRK
+  GramTcWork tc;
   int splits = 1, tiles = 0, vchunks = 1;
   int64_t kc = 0;
 };
 GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d);
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
                             int64_t d, double* L, cudaStream_t st);
+// G = SX^T SX alone: its lower triangle into L (d x d row-major); run_gram_full also writes the
+// whole symmetric G (d x d row-major).
+slso_status run_gram_matrix(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
+                            int64_t d, double* L, cudaStream_t st);
+slso_status run_gram_full(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s, int64_t d,
+                          double* L, double* G, cudaStream_t st);
 slso_status run_gram_check(Handle& h, const GramWork& g, const double* SX, int64_t s, int64_t d,
                            const double* Rinv, cudaStream_t st);
 

@@ -532,6 +532,27 @@ __global__ void __launch_bounds__(256) probe_final_kernel(const double* __restri
 
 }  // namespace
 
+slso_status run_cholesky(Handle& h, const GramWork& g, int64_t d, double* L, cudaStream_t st);
+
+// The lower triangle of L from the lower triangle of G's row-major store (mirrored into G's upper).
+__global__ void gram_mirror_kernel(const double* __restrict__ L, int d, double* __restrict__ G) {
+  const int64_t total = static_cast<int64_t>(d) * d;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / d, j = e % d;
+    G[e] = j <= i ? L[e] : L[j * d + i];
+  }
+}
+
+slso_status run_gram_full(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s, int64_t d,
+                          double* L, double* G, cudaStream_t st) {
+  SLSO_TRY(run_gram_matrix(h, ar, g, SX, s, d, L, st));
+  const unsigned b = static_cast<unsigned>(std::min<int64_t>(ceil_div(d * d, 256), static_cast<int64_t>(h.num_sms) * 8));
+  gram_mirror_kernel<<<b, 256, 0, st>>>(L, static_cast<int>(d), G);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
 GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
   GramWork g;
   const int64_t nb = ceil_div(d, kGt);
@@ -571,15 +592,28 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
   g.colmax = ar.take<unsigned long long>(d);
   g.cexp = ar.take<int>(d);
   g.cscale = ar.take<double>(d);
-  g.xh = ar.take<float>(static_cast<size_t>(s) * d);
-  g.xl = ar.take<float>(static_cast<size_t>(s) * d);
+  g.use_tc = gram_tc_applies(s, d);
+  if (g.use_tc) {
+    gram_tc_take(ar, s, d, &g.tc);
+  } else {
+    g.xh = ar.take<float>(static_cast<size_t>(s) * d);
+    g.xl = ar.take<float>(static_cast<size_t>(s) * d);
+  }
   return g;
 }
 
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
                             int64_t d, double* L, cudaStream_t st) {
+  SLSO_TRY(run_gram_matrix(h, ar, g, SX, s, d, L, st));
+  prof_begin(h, ar, ST_CHOL, st);
+  SLSO_TRY(run_cholesky(h, g, d, L, st));
+  prof_end(h, ar, st);
+  return SLSO_OK;
+}
+
+slso_status run_gram_matrix(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
+                            int64_t d, double* L, cudaStream_t st) {
   const int d_i = static_cast<int>(d);
-  const int nb = static_cast<int>(ceil_div(d, kGt));
   prof_begin(h, ar, ST_CHOL, st);
   SLSO_CHECK_CUDA(cudaMemsetAsync(g.colmax, 0, sizeof(unsigned long long) * d, st));
   const int cb = 2 * h.num_sms;
@@ -587,6 +621,14 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
   SLSO_CHECK_LAUNCH();
   gram_scale_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(g.colmax, d_i, g.cexp, g.cscale);
   SLSO_CHECK_LAUNCH();
+  prof_end(h, ar, st);
+  if (g.use_tc) {
+    prof_begin(h, ar, ST_SYRK, st);
+    SLSO_TRY(run_gram_tc(h, g.tc, SX, s, d, g.cexp, L, st));
+    prof_end(h, ar, st);
+    return SLSO_OK;
+  }
+  prof_begin(h, ar, ST_CHOL, st);
   gram_split_kernel<<<static_cast<unsigned>(8 * h.num_sms), 256, 0, st>>>(SX, s, d_i, g.cscale, g.xh, g.xl);
   SLSO_CHECK_LAUNCH();
   prof_end(h, ar, st);
@@ -604,6 +646,14 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
   const unsigned rb = static_cast<unsigned>(std::min<int64_t>(ceil_div(total, 256), static_cast<int64_t>(h.num_sms) * 8));
   gram_reduce_kernel<<<rb, 256, 0, st>>>(g.part, g.tiles, g.splits, d_i, g.cexp, L, h.state);
   SLSO_CHECK_LAUNCH();
+  prof_end(h, ar, st);
+  return SLSO_OK;
+}
+
+// Blocked right-looking Cholesky of the lower triangle of L in place (L = R^T afterwards).
+slso_status run_cholesky(Handle& h, const GramWork& g, int64_t d, double* L, cudaStream_t st) {
+  const int d_i = static_cast<int>(d);
+  const int nb = static_cast<int>(ceil_div(d, kGt));
   for (int k = 0; k < nb; ++k) {
     chol_panel_kernel<<<static_cast<unsigned>(nb - k), kGramThreads, 0, st>>>(L, d_i, k, g.ldiag, h.state);
     SLSO_CHECK_LAUNCH();
@@ -615,7 +665,6 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
   }
   chol_diag_store_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(g.ldiag, d_i, L, h.state);
   SLSO_CHECK_LAUNCH();
-  prof_end(h, ar, st);
   return SLSO_OK;
 }
 

@@ -1,0 +1,441 @@
+// Tensor-core Gram matrix G = SX^T SX for the Gram route of R (Algorithm 2/3 step 2), float64-class
+// accurate, on the bfloat16 tcgen05 path with exact integer accumulation (an Ozaki-type split).
+//
+// Column j of SX is scaled by 2^-e_j (its largest entry in [1/2, 1)) and rounded to 47 fractional
+// bits, a' = F 2^-47 with |F| < 2^47 (within 2^-48 of the column's maximum).  F is cut into six
+// signed 8-bit digits, F = sum_p d_p 2^(40 - 8p), each rounded to nearest from the remainder, so
+// that |d_p| <= 128 and bfloat16 holds every digit exactly.  Slice p stores E_p = d_p 2^(12 - 8p)
+// (exact), so a' = 2^-19 sum_p E_p and, for two columns,
+//   a'_i a'_j = 2^-38 sum_(p, q) E_p(i) E_q(j),
+// where a product E_p E_q = d_p d_q 2^(24 - 8(p + q)) depends on the digit order t = p + q only.
+// The pairs with t <= 5 are kept (21 of 36; the others lie below 2^-48 of the leading term).
+//
+// Exactness: a float32 accumulator holds a sum of products of one order t exactly while the
+// integer sum S_t = sum d_p d_q stays below 2^24 in magnitude: every product is a multiple of
+// 2^(24 - 8t) and every partial sum is then representable, whatever the order of the additions
+// inside the tensor core.  With |d_p d_q| <= 2^14 and t + 1 pairs of order t, a window of 256 rows
+// of SX keeps orders 0, 1 and 2 below 2^24 (3 x 256 x 2^14 < 2^24), so each gets its own
+// accumulator; orders 3..5 share a fourth (its float32 rounding lies 2^-24 below order 3, itself
+// 2^-24 below the leading order).  After every window the epilogue warps read the four
+// accumulators from TMEM and add them, converted exactly (orders 0-2) or rounded to an integer
+// (orders 3+), to int64 running sums:
+//   T = sum over windows of 2^24 S_0 + 2^16 S_1 + 2^8 S_2 + round(S_3 + 2^-8 S_4 + 2^-16 S_5),
+// and G_ij = 2^(e_i + e_j - 38) T_ij.  Integer sums are exact in any order, so G does not depend
+// on how the rows are split over CTAs.
+//
+// gram_tc_kernel: one 128 x 64 tile of the lower triangle of G over a range of rows of SX per CTA
+// (320 threads, one CTA per SM):
+//   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and columns
+//              32 (w / 4).. of each order's accumulator; int64 running sums in registers.
+//   warp 8     TMA producer: the six A slices (128 columns of SX x 32 rows) and six B slices
+//              (64 columns x 32 rows) per stage, 64-byte swizzle.
+//   warp 9     TMEM owner (two sets of four 64-column accumulators = 512 columns) and MMA issuer:
+//              2 x 21 tcgen05.mma (kind::f16, bfloat16, M = 128, N = 64, K = 16) per stage.
+// The two accumulator sets alternate between windows, so the epilogue of one window overlaps the
+// MMAs of the next.  Every mbarrier wait is bounded; a timeout sets DevState::timeout.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "tc.cuh"
+#include "tmap.cuh"
+
+namespace slso {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kThreadsG = 320;
+constexpr int kBMg = 128;   // tile rows (columns i of SX)
+constexpr int kBNg = 64;    // tile columns (columns j of SX)
+constexpr int kKBg = 32;    // rows of SX per stage: one 64-byte bfloat16 row per slice tile
+constexpr int kSlices = 6;  // 8-bit digits of the 47-bit fixed-point value
+constexpr int kOrders = 4;  // accumulators: digit order 0, 1, 2, and 3..5 together
+constexpr int kWinRows = 256;  // rows of SX per exact window
+constexpr int kKbPerWin = kWinRows / kKBg;
+constexpr int kStagesG = 3;
+constexpr int kEpiWarpsG = 8;
+constexpr int kWarpProdG = 8, kWarpMmaG = 9;
+constexpr uint32_t kASliceBytes = kBMg * 64;  // 8 KB
+constexpr uint32_t kBSliceBytes = kBNg * 64;  // 4 KB
+constexpr uint32_t kStageBytesG = kSlices * (kASliceBytes + kBSliceBytes);
+constexpr uint32_t kBarOffG = kStagesG * kStageBytesG;
+constexpr uint32_t kSmemG = kBarOffG + (2 * kStagesG + 4) * 8 + 16 + 1024;
+constexpr uint32_t kTmemColsG = 2 * kOrders * kBNg;  // 512
+constexpr int kPairs = 21;
+constexpr int kTimeoutIdG = 6;
+constexpr int kSplitBalanceSms = 152;  // GB300's SM count: fixed, so the plan does not depend on the device
+constexpr int64_t kMaxRowsTc = int64_t(1) << 25;  // keeps |T| < 2^63
+
+// The digit pairs (p, q), p + q <= 5, by order; the first pair of each accumulator starts it.
+__constant__ unsigned char c_pair_p[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ unsigned char c_pair_q[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+
+// rint(a 2^(47 - e)) for |a| < 2^e, from a's bits (integer operations only: the float64 pipe is
+// narrow on this part).  Round half away from zero; non-finite a sets bad.
+__device__ __forceinline__ long long fixed47(double a, int e, bool& bad) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a));
+  const int ex = static_cast<int>((u >> 52) & 0x7FFu);
+  if (ex == 0x7FF) {
+    bad = true;
+    return 0;
+  }
+  long long m = static_cast<long long>(u & ((1ull << 52) - 1));
+  int E;  // |a| = m 2^E
+  if (ex == 0) {
+    E = 1 - 1075;
+  } else {
+    m |= 1ll << 52;
+    E = ex - 1075;
+  }
+  const int sh = E + 47 - e;
+  long long F;
+  if (sh >= 0) {
+    F = m * (1ll << sh);  // subnormal columns only; |F| < 2^47 by the choice of e
+  } else {
+    const int rs = -sh;
+    F = rs >= 60 ? 0 : ((m + (1ll << (rs - 1))) >> rs);
+  }
+  return (u >> 63) ? -F : F;
+}
+
+// Slices E_p (p < 6) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
+// (6 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 32; K = rows of SX contiguous); rows
+// j >= d are zero.  Block (x: row block, y: column block): 32 rows x 32 columns of SX; threads (32, 8).
+__global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restrict__ SX, int64_t s, int d, int dpad,
+                                                         int64_t sp, const int* __restrict__ cexp,
+                                                         __nv_bfloat16* __restrict__ E, int* __restrict__ bad_flag) {
+  __shared__ __nv_bfloat16 tile[kSlices][32][34];  // [p][column][row]
+  const int j0 = blockIdx.y * 32;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  bool bad = false;
+  const int j = j0 + tx;
+  const int e = j < d ? cexp[j] : 0;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t i = i0 + rr;
+    long long r = 0;
+    if (j < d && i < s) r = fixed47(SX[i * d + j], e, bad);
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p) {
+      long long q = r;
+      if (p < kSlices - 1) {
+        const int w = 40 - 8 * p;
+        q = (r + (1ll << (w - 1))) >> w;
+        r -= q * (1ll << w);
+      }
+      // E_p = d_p 2^(12 - 8p): exact in float32 and in bfloat16 (|d_p| <= 128)
+      const float scale = __int_as_float((127 + 12 - 8 * p) << 23);  // 2^(12 - 8p)
+      tile[p][tx][rr] = __float2bfloat16_rn(static_cast<float>(q) * scale);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < kSlices; ++p)
+    for (int cc = ty; cc < 32; cc += 8) {
+      const int64_t row = static_cast<int64_t>(p) * dpad + j0 + cc;
+      E[row * sp + i0 + tx] = tile[p][cc][tx];
+    }
+  if (__syncthreads_or(bad) && tx == 0 && ty == 0) atomicOr(bad_flag, 1);
+}
+
+// t-th tile (I, J) of the 128 x 64 tiling of G's lower triangle: row blocks I of 128, then the
+// column blocks J < min(2I + 2, nbJ) that reach the diagonal.
+__device__ __forceinline__ void tc_tile(int t, int nbJ, int& I, int& J) {
+  int i = 0;
+  while (true) {
+    const int cnt = min(2 * i + 2, nbJ);
+    if (t < cnt) break;
+    t -= cnt;
+    ++i;
+  }
+  I = i;
+  J = t;
+}
+
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// CTA = (split q, tile t): blockIdx.x = q tiles + t.  Rows [q kc, min((q + 1) kc, s)) of SX in
+// windows of 256.  part[blockIdx.x][128][64]: the int64 sums T of the tile over those rows.
+__global__ void __launch_bounds__(kThreadsG, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t s,
+                   int dpad, int tiles, int nbJ, int64_t kc, long long* __restrict__ part,
+                   DevState* __restrict__ state) {
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBarOffG);  // TMA bytes of the stage landed
+  uint64_t* empty = full + kStagesG;                               // the MMAs reading it completed
+  uint64_t* acc_full = empty + kStagesG;                           // [2] window accumulated
+  uint64_t* acc_empty = acc_full + 2;                              // [2] epilogue read it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ int s_abort;
+  const volatile int* abort_flag = &s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x / tiles, t = blockIdx.x % tiles;
+  int I, J;
+  tc_tile(t, nbJ, I, J);
+  const int64_t r0 = static_cast<int64_t>(q) * kc;
+  const int64_t r1 = r0 + kc < s ? r0 + kc : s;
+  const int kb0 = static_cast<int>(r0 / kKBg);
+  const int nkb = r1 > r0 ? static_cast<int>((r1 - r0 + kKBg - 1) / kKBg) : 0;
+  const int nwin = (nkb + kKbPerWin - 1) / kKbPerWin;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int i = 0; i < kStagesG; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], kEpiWarpsG);
+    }
+    fence_mbar_init();
+  }
+  if (warp == kWarpMmaG) tmem_alloc(tmem_slot, kTmemColsG);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == kWarpProdG) {
+    if (lane == 0) {
+      int kb = 0;
+      bool ok = true;
+      for (; kb < nkb; ++kb) {
+        const int st = kb % kStagesG;
+        if (!mbar_wait(&empty[st], ((kb / kStagesG) & 1u) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        unsigned char* stage = smem + static_cast<uint32_t>(st) * kStageBytesG;
+        mbar_arrive_expect_tx(&full[st], kStageBytesG);
+        const int x = (kb0 + kb) * kKBg;
+#pragma unroll
+        for (int p = 0; p < kSlices; ++p) {
+          tma_load_2d(stage + p * kASliceBytes, &tmA, &full[st], x, p * dpad + I * kBMg);
+          tma_load_2d(stage + kSlices * kASliceBytes + p * kBSliceBytes, &tmB, &full[st], x, p * dpad + J * kBNg);
+        }
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(&state->timeout, kTimeoutIdG);
+        for (int j = (kb > kStagesG ? kb - kStagesG : 0); j < kb; ++j)  // let issued copies land (bounded)
+          mbar_wait(&full[j % kStagesG], (j / kStagesG) & 1u, nullptr, 50000000ull);
+      }
+    }
+  } else if (warp == kWarpMmaG) {
+    if (lane == 0) {
+      const uint32_t id = idesc(FMT_BF16, FMT_BF16, kBMg, kBNg);
+      int kb = 0;
+      bool ok = true;
+      for (int w = 0; w < nwin && ok; ++w) {
+        const int b = w & 1;
+        if (!mbar_wait(&acc_empty[b], ((w >> 1) & 1u) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dset = tmem_base + static_cast<uint32_t>(b * kOrders * kBNg);
+        const int kb_end = min(nkb, (w + 1) * kKbPerWin);
+        for (int kw = 0; kb < kb_end; ++kb, ++kw) {
+          const int st = kb % kStagesG;
+          if (!mbar_wait(&full[st], (kb / kStagesG) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          unsigned char* stage = smem + static_cast<uint32_t>(st) * kStageBytesG;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
+#pragma unroll
+            for (int pr = 0; pr < kPairs; ++pr) {
+              const int p = c_pair_p[pr], qq = c_pair_q[pr];
+              const int ord = min(p + qq, kOrders - 1);
+              // the first pair of each order starts its accumulator in the window's first K-step
+              const bool first_of_order = (pr == 0 || pr == 1 || pr == 3 || pr == 6);
+              const uint32_t acc = (kw | ks) != 0 || !first_of_order;
+              const uint64_t a = sdesc_sw64(stage + p * kASliceBytes) + o;
+              const uint64_t bd = sdesc_sw64(stage + kSlices * kASliceBytes + qq * kBSliceBytes) + o;
+              mma_f16(dset + static_cast<uint32_t>(ord * kBNg), a, bd, id, acc);
+            }
+          }
+          mma_commit(&empty[st]);
+        }
+        if (ok) mma_commit(&acc_full[b]);
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(&state->timeout, kTimeoutIdG);
+      }
+      // every MMA issued by this thread has completed before TMEM is released
+      if (kb > 0) mbar_wait(&empty[(kb - 1) % kStagesG], ((kb - 1) / kStagesG) & 1u, nullptr, 50000000ull);
+    }
+  } else {  // epilogue warps 0-7
+    const int lg = warp & 3, half = warp >> 2;
+    const uint32_t lane_off = static_cast<uint32_t>(lg * 32) << 16;
+    long long T[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) T[c] = 0;
+    bool ok = true;
+    for (int w = 0; w < nwin; ++w) {
+      const int b = w & 1;
+      int got = 0;
+      if (lane == 0) got = mbar_wait(&acc_full[b], (w >> 1) & 1u, abort_flag) ? 1 : 0;
+      got = __shfl_sync(0xFFFFFFFFu, got, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
+      if (!got) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + lane_off + static_cast<uint32_t>(b * kOrders * kBNg + half * 32);
+      uint32_t v[32];
+      // order 0: 2^24 S_0, |S_0| <= 2^22
+      tmem_ld_x32(taddr, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c]) * 0x1p-24f)) * (1ll << 24);
+      // order 1: 2^16 S_1, |S_1| <= 2^23
+      tmem_ld_x32(taddr + kBNg, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c]) * 0x1p-16f)) * (1ll << 16);
+      // order 2: 2^8 S_2, |S_2| < 2^24
+      tmem_ld_x32(taddr + 2 * kBNg, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c]) * 0x1p-8f)) * (1ll << 8);
+      // orders 3..5: S_3 + 2^-8 S_4 + 2^-16 S_5, |.| < 2^25, rounded to an integer
+      tmem_ld_x32(taddr + 3 * kBNg, v);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c])));
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    if (ok) {
+      long long* dst = part + (static_cast<int64_t>(blockIdx.x) * kBMg + lg * 32 + lane) * kBNg + half * 32;
+#pragma unroll
+      for (int c = 0; c < 32; c += 2) *reinterpret_cast<longlong2*>(dst + c) = make_longlong2(T[c], T[c + 1]);
+    } else if (lane == 0) {
+      atomicExch(&s_abort, 1);
+      atomicExch(&state->timeout, kTimeoutIdG);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kWarpMmaG) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemColsG);
+  }
+}
+
+// L[i d + j] (j <= i) = 2^(e_i + e_j - 38) times the sum over splits of T; a non-finite SX entry
+// writes NaN on the diagonal, so that the Cholesky breaks down and the route closes.  Opens the route.
+__global__ void gram_tc_reduce_kernel(const long long* __restrict__ part, int tiles, int splits, int d, int nbJ,
+                                      const int* __restrict__ cexp, const int* __restrict__ bad_flag,
+                                      double* __restrict__ L, DevState* __restrict__ st) {
+  const int64_t total = static_cast<int64_t>(d) * d;
+  const bool bad = *bad_flag != 0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
+    if (j > i) continue;
+    const int I = i / kBMg, J = j / kBNg;
+    int t = 0;
+    for (int r = 0; r < I; ++r) t += min(2 * r + 2, nbJ);
+    t += J;
+    const int64_t off = static_cast<int64_t>(i - I * kBMg) * kBNg + (j - J * kBNg);
+    long long T = 0;
+    for (int qq = 0; qq < splits; ++qq) T += part[(static_cast<int64_t>(qq) * tiles + t) * (kBMg * kBNg) + off];
+    double v = ldexp(static_cast<double>(T), cexp[i] + cexp[j] - 38);
+    if (bad && i == j) v = nan("");
+    L[e] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->gram_ok = 1;
+    st->gram_tried = 1;
+    st->gram_resid = 0.0;
+  }
+}
+
+}  // namespace
+
+bool gram_tc_applies(int64_t s, int64_t d) { return encode_fn() != nullptr && s < kMaxRowsTc && d >= 1; }
+
+void gram_tc_take(Arena& ar, int64_t s, int64_t d, GramTcWork* w) {
+  w->dpad = static_cast<int>(ceil_div(d, kBMg) * kBMg);
+  w->sp = ceil_div(s, 32) * 32;
+  const int nbI = static_cast<int>(ceil_div(d, kBMg));
+  w->nbJ = static_cast<int>(ceil_div(d, kBNg));
+  int tiles = 0;
+  for (int i = 0; i < nbI; ++i) tiles += std::min(2 * i + 2, w->nbJ);
+  w->tiles = tiles;
+  // splits: the smallest count (each split at least two windows) whose CTAs fill GB300's SMs within
+  // 6% of even, else the most even one
+  const int64_t wins = ceil_div(s, kWinRows);
+  double best = 1e30;
+  int best_s = 1;
+  for (int S = 1; S <= 16 && S <= std::max<int64_t>(1, wins / 2); ++S) {
+    const int64_t items = static_cast<int64_t>(tiles) * S;
+    const double waste = static_cast<double>(ceil_div(items, kSplitBalanceSms) * kSplitBalanceSms) /
+                         static_cast<double>(items);
+    if (waste < 1.06) {
+      best_s = S;
+      break;
+    }
+    if (waste < best) {
+      best = waste;
+      best_s = S;
+    }
+  }
+  w->splits = best_s;
+  w->kc = ceil_div(ceil_div(s, best_s), kWinRows) * kWinRows;
+  w->E = ar.take<__nv_bfloat16>(static_cast<size_t>(kSlices) * w->dpad * w->sp);
+  w->part = ar.take<long long>(static_cast<size_t>(w->splits) * tiles * kBMg * kBNg);
+  w->bad = ar.take<int>(1);
+}
+
+slso_status run_gram_tc(Handle& h, const GramTcWork& w, const double* SX, int64_t s, int64_t d, const int* cexp,
+                        double* L, cudaStream_t st) {
+  const int d_i = static_cast<int>(d);
+  SLSO_CHECK_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), st));
+  const dim3 gs(static_cast<unsigned>(w.sp / 32), static_cast<unsigned>(w.dpad / 32));
+  gram_slice_kernel<<<gs, dim3(32, 8), 0, st>>>(SX, s, d_i, w.dpad, w.sp, cexp, w.E, w.bad);
+  SLSO_CHECK_LAUNCH();
+  CUtensorMap mA, mB;
+  const uint64_t rows = static_cast<uint64_t>(kSlices) * w.dpad;
+  bool ok = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, s, rows, w.sp * 2, kKBg, kBMg,
+                     CU_TENSOR_MAP_SWIZZLE_64B) &&
+            make_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, s, rows, w.sp * 2, kKBg, kBNg,
+                     CU_TENSOR_MAP_SWIZZLE_64B);
+  if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Gram slices");
+  SLSO_TRY(raise_smem_limit(gram_tc_kernel, kSmemG));
+  gram_tc_kernel<<<static_cast<unsigned>(w.tiles * w.splits), kThreadsG, kSmemG, st>>>(
+      mA, mB, s, w.dpad, w.tiles, w.nbJ, w.kc, w.part, h.state);
+  SLSO_CHECK_LAUNCH();
+  const int64_t total = d * d;
+  const unsigned rb = static_cast<unsigned>(std::min<int64_t>(ceil_div(total, 256), static_cast<int64_t>(h.num_sms) * 8));
+  gram_tc_reduce_kernel<<<rb, 256, 0, st>>>(w.part, w.tiles, w.splits, d_i, w.nbJ, cexp, w.bad, L, h.state);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
+
+}  // namespace slso

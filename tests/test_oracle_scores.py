@@ -351,3 +351,34 @@ def test_partial_householder_steps_are_a_prefix():
     R = O.householder_r(A)
     Rp = O.householder_r(A, steps=5)
     np.testing.assert_allclose(Rp[:5], R[:5], atol=1e-13)
+
+
+def _gram_fractions(A):
+    """SX^T SX in exact rationals, each entry rounded once to float64 (Fraction -> float rounds
+    to nearest)."""
+    F = [[Fraction(float(v)) for v in row] for row in A]
+    s, d = len(F), len(F[0])
+    G = np.empty((d, d))
+    for i in range(d):
+        for j in range(d):
+            G[i, j] = float(sum(F[r][i] * F[r][j] for r in range(s)))
+    return G
+
+
+@pytest.mark.parametrize("case", ["gaussian", "spread", "integers", "zero_column", "tiny"])
+def test_gram_is_the_exactly_rounded_sx_t_sx(case):
+    rng = np.random.default_rng(7)
+    if case == "gaussian":
+        A = rng.standard_normal((37, 6))
+    elif case == "spread":  # entries over 30 binary orders within each column, mixed signs
+        A = rng.standard_normal((41, 5)) * np.exp2(rng.integers(-30, 1, size=(41, 5)))
+    elif case == "integers":
+        A = rng.integers(-(2**16) + 1, 2**16, size=(29, 4)).astype(np.float64)
+    elif case == "zero_column":
+        A = rng.standard_normal((23, 4))
+        A[:, 2] = 0.0
+    else:  # columns scaled far below 1 and far above (cross products of order 1, squares near the ends)
+        A = rng.standard_normal((19, 3)) * np.array([1e-160, 1.0, 1e150])
+    G = O.gram(A)
+    np.testing.assert_array_equal(G, _gram_fractions(A))
+    assert np.array_equal(G, G.T)
