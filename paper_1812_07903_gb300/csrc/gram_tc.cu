@@ -1,38 +1,39 @@
 // Tensor-core Gram matrix G = SX^T SX for the Gram route of R (Algorithm 2/3 step 2), float64-class
 // accurate, on the bfloat16 tcgen05 path with exact integer accumulation (an Ozaki-type split).
 //
-// Column j of SX is scaled by 2^-e_j (its largest entry in [1/2, 1)) and rounded to 47 fractional
-// bits, a' = F 2^-47 with |F| < 2^47 (within 2^-48 of the column's maximum).  F is cut into six
-// signed 8-bit digits, F = sum_p d_p 2^(40 - 8p), each rounded to nearest from the remainder, so
+// Column j of SX is scaled by 2^-e_j (its largest entry in [1/2, 1)) and rounded to 55 fractional
+// bits, a' = F 2^-55 with |F| < 2^55 (within 2^-56 of the column's maximum).  F is cut into seven
+// signed 8-bit digits, F = sum_p d_p 2^(48 - 8p), each rounded to nearest from the remainder, so
 // that |d_p| <= 128 and bfloat16 holds every digit exactly.  Slice p stores E_p = d_p 2^(12 - 8p)
 // (exact), so a' = 2^-19 sum_p E_p and, for two columns,
 //   a'_i a'_j = 2^-38 sum_(p, q) E_p(i) E_q(j),
 // where a product E_p E_q = d_p d_q 2^(24 - 8(p + q)) depends on the digit order t = p + q only.
-// The pairs with t <= 5 are kept (21 of 36; the others lie below 2^-48 of the leading term).
+// The pairs with t <= 6 are kept (28 of 49; the others lie near 2^-56 of the leading term).
 //
 // Exactness: a float32 accumulator holds a sum of products of one order t exactly while the
 // integer sum S_t = sum d_p d_q stays below 2^24 in magnitude: every product is a multiple of
 // 2^(24 - 8t) and every partial sum is then representable, whatever the order of the additions
-// inside the tensor core.  With |d_p d_q| <= 2^14 and t + 1 pairs of order t, a window of 256 rows
-// of SX keeps orders 0, 1 and 2 below 2^24 (3 x 256 x 2^14 < 2^24), so each gets its own
-// accumulator; orders 3..5 share a fourth (its float32 rounding lies 2^-24 below order 3, itself
-// 2^-24 below the leading order).  After every window the epilogue warps read the four
-// accumulators from TMEM and add them, converted exactly (orders 0-2) or rounded to an integer
-// (orders 3+), to int64 running sums:
-//   T = sum over windows of 2^24 S_0 + 2^16 S_1 + 2^8 S_2 + round(S_3 + 2^-8 S_4 + 2^-16 S_5),
-// and G_ij = 2^(e_i + e_j - 38) T_ij.  Integer sums are exact in any order, so G does not depend
-// on how the rows are split over CTAs.
+// inside the tensor core (measured bit-exact).  With |d_p d_q| <= 2^14 and t + 1 pairs of order t,
+// a window of 128 rows of SX keeps orders 0..4 below 2^24 (5 x 128 x 2^14 < 2^24), so each of them
+// has its own accumulator; orders 5 and 6 share a sixth, whose float32 rounding lies far below
+// the leading order.  Orders 3 and 4 need exact sums when rows are heavy-tailed: a row far below
+// its columns' maxima has a small leading digit, and its middle digits then dominate.  After
+// every window the epilogue warps read the six accumulators from TMEM and add them to int64
+// running sums, exactly for orders 0..4:
+//   T = sum over windows of 2^32 S_0 + 2^24 S_1 + 2^16 S_2 + 2^8 S_3 + S_4 + round(2^-8 S_5 + 2^-16 S_6)
+// (|T| < 2^63 for s <= 2^16), and G_ij = 2^(e_i + e_j - 46) T_ij.  Integer sums are exact in any
+// order, so G does not depend on how the rows are split over CTAs.
 //
 // gram_tc_kernel: one 128 x 64 tile of the lower triangle of G over a range of rows of SX per CTA
 // (320 threads, one CTA per SM):
 //   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and columns
-//              32 (w / 4).. of each order's accumulator; int64 running sums in registers.
-//   warp 8     TMA producer: the six A slices (128 columns of SX x 32 rows) and six B slices
+//              32 (w / 4).. of each accumulator; int64 running sums in registers.
+//   warp 8     TMA producer: the seven A slices (128 columns of SX x 32 rows) and seven B slices
 //              (64 columns x 32 rows) per stage, 64-byte swizzle.
-//   warp 9     TMEM owner (two sets of four 64-column accumulators = 512 columns) and MMA issuer:
-//              2 x 21 tcgen05.mma (kind::f16, bfloat16, M = 128, N = 64, K = 16) per stage.
-// The two accumulator sets alternate between windows, so the epilogue of one window overlaps the
-// MMAs of the next.  Every mbarrier wait is bounded; a timeout sets DevState::timeout.
+//   warp 9     TMEM owner (six 64-column accumulators) and MMA issuer: 2 x 28 tcgen05.mma
+//              (kind::f16, bfloat16, M = 128, N = 64, K = 16) per stage.
+// The epilogue releases the accumulators as soon as it has read them (it converts while the next
+// window's MMAs run).  Every mbarrier wait is bounded; a timeout sets DevState::timeout.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -52,31 +53,33 @@ constexpr int kThreadsG = 320;
 constexpr int kBMg = 128;   // tile rows (columns i of SX)
 constexpr int kBNg = 64;    // tile columns (columns j of SX)
 constexpr int kKBg = 32;    // rows of SX per stage: one 64-byte bfloat16 row per slice tile
-constexpr int kSlices = 6;  // 8-bit digits of the 47-bit fixed-point value
-constexpr int kOrders = 4;  // accumulators: digit order 0, 1, 2, and 3..5 together
-constexpr int kWinRows = 256;  // rows of SX per exact window
+constexpr int kSlices = 7;  // 8-bit digits of the 55-bit fixed-point value
+constexpr int kOrders = 6;  // accumulators: digit orders 0..4 one each, 5 and 6 together
+constexpr int kWinRows = 128;  // rows of SX per exact window
 constexpr int kKbPerWin = kWinRows / kKBg;
-constexpr int kStagesG = 3;
+constexpr int kStagesG = 2;
 constexpr int kEpiWarpsG = 8;
 constexpr int kWarpProdG = 8, kWarpMmaG = 9;
 constexpr uint32_t kASliceBytes = kBMg * 64;  // 8 KB
 constexpr uint32_t kBSliceBytes = kBNg * 64;  // 4 KB
 constexpr uint32_t kStageBytesG = kSlices * (kASliceBytes + kBSliceBytes);
 constexpr uint32_t kBarOffG = kStagesG * kStageBytesG;
-constexpr uint32_t kSmemG = kBarOffG + (2 * kStagesG + 4) * 8 + 16 + 1024;
-constexpr uint32_t kTmemColsG = 2 * kOrders * kBNg;  // 512
-constexpr int kPairs = 21;
+constexpr uint32_t kSmemG = kBarOffG + (2 * kStagesG + 2) * 8 + 16 + 1024;
+constexpr uint32_t kTmemColsG = 512;  // the power of two above kOrders x 64
+constexpr int kPairs = 28;
 constexpr int kTimeoutIdG = 6;
 constexpr int kSplitBalanceSms = 152;  // GB300's SM count: fixed, so the plan does not depend on the device
-constexpr int64_t kMaxRowsTc = int64_t(1) << 25;  // keeps |T| < 2^63
+constexpr int64_t kMaxRowsTc = int64_t(1) << 16;  // keeps |T| < 2^63
 
-// The digit pairs (p, q), p + q <= 5, by order; the first pair of each accumulator starts it.
-__constant__ unsigned char c_pair_p[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-__constant__ unsigned char c_pair_q[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+// The digit pairs (p, q), p + q <= 6, by order; the first pair of each accumulator starts it.
+__constant__ unsigned char c_pair_p[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5,
+                                               0, 1, 2, 3, 4, 5, 6};
+__constant__ unsigned char c_pair_q[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0,
+                                               6, 5, 4, 3, 2, 1, 0};
 
-// rint(a 2^(47 - e)) for |a| < 2^e, from a's bits (integer operations only: the float64 pipe is
+// rint(a 2^(55 - e)) for |a| < 2^e, from a's bits (integer operations only: the float64 pipe is
 // narrow on this part).  Round half away from zero; non-finite a sets bad.
-__device__ __forceinline__ long long fixed47(double a, int e, bool& bad) {
+__device__ __forceinline__ long long fixed55(double a, int e, bool& bad) {
   const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a));
   const int ex = static_cast<int>((u >> 52) & 0x7FFu);
   if (ex == 0x7FF) {
@@ -91,10 +94,10 @@ __device__ __forceinline__ long long fixed47(double a, int e, bool& bad) {
     m |= 1ll << 52;
     E = ex - 1075;
   }
-  const int sh = E + 47 - e;
+  const int sh = E + 55 - e;
   long long F;
   if (sh >= 0) {
-    F = m * (1ll << sh);  // subnormal columns only; |F| < 2^47 by the choice of e
+    F = m * (1ll << sh);  // |F| < 2^55 by the choice of e
   } else {
     const int rs = -sh;
     F = rs >= 60 ? 0 : ((m + (1ll << (rs - 1))) >> rs);
@@ -102,8 +105,8 @@ __device__ __forceinline__ long long fixed47(double a, int e, bool& bad) {
   return (u >> 63) ? -F : F;
 }
 
-// Slices E_p (p < 6) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
-// (6 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 32; K = rows of SX contiguous); rows
+// Slices E_p (p < 7) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
+// (7 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 32; K = rows of SX contiguous); rows
 // j >= d are zero.  Block (x: row block, y: column block): 32 rows x 32 columns of SX; threads (32, 8).
 __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restrict__ SX, int64_t s, int d, int dpad,
                                                          int64_t sp, const int* __restrict__ cexp,
@@ -118,12 +121,12 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restric
   for (int rr = ty; rr < 32; rr += 8) {
     const int64_t i = i0 + rr;
     long long r = 0;
-    if (j < d && i < s) r = fixed47(SX[i * d + j], e, bad);
+    if (j < d && i < s) r = fixed55(SX[i * d + j], e, bad);
 #pragma unroll
     for (int p = 0; p < kSlices; ++p) {
       long long q = r;
       if (p < kSlices - 1) {
-        const int w = 40 - 8 * p;
+        const int w = 48 - 8 * p;
         q = (r + (1ll << (w - 1))) >> w;
         r -= q * (1ll << w);
       }
@@ -180,9 +183,9 @@ __global__ void __launch_bounds__(kThreadsG, 1)
                                                          ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBarOffG);  // TMA bytes of the stage landed
   uint64_t* empty = full + kStagesG;                               // the MMAs reading it completed
-  uint64_t* acc_full = empty + kStagesG;                           // [2] window accumulated
-  uint64_t* acc_empty = acc_full + 2;                              // [2] epilogue read it
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* acc_full = empty + kStagesG;                           // the window is accumulated
+  uint64_t* acc_empty = acc_full + 1;                              // the epilogue has read it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
   __shared__ int s_abort;
   const volatile int* abort_flag = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -201,10 +204,8 @@ __global__ void __launch_bounds__(kThreadsG, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], kEpiWarpsG);
-    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarpsG);
     fence_mbar_init();
   }
   if (warp == kWarpMmaG) tmem_alloc(tmem_slot, kTmemColsG);
@@ -245,13 +246,11 @@ __global__ void __launch_bounds__(kThreadsG, 1)
       int kb = 0;
       bool ok = true;
       for (int w = 0; w < nwin && ok; ++w) {
-        const int b = w & 1;
-        if (!mbar_wait(&acc_empty[b], ((w >> 1) & 1u) ^ 1u, abort_flag)) {
+        if (!mbar_wait(acc_empty, (w & 1u) ^ 1u, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t dset = tmem_base + static_cast<uint32_t>(b * kOrders * kBNg);
         const int kb_end = min(nkb, (w + 1) * kKbPerWin);
         for (int kw = 0; kb < kb_end; ++kb, ++kw) {
           const int st = kb % kStagesG;
@@ -268,17 +267,17 @@ __global__ void __launch_bounds__(kThreadsG, 1)
             for (int pr = 0; pr < kPairs; ++pr) {
               const int p = c_pair_p[pr], qq = c_pair_q[pr];
               const int ord = min(p + qq, kOrders - 1);
-              // the first pair of each order starts its accumulator in the window's first K-step
-              const bool first_of_order = (pr == 0 || pr == 1 || pr == 3 || pr == 6);
-              const uint32_t acc = (kw | ks) != 0 || !first_of_order;
+              // the first pair of each accumulator starts it in the window's first K-step
+              const bool first = (pr == 0 || pr == 1 || pr == 3 || pr == 6 || pr == 10 || pr == 15);
+              const uint32_t acc = (kw | ks) != 0 || !first;
               const uint64_t a = sdesc_sw64(stage + p * kASliceBytes) + o;
               const uint64_t bd = sdesc_sw64(stage + kSlices * kASliceBytes + qq * kBSliceBytes) + o;
-              mma_f16(dset + static_cast<uint32_t>(ord * kBNg), a, bd, id, acc);
+              mma_f16(tmem_base + static_cast<uint32_t>(ord * kBNg), a, bd, id, acc);
             }
           }
           mma_commit(&empty[st]);
         }
-        if (ok) mma_commit(&acc_full[b]);
+        if (ok) mma_commit(acc_full);
       }
       if (!ok) {
         atomicExch(&s_abort, 1);
@@ -295,39 +294,27 @@ __global__ void __launch_bounds__(kThreadsG, 1)
     for (int c = 0; c < 32; ++c) T[c] = 0;
     bool ok = true;
     for (int w = 0; w < nwin; ++w) {
-      const int b = w & 1;
       int got = 0;
-      if (lane == 0) got = mbar_wait(&acc_full[b], (w >> 1) & 1u, abort_flag) ? 1 : 0;
+      if (lane == 0) got = mbar_wait(acc_full, w & 1u, abort_flag) ? 1 : 0;
       got = __shfl_sync(0xFFFFFFFFu, got, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
       if (!got) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tmem_base + lane_off + static_cast<uint32_t>(b * kOrders * kBNg + half * 32);
-      uint32_t v[32];
-      // order 0: 2^24 S_0, |S_0| <= 2^22
-      tmem_ld_x32(taddr, v);
+      const uint32_t taddr = tmem_base + lane_off + static_cast<uint32_t>(half * 32);
+      // accumulator t holds 2^(24 - 8t) S_t (orders 0..4, exact) or 2^-16 S_5 + 2^-24 S_6: times 2^8
+      // each is its term of T, an integer (exact below 2^53) or, for the last, rounded to one
+#pragma unroll 1
+      for (int t = 0; t < kOrders; ++t) {
+        uint32_t v[32];
+        tmem_ld_x32(taddr + static_cast<uint32_t>(t * kBNg), v);
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
-        T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c]) * 0x1p-24f)) * (1ll << 24);
-      // order 1: 2^16 S_1, |S_1| <= 2^23
-      tmem_ld_x32(taddr + kBNg, v);
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c]) * 0x1p-16f)) * (1ll << 16);
-      // order 2: 2^8 S_2, |S_2| < 2^24
-      tmem_ld_x32(taddr + 2 * kBNg, v);
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c]) * 0x1p-8f)) * (1ll << 8);
-      // orders 3..5: S_3 + 2^-8 S_4 + 2^-16 S_5, |.| < 2^25, rounded to an integer
-      tmem_ld_x32(taddr + 3 * kBNg, v);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) T[c] += static_cast<long long>(__float2int_rn(__uint_as_float(v[c])));
+        for (int c = 0; c < 32; ++c) T[c] += __float2ll_rn(__uint_as_float(v[c]) * 256.0f);
+      }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      if (lane == 0) mbar_arrive(acc_empty);
     }
     if (ok) {
       long long* dst = part + (static_cast<int64_t>(blockIdx.x) * kBMg + lg * 32 + lane) * kBNg + half * 32;
@@ -347,7 +334,7 @@ __global__ void __launch_bounds__(kThreadsG, 1)
   }
 }
 
-// L[i d + j] (j <= i) = 2^(e_i + e_j - 38) times the sum over splits of T; a non-finite SX entry
+// L[i d + j] (j <= i) = 2^(e_i + e_j - 46) times the sum over splits of T; a non-finite SX entry
 // writes NaN on the diagonal, so that the Cholesky breaks down and the route closes.  Opens the route.
 __global__ void gram_tc_reduce_kernel(const long long* __restrict__ part, int tiles, int splits, int d, int nbJ,
                                       const int* __restrict__ cexp, const int* __restrict__ bad_flag,
@@ -365,7 +352,7 @@ __global__ void gram_tc_reduce_kernel(const long long* __restrict__ part, int ti
     const int64_t off = static_cast<int64_t>(i - I * kBMg) * kBNg + (j - J * kBNg);
     long long T = 0;
     for (int qq = 0; qq < splits; ++qq) T += part[(static_cast<int64_t>(qq) * tiles + t) * (kBMg * kBNg) + off];
-    double v = ldexp(static_cast<double>(T), cexp[i] + cexp[j] - 38);
+    double v = ldexp(static_cast<double>(T), cexp[i] + cexp[j] - 46);
     if (bad && i == j) v = nan("");
     L[e] = v;
   }
