@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libslso.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["handle.cu", "sort.cu", "sketch.cu", "solve.cu", "gram.cu", "gram_tc.cu", "score.cu", "score_tc.cu", "gauss_tc.cu", "basis.cu", "api.cu", "order_static.cu", "sample.cu", "selftest.cu", "server.cu"]
+SOURCES = ["handle.cu", "sort.cu", "sketch.cu", "solve.cu", "gram.cu", "gram_tc.cu", "chol_ff.cu", "score.cu", "score_tc.cu", "gauss_tc.cu", "basis.cu", "api.cu", "order_static.cu", "sample.cu", "selftest.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -463,12 +463,22 @@ struct GramWork {
   float* xl = nullptr;
   bool use_tc = false;      // G from the tensor-core route (gram_tc.cu) instead of the float-float SYRK
   GramTcWork tc;
+  bool use_ff = false;      // Cholesky and R^-1 in float-float (chol_ff.cu) instead of float64
+  float2* Aff = nullptr;    // d x d float-float working matrices of chol_ff
+  float2* Xff = nullptr;
+  unsigned int* cbar = nullptr;
   int splits = 1, tiles = 0, vchunks = 1;
   int64_t kc = 0;
 };
 GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d);
+// With g.use_ff the factor's inverse is written to Rinv (column-major R^-1) as well, and
+// *rinv_done is set; otherwise the caller forms R^-1 from L.
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
-                            int64_t d, double* L, cudaStream_t st);
+                            int64_t d, double* L, double* Rinv, bool* rinv_done, cudaStream_t st);
+// chol_ff.cu: L (G's lower triangle in, R^T out) and Rinv from the float-float Cholesky.
+bool chol_ff_applies(int64_t d);
+slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
+                        unsigned int* bar, cudaStream_t st);
 // G = SX^T SX alone: its lower triangle into L (d x d row-major); run_gram_full also writes the
 // whole symmetric G (d x d row-major).
 slso_status run_gram_matrix(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,

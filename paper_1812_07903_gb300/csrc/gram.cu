@@ -592,6 +592,12 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
   g.colmax = ar.take<unsigned long long>(d);
   g.cexp = ar.take<int>(d);
   g.cscale = ar.take<double>(d);
+  g.use_ff = chol_ff_applies(d);
+  if (g.use_ff) {
+    g.Aff = ar.take<float2>(static_cast<size_t>(d) * d);
+    g.Xff = ar.take<float2>(static_cast<size_t>(d) * d);
+    g.cbar = ar.take<unsigned int>(4);
+  }
   g.use_tc = gram_tc_applies(s, d);
   if (g.use_tc) {
     gram_tc_take(ar, s, d, &g.tc);
@@ -603,10 +609,16 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
 }
 
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
-                            int64_t d, double* L, cudaStream_t st) {
+                            int64_t d, double* L, double* Rinv, bool* rinv_done, cudaStream_t st) {
   SLSO_TRY(run_gram_matrix(h, ar, g, SX, s, d, L, st));
   prof_begin(h, ar, ST_CHOL, st);
-  SLSO_TRY(run_cholesky(h, g, d, L, st));
+  if (g.use_ff) {
+    SLSO_TRY(run_chol_ff(h, L, g.cexp, d, g.Aff, g.Xff, Rinv, g.cbar, st));
+    *rinv_done = true;
+  } else {
+    SLSO_TRY(run_cholesky(h, g, d, L, st));
+    *rinv_done = false;
+  }
   prof_end(h, ar, st);
   return SLSO_OK;
 }

@@ -2,38 +2,36 @@
 // accurate, on the bfloat16 tcgen05 path with exact integer accumulation (an Ozaki-type split).
 //
 // Column j of SX is scaled by 2^-e_j (its largest entry in [1/2, 1)) and rounded to 55 fractional
-// bits, a' = F 2^-55 with |F| < 2^55 (within 2^-56 of the column's maximum).  F is cut into seven
-// signed 8-bit digits, F = sum_p d_p 2^(48 - 8p), each rounded to nearest from the remainder, so
-// that |d_p| <= 128 and bfloat16 holds every digit exactly.  Slice p stores E_p = d_p 2^(12 - 8p)
-// (exact), so a' = 2^-19 sum_p E_p and, for two columns,
-//   a'_i a'_j = 2^-38 sum_(p, q) E_p(i) E_q(j),
-// where a product E_p E_q = d_p d_q 2^(24 - 8(p + q)) depends on the digit order t = p + q only.
-// The pairs with t <= 6 are kept (28 of 49; the others lie near 2^-56 of the leading term).
+// bits, a' = F 2^-55 with |F| < 2^55 (within 2^-56 of the column's maximum).  F is cut into eight
+// signed 7-bit digits, F = sum_p d_p 2^(49 - 7p), each rounded to nearest from the remainder, so
+// that |d_p| <= 64 and bfloat16 holds every digit exactly.  Slice p stores E_p = d_p 2^(21 - 7p)
+// (exact), so for two columns
+//   a'_i a'_j = sum_(p, q) d_p(i) d_q(j) 2^(-12 - 7(p + q)),
+// and a product E_p E_q = d_p d_q 2^(42 - 7(p + q)) depends on the digit order t = p + q only.  The
+// 36 pairs with t <= 7 are kept; the others lie near 2^-56 of the leading term.
 //
 // Exactness: a float32 accumulator holds a sum of products of one order t exactly while the
-// integer sum S_t = sum d_p d_q stays below 2^24 in magnitude: every product is a multiple of
-// 2^(24 - 8t) and every partial sum is then representable, whatever the order of the additions
-// inside the tensor core (measured bit-exact).  With |d_p d_q| <= 2^14 and t + 1 pairs of order t,
-// a window of 128 rows of SX keeps orders 0..4 below 2^24 (5 x 128 x 2^14 < 2^24), so each of them
-// has its own accumulator; orders 5 and 6 share a sixth, whose float32 rounding lies far below
-// the leading order.  Orders 3 and 4 need exact sums when rows are heavy-tailed: a row far below
-// its columns' maxima has a small leading digit, and its middle digits then dominate.  After
-// every window the epilogue warps read the six accumulators from TMEM and add them to int64
-// running sums, exactly for orders 0..4:
-//   T = sum over windows of 2^32 S_0 + 2^24 S_1 + 2^16 S_2 + 2^8 S_3 + S_4 + round(2^-8 S_5 + 2^-16 S_6)
-// (|T| < 2^63 for s <= 2^16), and G_ij = 2^(e_i + e_j - 46) T_ij.  Integer sums are exact in any
-// order, so G does not depend on how the rows are split over CTAs.
+// integer sum S_t = sum d_p d_q stays within 2^24 in magnitude: every product is a multiple of
+// 2^(42 - 7t) and every partial sum is then representable, whatever the order of the additions
+// inside the tensor core (measured bit-exact).  With |d_p d_q| <= 2^12 and at most 8 pairs of one
+// order, a window of 512 rows of SX keeps every order within 2^24 (8 x 512 x 2^12), so each order
+// has its own accumulator and nothing is rounded: also orders 3..7 matter when rows are
+// heavy-tailed (a row far below its columns' maxima has small leading digits, and then its middle
+// digits dominate).  After every window the epilogue warps read the eight accumulators from TMEM
+// and add their exact integers to two int64 running sums per entry,
+//   T_hi = sum 2^21 S_0 + 2^14 S_1 + 2^7 S_2 + S_3,   T_lo = sum 2^21 S_4 + 2^14 S_5 + 2^7 S_6 + S_7
+// (each below 2^53 for s <= 2^20), and G_ij = 2^(e_i + e_j - 33) (T_hi + 2^-28 T_lo), rounded once
+// per entry.  Integer sums are exact in any order, so G does not depend on how the rows are split.
 //
 // gram_tc_kernel: one 128 x 64 tile of the lower triangle of G over a range of rows of SX per CTA
-// (320 threads, one CTA per SM):
-//   warps 0-7  epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and columns
-//              32 (w / 4).. of each accumulator; int64 running sums in registers.
-//   warp 8     TMA producer: the seven A slices (128 columns of SX x 32 rows) and seven B slices
+// (576 threads, one CTA per SM):
+//   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and columns
+//              16 (w / 4).. of each accumulator; two int64 running sums per entry in registers.
+//   warp 16    TMA producer: the eight A slices (128 columns of SX x 32 rows) and eight B slices
 //              (64 columns x 32 rows) per stage, 64-byte swizzle.
-//   warp 9     TMEM owner (six 64-column accumulators) and MMA issuer: 2 x 28 tcgen05.mma
+//   warp 17    TMEM owner (eight 64-column accumulators) and MMA issuer: 2 x 36 tcgen05.mma
 //              (kind::f16, bfloat16, M = 128, N = 64, K = 16) per stage.
-// The epilogue releases the accumulators as soon as it has read them (it converts while the next
-// window's MMAs run).  Every mbarrier wait is bounded; a timeout sets DevState::timeout.
+// Every mbarrier wait is bounded; a timeout sets DevState::timeout.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -49,33 +47,31 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreadsG = 320;
+constexpr int kThreadsG = 576;
 constexpr int kBMg = 128;   // tile rows (columns i of SX)
 constexpr int kBNg = 64;    // tile columns (columns j of SX)
 constexpr int kKBg = 32;    // rows of SX per stage: one 64-byte bfloat16 row per slice tile
-constexpr int kSlices = 7;  // 8-bit digits of the 55-bit fixed-point value
-constexpr int kOrders = 6;  // accumulators: digit orders 0..4 one each, 5 and 6 together
-constexpr int kWinRows = 128;  // rows of SX per exact window
+constexpr int kSlices = 8;  // 7-bit digits of the 56-bit fixed-point value
+constexpr int kOrders = 8;  // accumulators: one per digit order 0..7
+constexpr int kWinRows = 512;  // rows of SX per exact window
 constexpr int kKbPerWin = kWinRows / kKBg;
 constexpr int kStagesG = 2;
-constexpr int kEpiWarpsG = 8;
-constexpr int kWarpProdG = 8, kWarpMmaG = 9;
+constexpr int kEpiWarpsG = 16;
+constexpr int kWarpProdG = 16, kWarpMmaG = 17;
 constexpr uint32_t kASliceBytes = kBMg * 64;  // 8 KB
 constexpr uint32_t kBSliceBytes = kBNg * 64;  // 4 KB
 constexpr uint32_t kStageBytesG = kSlices * (kASliceBytes + kBSliceBytes);
 constexpr uint32_t kBarOffG = kStagesG * kStageBytesG;
 constexpr uint32_t kSmemG = kBarOffG + (2 * kStagesG + 2) * 8 + 16 + 1024;
-constexpr uint32_t kTmemColsG = 512;  // the power of two above kOrders x 64
-constexpr int kPairs = 28;
+constexpr uint32_t kTmemColsG = kOrders * kBNg;  // 512
+constexpr int kPairs = 36;
 constexpr int kTimeoutIdG = 6;
 constexpr int kSplitBalanceSms = 152;  // GB300's SM count: fixed, so the plan does not depend on the device
-constexpr int64_t kMaxRowsTc = int64_t(1) << 16;  // keeps |T| < 2^63
+constexpr int64_t kMaxRowsTc = int64_t(1) << 20;  // keeps |T_hi|, |T_lo| < 2^53
 
-// The digit pairs (p, q), p + q <= 6, by order; the first pair of each accumulator starts it.
-__constant__ unsigned char c_pair_p[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5,
-                                               0, 1, 2, 3, 4, 5, 6};
-__constant__ unsigned char c_pair_q[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0,
-                                               6, 5, 4, 3, 2, 1, 0};
+// The digit pairs (p, q), p + q <= 7, by order; the first pair of each order starts its accumulator.
+__constant__ unsigned char c_pair_p[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2,
+                                               3, 4, 5, 0, 1, 2, 3, 4, 5, 6, 0, 1, 2, 3, 4, 5, 6, 7};
 
 // rint(a 2^(55 - e)) for |a| < 2^e, from a's bits (integer operations only: the float64 pipe is
 // narrow on this part).  Round half away from zero; non-finite a sets bad.
@@ -105,8 +101,8 @@ __device__ __forceinline__ long long fixed55(double a, int e, bool& bad) {
   return (u >> 63) ? -F : F;
 }
 
-// Slices E_p (p < 7) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
-// (7 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 32; K = rows of SX contiguous); rows
+// Slices E_p (p < 8) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
+// (8 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 32; K = rows of SX contiguous); rows
 // j >= d are zero.  Block (x: row block, y: column block): 32 rows x 32 columns of SX; threads (32, 8).
 __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restrict__ SX, int64_t s, int d, int dpad,
                                                          int64_t sp, const int* __restrict__ cexp,
@@ -126,12 +122,12 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restric
     for (int p = 0; p < kSlices; ++p) {
       long long q = r;
       if (p < kSlices - 1) {
-        const int w = 48 - 8 * p;
+        const int w = 49 - 7 * p;
         q = (r + (1ll << (w - 1))) >> w;
         r -= q * (1ll << w);
       }
-      // E_p = d_p 2^(12 - 8p): exact in float32 and in bfloat16 (|d_p| <= 128)
-      const float scale = __int_as_float((127 + 12 - 8 * p) << 23);  // 2^(12 - 8p)
+      // E_p = d_p 2^(21 - 7p): exact in float32 and in bfloat16 (|d_p| <= 64)
+      const float scale = __int_as_float((127 + 21 - 7 * p) << 23);  // 2^(21 - 7p)
       tile[p][tx][rr] = __float2bfloat16_rn(static_cast<float>(q) * scale);
     }
   }
@@ -159,21 +155,18 @@ __device__ __forceinline__ void tc_tile(int t, int nbJ, int& I, int& J) {
   J = t;
 }
 
-__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, uint32_t* r) {
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // CTA = (split q, tile t): blockIdx.x = q tiles + t.  Rows [q kc, min((q + 1) kc, s)) of SX in
-// windows of 256.  part[blockIdx.x][128][64]: the int64 sums T of the tile over those rows.
+// windows of 256.  part[blockIdx.x][128][64][2]: the int64 sums (T_hi, T_lo) of the tile over those rows.
 __global__ void __launch_bounds__(kThreadsG, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t s,
                    int dpad, int tiles, int nbJ, int64_t kc, long long* __restrict__ part,
@@ -265,10 +258,11 @@ __global__ void __launch_bounds__(kThreadsG, 1)
             const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
 #pragma unroll
             for (int pr = 0; pr < kPairs; ++pr) {
-              const int p = c_pair_p[pr], qq = c_pair_q[pr];
-              const int ord = min(p + qq, kOrders - 1);
-              // the first pair of each accumulator starts it in the window's first K-step
-              const bool first = (pr == 0 || pr == 1 || pr == 3 || pr == 6 || pr == 10 || pr == 15);
+              // pairs by order t: indices t (t + 1) / 2 .. + t, p ascending, q = t - p
+              const int ord = pr < 1 ? 0 : pr < 3 ? 1 : pr < 6 ? 2 : pr < 10 ? 3 : pr < 15 ? 4 : pr < 21 ? 5 : pr < 28 ? 6 : 7;
+              const int p = c_pair_p[pr], qq = ord - p;
+              // the first pair of each order starts its accumulator in the window's first K-step
+              const bool first = pr == ord * (ord + 1) / 2;
               const uint32_t acc = (kw | ks) != 0 || !first;
               const uint64_t a = sdesc_sw64(stage + p * kASliceBytes) + o;
               const uint64_t bd = sdesc_sw64(stage + kSlices * kASliceBytes + qq * kBSliceBytes) + o;
@@ -286,12 +280,12 @@ __global__ void __launch_bounds__(kThreadsG, 1)
       // every MMA issued by this thread has completed before TMEM is released
       if (kb > 0) mbar_wait(&empty[(kb - 1) % kStagesG], ((kb - 1) / kStagesG) & 1u, nullptr, 50000000ull);
     }
-  } else {  // epilogue warps 0-7
-    const int lg = warp & 3, half = warp >> 2;
+  } else {  // epilogue warps 0-15
+    const int lg = warp & 3, cq = warp >> 2;
     const uint32_t lane_off = static_cast<uint32_t>(lg * 32) << 16;
-    long long T[32];
+    long long Th[16], Tl[16];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) T[c] = 0;
+    for (int c = 0; c < 16; ++c) Th[c] = Tl[c] = 0;
     bool ok = true;
     for (int w = 0; w < nwin; ++w) {
       int got = 0;
@@ -302,24 +296,29 @@ __global__ void __launch_bounds__(kThreadsG, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tmem_base + lane_off + static_cast<uint32_t>(half * 32);
-      // accumulator t holds 2^(24 - 8t) S_t (orders 0..4, exact) or 2^-16 S_5 + 2^-24 S_6: times 2^8
-      // each is its term of T, an integer (exact below 2^53) or, for the last, rounded to one
-#pragma unroll 1
-      for (int t = 0; t < kOrders; ++t) {
-        uint32_t v[32];
-        tmem_ld_x32(taddr + static_cast<uint32_t>(t * kBNg), v);
+      const uint32_t taddr = tmem_base + lane_off + static_cast<uint32_t>(cq * 16);
+      // accumulator t holds 2^(42 - 7t) S_t exactly, |S_t| <= 2^24
 #pragma unroll
-        for (int c = 0; c < 32; ++c) T[c] += __float2ll_rn(__uint_as_float(v[c]) * 256.0f);
+      for (int t = 0; t < kOrders; ++t) {
+        uint32_t v[16];
+        tmem_ld_x16(taddr + static_cast<uint32_t>(t * kBNg), v);
+        const float unscale = __int_as_float((127 - 42 + 7 * t) << 23);  // 2^(7t - 42)
+        const long long wgt = 1ll << (7 * (3 - (t & 3)));
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const long long S = __float2int_rn(__uint_as_float(v[c]) * unscale);
+          if (t < 4) Th[c] += S * wgt;
+          else Tl[c] += S * wgt;
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty);
     }
     if (ok) {
-      long long* dst = part + (static_cast<int64_t>(blockIdx.x) * kBMg + lg * 32 + lane) * kBNg + half * 32;
+      long long* dst = part + ((static_cast<int64_t>(blockIdx.x) * kBMg + lg * 32 + lane) * kBNg + cq * 16) * 2;
 #pragma unroll
-      for (int c = 0; c < 32; c += 2) *reinterpret_cast<longlong2*>(dst + c) = make_longlong2(T[c], T[c + 1]);
+      for (int c = 0; c < 16; ++c) *reinterpret_cast<longlong2*>(dst + 2 * c) = make_longlong2(Th[c], Tl[c]);
     } else if (lane == 0) {
       atomicExch(&s_abort, 1);
       atomicExch(&state->timeout, kTimeoutIdG);
@@ -334,8 +333,9 @@ __global__ void __launch_bounds__(kThreadsG, 1)
   }
 }
 
-// L[i d + j] (j <= i) = 2^(e_i + e_j - 46) times the sum over splits of T; a non-finite SX entry
-// writes NaN on the diagonal, so that the Cholesky breaks down and the route closes.  Opens the route.
+// L[i d + j] (j <= i) = 2^(e_i + e_j - 33) (T_hi + 2^-28 T_lo) with the sums over splits; a
+// non-finite SX entry writes NaN on the diagonal, so that the Cholesky breaks down and the route
+// closes.  Opens the route.
 __global__ void gram_tc_reduce_kernel(const long long* __restrict__ part, int tiles, int splits, int d, int nbJ,
                                       const int* __restrict__ cexp, const int* __restrict__ bad_flag,
                                       double* __restrict__ L, DevState* __restrict__ st) {
@@ -349,10 +349,15 @@ __global__ void gram_tc_reduce_kernel(const long long* __restrict__ part, int ti
     int t = 0;
     for (int r = 0; r < I; ++r) t += min(2 * r + 2, nbJ);
     t += J;
-    const int64_t off = static_cast<int64_t>(i - I * kBMg) * kBNg + (j - J * kBNg);
-    long long T = 0;
-    for (int qq = 0; qq < splits; ++qq) T += part[(static_cast<int64_t>(qq) * tiles + t) * (kBMg * kBNg) + off];
-    double v = ldexp(static_cast<double>(T), cexp[i] + cexp[j] - 46);
+    const int64_t off = (static_cast<int64_t>(i - I * kBMg) * kBNg + (j - J * kBNg)) * 2;
+    long long Th = 0, Tl = 0;
+    for (int qq = 0; qq < splits; ++qq) {
+      const longlong2 v = *reinterpret_cast<const longlong2*>(part + (static_cast<int64_t>(qq) * tiles + t) *
+                                                                          (kBMg * kBNg * 2) + off);
+      Th += v.x;
+      Tl += v.y;
+    }
+    double v = ldexp(static_cast<double>(Th) + ldexp(static_cast<double>(Tl), -28), cexp[i] + cexp[j] - 33);
     if (bad && i == j) v = nan("");
     L[e] = v;
   }
@@ -396,7 +401,7 @@ void gram_tc_take(Arena& ar, int64_t s, int64_t d, GramTcWork* w) {
   w->splits = best_s;
   w->kc = ceil_div(ceil_div(s, best_s), kWinRows) * kWinRows;
   w->E = ar.take<__nv_bfloat16>(static_cast<size_t>(kSlices) * w->dpad * w->sp);
-  w->part = ar.take<long long>(static_cast<size_t>(w->splits) * tiles * kBMg * kBNg);
+  w->part = ar.take<long long>(static_cast<size_t>(w->splits) * tiles * kBMg * kBNg * 2);
   w->bad = ar.take<int>(1);
 }
 

@@ -1331,12 +1331,15 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   // trinv_kernel keeps one column of R^-1 in shared memory: d doubles, above 48 KB for d > 6144
   SLSO_TRY(raise_smem_limit(trinv_kernel, sizeof(double) * d));
   if (gram) {
-    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, st));
+    bool rinv_done = false;
+    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, Rinv, &rinv_done, st));
     prof_begin(h, ar, ST_CHOL, st);
-    inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, invd, gram_ok, 1);
-    SLSO_CHECK_LAUNCH();
-    trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rc, d, d, nullptr, invd, Rinv, gram_ok, 1);
-    SLSO_CHECK_LAUNCH();
+    if (!rinv_done) {
+      inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, invd, gram_ok, 1);
+      SLSO_CHECK_LAUNCH();
+      trinv_kernel<<<static_cast<unsigned>(d), 256, sizeof(double) * d, st>>>(Rc, d, d, nullptr, invd, Rinv, gram_ok, 1);
+      SLSO_CHECK_LAUNCH();
+    }
     SLSO_TRY(run_gram_check(h, gw, SX, s, d, Rinv, st));
     prof_end(h, ar, st);
   }
