@@ -178,6 +178,41 @@ __device__ void tile_product(Smem& sm, float2* Y, int d, int r0, int c0, bool ad
   }
 }
 
+// acc[q] += sum_m P[m][i] Q[m][j0 + q] for this thread's row i = t / 8, columns j0 = 4 (t % 8) .. + 4.
+__device__ void tile_accumulate(const Smem& sm, ff* acc) {
+  const int t = threadIdx.x, i = t >> 3, j0 = (t & 7) * 4;
+  float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int m = 0; m < kFb; ++m) {
+    const float ah = sm.Ph[m][i], al = sm.Pl[m][i];
+    const float4 bh = *reinterpret_cast<const float4*>(&sm.Qh[m][j0]);
+    const float4 bl = *reinterpret_cast<const float4*>(&sm.Ql[m][j0]);
+    dot_term(ah, al, bh.x, bl.x, S[0], C[0]);
+    dot_term(ah, al, bh.y, bl.y, S[1], C[1]);
+    dot_term(ah, al, bh.z, bl.z, S[2], C[2]);
+    dot_term(ah, al, bh.w, bl.w, S[3], C[3]);
+    if ((m & 15) == 15) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+        S[q] = 0.f;
+        C[q] = 0.f;
+      }
+    }
+  }
+}
+
+// P[m][i] = Y[r0 + m][c0 + i] (zero beyond d)
+__device__ void load_p_rows(Smem& sm, const float2* Y, int d, int r0, int c0) {
+  for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
+    const int m = e >> 5, i = e & 31;
+    float2 v = make_float2(0.f, 0.f);
+    if (r0 + m < d && c0 + i < d) v = Y[static_cast<int64_t>(r0 + m) * d + c0 + i];
+    sm.Ph[m][i] = v.x;
+    sm.Pl[m][i] = v.y;
+  }
+}
+
 // P[m][i] = Y[r0 + i][c0 + m] (zero beyond d)
 __device__ void load_rows_t(Smem& sm, const float2* Y, int d, int r0, int c0) {
   for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
@@ -277,9 +312,15 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
 }
 
 // bar[0..1] grid barrier, bar[2] abort flag (zeroed by the host before the launch).
+// Right-hand sides after the factorisation (every CTA, tasks of 32 x 32 outputs): with the JL
+// matrix Pi (d x k, k > 0) and the probes Z (d x 4), both float64 row-major, Out = X'^T [Pi | Z]
+// (Out_ic = sum over m >= i of X'_mi [Pi | Z]_mc) gives M = R^-1 Pi = diag(2^-e) Out[:, :k] (float64,
+// d x k row-major; st->m_ready = 1) and Y'' = X'^T Z (float-float, d x 4) for the probe check.
 __global__ void __launch_bounds__(kFThreads, 1)
     chol_ff_kernel(double* __restrict__ L, const int* __restrict__ cexp, int d, float2* __restrict__ A,
-                   float2* __restrict__ X, double* __restrict__ Rinv, unsigned int* bar, DevState* __restrict__ st) {
+                   float2* __restrict__ X, double* __restrict__ Rinv, const double* __restrict__ Pi, int k,
+                   const double* __restrict__ Z, double* __restrict__ M, float2* __restrict__ Yff, unsigned int* bar,
+                   DevState* __restrict__ st) {
   if (*reinterpret_cast<volatile int32_t*>(&st->gram_ok) == 0) return;  // grid-uniform
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -372,6 +413,41 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
     if (!sync_all()) return;
   }
+  // Out = X'^T [Pi | Z]: output tiles (I, Cb), I over row blocks, Cb over 32-column blocks of [Pi | Z]
+  {
+    const int width = k + 4, ncb = (width + kFb - 1) / kFb;
+    for (int task = blockIdx.x; task < nb * ncb; task += gridDim.x) {
+      const int I = task / ncb, Cb = task % ncb;
+      const int i0 = I * kFb, c0 = Cb * kFb;
+      ff acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
+      for (int mb = I; mb < nb; ++mb) {
+        __syncthreads();
+        load_p_rows(sm, X, d, mb * kFb, i0);  // P[m][i] = X'[mb 32 + m][i0 + i]
+        for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
+          const int m = e >> 5, j = e & 31;  // Q[m][j] = [Pi | Z][mb 32 + m][c0 + j]
+          const int r = mb * kFb + m, c = c0 + j;
+          double v = 0.0;
+          if (r < d) v = c < k ? Pi[static_cast<int64_t>(r) * k + c] : (c < width ? Z[r * 4 + (c - k)] : 0.0);
+          const float h = __double2float_rn(v);
+          sm.Qh[m][j] = h;
+          sm.Ql[m][j] = __double2float_rn(v - static_cast<double>(h));
+        }
+        __syncthreads();
+        tile_accumulate(sm, acc);
+      }
+      const int i = i0 + (threadIdx.x >> 3), j0 = c0 + (threadIdx.x & 7) * 4;
+      if (i < d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = j0 + q;
+          if (c < k) M[static_cast<int64_t>(i) * k + c] = ldexp(static_cast<double>(acc[q].h) + static_cast<double>(acc[q].l), -cexp[i]);
+          else if (c < width) Yff[i * 4 + (c - k)] = make_float2(acc[q].h, acc[q].l);
+        }
+    }
+    if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) st->m_ready = 1;
+  }
   // L = D^-1 L' (row i times 2^e_i) and R^-1 = X^T with X = X' D (column i of X' times 2^-e_i)
   for (int64_t e = gtid; e < dd; e += gstride) {
     const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
@@ -384,14 +460,199 @@ __global__ void __launch_bounds__(kFThreads, 1)
   }
 }
 
+// ------------------------------------------------------------------ probe check in float-float
+// With SX' = SX D (column j times 2^-e_j, every entry in (-1, 1)), X' = L'^-1 and Y'' = X'^T Z, the
+// probe residual F Z = R^-T SX^T SX R^-1 Z - Z equals X' (SX'^T (SX' Y'')) - Z: every power of two
+// cancels, so float32's range suffices.  SX is read in float64 and split exactly into a float pair
+// with integer operations.
+
+// a 2^-e as hi + lo (hi: the leading 24 bits rounded, lo: the remaining 29 bits rounded to 24).
+__device__ __forceinline__ ff split_scaled(double a, int e) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a));
+  const int ex = static_cast<int>((u >> 52) & 0x7FFu);
+  if (ex == 0x7FF) return {CUDART_NAN_F, 0.f};
+  if (ex == 0) {  // zero or subnormal: the float64 path (rare)
+    const double v = ldexp(a, -e);
+    const float h = __double2float_rn(v);
+    return {h, __double2float_rn(v - static_cast<double>(h))};
+  }
+  const long long m = static_cast<long long>((u & ((1ull << 52) - 1)) | (1ull << 52));
+  const int E = ex - 1075 - e;  // |a 2^-e| = m 2^E
+  const long long hi = (m + (1ll << 28)) >> 29;
+  const long long lo = m - hi * (1ll << 29);
+  float fh = ldexpf(static_cast<float>(hi), E + 29);
+  float fl = ldexpf(static_cast<float>(lo), E);
+  if (u >> 63) {
+    fh = -fh;
+    fl = -fl;
+  }
+  return {fh, fl};
+}
+
+// W[r] = SX'_r . Y'' (4 probes, float-float): one warp per row.
+__global__ void __launch_bounds__(256) probe_w_ff_kernel(const double* __restrict__ SX, int64_t s, int d,
+                                                         const int* __restrict__ cexp, const float2* __restrict__ Yff,
+                                                         float2* __restrict__ Wff, const DevState* __restrict__ st) {
+  if (*reinterpret_cast<const volatile int32_t*>(&st->gram_ok) == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= s) return;
+  const double* row = SX + r * d;
+  float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+  ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  int cnt = 0;
+  for (int j = lane; j < d; j += 32) {
+    const ff a = split_scaled(row[j], cexp[j]);
+    const float4 y0 = *reinterpret_cast<const float4*>(Yff + 4 * j);      // probes 0, 1
+    const float4 y1 = *reinterpret_cast<const float4*>(Yff + 4 * j + 2);  // probes 2, 3
+    dot_term(a.h, a.l, y0.x, y0.y, S[0], C[0]);
+    dot_term(a.h, a.l, y0.z, y0.w, S[1], C[1]);
+    dot_term(a.h, a.l, y1.x, y1.y, S[2], C[2]);
+    dot_term(a.h, a.l, y1.z, y1.w, S[3], C[3]);
+    if ((++cnt & 15) == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+        S[q] = C[q] = 0.f;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ff v = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const ff w{__shfl_xor_sync(0xFFFFFFFFu, v.h, o), __shfl_xor_sync(0xFFFFFFFFu, v.l, o)};
+      v = ff_add(v, w);
+    }
+    if (lane == 0) Wff[r * 4 + q] = make_float2(v.h, v.l);
+  }
+}
+
+// vpart[b][j][q] = sum over the rows r of chunk b of SX'[r, j] W[r, q] (float-float).
+__global__ void __launch_bounds__(256) probe_v_ff_kernel(const double* __restrict__ SX, int64_t s, int d,
+                                                         const int* __restrict__ cexp, const float2* __restrict__ Wff,
+                                                         int64_t rows_per_chunk, float2* __restrict__ vpart,
+                                                         const DevState* __restrict__ st) {
+  if (*reinterpret_cast<const volatile int32_t*>(&st->gram_ok) == 0) return;
+  const int64_t r0 = blockIdx.x * rows_per_chunk;
+  const int64_t r1 = r0 + rows_per_chunk < s ? r0 + rows_per_chunk : s;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const int e = cexp[j];
+    float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+    ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int cnt = 0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const ff a = split_scaled(SX[r * d + j], e);
+      const float4 w0 = *reinterpret_cast<const float4*>(Wff + 4 * r);
+      const float4 w1 = *reinterpret_cast<const float4*>(Wff + 4 * r + 2);
+      dot_term(a.h, a.l, w0.x, w0.y, S[0], C[0]);
+      dot_term(a.h, a.l, w0.z, w0.w, S[1], C[1]);
+      dot_term(a.h, a.l, w1.x, w1.y, S[2], C[2]);
+      dot_term(a.h, a.l, w1.z, w1.w, S[3], C[3]);
+      if ((++cnt & 15) == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+          S[q] = C[q] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const ff v = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+      vpart[(static_cast<int64_t>(blockIdx.x) * d + j) * 4 + q] = make_float2(v.h, v.l);
+    }
+  }
+}
+
+// V''[j][q] = the chunk partials added in chunk order.
+__global__ void probe_vsum_ff_kernel(const float2* __restrict__ vpart, int chunks, int d, float2* __restrict__ V,
+                                     const DevState* __restrict__ st) {
+  if (*reinterpret_cast<const volatile int32_t*>(&st->gram_ok) == 0) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d * 4) return;
+  ff v{0.f, 0.f};
+  for (int b = 0; b < chunks; ++b) {
+    const float2 p = vpart[static_cast<int64_t>(b) * d * 4 + e];
+    v = ff_add(v, ff{p.x, p.y});
+  }
+  V[e] = make_float2(v.h, v.l);
+}
+
+// eres[c] = sum_q ((X' V'')_cq - Z_cq)^2 (float64 at the end): one CTA of 128 threads per row c.
+__global__ void __launch_bounds__(128) probe_u_ff_kernel(const float2* __restrict__ X, int d,
+                                                         const float2* __restrict__ V, const double* __restrict__ Z,
+                                                         double* __restrict__ eres, const DevState* __restrict__ st) {
+  if (*reinterpret_cast<const volatile int32_t*>(&st->gram_ok) == 0) return;
+  __shared__ float2 red[4][4];
+  const int c = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+  ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  int cnt = 0;
+  for (int i = threadIdx.x; i <= c; i += blockDim.x) {
+    const float2 x = X[static_cast<int64_t>(c) * d + i];
+    const float4 v0 = *reinterpret_cast<const float4*>(V + 4 * i);
+    const float4 v1 = *reinterpret_cast<const float4*>(V + 4 * i + 2);
+    dot_term(x.x, x.y, v0.x, v0.y, S[0], C[0]);
+    dot_term(x.x, x.y, v0.z, v0.w, S[1], C[1]);
+    dot_term(x.x, x.y, v1.x, v1.y, S[2], C[2]);
+    dot_term(x.x, x.y, v1.z, v1.w, S[3], C[3]);
+    if ((++cnt & 15) == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+        S[q] = C[q] = 0.f;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ff v = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const ff u{__shfl_xor_sync(0xFFFFFFFFu, v.h, o), __shfl_xor_sync(0xFFFFFFFFu, v.l, o)};
+      v = ff_add(v, u);
+    }
+    if (lane == 0) red[w][q] = make_float2(v.h, v.l);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double e = 0.0;
+    for (int q = 0; q < 4; ++q) {
+      ff u{0.f, 0.f};
+      for (int ww = 0; ww < 4; ++ww) u = ff_add(u, ff{red[ww][q].x, red[ww][q].y});
+      const double diff = (static_cast<double>(u.h) + static_cast<double>(u.l)) - Z[c * 4 + q];
+      e = fma(diff, diff, e);
+    }
+    eres[c] = e;
+  }
+}
+
 }  // namespace
+
+slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, const int* cexp, const float2* X,
+                         const float2* Yff, float2* Wff, float2* vpart, int chunks, float2* Vff, const double* Z,
+                         double* eres, cudaStream_t st) {
+  const int d_i = static_cast<int>(d);
+  probe_w_ff_kernel<<<static_cast<unsigned>(ceil_div(s, 8)), 256, 0, st>>>(SX, s, d_i, cexp, Yff, Wff, h.state);
+  SLSO_CHECK_LAUNCH();
+  const int64_t rpc = ceil_div(s, chunks);
+  const unsigned vb = static_cast<unsigned>(ceil_div(s, rpc));
+  probe_v_ff_kernel<<<vb, 256, 0, st>>>(SX, s, d_i, cexp, Wff, rpc, vpart, h.state);
+  SLSO_CHECK_LAUNCH();
+  probe_vsum_ff_kernel<<<static_cast<unsigned>(ceil_div(d * 4, 256)), 256, 0, st>>>(vpart, static_cast<int>(vb), d_i,
+                                                                                    Vff, h.state);
+  SLSO_CHECK_LAUNCH();
+  probe_u_ff_kernel<<<static_cast<unsigned>(d), 128, 0, st>>>(X, d_i, Vff, Z, eres, h.state);
+  SLSO_CHECK_LAUNCH();
+  return SLSO_OK;
+}
 
 size_t chol_ff_smem() { return sizeof(Smem); }
 
 bool chol_ff_applies(int64_t d) { return d >= 1 && d <= 8192; }
 
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
-                        unsigned int* bar, cudaStream_t st) {
+                        const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,
+                        cudaStream_t st) {
   const size_t smem = sizeof(Smem);
   SLSO_TRY(raise_smem_limit(chol_ff_kernel, smem));
   int occ = 0;
@@ -400,7 +661,8 @@ slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2
   SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 4, st));
   int d_i = static_cast<int>(d);
   DevState* stp = h.state;
-  void* args[] = {&L, &cexp, &d_i, &A, &X, &Rinv, &bar, &stp};
+  int k_i = static_cast<int>(k);
+  void* args[] = {&L, &cexp, &d_i, &A, &X, &Rinv, &Pi, &k_i, &Z, &M, &Yff, &bar, &stp};
   SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(chol_ff_kernel), dim3(h.num_sms), dim3(kFThreads),
                                               args, smem, st));
   note_launch();

@@ -56,6 +56,8 @@ struct DevState {
   double fro_r;          // ||R||_F
   double fro_rinv;       // ||R^-1||_F
   double gram_resid;     // Gram route: probe estimate of ||R^-T SX^T SX R^-1 - I||_F (NaN: breakdown)
+  int32_t m_ready;       // M = R^-1 Pi already written by the float-float Gram route
+  int32_t gemm_gate;     // 1: M is formed from R^-1 by the float64 product (certified, not yet written)
 };
 
 // ------------------------------------------------------------------ scratch arena
@@ -463,22 +465,33 @@ struct GramWork {
   float* xl = nullptr;
   bool use_tc = false;      // G from the tensor-core route (gram_tc.cu) instead of the float-float SYRK
   GramTcWork tc;
-  bool use_ff = false;      // Cholesky and R^-1 in float-float (chol_ff.cu) instead of float64
+  bool use_ff = false;      // Cholesky, R^-1, M and the probe check in float-float (chol_ff.cu)
   float2* Aff = nullptr;    // d x d float-float working matrices of chol_ff
   float2* Xff = nullptr;
   unsigned int* cbar = nullptr;
+  float2* Yff = nullptr;    // d x P: X'^T Z
+  float2* Wff = nullptr;    // s x P
+  float2* vff = nullptr;    // row-chunk partials of SX'^T W
+  float2* Vff = nullptr;    // d x P
   int splits = 1, tiles = 0, vchunks = 1;
   int64_t kc = 0;
 };
 GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d);
 // With g.use_ff the factor's inverse is written to Rinv (column-major R^-1) as well, and
 // *rinv_done is set; otherwise the caller forms R^-1 from L.
+// Pi (d x k, k > 0, or NULL) must be generated before the call: with g.use_ff, M = R^-1 Pi is
+// written too (state->m_ready).
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
-                            int64_t d, double* L, double* Rinv, bool* rinv_done, cudaStream_t st);
+                            int64_t d, double* L, double* Rinv, bool* rinv_done, const double* Pi, int64_t k,
+                            double* M, cudaStream_t st);
 // chol_ff.cu: L (G's lower triangle in, R^T out) and Rinv from the float-float Cholesky.
 bool chol_ff_applies(int64_t d);
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
-                        unsigned int* bar, cudaStream_t st);
+                        const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,
+                        cudaStream_t st);
+slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, const int* cexp, const float2* X,
+                         const float2* Yff, float2* Wff, float2* vpart, int chunks, float2* Vff, const double* Z,
+                         double* eres, cudaStream_t st);
 // G = SX^T SX alone: its lower triangle into L (d x d row-major); run_gram_full also writes the
 // whole symmetric G (d x d row-major).
 slso_status run_gram_matrix(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,

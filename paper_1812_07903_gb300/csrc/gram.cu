@@ -526,7 +526,10 @@ __global__ void __launch_bounds__(256) probe_final_kernel(const double* __restri
   if (threadIdx.x == 0) {
     const double resid = sqrt(tot / kProbes);
     st->gram_resid = resid;
-    if (!(resid <= kGramTol)) st->gram_ok = 0;
+    if (!(resid <= kGramTol)) {
+      st->gram_ok = 0;
+      st->m_ready = 0;
+    }
   }
 }
 
@@ -597,6 +600,10 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
     g.Aff = ar.take<float2>(static_cast<size_t>(d) * d);
     g.Xff = ar.take<float2>(static_cast<size_t>(d) * d);
     g.cbar = ar.take<unsigned int>(4);
+    g.Yff = ar.take<float2>(static_cast<size_t>(d) * kProbes);
+    g.Wff = ar.take<float2>(static_cast<size_t>(s) * kProbes);
+    g.vff = ar.take<float2>(static_cast<size_t>(2 * kGramBalanceSms) * d * kProbes);
+    g.Vff = ar.take<float2>(static_cast<size_t>(d) * kProbes);
   }
   g.use_tc = gram_tc_applies(s, d);
   if (g.use_tc) {
@@ -609,11 +616,15 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
 }
 
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
-                            int64_t d, double* L, double* Rinv, bool* rinv_done, cudaStream_t st) {
+                            int64_t d, double* L, double* Rinv, bool* rinv_done, const double* Pi, int64_t k,
+                            double* M, cudaStream_t st) {
   SLSO_TRY(run_gram_matrix(h, ar, g, SX, s, d, L, st));
   prof_begin(h, ar, ST_CHOL, st);
   if (g.use_ff) {
-    SLSO_TRY(run_chol_ff(h, L, g.cexp, d, g.Aff, g.Xff, Rinv, g.cbar, st));
+    probe_z_kernel<<<static_cast<unsigned>(ceil_div(d * kProbes, 256)), 256, 0, st>>>(static_cast<int>(d), g.Z,
+                                                                                       h.state);
+    SLSO_CHECK_LAUNCH();
+    SLSO_TRY(run_chol_ff(h, L, g.cexp, d, g.Aff, g.Xff, Rinv, Pi, Pi ? k : 0, g.Z, M, g.Yff, g.cbar, st));
     *rinv_done = true;
   } else {
     SLSO_TRY(run_cholesky(h, g, d, L, st));
@@ -683,6 +694,12 @@ slso_status run_cholesky(Handle& h, const GramWork& g, int64_t d, double* L, cud
 slso_status run_gram_check(Handle& h, const GramWork& g, const double* SX, int64_t s, int64_t d,
                            const double* Rinv, cudaStream_t st) {
   const int d_i = static_cast<int>(d);
+  if (g.use_ff) {
+    SLSO_TRY(run_probe_ff(h, SX, s, d, g.cexp, g.Xff, g.Yff, g.Wff, g.vff, 2 * kGramBalanceSms, g.Vff, g.Z, g.eres, st));
+    probe_final_kernel<<<1, 256, 0, st>>>(g.eres, d_i, h.state);
+    SLSO_CHECK_LAUNCH();
+    return SLSO_OK;
+  }
   probe_z_kernel<<<static_cast<unsigned>(ceil_div(d * kProbes, 256)), 256, 0, st>>>(d_i, g.Z, h.state);
   SLSO_CHECK_LAUNCH();
   probe_y_kernel<<<static_cast<unsigned>(d), 128, 0, st>>>(Rinv, d_i, g.Z, g.Y, h.state);

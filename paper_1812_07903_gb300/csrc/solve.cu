@@ -581,6 +581,7 @@ __global__ void certify_kernel(DevState* __restrict__ st, const double* __restri
   st->tau = tau;
   const bool ok = !force_svd && isfinite(fi) && fi > 0.0 && fr * fi < 1e-3 / tau;
   st->need_svd = ok ? 0 : 1;
+  st->gemm_gate = (ok && !st->m_ready) ? 1 : 0;
   if (ok) {
     st->rank = static_cast<int32_t>(d);
     st->sigma_max = CUDART_NAN;
@@ -1331,8 +1332,12 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   // trinv_kernel keeps one column of R^-1 in shared memory: d doubles, above 48 KB for d > 6144
   SLSO_TRY(raise_smem_limit(trinv_kernel, sizeof(double) * d));
   if (gram) {
+    if (k > 0) {  // M = R^-1 Pi comes out of the float-float factorisation
+      pi_kernel<<<grid1d(d * k, h), 256, 0, st>>>(d, k, seed_pi, Pi);
+      SLSO_CHECK_LAUNCH();
+    }
     bool rinv_done = false;
-    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, Rinv, &rinv_done, st));
+    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, Rinv, &rinv_done, Pi, k, M, st));
     prof_begin(h, ar, ST_CHOL, st);
     if (!rinv_done) {
       inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, invd, gram_ok, 1);
@@ -1452,14 +1457,15 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   certify_kernel<<<1, 1, 0, st>>>(h.state, fro2, d, tau, mode == 1 ? 1 : 0);
   SLSO_CHECK_LAUNCH();
   const int32_t* need = &h.state->need_svd;
-  if (k > 0) {
+  if (k > 0 && !gram) {
     pi_kernel<<<grid1d(d * k, h), 256, 0, st>>>(d, k, seed_pi, Pi);
     SLSO_CHECK_LAUNCH();
   }
   if (mode == 0) {
     if (k > 0) {
-      // M = R^-1 Pi, R^-1 column-major: element (i, m) at Rinv[m*d + i]
-      SLSO_TRY(launch_gemm(d, k, d, Rinv, 1, d, Pi, k, 1, M, need, 0, st));
+      // M = R^-1 Pi, R^-1 column-major: element (i, m) at Rinv[m*d + i]; skipped when the
+      // float-float Gram route has written M already (gemm_gate, set by certify_kernel)
+      SLSO_TRY(launch_gemm(d, k, d, Rinv, 1, d, Pi, k, 1, M, &h.state->gemm_gate, 1, st));
     } else {
       rinv_rowmajor_kernel<<<grid1d(d * d, h), 256, 0, st>>>(Rinv, d, M, need);
       SLSO_CHECK_LAUNCH();

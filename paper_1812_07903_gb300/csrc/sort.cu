@@ -40,27 +40,53 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const K* __restric
     hist[static_cast<int64_t>(i) * ntiles + blockIdx.x] = cnt[i];
 }
 
-// Exclusive prefix sum in place over `total` counts, one CTA of 1024 threads.
+// Exclusive prefix sum in place over `total` counts (a multiple of 4), one CTA of 1024 threads:
+// thread t owns a contiguous chunk, read with independent 16-byte loads so that they are all in
+// flight at once; the chunk sums are scanned across the CTA (warp shuffles, then one warp over
+// the warp totals) and every chunk is rewritten from its offset.
 __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ a, int64_t total) {
-  __shared__ uint32_t part[1024];
-  const int64_t chunk = (total + 1023) / 1024;
-  const int64_t lo = threadIdx.x * chunk;
-  const int64_t hi = lo + chunk < total ? lo + chunk : total;
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t q4 = total / 4;                    // uint4 groups
+  const int64_t per = (q4 + 1023) / 1024;          // groups per thread
+  const int64_t g0 = t * per, g1 = g0 + per < q4 ? g0 + per : q4;
+  uint4* a4 = reinterpret_cast<uint4*>(a);
   uint32_t sum = 0;
-  for (int64_t i = lo; i < hi; ++i) sum += a[i];
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  for (int64_t g = g0; g < g1; ++g) {
+    const uint4 v = a4[g];
+    sum += v.x + v.y + v.z + v.w;
   }
-  uint32_t run = part[threadIdx.x] - sum;  // exclusive
-  for (int64_t i = lo; i < hi; ++i) {
-    const uint32_t c = a[i];
-    a[i] = run;
-    run += c;
+  uint32_t x = sum;  // inclusive scan over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t ws = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, ws, o);
+      if (lane >= o) ws += y;
+    }
+    wsum[lane] = ws;
+  }
+  __syncthreads();
+  uint32_t run = (w > 0 ? wsum[w - 1] : 0u) + x - sum;  // exclusive
+  for (int64_t g = g0; g < g1; ++g) {
+    const uint4 v = a4[g];
+    uint4 o;
+    o.x = run;
+    run += v.x;
+    o.y = run;
+    run += v.y;
+    o.z = run;
+    run += v.z;
+    o.w = run;
+    run += v.w;
+    a4[g] = o;
   }
 }
 
