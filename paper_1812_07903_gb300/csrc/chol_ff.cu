@@ -67,23 +67,6 @@ __device__ __forceinline__ ff ff_fms(ff z, ff x, ff y) {
   const ff p = ff_mul(x, y);
   return ff_add(z, ff{-p.h, -p.l});
 }
-// sqrt(a), a > 0: y = fl(sqrt(a_h)), then y + (a - y^2) / (2y)
-__device__ __forceinline__ ff ff_sqrt(ff a) {
-  const float y = __fsqrt_rn(a.h);
-  const float p = __fmul_rn(y, y);
-  const float e = __fmaf_rn(y, y, -p);
-  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.h, p), e), a.l);
-  return fast_two_sum(y, __fmul_rn(r, __fdiv_rn(0.5f, y)));
-}
-// 1 / a: y = fl(1 / a_h), then y + y (1 - a y)
-__device__ __forceinline__ ff ff_recip(ff a) {
-  const float y = __frcp_rn(a.h);
-  const float p = __fmul_rn(a.h, y);
-  const float e = __fmaf_rn(a.h, y, -p);
-  const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), e), __fmul_rn(a.l, y));
-  return fast_two_sum(y, __fmul_rn(y, r));
-}
-
 // One term of a float-float dot product: (S, C) += (ah + al)(bh + bl), the product's rounding
 // error by FMA, the sum's by TwoSum; (S, C) is folded into a pair every 16 terms by the caller.
 __device__ __forceinline__ void dot_term(float ah, float al, float bh, float bl, float& S, float& C) {
@@ -130,53 +113,9 @@ struct Smem {
   float Ih[kFb][kFb + 1], Il[kFb][kFb + 1];  // identity -> L_kk^-1
   float Ph[kFb][kFb + 4], Pl[kFb][kFb + 4];  // task operands, [m][row]
   float Qh[kFb][kFb + 4], Ql[kFb][kFb + 4];  // [m][column]
-  float rh, rl;
+  float rh[kFb], rl[kFb], r2h[kFb], r2l[kFb], sh[kFb], sl[kFb];  // pivots: 1/L_jj, 1/L_jj^2, L_jj
   int bad;
 };
-
-// C (32 x 32 tile at rows r0, columns c0 of a row-major float-float matrix Y with pitch d) =
-// init + sign * sum_m P[m][i] Q[m][j]; init from Y (add = true) or zero.  Rows / columns beyond
-// nrow / ncol are not written; lower = true writes only j <= i (global indices).
-// Thread t: row i = t / 8, columns 4 (t % 8) .. + 4.
-__device__ void tile_product(Smem& sm, float2* Y, int d, int r0, int c0, bool add, float sign, bool lower) {
-  const int t = threadIdx.x, i = t >> 3, j0 = (t & 7) * 4;
-  float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-  ff acc[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
-#pragma unroll 4
-  for (int m = 0; m < kFb; ++m) {
-    const float ah = sm.Ph[m][i] * sign, al = sm.Pl[m][i] * sign;
-    const float4 bh = *reinterpret_cast<const float4*>(&sm.Qh[m][j0]);
-    const float4 bl = *reinterpret_cast<const float4*>(&sm.Ql[m][j0]);
-    dot_term(ah, al, bh.x, bl.x, S[0], C[0]);
-    dot_term(ah, al, bh.y, bl.y, S[1], C[1]);
-    dot_term(ah, al, bh.z, bl.z, S[2], C[2]);
-    dot_term(ah, al, bh.w, bl.w, S[3], C[3]);
-    if ((m & 15) == 15) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
-        S[q] = 0.f;
-        C[q] = 0.f;
-      }
-    }
-  }
-  const int gi = r0 + i;
-  if (gi >= d) return;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int gj = c0 + j0 + q;
-    if (gj >= d || (lower && gj > gi)) continue;
-    float2* y = Y + static_cast<int64_t>(gi) * d + gj;
-    ff v = acc[q];
-    if (add) {
-      const float2 o = *y;
-      v = ff_add(ff{o.x, o.y}, v);
-    }
-    *y = make_float2(v.h, v.l);
-  }
-}
 
 // acc[q] += sum_m P[m][i] Q[m][j0 + q] for this thread's row i = t / 8, columns j0 = 4 (t % 8) .. + 4.
 __device__ void tile_accumulate(const Smem& sm, ff* acc) {
@@ -202,49 +141,42 @@ __device__ void tile_accumulate(const Smem& sm, ff* acc) {
   }
 }
 
-// P[m][i] = Y[r0 + m][c0 + i] (zero beyond d)
-__device__ void load_p_rows(Smem& sm, const float2* Y, int d, int r0, int c0) {
-  for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-    const int m = e >> 5, i = e & 31;
-    float2 v = make_float2(0.f, 0.f);
-    if (r0 + m < d && c0 + i < d) v = Y[static_cast<int64_t>(r0 + m) * d + c0 + i];
-    sm.Ph[m][i] = v.x;
-    sm.Pl[m][i] = v.y;
-  }
+// 1 / sqrt(a), a > 0: y = rsqrtf(a_h) refined once in float32 and once in float-float (Newton for
+// the inverse square root, y' = y + y (1 - a y^2) / 2, the residual 1 - a y^2 formed exactly).
+__device__ __forceinline__ ff ff_rsqrt(ff a) {
+  float y = rsqrtf(a.h);
+  y = __fmul_rn(y, __fmaf_rn(-0.5f * a.h, __fmul_rn(y, y), 1.5f));
+  const float p = __fmul_rn(y, y);
+  const ff y2{p, __fmaf_rn(y, y, -p)};
+  const ff ay2 = ff_mul(a, y2);
+  const ff res = ff_add(ff{1.f, 0.f}, ff{-ay2.h, -ay2.l});
+  return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), res.h));
 }
 
-// P[m][i] = Y[r0 + i][c0 + m] (zero beyond d)
-__device__ void load_rows_t(Smem& sm, const float2* Y, int d, int r0, int c0) {
-  for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-    const int i = e >> 5, m = e & 31;
-    float2 v = make_float2(0.f, 0.f);
-    if (r0 + i < d && c0 + m < d) v = Y[static_cast<int64_t>(r0 + i) * d + c0 + m];
-    sm.Ph[m][i] = v.x;
-    sm.Pl[m][i] = v.y;
-  }
-}
-// Q[m][j] = Y[r0 + j][c0 + m]
-__device__ void load_q_rows_t(Smem& sm, const float2* Y, int d, int r0, int c0) {
-  for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-    const int j = e >> 5, m = e & 31;
-    float2 v = make_float2(0.f, 0.f);
-    if (r0 + j < d && c0 + m < d) v = Y[static_cast<int64_t>(r0 + j) * d + c0 + m];
-    sm.Qh[m][j] = v.x;
-    sm.Ql[m][j] = v.y;
-  }
-}
-// Q[m][j] = Y[r0 + m][c0 + j]
-__device__ void load_q_rows(Smem& sm, const float2* Y, int d, int r0, int c0) {
-  for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-    const int m = e >> 5, j = e & 31;
-    float2 v = make_float2(0.f, 0.f);
-    if (r0 + m < d && c0 + j < d) v = Y[static_cast<int64_t>(r0 + m) * d + c0 + j];
-    sm.Qh[m][j] = v.x;
-    sm.Ql[m][j] = v.y;
-  }
+// Pivot j of the diagonal block: r_j = 1 / sqrt(D_jj), r_j^2 and s_j = D_jj r_j = sqrt(D_jj); false on
+// a non-positive or non-finite pivot.
+__device__ __forceinline__ bool pivot(Smem& sm, int j) {
+  const ff piv{sm.Dh[j][j], sm.Dl[j][j]};
+  if (!(piv.h > 0.f) || !isfinite(piv.h) || !isfinite(piv.l)) return false;
+  const ff r = ff_rsqrt(piv);
+  const ff r2 = ff_mul(r, r);
+  const ff sq = ff_mul(piv, r);
+  sm.rh[j] = r.h;
+  sm.rl[j] = r.l;
+  sm.r2h[j] = r2.h;
+  sm.r2l[j] = r2.l;
+  sm.sh[j] = sq.h;
+  sm.sl[j] = sq.l;
+  return true;
 }
 
 // Step k, part A: L_kk and L_kk^-1 in shared memory (rows / columns beyond d: identity).
+// Right-looking over the 32 columns with the column and row scalings deferred: column j of D
+// keeps its unscaled values D_ij = L_ij L_jj, row j of the identity block keeps B_j (before the
+// division by L_jj), and the updates use r_j^2 = 1 / D_jj:
+//   D_im -= D_ij D_mj r_j^2 (j < m <= i),   B_ic -= D_ij B_jc r_j^2 (c <= j)   for rows i > j.
+// Warp 0 updates D_(j+1)(j+1) alone and forms pivot j + 1 at once while warps 1-7 do the rest, so
+// one barrier per column suffices.  The scalings are applied in one pass at the end.
 // Returns false (uniformly) on a non-positive or non-finite pivot.
 __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
   const int t = threadIdx.x;
@@ -257,57 +189,67 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
     sm.Ih[i][j] = i == j ? 1.f : 0.f;
     sm.Il[i][j] = 0.f;
   }
-  if (t == 0) sm.bad = 0;
   __syncthreads();
-  for (int j = 0; j < kFb; ++j) {
-    if (t == 0) {
-      const ff piv{sm.Dh[j][j], sm.Dl[j][j]};
-      if (!(piv.h > 0.f) || !isfinite(piv.h) || !isfinite(piv.l)) {
-        sm.bad = 1;
-      } else {
-        const ff s = ff_sqrt(piv);
-        const ff r = ff_recip(s);
-        sm.Dh[j][j] = s.h;
-        sm.Dl[j][j] = s.l;
-        sm.rh = r.h;
-        sm.rl = r.l;
+  if (t == 0) sm.bad = pivot(sm, 0) ? 0 : 1;
+  __syncthreads();
+  if (sm.bad) return false;
+  for (int j = 0; j < kFb - 1; ++j) {
+    const ff r2{sm.r2h[j], sm.r2l[j]};
+    const int n = kFb - 1 - j;  // rows below j
+    if (t < 32) {
+      if (t == 0) {
+        const ff dij{sm.Dh[j + 1][j], sm.Dl[j + 1][j]};
+        const ff v = ff_fms(ff{sm.Dh[j + 1][j + 1], sm.Dl[j + 1][j + 1]}, ff_mul(dij, dij), r2);
+        sm.Dh[j + 1][j + 1] = v.h;
+        sm.Dl[j + 1][j + 1] = v.l;
+        if (!pivot(sm, j + 1)) sm.bad = 1;
+      }
+    } else {
+      const int u = t - 32, stride = kFThreads - 32;
+      // D: rows i = j+1+a, columns m = j+1+b, b <= a, except (0, 0) (warp 0's)
+      const int tri = n * (n + 1) / 2;
+      for (int e = u + 1; e < tri; e += stride) {
+        int a = static_cast<int>((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        while (a * (a + 1) / 2 > e) --a;
+        const int b = e - a * (a + 1) / 2;
+        const int i = j + 1 + a, m = j + 1 + b;
+        const ff p = ff_mul(ff{sm.Dh[i][j], sm.Dl[i][j]}, ff{sm.Dh[m][j], sm.Dl[m][j]});
+        const ff v = ff_fms(ff{sm.Dh[i][m], sm.Dl[i][m]}, p, r2);
+        sm.Dh[i][m] = v.h;
+        sm.Dl[i][m] = v.l;
+      }
+      // B: rows i = j+1.., columns c <= j
+      const int w = j + 1;
+      for (int e = u; e < n * w; e += stride) {
+        const int i = j + 1 + e / w, c = e % w;
+        const ff p = ff_mul(ff{sm.Dh[i][j], sm.Dl[i][j]}, ff{sm.Ih[j][c], sm.Il[j][c]});
+        const ff v = ff_fms(ff{sm.Ih[i][c], sm.Il[i][c]}, p, r2);
+        sm.Ih[i][c] = v.h;
+        sm.Il[i][c] = v.l;
       }
     }
     __syncthreads();
     if (sm.bad) return false;
-    const ff r{sm.rh, sm.rl};
-    if (t < kFb) {
-      if (t > j) {
-        const ff v = ff_mul(ff{sm.Dh[t][j], sm.Dl[t][j]}, r);
-        sm.Dh[t][j] = v.h;
-        sm.Dl[t][j] = v.l;
-      }
-    } else if (t < 2 * kFb) {
-      const int c = t - kFb;
-      if (c <= j) {
-        const ff v = ff_mul(ff{sm.Ih[j][c], sm.Il[j][c]}, r);
-        sm.Ih[j][c] = v.h;
-        sm.Il[j][c] = v.l;
-      }
-    }
-    __syncthreads();
-    // rows i > j: D[i][m] -= L_ij L_mj (j < m <= i), I[i][c] -= L_ij I[j][c] (c <= j)
-    const int rows = kFb - 1 - j;
-    for (int e = t; e < rows * kFb; e += kFThreads) {
-      const int i = j + 1 + e / kFb, m = e % kFb;
-      const ff lij{sm.Dh[i][j], sm.Dl[i][j]};
-      if (m > j && m <= i) {
-        const ff v = ff_fms(ff{sm.Dh[i][m], sm.Dl[i][m]}, lij, ff{sm.Dh[m][j], sm.Dl[m][j]});
-        sm.Dh[i][m] = v.h;
-        sm.Dl[i][m] = v.l;
-      } else if (m <= j) {
-        const ff v = ff_fms(ff{sm.Ih[i][m], sm.Il[i][m]}, lij, ff{sm.Ih[j][m], sm.Il[j][m]});
-        sm.Ih[i][m] = v.h;
-        sm.Il[i][m] = v.l;
-      }
-    }
-    __syncthreads();
   }
+  // L_ij = D_ij r_j (i > j), L_jj = s_j; L_kk^-1 row j = B_j r_j
+  for (int e = t; e < kFb * kFb; e += kFThreads) {
+    const int i = e >> 5, j = e & 31;
+    if (i > j) {
+      const ff v = ff_mul(ff{sm.Dh[i][j], sm.Dl[i][j]}, ff{sm.rh[j], sm.rl[j]});
+      sm.Dh[i][j] = v.h;
+      sm.Dl[i][j] = v.l;
+    } else if (i == j) {
+      sm.Dh[i][j] = sm.sh[j];
+      sm.Dl[i][j] = sm.sl[j];
+    }
+    if (j <= i) {
+      const ff v = ff_mul(ff{sm.Ih[i][j], sm.Il[i][j]}, ff{sm.rh[i], sm.rl[i]});
+      sm.Ih[i][j] = v.h;
+      sm.Il[i][j] = v.l;
+    }
+  }
+  __syncthreads();
   return true;
 }
 
@@ -347,6 +289,24 @@ __global__ void __launch_bounds__(kFThreads, 1)
   const int nb = (d + kFb - 1) / kFb;
   for (int k = 0; k < nb; ++k) {
     const int k0 = k * kFb;
+    // part B's operand for this CTA's first task (panel rows of A, or the row block of B), fetched
+    // before the diagonal factorisation so that its latency hides behind it
+    const int npanel = nb - k - 1;
+    float2 bv[4];
+    auto fetch_b = [&](int task) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
+        if (task < npanel) {  // P[lo][hi] = A[r0 + hi][k0 + lo]
+          const int r0 = (k + 1 + task) * kFb;
+          bv[u] = (r0 + hi < d && k0 + lo < d) ? A[static_cast<int64_t>(r0 + hi) * d + k0 + lo] : make_float2(0.f, 0.f);
+        } else {  // Q[hi][lo] = B[k0 + hi][c0 + lo]
+          const int c0 = (task - npanel) * kFb;
+          bv[u] = (k0 + hi < d && c0 + lo < d) ? X[static_cast<int64_t>(k0 + hi) * d + c0 + lo] : make_float2(0.f, 0.f);
+        }
+      }
+    };
+    if (static_cast<int>(blockIdx.x) < nb) fetch_b(blockIdx.x);
     if (!factor_diag(sm, A, d, k0)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->gram_ok = 0;
@@ -355,30 +315,39 @@ __global__ void __launch_bounds__(kFThreads, 1)
       return;
     }
     // part B: tasks 0 .. nb-k-2 are the panel row blocks I = k+1.., then k+1 column tiles of X_k
-    const int npanel = nb - k - 1;
     for (int task = blockIdx.x; task < nb; task += gridDim.x) {
+      if (task != static_cast<int>(blockIdx.x)) fetch_b(task);
       __syncthreads();
-      if (task < npanel) {
-        const int r0 = (k + 1 + task) * kFb;
-        load_rows_t(sm, A, d, r0, k0);  // P[m][i] = A[r0+i][k0+m]
-        for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-          const int m = e >> 5, j = e & 31;  // Q[m][j] = Li[j][m]
-          sm.Qh[m][j] = sm.Ih[j][m];
-          sm.Ql[m][j] = sm.Il[j][m];
+      const bool panel = task < npanel;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
+        if (panel) {
+          sm.Ph[lo][hi] = bv[u].x;  // P[m][i] = A[r0 + i][k0 + m]
+          sm.Pl[lo][hi] = bv[u].y;
+          sm.Qh[lo][hi] = sm.Ih[hi][lo];  // Q[m][j] = Li[j][m]
+          sm.Ql[lo][hi] = sm.Il[hi][lo];
+        } else {
+          sm.Qh[hi][lo] = bv[u].x;  // Q[m][j] = B[k0 + m][c0 + j]
+          sm.Ql[hi][lo] = bv[u].y;
+          sm.Ph[lo][hi] = sm.Ih[hi][lo];  // P[m][i] = Li[i][m]
+          sm.Pl[lo][hi] = sm.Il[hi][lo];
         }
-        __syncthreads();
-        tile_product(sm, A, d, r0, k0, false, 1.f, false);
-      } else {
-        const int c0 = (task - npanel) * kFb;
-        for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-          const int m = e >> 5, i = e & 31;  // P[m][i] = Li[i][m]
-          sm.Ph[m][i] = sm.Ih[i][m];
-          sm.Pl[m][i] = sm.Il[i][m];
-        }
-        load_q_rows(sm, X, d, k0, c0);  // Q[m][j] = B[k0+m][c0+j]
-        __syncthreads();
-        tile_product(sm, X, d, k0, c0, false, 1.f, false);
       }
+      __syncthreads();
+      ff acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
+      tile_accumulate(sm, acc);
+      const int r0 = panel ? (k + 1 + task) * kFb : k0, c0 = panel ? k0 : (task - npanel) * kFb;
+      float2* Y = panel ? A : X;
+      const int gi = r0 + (threadIdx.x >> 3);
+      if (gi < d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int gj = c0 + (threadIdx.x & 7) * 4 + q;
+          if (gj < d) Y[static_cast<int64_t>(gi) * d + gj] = make_float2(acc[q].h, acc[q].l);
+        }
     }
     if (!sync_all()) return;
     if (blockIdx.x == 0)  // L_kk into A: every CTA has read A_kk before the barrier above
@@ -386,55 +355,140 @@ __global__ void __launch_bounds__(kFThreads, 1)
         const int i = e >> 5, j = e & 31;
         if (k0 + i < d && j <= i) A[static_cast<int64_t>(k0 + i) * d + k0 + j] = make_float2(sm.Dh[i][j], sm.Dl[i][j]);
       }
-    // part C: lower tiles (I, J) of the trailing matrix, then the (I, c) tiles of B
+    // part C: lower tiles (I, J) of the trailing matrix, then the (I, c) tiles of B.  Software
+    // pipelined: every thread fetches the next task's operand and output elements into registers
+    // before it computes the current one, so the L2 latency hides behind the arithmetic.
     const int ntri = npanel * (npanel + 1) / 2;
     const int ntask = ntri + npanel * (k + 1);
-    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
-      __syncthreads();
+    struct Task {
+      int r0, c0;
+      bool tri, diag;
+    };
+    auto decode = [&](int task) {
+      Task tk;
       if (task < ntri) {
         int a = static_cast<int>((sqrt(8.0 * task + 1.0) - 1.0) * 0.5);
         while ((a + 1) * (a + 2) / 2 <= task) ++a;
         while (a * (a + 1) / 2 > task) --a;
         const int b = task - a * (a + 1) / 2;
-        const int r0 = (k + 1 + a) * kFb, c0 = (k + 1 + b) * kFb;
-        load_rows_t(sm, A, d, r0, k0);    // P[m][i] = L[r0+i][k0+m]
-        load_q_rows_t(sm, A, d, c0, k0);  // Q[m][j] = L[c0+j][k0+m]
-        __syncthreads();
-        tile_product(sm, A, d, r0, c0, true, -1.f, a == b);
+        tk.r0 = (k + 1 + a) * kFb;
+        tk.c0 = (k + 1 + b) * kFb;
+        tk.tri = true;
+        tk.diag = a == b;
       } else {
         const int u = task - ntri;
-        const int a = u / (k + 1), c = u % (k + 1);
-        const int r0 = (k + 1 + a) * kFb, c0 = c * kFb;
-        load_rows_t(sm, A, d, r0, k0);  // P[m][i] = L[r0+i][k0+m]
-        load_q_rows(sm, X, d, k0, c0);  // Q[m][j] = X[k0+m][c0+j]
-        __syncthreads();
-        tile_product(sm, X, d, r0, c0, true, -1.f, false);
+        tk.r0 = (k + 1 + u / (k + 1)) * kFb;
+        tk.c0 = (u % (k + 1)) * kFb;
+        tk.tri = false;
+        tk.diag = false;
       }
+      return tk;
+    };
+    float2 pv[4], qv[4], ov[4];
+    const int ti = threadIdx.x >> 3, tj0 = (threadIdx.x & 7) * 4;
+    auto fetch = [&](const Task& tk) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
+        // P[lo][hi] = L[r0 + hi][k0 + lo]
+        pv[u] = (tk.r0 + hi < d && k0 + lo < d) ? A[static_cast<int64_t>(tk.r0 + hi) * d + k0 + lo] : make_float2(0.f, 0.f);
+        if (tk.tri)  // Q[lo][hi] = L[c0 + hi][k0 + lo]
+          qv[u] = (tk.c0 + hi < d && k0 + lo < d) ? A[static_cast<int64_t>(tk.c0 + hi) * d + k0 + lo] : make_float2(0.f, 0.f);
+        else  // Q[hi][lo] = X[k0 + hi][c0 + lo]
+          qv[u] = (k0 + hi < d && tk.c0 + lo < d) ? X[static_cast<int64_t>(k0 + hi) * d + tk.c0 + lo] : make_float2(0.f, 0.f);
+        // this thread's output elements (row ti, columns tj0 + u)
+        const int gi = tk.r0 + ti, gj = tk.c0 + tj0 + u;
+        const float2* Y = tk.tri ? A : X;
+        ov[u] = (gi < d && gj < d && !(tk.diag && gj > gi)) ? Y[static_cast<int64_t>(gi) * d + gj] : make_float2(0.f, 0.f);
+      }
+    };
+    int task = blockIdx.x;
+    Task cur{};
+    if (task < ntask) {
+      cur = decode(task);
+      fetch(cur);
+    }
+    while (task < ntask) {
+      __syncthreads();  // the previous task is done with the shared operands
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
+        sm.Ph[lo][hi] = pv[u].x;
+        sm.Pl[lo][hi] = pv[u].y;
+        if (cur.tri) {
+          sm.Qh[lo][hi] = qv[u].x;
+          sm.Ql[lo][hi] = qv[u].y;
+        } else {
+          sm.Qh[hi][lo] = qv[u].x;
+          sm.Ql[hi][lo] = qv[u].y;
+        }
+      }
+      float2 out[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) out[u] = ov[u];
+      __syncthreads();
+      const Task now = cur;
+      const int next = task + gridDim.x;
+      if (next < ntask) {
+        cur = decode(next);
+        fetch(cur);
+      }
+      ff acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
+      tile_accumulate(sm, acc);
+      const int gi = now.r0 + ti;
+      float2* Y = now.tri ? A : X;
+      if (gi < d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int gj = now.c0 + tj0 + q;
+          if (gj >= d || (now.diag && gj > gi)) continue;
+          const ff v = ff_add(ff{out[q].x, out[q].y}, ff{-acc[q].h, -acc[q].l});
+          Y[static_cast<int64_t>(gi) * d + gj] = make_float2(v.h, v.l);
+        }
+      task = next;
     }
     if (!sync_all()) return;
   }
-  // Out = X'^T [Pi | Z]: output tiles (I, Cb), I over row blocks, Cb over 32-column blocks of [Pi | Z]
+  // Out = X'^T [Pi | Z]: output tiles (I, Cb), I over row blocks, Cb over 32-column blocks of
+  // [Pi | Z]; the next m-block's operands are fetched into registers while this one is summed.
   {
     const int width = k + 4, ncb = (width + kFb - 1) / kFb;
     for (int task = blockIdx.x; task < nb * ncb; task += gridDim.x) {
       const int I = task / ncb, Cb = task % ncb;
       const int i0 = I * kFb, c0 = Cb * kFb;
+      float2 pv[4];
+      double qv[4];
+      auto fetch = [&](int mb) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = threadIdx.x + u * kFThreads, m = e >> 5, lo = e & 31;
+          const int r = mb * kFb + m;
+          pv[u] = (r < d && i0 + lo < d) ? X[static_cast<int64_t>(r) * d + i0 + lo] : make_float2(0.f, 0.f);
+          const int c = c0 + lo;
+          double v = 0.0;
+          if (r < d) v = c < k ? Pi[static_cast<int64_t>(r) * k + c] : (c < width ? Z[r * 4 + (c - k)] : 0.0);
+          qv[u] = v;
+        }
+      };
       ff acc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
+      fetch(I);
       for (int mb = I; mb < nb; ++mb) {
         __syncthreads();
-        load_p_rows(sm, X, d, mb * kFb, i0);  // P[m][i] = X'[mb 32 + m][i0 + i]
-        for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
-          const int m = e >> 5, j = e & 31;  // Q[m][j] = [Pi | Z][mb 32 + m][c0 + j]
-          const int r = mb * kFb + m, c = c0 + j;
-          double v = 0.0;
-          if (r < d) v = c < k ? Pi[static_cast<int64_t>(r) * k + c] : (c < width ? Z[r * 4 + (c - k)] : 0.0);
-          const float h = __double2float_rn(v);
-          sm.Qh[m][j] = h;
-          sm.Ql[m][j] = __double2float_rn(v - static_cast<double>(h));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = threadIdx.x + u * kFThreads, m = e >> 5, lo = e & 31;
+          sm.Ph[m][lo] = pv[u].x;  // P[m][i] = X'[mb 32 + m][i0 + i]
+          sm.Pl[m][lo] = pv[u].y;
+          const float h = __double2float_rn(qv[u]);  // Q[m][j] = [Pi | Z][mb 32 + m][c0 + j]
+          sm.Qh[m][lo] = h;
+          sm.Ql[m][lo] = __double2float_rn(qv[u] - static_cast<double>(h));
         }
         __syncthreads();
+        if (mb + 1 < nb) fetch(mb + 1);
         tile_accumulate(sm, acc);
       }
       const int i = i0 + (threadIdx.x >> 3), j0 = c0 + (threadIdx.x & 7) * 4;
