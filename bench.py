@@ -118,50 +118,68 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle timing
-def oracle_throughput(n, d, s, k, kind, seed_S, seed_Pi, rows_sample, qr_steps, X_rows=None):
-    """Time the FP64 oracle on a bounded sample and scale to rows/s of the full workload.
+def oracle_job(Xn, kind, s, k, seed_S, seed_Pi):
+    """One whole sketched-score job of the FP64 oracle (Oracle B, the same S and Pi as the GPU), timed:
+    sketch, R by LAPACK's QR, SVD of R, M, all row scores, then the "dec" order.  Returns
+    (scores, oracle_rank, seconds for the scores, seconds for the order)."""
+    from oracle import slso_oracle as O
 
-    Per-row stages (sketch, scores) are timed on `rows_sample` rows; the s x d Householder QR is
-    timed for its first `qr_steps` columns and scaled by the flop ratio of the full loop; the
-    SVD of R and M are timed whole.
-    """
+    t0 = time.perf_counter()
+    SX = O.sketch(Xn, kind, s, seed_S)
+    sv = O.sketched_svd(SX, qr="lapack")
+    M = O.m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], O.jl_matrix(Xn.shape[1], k, seed_Pi) if k else None)
+    want = O.row_scores(Xn, M)
+    t1 = time.perf_counter()
+    O.order_dec(want)
+    t2 = time.perf_counter()
+    return want, sv["rank"], t1 - t0, t2 - t1
+
+
+def oracle_exact_seconds(Xn):
+    """Oracle A (exact scores, the hat-matrix diagonal from R of X by blocked QR and its SVD) on all rows of Xn."""
     import numpy as np
-    import torch
 
     from oracle import slso_oracle as O
-    from paper_1812_07903_gb300 import inputs
 
-    if X_rows is None:
-        X_rows = inputs.snr_student_t(rows_sample, d, seed=WORKLOAD["xseed"], device="cpu").numpy()
-    Xs = np.asarray(X_rows[:rows_sample])
     t0 = time.perf_counter()
-    SXs = O.sketch(Xs, kind, s, seed_S)
-    t_sketch = time.perf_counter() - t0
-    A = SXs if SXs.shape[0] >= d else np.vstack([SXs, np.zeros((d - SXs.shape[0], d))])
-    A = A + np.random.default_rng(0).standard_normal(A.shape) * 1e-3  # full rank, same cost
-    t0 = time.perf_counter()
-    O.householder_r(A, steps=qr_steps)
-    t_qr_part = time.perf_counter() - t0
-    work = lambda m: sum((s - j) * (d - j) for j in range(m))  # noqa: E731
-    t_qr = t_qr_part * work(d) / work(qr_steps)
-    R = O.householder_r_lapack(A)
-    t0 = time.perf_counter()
-    sig, V, U = O.svd_of_r(R)
-    Pi = O.jl_matrix(d, k, seed_Pi) if k > 0 else None
-    M = O.m_matrix(sig, V, U, d, Pi)
-    t_svd = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.row_scores(Xs, M)
-    t_scores = time.perf_counter() - t0
-    total = (t_sketch + t_scores) * (n / rows_sample) + t_qr + t_svd
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
-    sample = (f"sketch+scores on {rows_sample} of {n} rows scaled by n; Householder loop on the first "
-              f"{qr_steps} of {d} columns scaled by its flop share; SVD of R and M timed whole")
-    return n / total, total, cores, sample
+    O.exact_leverage_rows(Xn, np.arange(Xn.shape[0]))
+    return time.perf_counter() - t0
+
+
+ONE_THREAD_CODE = r"""
+import os, sys, json, time
+for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ[v] = "1"
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import bench
+from paper_1812_07903_gb300 import inputs
+a = json.loads(sys.argv[2])
+X = inputs.snr_student_t(a["n"], a["d"], seed=a["xseed"], device="cpu").numpy()
+_, _, t_sc, t_od = bench.oracle_job(X, a["kind"], a["s"], a["k"], a["seed_S"], a["seed_Pi"])
+print(json.dumps({"seconds": t_sc + t_od}))
+"""
+
+
+def oracle_one_thread(n, d, s, k, kind, seed_S, seed_Pi, xseed):
+    """The same whole job on n rows with the BLAS limited to one thread (a child process, so that the
+    thread limits are set before numpy loads its BLAS)."""
+    import subprocess
+
+    args = json.dumps({"n": n, "d": d, "s": s, "k": k, "kind": kind, "seed_S": seed_S, "seed_Pi": seed_Pi,
+                       "xseed": xseed})
+    r = subprocess.run([sys.executable, "-c", ONE_THREAD_CODE, ROOT, args], capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+REF_ROWS = 65536  # the reference arm's bounded sample: a whole job on the first rows of the workload
 
 
 def run_reference(args):
@@ -170,25 +188,24 @@ def run_reference(args):
         return 0
     W = WORKLOAD
     n, d, s, k = W["n"], W["d"], W["s"], W["k"]
-    import numpy as np  # noqa: F401
-
     from paper_1812_07903_gb300 import inputs
 
-    X_rows = inputs.snr_student_t(16384, d, seed=W["xseed"], device="cpu").numpy()
-    vals, totals = [], []
+    Xn = inputs.snr_student_t(REF_ROWS, d, seed=W["xseed"], device="cpu").numpy()
+    secs = []
     for it in range(args.warmup + args.steps):
-        v, tot, cores, sample = oracle_throughput(n, d, s, k, W["kind"], W["seed_S"], W["seed_Pi"],
-                                                  rows_sample=16384, qr_steps=16, X_rows=X_rows)
+        _, _, t_sc, t_od = oracle_job(Xn, W["kind"], s, k, W["seed_S"], W["seed_Pi"])
         if it >= args.warmup:
-            vals.append(v)
-            totals.append(tot)
-    v = statistics.median(vals)
+            secs.append(t_sc + t_od)
+    t = statistics.median(secs)
+    v = REF_ROWS / t
+    sample = (f"whole sketched-score job (sketch, LAPACK QR, SVD of R, M, scores, dec order) on {REF_ROWS} rows "
+              f"of the {n}-row workload, measured per step; the s x d factor does not shrink with the sample")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(totals) * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(n, d, s, k, W["kind"]),
-        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": host_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -203,9 +220,19 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
     sketch kind 1/3 each, k = 64.  Capacity is calibrated by running the first 16 jobs one at a time
     through the direct entry points; arrivals are then Poisson at `load` x that rate.
     """
+    import numpy as np
+
     jobs = inputs.serving_jobs(n_jobs=n_jobs, seed=seed, rate_per_s=1.0)
+    # every job's rows are a window of a per-width pool of mixture rows (seeded offset), so that the
+    # trace fits the device whatever its length
+    pools = {}
+    gen = np.random.default_rng(seed + 1)
+    pool_rows = 2 << 20
     for jb in jobs:
-        jb["X"] = inputs.gaussian_mixture(jb["n"], jb["d"], seed=jb["seed"], device="cuda")
+        if jb["d"] not in pools:
+            pools[jb["d"]] = inputs.gaussian_mixture(pool_rows, jb["d"], seed=20000 + jb["d"], device="cuda")
+        off = int(gen.integers(0, pool_rows - jb["n"] + 1))
+        jb["X"] = pools[jb["d"]][off: off + jb["n"]]
     torch.cuda.synchronize()
     calib = jobs[: min(16, n_jobs)]
     for jb in calib[:2]:  # warm-up
@@ -242,7 +269,8 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
     rows = sum(jb["n"] for jb in jobs)
     return {
         "workload": f"{n_jobs} jobs, Poisson arrivals at {load} x calibrated capacity, n=2^U[12,20], "
-                    "d in {64,128,256,300,784}, 8-cluster mixture rows, CountSketch/SRHT/Gaussian 1/3 each, k=64",
+                    "d in {64,128,256,300,784}, rows a seeded window of a per-d pool of 8-cluster mixture rows, "
+                    "CountSketch/SRHT/Gaussian 1/3 each, k=64",
         "slots": slots, "jobs": n_jobs, "failed": bad, "calibrated_service_ms": service_s * 1e3,
         "arrival_rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
         "makespan_s": makespan, "jobs_per_s": n_jobs / makespan, "rows_per_s": rows / makespan,
@@ -361,7 +389,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the FP64 oracle comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--serving-jobs", type=int, default=96, help="jobs in the serving trace (0 skips it)")
+    ap.add_argument("--serving-jobs", type=int, default=512, help="jobs in the serving trace (0 skips it)")
     ap.add_argument("--config", default="benchmark", choices=["benchmark", "large"],
                     help="large: the 4M x 3072 bfloat16 Gaussian-sketch workload (its own JSON line)")
     args = ap.parse_args()
@@ -596,17 +624,12 @@ def main():
                        "single_call_value": job_rows_per_s(n, world, ms_single)}
         del Xh
 
-    # ---- precision against the FP64 oracle, and the oracle's own throughput (rank 0, N = 1)
+    # ---- precision against the FP64 oracle, and the oracle's own measured throughput (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_precision:
         from oracle import slso_oracle as O
 
         Xn = X.cpu().numpy()
-        t0 = time.perf_counter()
-        SX = O.sketch(Xn, kind, s, W["seed_S"])
-        sv = O.sketched_svd(SX, qr="lapack")
-        M = O.m_matrix(sv["sigma"], sv["V"], sv["U_R"], sv["rank"], O.jl_matrix(d, k, W["seed_Pi"]))
-        want = O.row_scores(Xn, M)
-        t_or = time.perf_counter() - t0
+        want, orank, t_or, t_od = oracle_job(Xn, kind, s, k, W["seed_S"], W["seed_Pi"])
         stats = {}
         for name, got in (("f32", scores), ("bf16", scores_bf), ("bf16_corrected", scores_bc), ("fp8", scores_f8),
                           ("fp8_corrected", scores_f8c)):
@@ -620,13 +643,23 @@ def main():
                            "top1pct_overlap": len(og & ow) / top,
                            "zero_rows": int(np.sum(~pos)), "zero_rows_nonzero_gpu": int(np.sum(g[~pos] != 0))}
         line["precision_vs_fp64_oracle"] = stats
-        line["precision_vs_fp64_oracle"]["oracle_rank"] = sv["rank"]
-        line["precision_vs_fp64_oracle"]["oracle_seconds"] = t_or
+        line["precision_vs_fp64_oracle"]["oracle_rank"] = orank
         if not args.no_cpu_baseline:
-            v, tot, cores, sample = oracle_throughput(n, d, s, k, kind, W["seed_S"], W["seed_Pi"],
-                                                      rows_sample=65536, qr_steps=96, X_rows=Xn)
-            line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": cores, "kind": "oracle",
-                                    "sample": sample, "est_seconds_full_job": tot}
+            cores = host_cores()
+            rows_a = 131072
+            t_a = oracle_exact_seconds(Xn[:rows_a])
+            t_1 = oracle_one_thread(REF_ROWS, d, s, k, kind, W["seed_S"], W["seed_Pi"], W["xseed"])
+            line["cpu_baseline"] = {
+                "value": n / (t_or + t_od), "unit": "rows/s", "cores": cores, "kind": "oracle",
+                "sample": f"whole job, all {n} rows, measured: sketch + LAPACK QR + SVD of R + M + scores (Oracle B, "
+                          "same S and Pi) then the dec order",
+                "seconds": t_or + t_od, "scores_seconds": t_or, "order_seconds": t_od,
+                "exact_scores": {"kind": "oracle A (exact, blocked QR of X + SVD)", "rows": rows_a,
+                                 "seconds": t_a, "rows_per_s": rows_a / t_a, "cores": cores},
+                "one_thread": ({"rows": REF_ROWS, "seconds": t_1, "rows_per_s": REF_ROWS / t_1, "cores": 1,
+                                "sample": f"whole job on the first {REF_ROWS} rows, BLAS on one thread"}
+                               if t_1 else None),
+            }
     if rank == 0 and world == 1 and args.serving_jobs > 0:
         del X
         torch.cuda.empty_cache()

@@ -57,9 +57,12 @@ typedef enum { SLSO_F64 = 0, SLSO_F32 = 1, SLSO_BF16 = 2, SLSO_FP8_E4M3 = 3 } sl
  *  SRHT         sqrt(n_pad/s) P (H/sqrt(n_pad)) D on X zero-padded to n_pad = 2^ceil(log2 n)
  *               rows; D_i = 1 - 2 (w0 & 1) at counter (lo i, hi i, 0, 2); P keeps the s rows
  *               j with the smallest (w0 at counter (lo j, hi j, 0, 3), j), in ascending j.
- *  GAUSSIAN     (1/sqrt(s)) G, G_ji = bf16_rne(BoxMuller(w0, w1)) at counter (lo i, hi i, j, 4),
- *               BoxMuller(w0, w1) = sqrt(-2 ln((w0+1) 2^-32)) cos(2 pi w1 2^-32), the bf16
- *               rounding decided on the float64 value. */
+ *  GAUSSIAN     (1/sqrt(s)) G, G_ji = bf16_rne(g) with four consecutive columns i sharing one
+ *               Philox block: b = floor(i / 4), counter (lo b, hi b, j, 4); i mod 4 = 0, 1 take
+ *               the cosine and sine normals of the Box-Muller pair (w0, w1), i mod 4 = 2, 3 those
+ *               of (w2, w3); BoxMuller(w0, w1) = sqrt(-2 ln((w0+1) 2^-32)) cos(2 pi w1 2^-32) and
+ *               the sine normal is the cosine of the angle word shifted by 2^30; the bf16
+ *               rounding is decided on the float64 value. */
 /* OSNAP (Sec. 3.1.2, a variant of CountSketch): z blocks of s/z rows, one +-1/sqrt(z) per block in
  * each column of S, bucket b s/z + ((w0 s/z) >> 32), sign 1 - 2 (w1 & 1) from Philox at counter
  * (lo i, hi i, b, 7); z = slso_params.nnz (0: 4); slso_sketch uses z = 4. */
@@ -71,14 +74,18 @@ typedef enum { SLSO_POLICY_DEC = 0, SLSO_POLICY_SWR = 1, SLSO_POLICY_SWOR = 2 } 
 /* The factor R of SX (Algorithm 2/3 step 2).  With R_jj > 0 and SX of full column rank R is unique,
  * so both give the same R up to rounding.
  *  HOUSEHOLDER  unpivoted Householder QR of SX, float64 (orthogonality error ~ kappa(SX) u).
- *  AUTO         for compute != F64: the Gram route first, R = chol(SX^T SX) (float64 SYRK and
- *               blocked Cholesky, half the FMAs of Householder), kept only when a check with 4
- *               seeded Gaussian probes z (Philox at counter (lo c, hi c, q, 8)) estimates
- *               ||R^-T SX^T SX R^-1 - I||_F <= 1e-8 (its error grows like kappa(SX)^2 u; the
- *               relative error of every score is at most that norm); otherwise, and always for
- *               compute = F64, Householder.  Decided on the device; slso_info reports it.
- *               Its scratch (the float32 split of SX, 8 s d bytes, plus O(d^2)) is taken
- *               whether or not the route stands; slso_workspace_size includes it. */
+ *  AUTO         for compute != F64: the Gram route first, R = chol(SX^T SX), kept only when a
+ *               check with 4 seeded Gaussian probes z (Philox at counter (lo c, hi c, q, 8))
+ *               estimates ||R^-T SX^T SX R^-1 - I||_F <= 1e-8 (its error grows like kappa(SX)^2 u;
+ *               the relative error of every score is at most that norm); otherwise, and always
+ *               for compute = F64, Householder.  Decided on the device; slso_info reports it.
+ *               G = SX^T SX comes from exact digit products on the tensor cores (slso_gram; a
+ *               float-float SYRK on the float32 pipe where the tensor route does not apply), and
+ *               for d <= 8192 the Cholesky factor, R^-1, M = R^-1 Pi and the probe check are
+ *               computed in float-float arithmetic (pairs of float32 values, ~2^-48), else in
+ *               float64.  Its scratch (the digit slices of SX, 16 dpad s bytes, or the float32
+ *               split, 8 s d bytes, plus O(d^2)) is taken whether or not the route stands;
+ *               slso_workspace_size includes it. */
 typedef enum { SLSO_FACTOR_AUTO = 0, SLSO_FACTOR_HOUSEHOLDER = 1 } slso_factor;
 
 typedef struct slso_handle slso_handle;

@@ -193,40 +193,49 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
   if (t == 0) sm.bad = pivot(sm, 0) ? 0 : 1;
   __syncthreads();
   if (sm.bad) return false;
+  // warps 1-7 own fixed positions (i, m), m <= i, of the 528 in the lower triangle (at most 3 each):
+  // while j < m the position is D_im's update, while m <= j < i it is B_im's
+  constexpr int kPos = kFb * (kFb + 1) / 2;
+  int pi[3], pm[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int e = t - 32 + q * (kFThreads - 32);
+    pi[q] = -1;
+    pm[q] = 0;
+    if (t >= 32 && e < kPos) {
+      int a = static_cast<int>((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+      while ((a + 1) * (a + 2) / 2 <= e) ++a;
+      while (a * (a + 1) / 2 > e) --a;
+      pi[q] = a;
+      pm[q] = e - a * (a + 1) / 2;
+    }
+  }
   for (int j = 0; j < kFb - 1; ++j) {
     const ff r2{sm.r2h[j], sm.r2l[j]};
-    const int n = kFb - 1 - j;  // rows below j
-    if (t < 32) {
-      if (t == 0) {
-        const ff dij{sm.Dh[j + 1][j], sm.Dl[j + 1][j]};
-        const ff v = ff_fms(ff{sm.Dh[j + 1][j + 1], sm.Dl[j + 1][j + 1]}, ff_mul(dij, dij), r2);
-        sm.Dh[j + 1][j + 1] = v.h;
-        sm.Dl[j + 1][j + 1] = v.l;
-        if (!pivot(sm, j + 1)) sm.bad = 1;
-      }
-    } else {
-      const int u = t - 32, stride = kFThreads - 32;
-      // D: rows i = j+1+a, columns m = j+1+b, b <= a, except (0, 0) (warp 0's)
-      const int tri = n * (n + 1) / 2;
-      for (int e = u + 1; e < tri; e += stride) {
-        int a = static_cast<int>((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
-        while ((a + 1) * (a + 2) / 2 <= e) ++a;
-        while (a * (a + 1) / 2 > e) --a;
-        const int b = e - a * (a + 1) / 2;
-        const int i = j + 1 + a, m = j + 1 + b;
-        const ff p = ff_mul(ff{sm.Dh[i][j], sm.Dl[i][j]}, ff{sm.Dh[m][j], sm.Dl[m][j]});
-        const ff v = ff_fms(ff{sm.Dh[i][m], sm.Dl[i][m]}, p, r2);
-        sm.Dh[i][m] = v.h;
-        sm.Dl[i][m] = v.l;
-      }
-      // B: rows i = j+1.., columns c <= j
-      const int w = j + 1;
-      for (int e = u; e < n * w; e += stride) {
-        const int i = j + 1 + e / w, c = e % w;
-        const ff p = ff_mul(ff{sm.Dh[i][j], sm.Dl[i][j]}, ff{sm.Ih[j][c], sm.Il[j][c]});
-        const ff v = ff_fms(ff{sm.Ih[i][c], sm.Il[i][c]}, p, r2);
-        sm.Ih[i][c] = v.h;
-        sm.Il[i][c] = v.l;
+    if (t == 0) {
+      const ff dij{sm.Dh[j + 1][j], sm.Dl[j + 1][j]};
+      const ff v = ff_fms(ff{sm.Dh[j + 1][j + 1], sm.Dl[j + 1][j + 1]}, ff_mul(dij, dij), r2);
+      sm.Dh[j + 1][j + 1] = v.h;
+      sm.Dl[j + 1][j + 1] = v.l;
+      if (!pivot(sm, j + 1)) sm.bad = 1;
+    } else if (t >= 32) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int i = pi[q], m = pm[q];
+        if (i <= j) continue;  // inactive (also the unused slots, i = -1)
+        const ff dij{sm.Dh[i][j], sm.Dl[i][j]};
+        if (m > j) {
+          if (i == j + 1 && m == j + 1) continue;  // warp 0's element
+          const ff p = ff_mul(dij, ff{sm.Dh[m][j], sm.Dl[m][j]});
+          const ff v = ff_fms(ff{sm.Dh[i][m], sm.Dl[i][m]}, p, r2);
+          sm.Dh[i][m] = v.h;
+          sm.Dl[i][m] = v.l;
+        } else {
+          const ff p = ff_mul(dij, ff{sm.Ih[j][m], sm.Il[j][m]});
+          const ff v = ff_fms(ff{sm.Ih[i][m], sm.Il[i][m]}, p, r2);
+          sm.Ih[i][m] = v.h;
+          sm.Il[i][m] = v.l;
+        }
       }
     }
     __syncthreads();
