@@ -119,14 +119,22 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st) {
   const double tau = p->tau < 0 ? default_tau(p->s, d) : p->tau;
   double* SX = ar.take<double>(static_cast<size_t>(p->s) * d);
+  // FP8 scores of float32 / bfloat16 X after a CountSketch or OSNAP: the column maxima of |X| come
+  // out of the sketch's pass over X, so X is read twice in all
+  const bool fuse_max = p->compute == SLSO_FP8_E4M3 && xdt != SLSO_F64 &&
+                        (p->kind == SLSO_COUNTSKETCH || p->kind == SLSO_OSNAP);
+  unsigned int* colmax = fuse_max ? ar.take<unsigned int>(d) : nullptr;
+  SketchBlock blk;
+  blk.colmax = colmax;
+  if (colmax && !ar.measure()) SLSO_CHECK_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * d, st));
   prof_begin(h, ar, ST_SKETCH, st);
-  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, p->nnz, SX, st));
+  SLSO_TRY(run_sketch(h, ar, X, n, d, ldx, xdt, p->kind, p->s, p->seed_S, p->nnz, SX, st, &blk));
   prof_end(h, ar, st);
   SolveOut so;
   SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st, use_gram(p)));
   const int64_t kk = p->k > 0 ? p->k : d;
   prof_begin(h, ar, ST_SCORES, st);
-  SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, so.M, kk, p->compute, scores, p->correct_frac, st));
+  SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, so.M, kk, p->compute, scores, p->correct_frac, st, colmax));
   prof_end(h, ar, st);
   return SLSO_OK;
 }

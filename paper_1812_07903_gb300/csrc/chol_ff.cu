@@ -262,7 +262,8 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
   return true;
 }
 
-// bar[0..1] grid barrier, bar[2] abort flag (zeroed by the host before the launch).
+// bar[0..1] grid barrier, bar[2] abort flag, bar[3] lookahead breakdown (zeroed by the host before
+// the launch).  Dbuf (2 x 32 x 32 float-float): the next diagonal block's inverse as CTA 0 publishes it.
 // Right-hand sides after the factorisation (every CTA, tasks of 32 x 32 outputs): with the JL
 // matrix Pi (d x k, k > 0) and the probes Z (d x 4), both float64 row-major, Out = X'^T [Pi | Z]
 // (Out_ic = sum over m >= i of X'_mi [Pi | Z]_mc) gives M = R^-1 Pi = diag(2^-e) Out[:, :k] (float64,
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     chol_ff_kernel(double* __restrict__ L, const int* __restrict__ cexp, int d, float2* __restrict__ A,
                    float2* __restrict__ X, double* __restrict__ Rinv, const double* __restrict__ Pi, int k,
                    const double* __restrict__ Z, double* __restrict__ M, float2* __restrict__ Yff, unsigned int* bar,
-                   DevState* __restrict__ st) {
+                   float2* __restrict__ Dbuf, DevState* __restrict__ st) {
   if (*reinterpret_cast<volatile int32_t*>(&st->gram_ok) == 0) return;  // grid-uniform
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -316,7 +317,20 @@ __global__ void __launch_bounds__(kFThreads, 1)
       }
     };
     if (static_cast<int>(blockIdx.x) < nb) fetch_b(blockIdx.x);
-    if (!factor_diag(sm, A, d, k0)) {
+    bool good = true;
+    if (k == 0) {
+      good = factor_diag(sm, A, d, k0);
+    } else if (*reinterpret_cast<volatile int*>(bar + 3) != 0) {  // CTA 0's lookahead broke down
+      good = false;
+    } else if (blockIdx.x != 0) {  // L_kk^-1 as CTA 0 published it during the previous step
+      for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
+        const float2 v = Dbuf[kFb * kFb + e];
+        sm.Ih[e >> 5][e & 31] = v.x;
+        sm.Il[e >> 5][e & 31] = v.y;
+      }
+      __syncthreads();
+    }
+    if (!good) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->gram_ok = 0;
         st->gram_resid = CUDART_NAN;
@@ -359,7 +373,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         }
     }
     if (!sync_all()) return;
-    if (blockIdx.x == 0)  // L_kk into A: every CTA has read A_kk before the barrier above
+    if (k == 0 && blockIdx.x == 0)  // L_00 into A: every CTA has read A_00 before the barrier above
       for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
         const int i = e >> 5, j = e & 31;
         if (k0 + i < d && j <= i) A[static_cast<int64_t>(k0 + i) * d + k0 + j] = make_float2(sm.Dh[i][j], sm.Dl[i][j]);
@@ -411,7 +425,10 @@ __global__ void __launch_bounds__(kFThreads, 1)
         ov[u] = (gi < d && gj < d && !(tk.diag && gj > gi)) ? Y[static_cast<int64_t>(gi) * d + gj] : make_float2(0.f, 0.f);
       }
     };
-    int task = blockIdx.x;
+    // CTA 0 takes only task 0, the update of the next diagonal tile, and then factors that block
+    // (lookahead); the other CTAs share tasks 1.. round-robin.
+    const int cstride = blockIdx.x == 0 ? ntask : static_cast<int>(gridDim.x) - 1;
+    int task = blockIdx.x == 0 ? 0 : static_cast<int>(blockIdx.x);
     Task cur{};
     if (task < ntask) {
       cur = decode(task);
@@ -437,7 +454,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (int u = 0; u < 4; ++u) out[u] = ov[u];
       __syncthreads();
       const Task now = cur;
-      const int next = task + gridDim.x;
+      const int next = task + cstride;
       if (next < ntask) {
         cur = decode(next);
         fetch(cur);
@@ -457,6 +474,20 @@ __global__ void __launch_bounds__(kFThreads, 1)
           Y[static_cast<int64_t>(gi) * d + gj] = make_float2(v.h, v.l);
         }
       task = next;
+    }
+    if (blockIdx.x == 0 && npanel > 0) {
+      // block k+1: factor it (its tile was CTA 0's task), write L into A and publish L^-1
+      __syncthreads();
+      const int k1 = k0 + kFb;
+      if (factor_diag(sm, A, d, k1)) {
+        for (int e = threadIdx.x; e < kFb * kFb; e += kFThreads) {
+          const int i = e >> 5, j = e & 31;
+          if (k1 + i < d && j <= i) A[static_cast<int64_t>(k1 + i) * d + k1 + j] = make_float2(sm.Dh[i][j], sm.Dl[i][j]);
+          Dbuf[kFb * kFb + e] = make_float2(sm.Ih[i][j], sm.Il[i][j]);
+        }
+      } else if (threadIdx.x == 0) {
+        atomicExch(reinterpret_cast<int*>(bar + 3), 1);
+      }
     }
     if (!sync_all()) return;
   }
@@ -715,7 +746,8 @@ bool chol_ff_applies(int64_t d) { return d >= 1 && d <= 8192; }
 
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
                         const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,
-                        cudaStream_t st) {
+                        float2* Dbuf, cudaStream_t st) {
+  if (h.num_sms < 2) return fail(SLSO_ERR_CUDA, "the float-float Cholesky needs at least two SMs");
   const size_t smem = sizeof(Smem);
   SLSO_TRY(raise_smem_limit(chol_ff_kernel, smem));
   int occ = 0;
@@ -725,7 +757,7 @@ slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2
   int d_i = static_cast<int>(d);
   DevState* stp = h.state;
   int k_i = static_cast<int>(k);
-  void* args[] = {&L, &cexp, &d_i, &A, &X, &Rinv, &Pi, &k_i, &Z, &M, &Yff, &bar, &stp};
+  void* args[] = {&L, &cexp, &d_i, &A, &X, &Rinv, &Pi, &k_i, &Z, &M, &Yff, &bar, &Dbuf, &stp};
   SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(chol_ff_kernel), dim3(h.num_sms), dim3(kFThreads),
                                               args, smem, st));
   note_launch();

@@ -409,6 +409,9 @@ struct SketchBlock {
   int64_t n_total = 0;  // 0: the block is the whole X
   bool accumulate = false;
   const uint32_t* srht_rows = nullptr;
+  // CountSketch / OSNAP of float32 or bfloat16 X: also max_i |X_ij| per column j into colmax (float
+  // bits; the caller zeroes it), for the FP8 scores' column scales
+  unsigned int* colmax = nullptr;
 };
 slso_status run_sketch(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, int32_t kind, int64_t s, uint64_t seed, int nnz, double* SX,
@@ -469,6 +472,7 @@ struct GramWork {
   float2* Aff = nullptr;    // d x d float-float working matrices of chol_ff
   float2* Xff = nullptr;
   unsigned int* cbar = nullptr;
+  float2* Dbuf = nullptr;   // 2 x 32 x 32: the lookahead's diagonal block
   float2* Yff = nullptr;    // d x P: X'^T Z
   float2* Wff = nullptr;    // s x P
   float2* vff = nullptr;    // row-chunk partials of SX'^T W
@@ -488,7 +492,7 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
 bool chol_ff_applies(int64_t d);
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
                         const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,
-                        cudaStream_t st);
+                        float2* Dbuf, cudaStream_t st);
 slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, const int* cexp, const float2* X,
                          const float2* Yff, float2* Wff, float2* vpart, int chunks, float2* Vff, const double* Z,
                          double* eres, cudaStream_t st);
@@ -524,9 +528,10 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
                          int64_t s, uint64_t seed, int64_t row0, bool accumulate, double* SX, cudaStream_t st,
                          bool* used);
 // score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
+// colmax_pre (FP8 only, optional): the column maxima of |X| already formed by the sketch pass.
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
-                          cudaStream_t st);
+                          cudaStream_t st, const unsigned int* colmax_pre = nullptr);
 
 // Y = X M (M d x kk row-major float64) written to U (float32, row stride ldu) on the tensor cores
 // for float32 / bfloat16 X (score_tc.cu); *used = false when the SIMT kernel must run instead.
@@ -538,6 +543,6 @@ slso_status run_product_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64
 slso_status score_sum(Handle& h, Arena& ar, const void* scores, int32_t sdt, int64_t n, cudaStream_t st);
 slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, const double* M, int64_t kk, int32_t compute, void* scores,
-                       double correct_frac, cudaStream_t st);
+                       double correct_frac, cudaStream_t st, const unsigned int* colmax_pre = nullptr);
 
 }  // namespace slso

@@ -237,7 +237,7 @@ slso_status correct_top_rows(Handle& h, Arena& ar, const T* X, int64_t n, int64_
 template <class T>
 slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx,
                          const double* M, int64_t kk, int32_t compute, double correct_frac, void* scores,
-                         cudaStream_t st) {
+                         cudaStream_t st, const unsigned int* colmax_pre) {
   const int64_t ncb = ceil_div(kk, kBn);
   dim3 grid(static_cast<unsigned>(ceil_div(n, kBm)), static_cast<unsigned>(ncb));
   double* sums = ar.take<double>(kSumBlocks);
@@ -253,7 +253,7 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
   bool used_tc = false;
   SLSO_TRY(run_scores_tc(h, ar, X, n, d, ldx, std::is_same<T, float>::value ? SLSO_F32
                                                 : (std::is_same<T, double>::value ? SLSO_F64 : SLSO_BF16),
-                         M, kk, compute, static_cast<float*>(scores), &used_tc, st));
+                         M, kk, compute, static_cast<float*>(scores), &used_tc, st, colmax_pre));
   if (used_tc) {
     SLSO_TRY(correct_top_rows(h, ar, X, n, d, ldx, M, kk, compute, correct_frac, static_cast<float*>(scores), st));
     if (ar.measure()) return SLSO_OK;
@@ -282,11 +282,11 @@ slso_status scores_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
 
 slso_status run_scores(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                        int32_t xdt, const double* M, int64_t kk, int32_t compute, void* scores,
-                       double correct_frac, cudaStream_t st) {
+                       double correct_frac, cudaStream_t st, const unsigned int* colmax_pre) {
   switch (xdt) {
-    case SLSO_F64: return scores_typed(h, ar, static_cast<const double*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
-    case SLSO_F32: return scores_typed(h, ar, static_cast<const float*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
-    case SLSO_BF16: return scores_typed(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st);
+    case SLSO_F64: return scores_typed(h, ar, static_cast<const double*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st, colmax_pre);
+    case SLSO_F32: return scores_typed(h, ar, static_cast<const float*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st, colmax_pre);
+    case SLSO_BF16: return scores_typed(h, ar, static_cast<const __nv_bfloat16*>(X), n, d, ldx, M, kk, compute, correct_frac, scores, st, colmax_pre);
     default: return fail(SLSO_ERR_DTYPE, "unsupported X dtype %d", xdt);
   }
 }

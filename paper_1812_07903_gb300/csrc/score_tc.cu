@@ -731,7 +731,7 @@ __global__ void prep_b_fp8_kernel(const double* __restrict__ M, int64_t d, int64
 // take the SIMT kernel instead (k > 256, unaligned X, or an unsupported dtype pair).
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
-                          cudaStream_t st) {
+                          cudaStream_t st, const unsigned int* colmax_pre) {
   *used = false;
   int mode = -1;
   if (xdt == SLSO_F32 && compute == SLSO_F32) mode = MODE_TF32X3;
@@ -782,16 +782,18 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
          make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, 32, L.N);
     mB2 = mB1;
   } else if (fp8) {
-    SLSO_CHECK_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * d, st));
-    const int64_t rows_per_cta = std::max<int64_t>(1024, ceil_div(n, 256));
-    dim3 g(static_cast<unsigned>(ceil_div(d, 256)), static_cast<unsigned>(ceil_div(n, rows_per_cta)));
-    if (xdt == SLSO_F32)
-      colabsmax_kernel<float><<<g, 256, 0, st>>>(static_cast<const float*>(X), n, d, ldx, rows_per_cta, colmax);
-    else
-      colabsmax_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), n, d, ldx,
-                                                        rows_per_cta, colmax);
-    SLSO_CHECK_LAUNCH();
-    fp8_scales_kernel<<<1, 1024, 0, st>>>(colmax, M, d, kk, Kpad, cscale, escale);
+    if (!colmax_pre) {  // the column maxima by a pass of their own (no sketch pass formed them)
+      SLSO_CHECK_CUDA(cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * d, st));
+      const int64_t rows_per_cta = std::max<int64_t>(1024, ceil_div(n, 256));
+      dim3 g(static_cast<unsigned>(ceil_div(d, 256)), static_cast<unsigned>(ceil_div(n, rows_per_cta)));
+      if (xdt == SLSO_F32)
+        colabsmax_kernel<float><<<g, 256, 0, st>>>(static_cast<const float*>(X), n, d, ldx, rows_per_cta, colmax);
+      else
+        colabsmax_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), n, d, ldx,
+                                                          rows_per_cta, colmax);
+      SLSO_CHECK_LAUNCH();
+    }
+    fp8_scales_kernel<<<1, 1024, 0, st>>>(colmax_pre ? colmax_pre : colmax, M, d, kk, Kpad, cscale, escale);
     SLSO_CHECK_LAUNCH();
     prep_b_fp8_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, cscale, escale,
                                           static_cast<__nv_fp8_storage_t*>(B0));

@@ -75,20 +75,28 @@ struct VecLoad<T, 1> {
   __device__ static void load(const T* p, float* o) { o[0] = to_float(p[0]); }
 };
 
-// One CTA per (bucket, column tile of blockDim*VEC columns).  float32/bf16 X.
-template <class T, int VEC, int UNROLL>
+// One CTA per (group of bpc consecutive buckets, column tile of blockDim*VEC columns).  float32/bf16
+// X.  CMAX: also the largest |x| of every column over the rows the CTA reads (an atomicMax of the
+// float bits per column and CTA), so that the FP8 scores' column scales need no pass of their own.
+template <class T, int VEC, int UNROLL, bool CMAX>
 __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X, int64_t d, int64_t ldx,
                                                         const uint32_t* __restrict__ rows,
                                                         const uint32_t* __restrict__ start,
                                                         double* __restrict__ SX, double scale, int acc,
-                                                        DevState* __restrict__ state) {
-  const uint32_t b = blockIdx.x;
+                                                        DevState* __restrict__ state, uint32_t nbuckets, int bpc,
+                                                        unsigned int* __restrict__ colmax) {
   const int64_t c0 = (static_cast<int64_t>(blockIdx.y) * blockDim.x + threadIdx.x) * VEC;
   const bool active = c0 < d;
+  bool bad = false;
+  float cm[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) cm[v] = 0.0f;
+  const uint32_t bfirst = blockIdx.x * static_cast<uint32_t>(bpc);
+  const uint32_t blast = bfirst + bpc < nbuckets ? bfirst + bpc : nbuckets;
+  for (uint32_t b = bfirst; b < blast; ++b) {
   float hi[VEC], lo[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) hi[v] = lo[v] = 0.0f;
-  bool bad = false;
   const uint32_t p0 = start[b], p1 = start[b + 1];
   uint32_t p = p0;
   for (; p + UNROLL <= p1; p += UNROLL) {
@@ -106,6 +114,7 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
       for (int v = 0; v < VEC; ++v) {
         const float xv = active ? x[u][v] : 0.0f;
         bad |= !isfinite(xv);
+        if (CMAX) cm[v] = fmaxf(cm[v], fabsf(xv));
         two_sum_acc(hi[v], lo[v], neg ? -xv : xv);
       }
     }
@@ -119,6 +128,7 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
     for (int v = 0; v < VEC; ++v) {
       const float xv = active ? x[v] : 0.0f;
       bad |= !isfinite(xv);
+      if (CMAX) cm[v] = fmaxf(cm[v], fabsf(xv));
       two_sum_acc(hi[v], lo[v], neg ? -xv : xv);
     }
   }
@@ -130,6 +140,12 @@ __global__ void __launch_bounds__(256) cs_gather_kernel(const T* __restrict__ X,
         const double t = (static_cast<double>(hi[v]) + static_cast<double>(lo[v])) * scale;
         *o = acc ? *o + t : t;
       }
+  }
+  }
+  if (CMAX && active) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+      if (c0 + v < d && cm[v] > 0.0f) atomicMax(colmax + c0 + v, __float_as_uint(cm[v]));
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&state->nonfinite, 1);
 }
@@ -359,7 +375,7 @@ int grid_for(int64_t n, const Handle& h) {
 template <class T>
 slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t ldx,
                         int64_t s, uint64_t seed, int z, uint32_t tag, int64_t row0, int acc, double* SX,
-                        cudaStream_t st) {
+                        cudaStream_t st, unsigned int* colmax) {
   const int64_t N = n * z;
   uint32_t* keys = ar.take<uint32_t>(N);
   uint32_t* vals = ar.take<uint32_t>(N);
@@ -383,15 +399,29 @@ slso_status countsketch(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, 
   } else {
     const bool vec = (d % 4 == 0) && (ldx % 4 == 0) &&
                      (reinterpret_cast<uintptr_t>(X) % (4 * sizeof(T)) == 0);
+    // with the column maxima, a CTA walks 16 consecutive buckets (one atomic per column per CTA)
+    const int bpc = colmax ? 16 : 1;
+    const unsigned gb = static_cast<unsigned>(ceil_div(s, bpc));
+    const uint32_t nbk = static_cast<uint32_t>(s);
     if (vec) {
       const int64_t thr_needed = ceil_div(d, 4);
       const int threads = static_cast<int>(std::min<int64_t>(256, ceil_div(thr_needed, 32) * 32));
-      dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(thr_needed, threads)));
-      cs_gather_kernel<T, 4, 4><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state);
+      dim3 grid(gb, static_cast<unsigned>(ceil_div(thr_needed, threads)));
+      if (colmax)
+        cs_gather_kernel<T, 4, 4, true><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state, nbk,
+                                                                  bpc, colmax);
+      else
+        cs_gather_kernel<T, 4, 4, false><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state,
+                                                                   nbk, bpc, nullptr);
     } else {
       const int threads = static_cast<int>(std::min<int64_t>(256, ceil_div(d, 32) * 32));
-      dim3 grid(static_cast<unsigned>(s), static_cast<unsigned>(ceil_div(d, threads)));
-      cs_gather_kernel<T, 1, 8><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state);
+      dim3 grid(gb, static_cast<unsigned>(ceil_div(d, threads)));
+      if (colmax)
+        cs_gather_kernel<T, 1, 8, true><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state, nbk,
+                                                                  bpc, colmax);
+      else
+        cs_gather_kernel<T, 1, 8, false><<<grid, threads, 0, st>>>(X, d, ldx, vs, start, SX, scale, acc, h.state,
+                                                                   nbk, bpc, nullptr);
     }
   }
   SLSO_CHECK_LAUNCH();
@@ -459,10 +489,10 @@ slso_status sketch_typed(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d,
   const int acc = b.accumulate ? 1 : 0;
   switch (kind) {
     case SLSO_COUNTSKETCH:
-      return countsketch(h, ar, X, n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, b.row0, acc, SX, st);
+      return countsketch(h, ar, X, n, d, ldx, s, seed, 1, TAG_COUNTSKETCH, b.row0, acc, SX, st, b.colmax);
     case SLSO_OSNAP:
       return countsketch(h, ar, X, n, d, ldx, s, seed, nnz > 0 ? nnz : kOsnapDefaultNnz, TAG_OSNAP, b.row0, acc,
-                         SX, st);
+                         SX, st, b.colmax);
     case SLSO_SRHT:
       return srht(h, ar, X, n, d, ldx, s, seed, b.srht_rows, b.row0, b.n_total > 0 ? b.n_total : n, acc, SX, st);
     default:

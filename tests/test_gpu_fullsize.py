@@ -9,7 +9,8 @@ applied to the GPU's own sketch, "Oracle C"):
   the GPU's SX; float32 scores of sampled rows and of the top rows within 1e-4; the order equal
   to a stable (score, index) sort of the GPU's scores; bfloat16 median error under 2%.  R comes
   from the Gram route (probe residual under 1e-10), and every score is within 1e-6 of the scores
-  with the Householder R (factor='householder').
+  with the Householder R (factor='householder').  Then every one of the 10^6 float32 scores against
+  the whole oracle (LAPACK's QR) within 1e-4, and the FP8 scores' median error under 3%.
 * 60,000 x 784 image-like, CountSketch s = 8192 and SRHT s = 2048, k = 64: the whole oracle,
   rank 716 (68 zero columns), every row's score within 1e-4.
 * 4,000,000 x 3072 bfloat16 with a 1% rank-16 outlier subspace, Gaussian s = 6144 on tensor
@@ -78,6 +79,15 @@ def test_benchmark_workload_1m_x_1024_countsketch():
     bf, _ = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="bf16")
     rel = np.abs(bf.cpu().numpy()[rows] - want) / want
     assert float(np.median(rel)) < 2e-2
+
+    # every row against the whole oracle (its own sketch, LAPACK's QR, the same S and Pi):
+    # float32 path within 1e-4; FP8 with the column scales from the sketch's pass, median < 3%
+    want_all, oinfo = O.sketched_leverage(Xh, "countsketch", s, k, seed_S, seed_Pi, qr="lapack")
+    assert oinfo["rank"] == d
+    assert _max_rel(sc, want_all) < 1e-4
+    f8, _ = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="fp8")
+    pos = want_all > 0
+    assert float(np.median(np.abs(f8.cpu().numpy()[pos] - want_all[pos]) / want_all[pos])) < 3e-2
 
 
 @pytest.mark.parametrize("kind,s", [("countsketch", 8192), ("srht", 2048)])
