@@ -360,6 +360,73 @@ def large_bench(args):
     print(json.dumps(out))
 
 
+SHAPES = {
+    # the paper's SST sentence matrix (56 steps x 300-d word vectors) and CMU-MOSI early-fusion
+    # matrix (325 features per step, d = 9750 as printed); synthetic rows of those layouts
+    "text": dict(n=131072, d=16800, s=32768, k=128, gen="text_sequences", xseed=1006, seed_S=2006, seed_Pi=3006,
+                 desc="text_sequences 131072x16800 float32 (SST-shaped: 56 steps x 300-d word vectors, Zipf "
+                      "words, left zero padding)"),
+    "multimodal": dict(n=131072, d=9750, s=16384, k=128, gen="multimodal_sequences", xseed=1007, seed_S=2007,
+                       seed_Pi=3007, desc="multimodal_sequences 131072x9750 float32 (CMU-MOSI-shaped: 325 "
+                                          "early-fused features per step, d = 9750)"),
+}
+
+
+def shape_bench(args, name):
+    """The paper's text- and multimodal-shaped feature matrices: CountSketch leverage + dec order in
+    float32 and bfloat16; one JSON line with stage times and the Gram product's tensor rate."""
+    import torch
+
+    from paper_1812_07903_gb300 import api, inputs
+
+    W = SHAPES[name]
+    n = args.n if args.n != WORKLOAD["n"] else W["n"]
+    d, s, k = W["d"], W["s"], W["k"]
+    torch.cuda.set_device(0)
+    X = getattr(inputs, W["gen"])(n, seed=W["xseed"], device="cuda")
+    h = api.Handle(0)
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    order = torch.empty(n, dtype=torch.int64, device="cuda")
+    peaks, peak_src = _peaks()
+    out = {"config": {"workload": W["desc"] + f", countsketch s={s}, JL k={k}; leverage + dec order", "n": n, "d": d,
+                      "s": s, "k": k, "sketch": "countsketch", "l2": "X larger than L2; no flush"},
+           "metric": "scored rows/s", "unit": "rows/s", "steps": args.steps, "warmup": args.warmup}
+    for compute in ("f32", "bf16"):
+        def step(info=False):
+            r = api.leverage(X, "countsketch", s, k, W["seed_S"], W["seed_Pi"], compute=compute, out=scores,
+                             want_info=info, handle=h)
+            api.order(scores, out=order, handle=h)
+            return r
+        _, info = step(True)
+        for _ in range(max(0, args.warmup - 1)):
+            step()
+        torch.cuda.synchronize()
+        api.profile(True, handle=h)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        stages, launches = api.profile_read(handle=h)
+        api.profile(False, handle=h)
+        per = {nm: v_ / args.steps for nm, (v_, c) in stages.items() if c}
+        # the Gram product: 36 digit products over the 128 x 64 tiles of the lower triangle
+        nbi, nbj = -(-d // 128), -(-d // 64)
+        tiles = sum(min(2 * i + 2, nbj) for i in range(nbi))
+        digit_flops = 36.0 * tiles * 128 * 64 * 2.0 * s
+        syrk_ms = per.get("syrk", float("nan"))
+        out[compute] = {"value": n / (ms / 1e3), "ms_per_step": ms, "gpu_launches": int(launches),
+                        "stages_ms_per_step": {nm: round(v_, 3) for nm, v_ in per.items()},
+                        "gram_route": info["gram_route"], "gram_resid": info["gram_resid"], "rank": info["rank"],
+                        "gram_digit_tflops": digit_flops / (syrk_ms / 1e3) / 1e12,
+                        "gram_frac_of_bf16_peak": digit_flops / (syrk_ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+                        "peak": {"bf16_tflops": peaks["bf16_tflops"], "source": peak_src}}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def max_over_ranks(ms, world, device):
     """The slowest rank's time: every rank of an N-rank run gets the same value (weak scaling times
@@ -390,13 +457,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=512, help="jobs in the serving trace (0 skips it)")
-    ap.add_argument("--config", default="benchmark", choices=["benchmark", "large"],
-                    help="large: the 4M x 3072 bfloat16 Gaussian-sketch workload (its own JSON line)")
+    ap.add_argument("--config", default="benchmark", choices=["benchmark", "large", "text", "multimodal"],
+                    help="large: the 4M x 3072 bfloat16 Gaussian-sketch workload; text / multimodal: the SST- and "
+                         "CMU-MOSI-shaped matrices (each its own JSON line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "large":
         return large_bench(args)
+    if args.config in SHAPES:
+        return shape_bench(args, args.config)
 
     import numpy as np
     import torch

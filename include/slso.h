@@ -81,9 +81,8 @@ typedef enum { SLSO_POLICY_DEC = 0, SLSO_POLICY_SWR = 1, SLSO_POLICY_SWOR = 2 } 
  *               for compute = F64, Householder.  Decided on the device; slso_info reports it.
  *               G = SX^T SX comes from exact digit products on the tensor cores (slso_gram; a
  *               float-float SYRK on the float32 pipe where the tensor route does not apply), and
- *               for d <= 8192 the Cholesky factor, R^-1, M = R^-1 Pi and the probe check are
- *               computed in float-float arithmetic (pairs of float32 values, ~2^-48), else in
- *               float64.  Its scratch (the digit slices of SX, 16 dpad s bytes, or the float32
+ *               the Cholesky factor, R^-1, M = R^-1 Pi and the probe check are computed in
+ *               float-float arithmetic (pairs of float32 values, ~2^-48).  Its scratch (the digit slices of SX, 16 dpad s bytes, or the float32
  *               split, 8 s d bytes, plus O(d^2)) is taken whether or not the route stands;
  *               slso_workspace_size includes it. */
 typedef enum { SLSO_FACTOR_AUTO = 0, SLSO_FACTOR_HOUSEHOLDER = 1 } slso_factor;
@@ -155,13 +154,14 @@ slso_status slso_sketched_svd(slso_handle* handle, const double* SX, int64_t s, 
 /* Gram matrix G = SX^T SX (d x d float64, row-major, symmetric) as the float32 compute path's
  * Gram route forms it for R (R^T R = G at full column rank; Algorithm 2/3 step 2).  Each column j
  * of SX (s x d float64, row-major, s >= 1) is scaled by 2^-e_j, its largest entry then in [1/2, 1),
- * rounded to 47 fractional bits and cut into six signed 8-bit digits; the digit products of order
- * <= 5 run on the tensor cores (bfloat16, float32 accumulation) in 256-row windows where every
- * partial sum of orders 0-2 is an exact integer, and the windows are added as exact int64 sums,
- * so G is deterministic and, for integer-valued columns with at most 47 significant bits below
- * their scale, exact.  Where the tensor route does not apply (s >= 2^25) a float-float SYRK on the
- * float32 pipe forms G instead.  SX, G: caller-owned device memory; asynchronous on stream.
- * Errors: SHAPE unless 1 <= d <= 8192 and 1 <= s < 2^31; INVALID_ARG for NULL pointers. */
+ * rounded to 55 fractional bits and cut into eight signed 7-bit digits; the 36 digit products of
+ * order <= 7 run on the tensor cores (bfloat16, float32 accumulation, one accumulator per order) in
+ * 512-row windows in which every partial sum is an exact integer, and the windows are added as
+ * exact int64 sums, so G is deterministic and, for integer-valued columns with at most 55
+ * significant bits below their scale, exact.  Where the tensor route does not apply (s >= 2^20) a
+ * float-float SYRK on the float32 pipe forms G instead.  SX, G: caller-owned device memory;
+ * asynchronous on stream.
+ * Errors: SHAPE unless 1 <= d <= 24576 and 1 <= s < 2^31; INVALID_ARG for NULL pointers. */
 slso_status slso_gram(slso_handle* handle, const double* SX, int64_t s, int64_t d, double* G, void* stream);
 
 /* Approximate leverage scores (Algorithm 3 with the JL projection Pi):

@@ -65,7 +65,7 @@ slso_status check_params(const slso_params* p, int64_t n, int64_t d) {
   if (!(p->correct_frac >= 0.0 && p->correct_frac <= 1.0))
     return fail(SLSO_ERR_INVALID_ARG, "correct_frac must be in [0, 1]");
   if (std::isnan(p->tau)) return fail(SLSO_ERR_INVALID_ARG, "tau is NaN");
-  if (d > 8192) return fail(SLSO_ERR_SHAPE, "d=%lld exceeds 8192", (long long)d);
+  if (d > kMaxD) return fail(SLSO_ERR_SHAPE, "d=%lld exceeds %lld", (long long)d, (long long)kMaxD);
   if (p->factor != SLSO_FACTOR_AUTO && p->factor != SLSO_FACTOR_HOUSEHOLDER)
     return fail(SLSO_ERR_INVALID_ARG, "unknown factor %d", p->factor);
   return SLSO_OK;
@@ -180,7 +180,7 @@ extern "C" slso_status slso_sketched_svd(slso_handle* handle, const double* SX, 
   SLSO_TRY(check_handle(handle, &h));
   if (!SX || !sigma || !V) return fail(SLSO_ERR_INVALID_ARG, "SX, sigma and V must be non-NULL");
   if (d < 1 || s < d) return fail(SLSO_ERR_SHAPE, "need 1 <= d <= s (s=%lld, d=%lld)", (long long)s, (long long)d);
-  if (d > 8192 || s >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "d <= 8192 and s < 2^31 required");
+  if (d > kMaxD || s >= (int64_t(1) << 31)) return fail(SLSO_ERR_SHAPE, "d <= %lld and s < 2^31 required", (long long)kMaxD);
   if (std::isnan(tau)) return fail(SLSO_ERR_INVALID_ARG, "tau is NaN");
   const double t = tau < 0 ? default_tau(s, d) : tau;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -199,8 +199,9 @@ extern "C" slso_status slso_gram(slso_handle* handle, const double* SX, int64_t 
   Handle* h = nullptr;
   SLSO_TRY(check_handle(handle, &h));
   if (!SX || !G) return fail(SLSO_ERR_INVALID_ARG, "SX and G must be non-NULL");
-  if (d < 1 || d > 8192 || s < 1 || s >= (int64_t(1) << 31))
-    return fail(SLSO_ERR_SHAPE, "need 1 <= d <= 8192 and 1 <= s < 2^31 (s=%lld, d=%lld)", (long long)s, (long long)d);
+  if (d < 1 || d > kMaxD || s < 1 || s >= (int64_t(1) << 31))
+    return fail(SLSO_ERR_SHAPE, "need 1 <= d <= %lld and 1 <= s < 2^31 (s=%lld, d=%lld)", (long long)kMaxD, (long long)s,
+                (long long)d);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return run_plan(*h, [&](Arena& ar) {
     GramWork g = gram_take(*h, ar, s, d);

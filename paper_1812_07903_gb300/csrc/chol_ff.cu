@@ -742,7 +742,7 @@ slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, cons
 
 size_t chol_ff_smem() { return sizeof(Smem); }
 
-bool chol_ff_applies(int64_t d) { return d >= 1 && d <= 8192; }
+bool chol_ff_applies(int64_t d) { return d >= 1 && d <= kMaxD; }
 
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
                         const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,

@@ -130,6 +130,8 @@ slso_status raise_smem_limit(F* fn, size_t bytes) {
 slso_status check_handle(slso_handle* hp, Handle** out);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// Largest d (columns of X): R^-1's column-at-a-time kernel keeps d doubles in shared memory.
+constexpr int64_t kMaxD = 24576;
 inline size_t dtype_size(int32_t dt) {
   switch (dt) {
     case SLSO_F64: return 8;

@@ -124,7 +124,7 @@ slso_status check_job(const slso_job* j) {
   }
   if (j->job == SLSO_JOB_SKETCHED_SVD) {
     if (!j->X || !j->sigma || !j->V) return fail(SLSO_ERR_INVALID_ARG, "sketched SVD job needs SX, sigma and V");
-    if (j->d < 1 || j->n < j->d || j->d > 8192 || j->n >= (int64_t(1) << 31))
+    if (j->d < 1 || j->n < j->d || j->d > kMaxD || j->n >= (int64_t(1) << 31))
       return fail(SLSO_ERR_SHAPE, "sketched SVD job needs 1 <= d <= s (s=%lld, d=%lld)", (long long)j->n,
                   (long long)j->d);
     return SLSO_OK;

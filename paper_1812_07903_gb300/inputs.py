@@ -18,6 +18,12 @@ these generators stand in for their shapes and structure:
 * ``outlier_subspace``: N(0, I) rows with 1% of rows replaced by 20 B^T z from a random
   rank-16 subspace.
 * ``serving_jobs``: a Poisson arrival trace of jobs of uneven n, d and sketch kind.
+* ``text_sequences``: SST-shaped rows (Sec. 5.4): a word sequence of length <= 56, each word a
+  300-d vector of a seeded synthetic vocabulary (Zipf word frequencies), left-zero-padded to 56
+  steps and flattened, d = 56 x 300 = 16800.
+* ``multimodal_sequences``: CMU-MOSI-shaped rows (Sec. 5.5): time steps of early-fused features (a
+  300-d word vector, 20 visual and 5 acoustic values, 325 per step), d = 9750 as the paper prints
+  it, which with 325 features per step is 30 steps (the paper's "20 x 325 = 9750" does not hold).
 """
 from __future__ import annotations
 
@@ -152,3 +158,63 @@ def serving_jobs(n_jobs=512, log2_min=12, log2_max=20, rate_per_s=100.0, seed=40
         jobs.append({"job": j, "arrival_s": float(t[j]), "n": n, "d": d, "kind": kind,
                      "s": serving_sketch_rows(n, d, kind), "k": 64, "seed": 10000 + j})
     return jobs
+
+
+def _zipf_words(n_tok, vocab, g, device):
+    """Word ids with Zipf(1) frequencies over ``vocab`` words (inverse CDF of seeded uniforms)."""
+    w = 1.0 / torch.arange(1, vocab + 1, device=device, dtype=torch.float64)
+    cdf = torch.cumsum(w, 0) / w.sum()
+    u = torch.rand(n_tok, generator=g, device=device, dtype=torch.float64)
+    return torch.clamp(torch.searchsorted(cdf, u), max=vocab - 1)
+
+
+def text_sequences(n, steps=56, emb=300, vocab=20000, seed=1006, device="cpu", dtype=torch.float32,
+                   chunk=1 << 14):
+    """SST-shaped sentence matrix: n x (steps * emb), float32.
+
+    The vocabulary holds ``vocab`` seeded embedding vectors (N(0, I/emb) plus a shared offset, as
+    word vectors share a common direction).  Sentence lengths are 1 + Poisson(17), with 2% of the
+    rows at the maximum (sentences truncated at ``steps`` words), so that every step's columns
+    have full rank.  A sentence of L words fills the last L steps (zero padding on the left).
+    """
+    g = _gen(seed, device)
+    E = torch.randn(vocab, emb, generator=g, device=device, dtype=torch.float32) / math.sqrt(emb)
+    E += 0.1 * torch.randn(1, emb, generator=g, device=device, dtype=torch.float32) / math.sqrt(emb)
+    X = torch.zeros(n, steps * emb, device=device, dtype=dtype)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        m = b - a
+        lam = torch.full((m,), 17.0, device=device, dtype=torch.float64)
+        L = 1 + torch.poisson(lam, generator=g).to(torch.int64)
+        trunc = torch.rand(m, generator=g, device=device) < 0.03
+        L = torch.where(trunc, torch.full_like(L, steps), torch.clamp(L, max=steps))
+        ids = _zipf_words(m * steps, vocab, g, device).view(m, steps)
+        blk = E[ids]  # m x steps x emb
+        pos = torch.arange(steps, device=device).view(1, steps)
+        live = (pos >= (steps - L).view(m, 1)).to(blk.dtype).unsqueeze(-1)
+        X[a:b] = (blk * live).reshape(m, steps * emb).to(dtype)
+    return X
+
+
+def multimodal_sequences(n, steps=30, emb=300, visual=20, acoustic=5, vocab=20000, seed=1007, device="cpu",
+                         dtype=torch.float32, chunk=1 << 14):
+    """CMU-MOSI-shaped early-fusion matrix: n x (steps * (emb + visual + acoustic)), float32.
+
+    Every time step concatenates a word vector (the same synthetic vocabulary construction as
+    ``text_sequences``, Zipf frequencies), ``visual`` facial-expression-like values (a per-clip
+    level plus N(0, 0.5^2) per step) and ``acoustic`` prosody-like values (N(0, 1)).
+    """
+    g = _gen(seed, device)
+    E = torch.randn(vocab, emb, generator=g, device=device, dtype=torch.float32) / math.sqrt(emb)
+    feat = emb + visual + acoustic
+    X = torch.empty(n, steps * feat, device=device, dtype=dtype)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        m = b - a
+        ids = _zipf_words(m * steps, vocab, g, device).view(m, steps)
+        words = E[ids]  # m x steps x emb
+        level = torch.randn(m, 1, visual, generator=g, device=device, dtype=torch.float32)
+        vis = level + 0.5 * torch.randn(m, steps, visual, generator=g, device=device, dtype=torch.float32)
+        aco = torch.randn(m, steps, acoustic, generator=g, device=device, dtype=torch.float32)
+        X[a:b] = torch.cat([words, vis, aco], dim=2).reshape(m, steps * feat).to(dtype)
+    return X
