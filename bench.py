@@ -34,17 +34,70 @@ METRIC = "scored rows/s (BF16 vs FP32, ≤2% median rel err) + roofline %; p99 j
 WORKLOAD = dict(n=1_000_000, d=1024, s=16384, k=128, kind="countsketch", xseed=1003, seed_S=2003, seed_Pi=3003)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070 / 1e3  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz = 1.26
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3
-# float-float multiply-add (TwoProd by FMA with the split operand's cross terms, TwoSum): 12 float32
-# instructions, so the float32 pipe's issue rate bounds the Gram SYRK at this many TFLOP/s
-FF_SYRK_PEAK_TFLOPS = 152 * 128 * 2.070 / 12 * 2 / 1e3
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the named kernel at
-# s = 16384, d = 1024 from one ncu capture of its current source; None whenever the kernel changed
-# since, until it is captured again.
-QR_TRAFFIC_BYTES = None  # qr_left_kernel<64, 256>
-SYRK_TRAFFIC_BYTES = 177_818_112 + 8_952_320  # gram_syrk_kernel<true>
+# float-float multiply-add (TwoProd by FMA, TwoSum and the renormalisation): about 12 float32
+# instructions, so the float32 pipe's issue rate bounds float-float work at this many TFLOP/s
+FF_PEAK_TFLOPS = 152 * 128 * 2.070 / 12 * 2 / 1e3
+# bfloat16 digit products of the exact Gram split: 8 digits a column, the 36 pairs (p, q) with
+# p + q <= 7 (a symmetric pair counted once per product)
+GRAM_DIGIT_PRODUCTS = 36
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each stage's kernel on the
+# 1,000,000 x 1024 workload (s = 16384, k = 128), from one ncu capture of its current source; None
+# whenever the kernel changed since, until it is captured again.
+TRAFFIC_BYTES = {"scores": None, "sketch": None, "syrk": None, "chol": None}
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point
+
+
+def stage_rooflines(per, n, d, s, k, peaks, peak_src):
+    """Roofline of each timed stage's dominant kernel on the n x d float32 step (k = JL width):
+    algorithmic bytes or flops per call over the stage's CUDA-event time."""
+    out = {}
+    full = (n, d, s, k) == (WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["s"], WORKLOAD["k"])
+    tr = (lambda nm: TRAFFIC_BYTES.get(nm)) if full else (lambda nm: None)
+    hbm = peaks["hbm_gbs"]
+    if "scores" in per:  # X read once, l written; Y = X M never leaves the SM
+        b = n * d * 4.0 + n * 4.0
+        a = b / (per["scores"] / 1e3) / 1e9
+        out["scores"] = {"kernel": "score_tm_kernel (X M on tcgen05, X's pieces in TMEM, row norms)", "bound": "hbm",
+                         "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm, "traffic": tr("scores"),
+                         "algorithmic": b, "peak_source": peak_src, "ms": per["scores"]}
+    if "sketch" in per:  # X read once, SX (float64) written once
+        b = n * d * 4.0 + s * d * 8.0
+        a = b / (per["sketch"] / 1e3) / 1e9
+        out["sketch"] = {"kernel": "cs_gather_kernel (CountSketch bucket sums + FP8 column maxima)", "bound": "hbm",
+                         "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm, "traffic": tr("sketch"),
+                         "algorithmic": b, "peak_source": peak_src, "ms": per["sketch"]}
+    if "syrk" in per:  # 36 bf16 digit SYRKs over the lower triangle, 2 flops a multiply-add
+        f = GRAM_DIGIT_PRODUCTS * float(s) * d * (d + 1)
+        a = f / (per["syrk"] / 1e3) / 1e12
+        pk = peaks["bf16_tflops_sustained"]
+        out["syrk"] = {"kernel": "gram_tc_kernel (exact G = SX^T SX from bfloat16 digits on tcgen05)",
+                       "bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                       "traffic": tr("syrk"), "algorithmic": f, "peak_source": peak_src + " (bf16 sustained)",
+                       "ms": per["syrk"]}
+    if "chol" in per:  # Cholesky d^3/3 + triangular inverse d^3/3 + M and probes d^2 (k + 4), float-float
+        f = 2.0 * d ** 3 / 3.0 + d * d * (k + 4.0)
+        a = f / (per["chol"] / 1e3) / 1e12
+        out["chol"] = {"kernel": "chol_ff_kernel (float-float Cholesky, R^-1, M in one cooperative launch)",
+                       "bound": "alu", "achieved": a, "peak": FF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": a / FF_PEAK_TFLOPS, "traffic": tr("chol"), "algorithmic": f,
+                       "peak_source": "derived: 152 SM x 128 FP32 lanes x 2.07 GHz / 12 instructions per "
+                                      "float-float multiply-add x 2 flops", "ms": per["chol"]}
+    if "qr" in per and per["qr"] > 0.01:
+        f = 2.0 * s * d * d - 2.0 * d ** 3 / 3.0
+        a = f / (per["qr"] / 1e3) / 1e12
+        out["qr"] = {"kernel": "qr_kernel (FP64 Householder, cooperative)", "bound": "alu", "achieved": a,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a / FP64_PEAK_TFLOPS, "traffic": None,
+                     "algorithmic": f, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz",
+                     "ms": per["qr"]}
+    if "order" in per:  # scores read, 64-bit order written, one 32-bit key pass per radix digit pass
+        b = n * 4.0 + n * 8.0
+        a = b / (per["order"] / 1e3) / 1e9
+        out["order"] = {"kernel": "radix order (key/index passes)", "bound": "hbm", "achieved": a, "peak": hbm,
+                        "unit": "GB/s", "frac": a / hbm, "traffic": None, "algorithmic": b,
+                        "peak_source": peak_src, "ms": per["order"]}
+    return out
 
 
 def _peaks():
@@ -427,6 +480,67 @@ def shape_bench(args, name):
     print(json.dumps(out))
 
 
+IMAGE = dict(n=60000, d=784, k=64, xseed=1002, seed_S=2002, seed_Pi=3002,
+             kinds=(("srht", 2048), ("countsketch", 8192)))
+
+
+def image_bench(args):
+    """The MNIST-shaped image matrix (60000 x 784, 68 zero columns, rank 716): the SRHT (s = 2048,
+    padded to 65536 rows) and CountSketch (s = 8192) sketches alone and the whole leverage + dec
+    order in float32; one JSON line with the sketch's achieved HBM rate."""
+    import torch
+
+    from paper_1812_07903_gb300 import api, inputs
+
+    W = IMAGE
+    n, d, k = W["n"], W["d"], W["k"]
+    torch.cuda.set_device(0)
+    X, _ = inputs.image_like(n, d, seed=W["xseed"], device="cuda")
+    h = api.Handle(0)
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    order = torch.empty(n, dtype=torch.int64, device="cuda")
+    peaks, peak_src = _peaks()
+    out = {"config": {"workload": f"image_like {n}x{d} float32 (MNIST-shaped: uint8/255 pixels, rank-50 "
+                                  "structure + noise, 68 zero columns); leverage + dec order, JL k=64",
+                      "n": n, "d": d, "k": k, "l2": "X (188 MB) larger than L2; no flush"},
+           "metric": "scored rows/s", "unit": "rows/s", "steps": args.steps, "warmup": args.warmup}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        api.profile(True, handle=h)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        stages, launches = api.profile_read(handle=h)
+        api.profile(False, handle=h)
+        return e0.elapsed_time(e1) / args.steps, stages, launches
+
+    for kind, s in W["kinds"]:
+        ms_sk, _, l_sk = timed(lambda: api.sketch(X, kind, s, W["seed_S"], handle=h))
+        _, info = api.leverage(X, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", out=scores, handle=h)
+
+        def step():
+            api.leverage(X, kind, s, k, W["seed_S"], W["seed_Pi"], compute="f32", out=scores, want_info=False,
+                         handle=h)
+            api.order(scores, out=order, handle=h)
+        ms, stages, launches = timed(step)
+        xbytes = n * d * 4.0
+        out[kind] = {"s": s, "sketch_ms": ms_sk, "sketch_launches_per_call": l_sk / args.steps,
+                     "sketch_x_read_gbs": xbytes / (ms_sk / 1e3) / 1e9,
+                     "sketch_frac_of_hbm": xbytes / (ms_sk / 1e3) / 1e9 / peaks["hbm_gbs"],
+                     "value": n / (ms / 1e3), "ms_per_step": ms, "gpu_launches": int(launches),
+                     "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages.items() if c},
+                     "rank": info["rank"], "svd_route": info["svd_route"], "gram_route": info["gram_route"]}
+    out["peak"] = {"hbm_gbs": peaks["hbm_gbs"], "source": peak_src}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def max_over_ranks(ms, world, device):
     """The slowest rank's time: every rank of an N-rank run gets the same value (weak scaling times
@@ -457,7 +571,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=512, help="jobs in the serving trace (0 skips it)")
-    ap.add_argument("--config", default="benchmark", choices=["benchmark", "large", "text", "multimodal"],
+    ap.add_argument("--config", default="benchmark", choices=["benchmark", "large", "text", "multimodal", "image"],
                     help="large: the 4M x 3072 bfloat16 Gaussian-sketch workload; text / multimodal: the SST- and "
                          "CMU-MOSI-shaped matrices (each its own JSON line)")
     args = ap.parse_args()
@@ -467,6 +581,8 @@ def main():
         return large_bench(args)
     if args.config in SHAPES:
         return shape_bench(args, args.config)
+    if args.config == "image":
+        return image_bench(args)
 
     import numpy as np
     import torch
@@ -538,42 +654,17 @@ def main():
     value16 = job_rows_per_s(n, world, ms16)
     peaks, peak_src = _peaks()
 
-    # ---- roofline of the dominant stage's kernel
+    # ---- roofline of every stage's kernel, and the dominant one
     per = {name: ms_ / args.steps for name, (ms_, c) in stages32.items() if c}
-    dom = max(per, key=per.get)
-    if "syrk" in per and per["syrk"] >= per.get("qr", 0.0):
-        # the Gram route's SYRK (float-float on the float32 pipe): s d (d + 1) / 2 multiply-adds of
-        # float64-class accuracy, 2 flops each, against 12 float32 instructions per multiply-add
-        flops = float(s) * d * (d + 1)
-        ach = flops / (per["syrk"] / 1e3) / 1e12
-        roof = {"kernel": "gram_syrk_kernel (float-float SYRK G = SX^T SX)", "bound": "alu", "achieved": ach,
-                "peak": FF_SYRK_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FF_SYRK_PEAK_TFLOPS,
-                "traffic": SYRK_TRAFFIC_BYTES if (s, d) == (16384, 1024) else None,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2.07 GHz / 12 instructions per float-float "
-                               "multiply-add x 2 flops"}
-    elif dom == "qr":
-        flops = 2.0 * s * d * d - 2.0 * d ** 3 / 3.0
-        ach = flops / (per["qr"] / 1e3) / 1e12
-        roof = {"kernel": "qr_kernel (FP64 Householder, cooperative)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": QR_TRAFFIC_BYTES if (s, d) == (16384, 1024) else None,
-                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz (probe measured 1.198)"}
-    elif dom == "sketch":
-        byts = n * d * 4.0 + s * d * 8.0
-        ach = byts / (per["sketch"] / 1e3) / 1e9
-        roof = {"kernel": "countsketch gather", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src}
-    else:
-        flops = 2.0 * n * d * k
-        ach = flops / (per[dom] / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "peak_source": "derived FP32 FMA peak"}
+    roofs = stage_rooflines(per, n, d, s, k, peaks, peak_src)
+    dom = max(roofs, key=lambda nm: roofs[nm]["ms"])
+    roof = dict(roofs[dom])
 
     line = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(n, d, s, k, kind),
-        "roofline": roof, "gpu_launches": int(launches32),
+        "roofline": roof, "stage_rooflines": roofs, "gpu_launches": int(launches32),
         "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages32.items() if c},
         "bf16": {"value": value16, "unit": "rows/s", "ms_per_step": ms16,
                  "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages16.items() if c}},
@@ -585,8 +676,9 @@ def main():
         "fp8_corrected": {"value": job_rows_per_s(n, world, ms8c), "unit": "rows/s", "ms_per_step": ms8c,
                           "correct_frac": CORRECT_FRAC,
                           "stages_ms_per_step": {nm: round(v_ / args.steps, 4) for nm, (v_, c) in stages8c.items() if c}},
-        "solve": "R = chol(SX^T SX) (float-float SYRK, fp64 Cholesky) kept by a 4-probe orthogonality check "
-                 "(else fp64 Householder QR); certified R^-1",
+        "solve": "G = SX^T SX exactly split into bfloat16 digits on the tensor cores; float-float Cholesky, "
+                 "R^-1 and M = R^-1 Pi in one cooperative kernel; kept by a 4-probe orthogonality check "
+                 "(else fp64 Householder QR)",
         "rank_info": {"rank": info["rank"], "svd_route": info["svd_route"], "score_sum": info["score_sum"],
                       "gram_route": info["gram_route"], "gram_resid": info["gram_resid"]},
         "clocks": clk,

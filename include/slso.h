@@ -333,6 +333,22 @@ slso_status slso_order_static(const void* scores, int32_t sdt, int64_t n, int64_
  * caller a fixed footprint and to exercise allocation-failure paths. */
 slso_status slso_set_pool_limit(slso_handle* handle, size_t bytes);
 
+/* Operand form of the float32 score product X M (Algorithm 3 step 4) for k <= 128 on the tensor
+ * cores (float32 X, compute SLSO_F32).  X = Xhi + Xlo and M = Mhi + Mlo with tf32 high parts;
+ * all forms accumulate in float32 and keep Y = X M on the SM.
+ *   SLSO_SCORE_FORM_MIXED (default): Xhi Mhi in tf32 plus bf16(Xlo) bf16(Mhi) + bf16(Xhi)
+ *     bf16(Mlo) in bfloat16, X's pieces in tensor memory; every rounded or dropped term is below
+ *     2^-18 |x_il m_lj|.
+ *   SLSO_SCORE_FORM_TF32X3: Xhi Mhi + Xhi Mlo + Xlo Mhi in tf32, X's pieces in tensor memory
+ *     (below 2^-21 |x_il m_lj|).
+ *   SLSO_SCORE_FORM_TF32X3_SMEM: the same products with X's pieces in shared memory.
+ * The choice holds for later calls on the handle; other shapes and precisions ignore it.
+ * Unknown forms: SLSO_ERR_INVALID_ARG. */
+#define SLSO_SCORE_FORM_MIXED 0
+#define SLSO_SCORE_FORM_TF32X3 1
+#define SLSO_SCORE_FORM_TF32X3_SMEM 2
+slso_status slso_set_score_form(slso_handle* handle, int32_t form);
+
 /* Self-test of the bounded device-side waits every kernel relies on (no GPU fault involved):
  * what = 0 runs the ready-flag wait of the QR on a flag that nothing sets, what = 1 the
  * mbarrier wait of the tensor-core kernels on a barrier that nothing completes, each limited to

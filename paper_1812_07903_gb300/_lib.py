@@ -23,7 +23,7 @@ EXPORTS = (
     "slso_version", "slso_last_error", "slso_create", "slso_destroy", "slso_workspace_size",
     "slso_sketch", "slso_sketched_svd", "slso_gram", "slso_leverage", "slso_order", "slso_rank_rows_host",
     "slso_profile", "slso_profile_read", "slso_order_static", "slso_sample_order",
-    "slso_rank_rows_host_batch", "slso_set_pool_limit", "slso_selftest_wait", "slso_server_cancel",
+    "slso_rank_rows_host_batch", "slso_set_pool_limit", "slso_set_score_form", "slso_selftest_wait", "slso_server_cancel",
     "slso_approx_u", "slso_rank_rows_streamed",
     "slso_server_create", "slso_server_destroy", "slso_server_submit", "slso_server_poll", "slso_server_stats",
     "slso_server_counters",
@@ -97,6 +97,7 @@ def load():
         "slso_sample_order": ([vp, vp, i32, i64, i32, ctypes.c_uint64, vp, vp], i32),
         "slso_rank_rows_host_batch": ([vp, i64, vp, i64, i64, i64, i32, vp, vp, vp, vp, vp], i32),
         "slso_set_pool_limit": ([vp, ctypes.c_size_t], i32),
+        "slso_set_score_form": ([vp, i32], i32),
         "slso_rank_rows_streamed": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), i64, vp, vp,
                                      ctypes.POINTER(Info), vp], i32),
         "slso_approx_u": ([vp, vp, i64, i64, i64, i32, ctypes.POINTER(Params), vp, i64, ctypes.POINTER(Info), vp], i32),

@@ -267,6 +267,16 @@ def set_pool_limit(nbytes, handle=None):
     L.check(L.load().slso_set_pool_limit(h.ptr, int(nbytes)))
 
 
+SCORE_FORMS = {"mixed": 0, "tf32x3": 1, "tf32x3_smem": 2}
+
+
+def set_score_form(form, handle=None):
+    """slso_set_score_form: operand form of the float32 score product for k <= 128 ("mixed",
+    "tf32x3", "tf32x3_smem")."""
+    h = handle or default_handle()
+    L.check(L.load().slso_set_score_form(h.ptr, SCORE_FORMS[form]))
+
+
 def selftest_wait(what="flag", limit_us=2000, handle=None):
     """slso_selftest_wait: run a bounded device wait that nothing signals; raises SlsoError(TIMEOUT)."""
     h = handle or default_handle()

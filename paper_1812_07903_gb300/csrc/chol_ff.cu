@@ -153,20 +153,32 @@ __device__ __forceinline__ ff ff_rsqrt(ff a) {
   return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), res.h));
 }
 
-// Pivot j of the diagonal block: r_j = 1 / sqrt(D_jj), r_j^2 and s_j = D_jj r_j = sqrt(D_jj); false on
-// a non-positive or non-finite pivot.
-__device__ __forceinline__ bool pivot(Smem& sm, int j) {
-  const ff piv{sm.Dh[j][j], sm.Dl[j][j]};
+// 1 / a: y0 ~ 1 / a_h (the hardware's approximate reciprocal, relative error below 2^-22), one
+// float32 Newton step y = y0 + y0 (1 - a_h y0) (error about 2^-24), then y + y (1 - a y) in
+// float-float with the residual formed exactly (error about 2^-48).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ ff ff_recip(ff a) {
+  const float y0 = rcp_approx(a.h);
+  const float y = __fmaf_rn(y0, __fmaf_rn(-a.h, y0, 1.0f), y0);
+  const float p = __fmul_rn(a.h, y);
+  const float e = __fmaf_rn(a.h, y, -p);
+  const float r = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), e), __fmul_rn(a.l, y));
+  return fast_two_sum(y, __fmul_rn(y, r));
+}
+
+// Pivot j of the diagonal block: r_j^2 = 1 / D_jj (all the column updates need); false on a
+// non-positive or non-finite pivot.  r_j = 1 / sqrt(D_jj) and s_j = sqrt(D_jj) follow at the end.
+__device__ __forceinline__ bool pivot(Smem& sm, int j, ff piv) {
   if (!(piv.h > 0.f) || !isfinite(piv.h) || !isfinite(piv.l)) return false;
-  const ff r = ff_rsqrt(piv);
-  const ff r2 = ff_mul(r, r);
-  const ff sq = ff_mul(piv, r);
-  sm.rh[j] = r.h;
-  sm.rl[j] = r.l;
+  const ff r2 = ff_recip(piv);
   sm.r2h[j] = r2.h;
   sm.r2l[j] = r2.l;
-  sm.sh[j] = sq.h;
-  sm.sl[j] = sq.l;
+  sm.sh[j] = piv.h;  // the pivot itself, for the final pass
+  sm.sl[j] = piv.l;
   return true;
 }
 
@@ -190,7 +202,7 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
     sm.Il[i][j] = 0.f;
   }
   __syncthreads();
-  if (t == 0) sm.bad = pivot(sm, 0) ? 0 : 1;
+  if (t == 0) sm.bad = pivot(sm, 0, ff{sm.Dh[0][0], sm.Dl[0][0]}) ? 0 : 1;
   __syncthreads();
   if (sm.bad) return false;
   // warps 1-7 own fixed positions (i, m), m <= i, of the 528 in the lower triangle (at most 3 each):
@@ -217,30 +229,59 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
       const ff v = ff_fms(ff{sm.Dh[j + 1][j + 1], sm.Dl[j + 1][j + 1]}, ff_mul(dij, dij), r2);
       sm.Dh[j + 1][j + 1] = v.h;
       sm.Dl[j + 1][j + 1] = v.l;
-      if (!pivot(sm, j + 1)) sm.bad = 1;
+      if (!pivot(sm, j + 1, v)) sm.bad = 1;
     } else if (t >= 32) {
+      // branch-free over the slots: target -= D_ij src r_j^2 with (target, src) = (D_im, D_mj)
+      // while m > j, (B_im, B_jm) while m <= j; inactive slots compute on row 0 and store nothing.
+      // Every slot's operands are loaded before any store, so that the three chains interleave
+      // (a store through one slot's pointer could otherwise alias the next slot's loads).
+      float ah[3], al[3], bh[3], bl[3], ch[3], cl[3];
+      float* th[3];
+      float* tl[3];
+      bool on[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int i = pi[q], m = pm[q];
-        if (i <= j) continue;  // inactive (also the unused slots, i = -1)
-        const ff dij{sm.Dh[i][j], sm.Dl[i][j]};
-        if (m > j) {
-          if (i == j + 1 && m == j + 1) continue;  // warp 0's element
-          const ff p = ff_mul(dij, ff{sm.Dh[m][j], sm.Dl[m][j]});
-          const ff v = ff_fms(ff{sm.Dh[i][m], sm.Dl[i][m]}, p, r2);
-          sm.Dh[i][m] = v.h;
-          sm.Dl[i][m] = v.l;
-        } else {
-          const ff p = ff_mul(dij, ff{sm.Ih[j][m], sm.Il[j][m]});
-          const ff v = ff_fms(ff{sm.Ih[i][m], sm.Il[i][m]}, p, r2);
-          sm.Ih[i][m] = v.h;
-          sm.Il[i][m] = v.l;
-        }
+        on[q] = i > j && !(i == j + 1 && m == j + 1);
+        const bool dpart = m > j;
+        const int ii = on[q] ? i : 0;
+        th[q] = dpart ? &sm.Dh[ii][m] : &sm.Ih[ii][m];
+        tl[q] = dpart ? &sm.Dl[ii][m] : &sm.Il[ii][m];
+        bh[q] = dpart ? sm.Dh[m][j] : sm.Ih[j][m];
+        bl[q] = dpart ? sm.Dl[m][j] : sm.Il[j][m];
+        ah[q] = sm.Dh[ii][j];
+        al[q] = sm.Dl[ii][j];
+        ch[q] = *th[q];
+        cl[q] = *tl[q];
       }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const ff v = ff_fms(ff{ch[q], cl[q]}, ff_mul(ff{ah[q], al[q]}, ff{bh[q], bl[q]}), r2);
+        ch[q] = v.h;
+        cl[q] = v.l;
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (on[q]) {
+          *th[q] = ch[q];
+          *tl[q] = cl[q];
+        }
     }
     __syncthreads();
     if (sm.bad) return false;
   }
+  // r_j = 1 / sqrt(D_jj) and s_j = sqrt(D_jj) from the pivots (sh, sl hold D_jj)
+  if (t < kFb) {
+    const ff piv{sm.sh[t], sm.sl[t]};
+    const ff r = ff_rsqrt(piv);
+    const ff sq = ff_mul(piv, r);
+    sm.rh[t] = r.h;
+    sm.rl[t] = r.l;
+    __syncwarp();
+    sm.sh[t] = sq.h;
+    sm.sl[t] = sq.l;
+  }
+  __syncthreads();
   // L_ij = D_ij r_j (i > j), L_jj = s_j; L_kk^-1 row j = B_j r_j
   for (int e = t; e < kFb * kFb; e += kFThreads) {
     const int i = e >> 5, j = e & 31;
@@ -264,15 +305,16 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
 
 // bar[0..1] grid barrier, bar[2] abort flag, bar[3] lookahead breakdown (zeroed by the host before
 // the launch).  Dbuf (2 x 32 x 32 float-float): the next diagonal block's inverse as CTA 0 publishes it.
-// Right-hand sides after the factorisation (every CTA, tasks of 32 x 32 outputs): with the JL
-// matrix Pi (d x k, k > 0) and the probes Z (d x 4), both float64 row-major, Out = X'^T [Pi | Z]
-// (Out_ic = sum over m >= i of X'_mi [Pi | Z]_mc) gives M = R^-1 Pi = diag(2^-e) Out[:, :k] (float64,
-// d x k row-major; st->m_ready = 1) and Y'' = X'^T Z (float-float, d x 4) for the probe check.
+// Right-hand sides: with the JL matrix Pi (d x k_rhs; none when k_rhs = 0) and the probes Z (d x 4),
+// both float64 row-major, Out = X'^T [Pi | Z] (Out_ic = sum over m >= i of X'_mi [Pi | Z]_mc; d x
+// (k_rhs + 4) float-float, accumulated row block by row block in part C of the step that finishes
+// that block of X') gives M = R^-1 Pi = diag(2^-e) Out[:, :k_rhs] (float64, d x k_rhs row-major;
+// st->m_ready = 1) and Y'' = X'^T Z (float-float, d x 4) for the probe check.
 __global__ void __launch_bounds__(kFThreads, 1)
     chol_ff_kernel(double* __restrict__ L, const int* __restrict__ cexp, int d, float2* __restrict__ A,
-                   float2* __restrict__ X, double* __restrict__ Rinv, const double* __restrict__ Pi, int k,
+                   float2* __restrict__ X, double* __restrict__ Rinv, const double* __restrict__ Pi, int k_rhs,
                    const double* __restrict__ Z, double* __restrict__ M, float2* __restrict__ Yff, unsigned int* bar,
-                   float2* __restrict__ Dbuf, DevState* __restrict__ st) {
+                   float2* __restrict__ Dbuf, float2* __restrict__ Out, DevState* __restrict__ st) {
   if (*reinterpret_cast<volatile int32_t*>(&st->gram_ok) == 0) return;  // grid-uniform
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -290,6 +332,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
     X[e] = make_float2(i == j ? 1.f : 0.f, 0.f);
   }
+  for (int64_t e = gtid; e < static_cast<int64_t>(d) * (k_rhs + 4); e += gstride) Out[e] = make_float2(0.f, 0.f);
   auto sync_all = [&]() -> bool {
     if (grid_barrier_ff(bar, bar + 1, abort_flag)) return true;
     if (threadIdx.x == 0) atomicExch(&st->timeout, 7);
@@ -382,14 +425,26 @@ __global__ void __launch_bounds__(kFThreads, 1)
     // pipelined: every thread fetches the next task's operand and output elements into registers
     // before it computes the current one, so the L2 latency hides behind the arithmetic.
     const int ntri = npanel * (npanel + 1) / 2;
-    const int ntask = ntri + npanel * (k + 1);
+    const int nbt = npanel * (k + 1);
+    const int width = k_rhs + 4, ncb = (width + kFb - 1) / kFb;
+    // the right-hand sides: row block k of X' is final after part B, so its share of
+    // Out = X'^T [Pi | Z] goes into the tiles (I <= k, Cb) now
+    const int ntask = ntri + nbt + (k + 1) * ncb;
     struct Task {
       int r0, c0;
-      bool tri, diag;
+      bool tri, diag, rhs;
     };
     auto decode = [&](int task) {
       Task tk;
-      if (task < ntri) {
+      tk.rhs = false;
+      if (task >= ntri + nbt) {  // Out tile (I, Cb) += X'[k0.., I block]^T [Pi | Z][k0.., Cb block]
+        const int u = task - ntri - nbt;
+        tk.r0 = (u / ncb) * kFb;
+        tk.c0 = (u % ncb) * kFb;
+        tk.tri = false;
+        tk.diag = false;
+        tk.rhs = true;
+      } else if (task < ntri) {
         int a = static_cast<int>((sqrt(8.0 * task + 1.0) - 1.0) * 0.5);
         while ((a + 1) * (a + 2) / 2 <= task) ++a;
         while (a * (a + 1) / 2 > task) --a;
@@ -410,6 +465,23 @@ __global__ void __launch_bounds__(kFThreads, 1)
     float2 pv[4], qv[4], ov[4];
     const int ti = threadIdx.x >> 3, tj0 = (threadIdx.x & 7) * 4;
     auto fetch = [&](const Task& tk) {
+      if (tk.rhs) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
+          // P[hi][lo] = X'[k0 + hi][r0 + lo];  Q[hi][lo] = [Pi | Z][k0 + hi][c0 + lo] (float64 -> pair)
+          pv[u] = (k0 + hi < d && tk.r0 + lo < d) ? X[static_cast<int64_t>(k0 + hi) * d + tk.r0 + lo]
+                                                  : make_float2(0.f, 0.f);
+          const int r = k0 + hi, c = tk.c0 + lo;
+          double v = 0.0;
+          if (r < d) v = c < k_rhs ? Pi[static_cast<int64_t>(r) * k_rhs + c] : (c < width ? Z[r * 4 + (c - k_rhs)] : 0.0);
+          const float h = __double2float_rn(v);
+          qv[u] = make_float2(h, __double2float_rn(v - static_cast<double>(h)));
+          const int gi = tk.r0 + ti, gj = tk.c0 + tj0 + u;
+          ov[u] = (gi < d && gj < width) ? Out[static_cast<int64_t>(gi) * width + gj] : make_float2(0.f, 0.f);
+        }
+        return;
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
@@ -439,6 +511,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = threadIdx.x + u * kFThreads, hi = e >> 5, lo = e & 31;
+        if (cur.rhs) {
+          sm.Ph[hi][lo] = pv[u].x;
+          sm.Pl[hi][lo] = pv[u].y;
+          sm.Qh[hi][lo] = qv[u].x;
+          sm.Ql[hi][lo] = qv[u].y;
+          continue;
+        }
         sm.Ph[lo][hi] = pv[u].x;
         sm.Pl[lo][hi] = pv[u].y;
         if (cur.tri) {
@@ -464,6 +543,18 @@ __global__ void __launch_bounds__(kFThreads, 1)
       for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
       tile_accumulate(sm, acc);
       const int gi = now.r0 + ti;
+      if (now.rhs) {
+        if (gi < d)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int gj = now.c0 + tj0 + q;
+            if (gj >= width) continue;
+            const ff v = ff_add(ff{out[q].x, out[q].y}, acc[q]);
+            Out[static_cast<int64_t>(gi) * width + gj] = make_float2(v.h, v.l);
+          }
+        task = next;
+        continue;
+      }
       float2* Y = now.tri ? A : X;
       if (gi < d)
 #pragma unroll
@@ -491,57 +582,6 @@ __global__ void __launch_bounds__(kFThreads, 1)
     }
     if (!sync_all()) return;
   }
-  // Out = X'^T [Pi | Z]: output tiles (I, Cb), I over row blocks, Cb over 32-column blocks of
-  // [Pi | Z]; the next m-block's operands are fetched into registers while this one is summed.
-  {
-    const int width = k + 4, ncb = (width + kFb - 1) / kFb;
-    for (int task = blockIdx.x; task < nb * ncb; task += gridDim.x) {
-      const int I = task / ncb, Cb = task % ncb;
-      const int i0 = I * kFb, c0 = Cb * kFb;
-      float2 pv[4];
-      double qv[4];
-      auto fetch = [&](int mb) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = threadIdx.x + u * kFThreads, m = e >> 5, lo = e & 31;
-          const int r = mb * kFb + m;
-          pv[u] = (r < d && i0 + lo < d) ? X[static_cast<int64_t>(r) * d + i0 + lo] : make_float2(0.f, 0.f);
-          const int c = c0 + lo;
-          double v = 0.0;
-          if (r < d) v = c < k ? Pi[static_cast<int64_t>(r) * k + c] : (c < width ? Z[r * 4 + (c - k)] : 0.0);
-          qv[u] = v;
-        }
-      };
-      ff acc[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = {0.f, 0.f};
-      fetch(I);
-      for (int mb = I; mb < nb; ++mb) {
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = threadIdx.x + u * kFThreads, m = e >> 5, lo = e & 31;
-          sm.Ph[m][lo] = pv[u].x;  // P[m][i] = X'[mb 32 + m][i0 + i]
-          sm.Pl[m][lo] = pv[u].y;
-          const float h = __double2float_rn(qv[u]);  // Q[m][j] = [Pi | Z][mb 32 + m][c0 + j]
-          sm.Qh[m][lo] = h;
-          sm.Ql[m][lo] = __double2float_rn(qv[u] - static_cast<double>(h));
-        }
-        __syncthreads();
-        if (mb + 1 < nb) fetch(mb + 1);
-        tile_accumulate(sm, acc);
-      }
-      const int i = i0 + (threadIdx.x >> 3), j0 = c0 + (threadIdx.x & 7) * 4;
-      if (i < d)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = j0 + q;
-          if (c < k) M[static_cast<int64_t>(i) * k + c] = ldexp(static_cast<double>(acc[q].h) + static_cast<double>(acc[q].l), -cexp[i]);
-          else if (c < width) Yff[i * 4 + (c - k)] = make_float2(acc[q].h, acc[q].l);
-        }
-    }
-    if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) st->m_ready = 1;
-  }
   // L = D^-1 L' (row i times 2^e_i) and R^-1 = X^T with X = X' D (column i of X' times 2^-e_i)
   for (int64_t e = gtid; e < dd; e += gstride) {
     const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
@@ -552,6 +592,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const float2 x = X[e];  // X'[i][j]: (R^-1)_ji at Rinv[i d + j]
     Rinv[e] = j <= i ? ldexp(static_cast<double>(x.x) + static_cast<double>(x.y), -cexp[j]) : 0.0;
   }
+  // M = R^-1 Pi = diag(2^-e) Out[:, :k] (float64) and Y'' = Out[:, k..k+3] (float-float)
+  const int width = k_rhs + 4;
+  for (int64_t e = gtid; e < static_cast<int64_t>(d) * width; e += gstride) {
+    const int i = static_cast<int>(e / width), c = static_cast<int>(e % width);
+    const float2 o = Out[e];
+    if (c < k_rhs) M[static_cast<int64_t>(i) * k_rhs + c] = ldexp(static_cast<double>(o.x) + static_cast<double>(o.y), -cexp[i]);
+    else Yff[i * 4 + (c - k_rhs)] = o;
+  }
+  if (k_rhs > 0 && blockIdx.x == 0 && threadIdx.x == 0) st->m_ready = 1;
 }
 
 // ------------------------------------------------------------------ probe check in float-float
@@ -746,7 +795,7 @@ bool chol_ff_applies(int64_t d) { return d >= 1 && d <= kMaxD; }
 
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
                         const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,
-                        float2* Dbuf, cudaStream_t st) {
+                        float2* Dbuf, float2* Out, cudaStream_t st) {
   if (h.num_sms < 2) return fail(SLSO_ERR_CUDA, "the float-float Cholesky needs at least two SMs");
   const size_t smem = sizeof(Smem);
   SLSO_TRY(raise_smem_limit(chol_ff_kernel, smem));
@@ -757,7 +806,7 @@ slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2
   int d_i = static_cast<int>(d);
   DevState* stp = h.state;
   int k_i = static_cast<int>(k);
-  void* args[] = {&L, &cexp, &d_i, &A, &X, &Rinv, &Pi, &k_i, &Z, &M, &Yff, &bar, &Dbuf, &stp};
+  void* args[] = {&L, &cexp, &d_i, &A, &X, &Rinv, &Pi, &k_i, &Z, &M, &Yff, &bar, &Dbuf, &Out, &stp};
   SLSO_CHECK_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(chol_ff_kernel), dim3(h.num_sms), dim3(kFThreads),
                                               args, smem, st));
   note_launch();

@@ -109,6 +109,7 @@ struct Handle {
   int nrec = 0;
   int open_rec = -1;
   long long launches_at_enable = 0;
+  int score_form = 0;              // float32 scores, k <= 128: SLSO_SCORE_FORM_* (slso_set_score_form)
 };
 constexpr int kProfCap = 4096;
 
@@ -475,6 +476,7 @@ struct GramWork {
   float2* Xff = nullptr;
   unsigned int* cbar = nullptr;
   float2* Dbuf = nullptr;   // 2 x 32 x 32: the lookahead's diagonal block
+  float2* Outff = nullptr;  // d x (k + 4): X'^T [Pi | Z]
   float2* Yff = nullptr;    // d x P: X'^T Z
   float2* Wff = nullptr;    // s x P
   float2* vff = nullptr;    // row-chunk partials of SX'^T W
@@ -482,7 +484,8 @@ struct GramWork {
   int splits = 1, tiles = 0, vchunks = 1;
   int64_t kc = 0;
 };
-GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d);
+// k: the JL width of the call (0: none), for the float-float route's right-hand sides.
+GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d, int64_t k = 0);
 // With g.use_ff the factor's inverse is written to Rinv (column-major R^-1) as well, and
 // *rinv_done is set; otherwise the caller forms R^-1 from L.
 // Pi (d x k, k > 0, or NULL) must be generated before the call: with g.use_ff, M = R^-1 Pi is
@@ -494,7 +497,7 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
 bool chol_ff_applies(int64_t d);
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,
                         const double* Pi, int64_t k, const double* Z, double* M, float2* Yff, unsigned int* bar,
-                        float2* Dbuf, cudaStream_t st);
+                        float2* Dbuf, float2* Out, cudaStream_t st);
 slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, const int* cexp, const float2* X,
                          const float2* Yff, float2* Wff, float2* vpart, int chunks, float2* Vff, const double* Z,
                          double* eres, cudaStream_t st);

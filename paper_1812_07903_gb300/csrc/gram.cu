@@ -556,7 +556,7 @@ slso_status run_gram_full(Handle& h, const Arena& ar, const GramWork& g, const d
   return SLSO_OK;
 }
 
-GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
+GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d, int64_t k) {
   GramWork g;
   const int64_t nb = ceil_div(d, kGt);
   g.tiles = static_cast<int>(nb * (nb + 1) / 2);
@@ -601,6 +601,7 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d) {
     g.Xff = ar.take<float2>(static_cast<size_t>(d) * d);
     g.cbar = ar.take<unsigned int>(4);
     g.Dbuf = ar.take<float2>(2 * 32 * 32);
+    g.Outff = ar.take<float2>(static_cast<size_t>(d) * (k + 4));
     g.Yff = ar.take<float2>(static_cast<size_t>(d) * kProbes);
     g.Wff = ar.take<float2>(static_cast<size_t>(s) * kProbes);
     g.vff = ar.take<float2>(static_cast<size_t>(2 * kGramBalanceSms) * d * kProbes);
@@ -625,7 +626,8 @@ slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const
     probe_z_kernel<<<static_cast<unsigned>(ceil_div(d * kProbes, 256)), 256, 0, st>>>(static_cast<int>(d), g.Z,
                                                                                        h.state);
     SLSO_CHECK_LAUNCH();
-    SLSO_TRY(run_chol_ff(h, L, g.cexp, d, g.Aff, g.Xff, Rinv, Pi, Pi ? k : 0, g.Z, M, g.Yff, g.cbar, g.Dbuf, st));
+    SLSO_TRY(run_chol_ff(h, L, g.cexp, d, g.Aff, g.Xff, Rinv, Pi, Pi ? k : 0, g.Z, M, g.Yff, g.cbar, g.Dbuf, g.Outff,
+                         st));
     *rinv_done = true;
   } else {
     SLSO_TRY(run_cholesky(h, g, d, L, st));

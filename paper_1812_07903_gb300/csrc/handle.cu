@@ -153,6 +153,15 @@ extern "C" slso_status slso_set_pool_limit(slso_handle* handle, size_t bytes) {
   return SLSO_OK;
 }
 
+extern "C" slso_status slso_set_score_form(slso_handle* handle, int32_t form) {
+  Handle* h = nullptr;
+  SLSO_TRY(check_handle(handle, &h));
+  if (form < SLSO_SCORE_FORM_MIXED || form > SLSO_SCORE_FORM_TF32X3_SMEM)
+    return fail(SLSO_ERR_INVALID_ARG, "unknown score form");
+  h->score_form = form;
+  return SLSO_OK;
+}
+
 extern "C" slso_status slso_profile(slso_handle* handle, int enable) {
   Handle* h = nullptr;
   SLSO_TRY(check_handle(handle, &h));

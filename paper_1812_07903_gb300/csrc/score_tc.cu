@@ -599,6 +599,302 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Float32-accurate scores with the X operands in tensor memory, k <= 128.  The converters read
+// each float32 row of the TMA's tile from shared memory once and write its operand pieces to
+// TMEM with tcgen05.st, and the MMAs take A from TMEM: shared memory then carries only the TMA's
+// writes, the converters' reads and the B operand reads (the form that keeps X's operands in
+// shared memory also writes them there and reads them back for every product, and shared-memory
+// bandwidth bounded it).  K-blocks of 16 floats (64-byte rows, 64B swizzle).  Products, all
+// accumulated in float32 in TMEM:
+//   HYB = false (3xTF32): Xhi Mhi + Xhi Mlo + Xlo Mhi with tf32 pieces (6 tf32 MMAs of K 8 per
+//               K-block and tile).
+//   HYB = true:   Xhi Mhi in tf32 (exact products) plus bf16(Xlo) bf16(Mhi) + bf16(Xhi) bf16(Mlo)
+//               in bfloat16 (2 tf32 + 2 bf16 MMAs of K 16: 2/3 of the tensor time): each dropped
+//               or rounded term is below 2^-18 |x_il m_lj|.
+// T = 2: a work item is two 128-row tiles that share each K-block of B, the whole K summed in one
+//   accumulator per tile (nbuf sets of 2N columns: the epilogue of one item overlaps the next).
+// T = 1, for long rows: the tensor core's float32 accumulation rounds its sums toward zero, a bias
+//   that grows with the number of MMAs summed into one accumulator (about 2^-25 of the sum per
+//   MMA: 1e-4 over the ~4000 MMAs of a 16800-long row).  K is cut into chunks of L.chunk K-blocks,
+//   each summed into a fresh accumulator (two, ping-pong), and the epilogue adds every chunk into
+//   a running sum kept in TMEM with round-to-nearest float32 additions.
+// TMEM: the accumulators from column 0 (T = 1: then the running sum, N columns), then one A slot
+// of 32 T columns per stage: per tile 32 columns = Xhi (16 tf32) and either Xlo (16 tf32) or
+// bf16(Xlo), bf16(Xhi) (8 columns each, two elements per column).  Converter warp w may only reach
+// TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, so warp w converts rows 32 (w % 4) + lane of tile
+// (w - 6) / 4 (for T = 1 the warps of tile 1 only arrive).  Every wait is bounded.
+struct LayoutTm {
+  int N, KB, S, nbuf;
+  int chunk, nchunk;            // K-blocks per accumulation chunk, chunks per work item
+  uint32_t bh_bytes, bx_bytes;  // B hi tile (N x 64 B); each further B tile (N x 32 B or N x 64 B)
+  uint32_t stage_bytes, bar_off, smem_bytes, run_col, abase, tmem_cols;
+};
+
+constexpr int kMaxStagesTm = 4;
+constexpr uint32_t kXtTm = kBM * 16 * 4;  // one 128-row x 16-float tile
+
+template <bool HYB, int T>
+__global__ void __launch_bounds__(kThreads, 1)
+    score_tm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBh,
+                    const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
+                    const LayoutTm L, int64_t n, int nwork, float* __restrict__ scores,
+                    DevState* __restrict__ state) {
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar_off);  // TMA bytes landed
+  uint64_t* cvt = full + kMaxStagesTm;                              // A pieces in TMEM
+  uint64_t* empty = cvt + kMaxStagesTm;                             // MMAs reading the stage done
+  uint64_t* acc_full = empty + kMaxStagesTm;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ int s_abort;
+  const volatile int* abort_flag = &s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int i = 0; i < L.S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&cvt[i], kConvThreads);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 128);
+    }
+    fence_mbar_init();
+  }
+  if (warp == kWarpMma) tmem_alloc(tmem_slot, L.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == kWarpProducer) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      const uint32_t tx = T * kXtTm + L.bh_bytes + (HYB ? 2u : 1u) * L.bx_bytes;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        const int y0 = w * T * kBM;
+        for (int kb = 0; kb < L.KB; ++kb, ++it) {
+          const int st = it % L.S;
+          if (!mbar_wait(&empty[st], ((it / L.S) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
+          const int x = kb * 16;
+          mbar_arrive_expect_tx(&full[st], tx);
+#pragma unroll
+          for (int u = 0; u < T; ++u) tma_load_2d(stage + u * kXtTm, &tmX, &full[st], x, y0 + u * kBM);
+          unsigned char* b = stage + T * kXtTm;
+          tma_load_2d(b, &tmBh, &full[st], x, 0);
+          tma_load_2d(b + L.bh_bytes, &tmB1, &full[st], x, 0);
+          if (HYB) tma_load_2d(b + L.bh_bytes + L.bx_bytes, &tmB2, &full[st], x, 0);
+        }
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(&state->timeout, 3);
+        for (int j = (it > L.S ? it - L.S : 0); j < it; ++j)  // let issued copies land (bounded)
+          mbar_wait(&full[j % L.S], (j / L.S) & 1u, nullptr, 50000000ull);
+      }
+    }
+  } else if (warp == kWarpMma) {
+    if (lane == 0) {
+      const uint32_t idt = idesc(FMT_TF32, FMT_TF32, kBM, static_cast<uint32_t>(L.N));
+      const uint32_t idb = idesc(FMT_BF16, FMT_BF16, kBM, static_cast<uint32_t>(L.N));
+      int it = 0, cc = 0;  // K-blocks and accumulation chunks issued so far
+      bool ok = true;
+      uint32_t dbase = 0;
+      for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+        for (int kb = 0; kb < L.KB; ++kb, ++it) {
+          const int kc = kb % L.chunk;  // K-block within its chunk
+          if (kc == 0) {                 // a fresh accumulator set for this chunk
+            const int ab = cc % L.nbuf;
+            if (!mbar_wait(&acc_empty[ab], ((cc / L.nbuf) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            dbase = tmem_base + static_cast<uint32_t>(ab * T * L.N);
+          }
+          const int st = it % L.S;
+          if (!mbar_wait(&cvt[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          unsigned char* b = smem + static_cast<uint32_t>(st) * L.stage_bytes + T * kXtTm;
+          const uint64_t bh = sdesc_sw64(b);
+          const uint32_t aslot = tmem_base + L.abase + static_cast<uint32_t>(st * 32 * T);
+#pragma unroll
+          for (int u = 0; u < T; ++u) {
+            const uint32_t du = dbase + static_cast<uint32_t>(u * L.N);
+            const uint32_t a = aslot + static_cast<uint32_t>(u * 32);
+            if (HYB) {
+              mma_tf32_ts(du, a, bh, idt, kc != 0);
+              mma_tf32_ts(du, a + 8, bh + 2, idt, 1u);  // + 32 bytes along K
+              mma_f16_ts(du, a + 16, sdesc_sw32(b + L.bh_bytes), idb, 1u);                // bf16(Xlo) bf16(Mhi)
+              mma_f16_ts(du, a + 24, sdesc_sw32(b + L.bh_bytes + L.bx_bytes), idb, 1u);  // bf16(Xhi) bf16(Mlo)
+            } else {
+              const uint64_t bl = sdesc_sw64(b + L.bh_bytes);
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t o = static_cast<uint64_t>(ks * 2);
+                const uint32_t ak = a + static_cast<uint32_t>(ks * 8);
+                mma_tf32_ts(du, ak, bh + o, idt, (kc | ks) != 0);
+                mma_tf32_ts(du, ak, bl + o, idt, 1u);
+                mma_tf32_ts(du, ak + 16, bh + o, idt, 1u);
+              }
+            }
+          }
+          mma_commit(&empty[st]);
+          if (kc == L.chunk - 1 || kb == L.KB - 1) {  // the chunk is summed
+            mma_commit(&acc_full[cc % L.nbuf]);
+            ++cc;
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(&state->timeout, 3);
+      }
+      // all MMAs issued by this thread have completed before TMEM is released
+      if (it > 0) mbar_wait(&empty[(it - 1) % L.S], ((it - 1) / L.S) & 1u, nullptr, 50000000ull);
+    }
+  } else if (warp >= kWarpConvert0) {
+    const int u = (warp - kWarpConvert0) >> 2;  // tile
+    const int q = warp & 3;                      // TMEM lane quarter
+    const int r = q * 32 + lane;                 // row of the tile
+    const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
+    int it = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+      for (int kb = 0; kb < L.KB; ++kb, ++it) {
+        const int st = it % L.S;
+        // every lane acquires the TMA's bytes; the outcome is made warp-uniform (tcgen05.st is
+        // .sync.aligned)
+        const bool got = mbar_wait(&full[st], (it / L.S) & 1u, abort_flag);
+        if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }
+        if (u < T) {
+          // row r of the tile: 64 bytes, 16-byte chunk c stored at chunk c ^ ((r >> 1) & 3)
+          const uint4* row = reinterpret_cast<const uint4*>(smem + static_cast<uint32_t>(st) * L.stage_bytes +
+                                                            u * kXtTm + r * 64);
+          uint32_t x[16];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 v = row[c ^ ((r >> 1) & 3)];
+            x[4 * c] = v.x;
+            x[4 * c + 1] = v.y;
+            x[4 * c + 2] = v.z;
+            x[4 * c + 3] = v.w;
+          }
+          uint32_t a[32];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) a[e] = rne_tf32(x[e]);
+          if (HYB) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+              const float l0 = __uint_as_float(x[e]) - __uint_as_float(a[e]);
+              const float l1 = __uint_as_float(x[e + 1]) - __uint_as_float(a[e + 1]);
+              const __nv_bfloat162 lp = __floats2bfloat162_rn(l0, l1);  // .x (low half) = element e
+              const __nv_bfloat162 hp = __floats2bfloat162_rn(__uint_as_float(a[e]), __uint_as_float(a[e + 1]));
+              a[16 + e / 2] = *reinterpret_cast<const uint32_t*>(&lp);
+              a[24 + e / 2] = *reinterpret_cast<const uint32_t*>(&hp);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              a[16 + e] = rne_tf32(__float_as_uint(__uint_as_float(x[e]) - __uint_as_float(a[e])));
+          }
+          tmem_st_32x32b_x32(tmem_base + lane_addr + L.abase + static_cast<uint32_t>(st * 32 * T + u * 32), a);
+          tc_fence_before();
+        }
+        mbar_arrive(&cvt[st]);
+      }
+    }
+    if (!ok && lane == 0) {
+      atomicExch(&s_abort, 1);
+      atomicExch(&state->timeout, 3);
+    }
+  } else {  // warps 0-3: epilogue; warp w reads TMEM lanes 32w..32w+31 = tile rows 32w..32w+31
+    int cc = 0;
+    const uint32_t lanes = static_cast<uint32_t>(warp * 32) << 16;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+      float sum[T];
+#pragma unroll
+      for (int u = 0; u < T; ++u) sum[u] = 0.0f;
+      bool ok = true;
+      for (int ci = 0; ci < L.nchunk; ++ci, ++cc) {
+        const int ab = cc % L.nbuf;
+        int got = 0;
+        if (lane == 0) got = mbar_wait(&acc_full[ab], (cc / L.nbuf) & 1u, abort_flag) ? 1 : 0;
+        got = __shfl_sync(0xFFFFFFFFu, got, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+        const bool last = ci == L.nchunk - 1;
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+          const uint32_t taddr = tmem_base + lanes + static_cast<uint32_t>(ab * T * L.N + u * L.N);
+          for (int c0 = 0; c0 < L.N; c0 += 32) {
+            float v[32];
+            tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c0), v);
+            if (L.nchunk > 1) {  // T = 1: fold into the running sum (round to nearest)
+              const uint32_t raddr = tmem_base + lanes + L.run_col + static_cast<uint32_t>(c0);
+              if (ci > 0) {
+                float rs[32];
+                tmem_ld_32x32b_x32(raddr, rs);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(v[i], rs[i]);
+              }
+              if (!last) {
+                uint32_t vb[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) vb[i] = __float_as_uint(v[i]);
+                tmem_st_32x32b_x32(raddr, vb);
+              }
+            }
+            if (last)
+#pragma unroll
+              for (int i = 0; i < 32; ++i) sum[u] = fmaf(v[i], v[i], sum[u]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[ab]);  // the accumulators are read: the next chunk may start
+      }
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(&s_abort, 1);
+          atomicExch(&state->timeout, 3);
+        }
+        break;
+      }
+#pragma unroll
+      for (int u = 0; u < T; ++u) {
+        const int64_t row = (static_cast<int64_t>(w) * T + u) * kBM + warp * 32 + lane;
+        if (row < n) scores[row] = sum[u];
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kWarpMma) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, L.tmem_cols);
+  }
+}
+
+// B = M^T pieces for the mixed tf32/bfloat16 products: Bh = tf32(m) (float32 bits), and the
+// bfloat16 roundings of Bh and of m - Bh.
+__global__ void prep_b_hyb_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
+                                  float* __restrict__ Bh, __nv_bfloat16* __restrict__ Bhb,
+                                  __nv_bfloat16* __restrict__ Blb) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < N * Kpad;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t c = e / Kpad, k = e % Kpad;
+    const double m = (c < kk && k < d) ? M[k * kk + c] : 0.0;
+    const float hi = __uint_as_float(rne_tf32(__float_as_uint(static_cast<float>(m))));
+    Bh[e] = hi;
+    Bhb[e] = __float2bfloat16_rn(hi);
+    Blb[e] = __float2bfloat16_rn(static_cast<float>(m - static_cast<double>(hi)));
+  }
+}
+
 // B = M^T (N x Kpad, K contiguous) split into tf32-exact high parts and float32 remainders.
 __global__ void prep_b_tf32_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
                                    float* __restrict__ Bhi, float* __restrict__ Blo) {
@@ -742,8 +1038,17 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   if (xdt == SLSO_BF16 && compute == SLSO_FP8_E4M3) mode = MODE_FP8_BF16;
   if (mode < 0 || kk > 256 || kk < 1) return SLSO_OK;
   const size_t esz = dtype_size(xdt);
-  if (reinterpret_cast<uintptr_t>(X) % 16 != 0 || (ldx * esz) % 16 != 0) return SLSO_OK;
   if (!encode_fn()) return SLSO_OK;
+  if (reinterpret_cast<uintptr_t>(X) % 16 != 0 || (ldx * esz) % 16 != 0) {
+    // TMA rows start on 16-byte boundaries: stage X once with its row pitch rounded up to 16
+    // bytes (a strided copy at copy bandwidth, far cheaper than the SIMT product)
+    const int64_t ldp = ceil_div(d * static_cast<int64_t>(esz), 16) * 16 / static_cast<int64_t>(esz);
+    char* Xp = ar.take<char>(static_cast<size_t>(n) * ldp * esz);
+    if (!ar.measure() && n > 0)
+      SLSO_CHECK_CUDA(cudaMemcpy2DAsync(Xp, ldp * esz, X, ldx * esz, d * esz, n, cudaMemcpyDeviceToDevice, st));
+    X = Xp;
+    ldx = ldp;
+  }
   const Layout L = make_layout(mode, kk, d);
   const int64_t Kpad = static_cast<int64_t>(L.KB) * L.kbe;
   const bool fp8 = mode == MODE_FP8_F32 || mode == MODE_FP8_BF16;
@@ -775,9 +1080,13 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   bool ok;
   const CUtensorMapDataType xdt_map = (xdt == SLSO_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   ok = make_map(&mX, xdt_map, X, d, n, ldx * esz, static_cast<uint32_t>(L.box_cols), kBM);
+  const bool tm = mode == MODE_TF32X3 && L.N <= 128 && h.score_form != SLSO_SCORE_FORM_TF32X3_SMEM;
+  const bool hyb = tm && h.score_form == SLSO_SCORE_FORM_MIXED;
   if (mode == MODE_TF32X3) {
-    prep_b_tf32_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<float*>(B0), static_cast<float*>(B1));
-    SLSO_CHECK_LAUNCH();
+    if (!hyb) {  // the mixed form prepares its own pieces below
+      prep_b_tf32_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<float*>(B0), static_cast<float*>(B1));
+      SLSO_CHECK_LAUNCH();
+    }
     ok = ok && make_map(&mB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, 32, L.N) &&
          make_map(&mB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, 32, L.N);
     mB2 = mB1;
@@ -815,6 +1124,63 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   }
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
   const int ntiles = static_cast<int>(ceil_div(n, kBM));
+  if (tm) {
+    // X's operand pieces in TMEM; K-blocks of 16 floats.  Rows up to 2048 long: two tiles per
+    // work item, one accumulator per tile; longer rows: one tile, K summed in chunks of 512
+    LayoutTm T{};
+    T.N = L.N;
+    T.KB = static_cast<int>(ceil_div(d, 16));
+    const int tiles = T.KB > 128 ? 1 : 2;
+    T.chunk = tiles == 1 ? 32 : T.KB;
+    T.nchunk = static_cast<int>(ceil_div(T.KB, T.chunk));
+    T.bh_bytes = static_cast<uint32_t>(L.N) * 64u;
+    T.bx_bytes = hyb ? static_cast<uint32_t>(L.N) * 32u : T.bh_bytes;
+    T.stage_bytes = tiles * kXtTm + T.bh_bytes + (hyb ? 2u : 1u) * T.bx_bytes;
+    T.S = kMaxStagesTm;
+    if (tiles == 2) {
+      T.nbuf = (2 * 2 * L.N + T.S * 64 <= 512) ? 2 : 1;
+      T.run_col = 0;
+      T.abase = static_cast<uint32_t>(T.nbuf * 2 * L.N);
+    } else {  // two chunk accumulators, the running sum, then the A slots: 3N + 4 x 32 <= 512
+      T.nbuf = 2;
+      T.run_col = static_cast<uint32_t>(2 * L.N);
+      T.abase = static_cast<uint32_t>(3 * L.N);
+    }
+    T.tmem_cols = 512;
+    T.bar_off = static_cast<uint32_t>(T.S) * T.stage_bytes;
+    T.smem_bytes = T.bar_off + (3 * kMaxStagesTm + 4) * 8 + 8 + 1024;
+    // B pieces (Kpad is a multiple of 32 floats, so of 16)
+    CUtensorMap mXt, mBh, mB1t, mB2t;
+    bool okt = make_map(&mXt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * esz, 16, kBM, CU_TENSOR_MAP_SWIZZLE_64B) &&
+               make_map(&mBh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, 16, L.N,
+                        CU_TENSOR_MAP_SWIZZLE_64B);
+    if (hyb) {
+      __nv_bfloat16* Bhb = static_cast<__nv_bfloat16*>(B1);  // the float B1 holds both bf16 pieces
+      __nv_bfloat16* Blb = Bhb + static_cast<size_t>(L.N) * Kpad;
+      prep_b_hyb_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<float*>(B0), Bhb, Blb);
+      SLSO_CHECK_LAUNCH();
+      okt = okt &&
+            make_map(&mB1t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bhb, Kpad, L.N, Kpad * 2, 16, L.N,
+                     CU_TENSOR_MAP_SWIZZLE_32B) &&
+            make_map(&mB2t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Blb, Kpad, L.N, Kpad * 2, 16, L.N,
+                     CU_TENSOR_MAP_SWIZZLE_32B);
+    } else {
+      okt = okt && make_map(&mB1t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, 16, L.N,
+                            CU_TENSOR_MAP_SWIZZLE_64B);
+      mB2t = mB1t;
+    }
+    if (!okt) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
+    const int nwork = (ntiles + tiles - 1) / tiles;
+    const int gridt = std::min(nwork, h.num_sms);
+    auto launch = [&](auto kern) -> slso_status {
+      SLSO_TRY(raise_smem_limit(kern, T.smem_bytes));
+      kern<<<gridt, kThreads, T.smem_bytes, st>>>(mXt, mBh, mB1t, mB2t, T, n, nwork, scores, h.state);
+      SLSO_CHECK_LAUNCH();
+      return SLSO_OK;
+    };
+    if (hyb) return tiles == 2 ? launch(score_tm_kernel<true, 2>) : launch(score_tm_kernel<true, 1>);
+    return tiles == 2 ? launch(score_tm_kernel<false, 2>) : launch(score_tm_kernel<false, 1>);
+  }
   if (mode == MODE_TF32X3 && L.N <= 128) {
     // two 128-row tiles per work item share each B K-block
     // K-blocks of 16 floats (64-byte rows, 64B swizzle): 4 stages of 48 KB at k = 128

@@ -1323,7 +1323,7 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   double* E2 = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* Qm = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
   double* W0m = precond ? ar.take<double>(static_cast<size_t>(d) * d) : nullptr;
-  const GramWork gw = gram ? gram_take(h, ar, s, d) : GramWork{};
+  const GramWork gw = gram ? gram_take(h, ar, s, d, k) : GramWork{};
   if (ar.measure()) return SLSO_OK;
 
   // ---- Gram route (leverage only): R = chol(SX^T SX) into Rc, R^-1, probe check.  gram_ok

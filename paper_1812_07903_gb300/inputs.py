@@ -173,9 +173,13 @@ def text_sequences(n, steps=56, emb=300, vocab=20000, seed=1006, device="cpu", d
     """SST-shaped sentence matrix: n x (steps * emb), float32.
 
     The vocabulary holds ``vocab`` seeded embedding vectors (N(0, I/emb) plus a shared offset, as
-    word vectors share a common direction).  Sentence lengths are 1 + Poisson(17), with 2% of the
-    rows at the maximum (sentences truncated at ``steps`` words), so that every step's columns
-    have full rank.  A sentence of L words fills the last L steps (zero padding on the left).
+    word vectors share a common direction).  Sentence lengths are round(16 exp(0.55 z)), z ~ N(0, 1)
+    (mean about 19.6 words, a right tail like a sentiment treebank's), clipped to [1, steps], with
+    3% of the rows at the maximum (sentences truncated at ``steps`` words).  A sentence of L words
+    fills the last L steps (zero padding on the left), so the columns of steps 0..p are nonzero
+    only on rows with L >= steps - p; at n = 131072 and emb = 300 those rows outnumber the
+    columns 300 (p + 1) at least twice over for every p, so the matrix has full column rank (with
+    Poisson lengths the leftmost steps share a few thousand rows and the rank falls short of d).
     """
     g = _gen(seed, device)
     E = torch.randn(vocab, emb, generator=g, device=device, dtype=torch.float32) / math.sqrt(emb)
@@ -184,10 +188,10 @@ def text_sequences(n, steps=56, emb=300, vocab=20000, seed=1006, device="cpu", d
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
         m = b - a
-        lam = torch.full((m,), 17.0, device=device, dtype=torch.float64)
-        L = 1 + torch.poisson(lam, generator=g).to(torch.int64)
+        z = torch.randn(m, generator=g, device=device, dtype=torch.float64)
+        L = torch.round(16.0 * torch.exp(0.55 * z)).to(torch.int64).clamp(1, steps)
         trunc = torch.rand(m, generator=g, device=device) < 0.03
-        L = torch.where(trunc, torch.full_like(L, steps), torch.clamp(L, max=steps))
+        L = torch.where(trunc, torch.full_like(L, steps), L)
         ids = _zipf_words(m * steps, vocab, g, device).view(m, steps)
         blk = E[ids]  # m x steps x emb
         pos = torch.arange(steps, device=device).view(1, steps)

@@ -60,11 +60,14 @@ def test_countsketch_ragged_leading_dimension():
     assert _rel_to_max(SX, want) < 1e-12
 
 
-SRHT_CASES = [(1, 3, 1), (100, 5, 64), (5000, 64, 512), (20000, 100, 2048), (70000, 24, 1024)]
+# padded heights 1 (shared-memory kernel), 64, 128, 512 (register kernel, R = 1, 2, 8) and 4096-row
+# chunks (R = 64) with 1, 2, 5 and 18 chunks; ragged 8-column slabs (d = 5, 9, 17, 100)
+SRHT_CASES = [(1, 3, 1), (64, 8, 16), (100, 5, 64), (300, 9, 40), (2049, 17, 100), (5000, 64, 512),
+              (20000, 100, 2048), (70000, 24, 1024)]
 
 
 @pytest.mark.parametrize("n,d,s", SRHT_CASES)
-@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64, torch.bfloat16])
 def test_srht_matches_oracle(n, d, s, dtype):
     X = inputs.lognormal_rows(n, d, seed=3 * n + d, dtype=dtype)
     SX = api.sketch(_dev(X), "srht", s, 31).cpu().numpy()
@@ -257,6 +260,44 @@ def test_tensor_core_float32_scores_match_oracle(n, d, k):
     want, oinfo = O.sketched_leverage(_np(X), "countsketch", s, k, 5, 6)
     assert info["rank"] == oinfo["rank"] == d
     assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
+
+
+@pytest.mark.parametrize("form", ["mixed", "tf32x3", "tf32x3_smem"])
+@pytest.mark.parametrize("n,d,k", [(1000, 100, 48), (777, 33, 100), (12345, 320, 128), (4096, 1024, 16),
+                                   (70000, 200, 128), (6000, 2600, 64)])
+def test_float32_score_forms_match_oracle(form, n, d, k):
+    """Every operand form of the float32 score product for k <= 128 (X's pieces in tensor memory,
+    mixed tf32/bfloat16 or 3xTF32 products, or in shared memory) within the float32 bound: ragged
+    row tiles and K-blocks, N from 32 to 128, several work items per CTA, rows longer than 2048
+    (one tile per work item, K summed in chunks of 512 with a ragged last chunk), row pitch not a
+    multiple of 16 bytes (d = 33: X staged with a padded pitch)."""
+    X = inputs.lognormal_rows(n, d, seed=n + k + 1, dtype=torch.float32)
+    s = max(2 * d, 256)
+    h = api.Handle(0)
+    api.set_score_form(form, handle=h)
+    sc, info = api.leverage(_dev(X), "countsketch", s, k, 5, 6, compute="f32", handle=h)
+    want, oinfo = O.sketched_leverage(_np(X), "countsketch", s, k, 5, 6)
+    assert info["rank"] == oinfo["rank"] == d
+    assert _max_rel(sc.cpu().numpy().astype(np.float64), want) < 1e-4
+
+
+def test_score_forms_agree_with_each_other():
+    """The mixed form against 3xTF32 on one matrix: both within a few 2^-20 of each other."""
+    X = _dev(inputs.snr_student_t(50000, 512, seed=77))
+    out = {}
+    for form in ("mixed", "tf32x3"):
+        h = api.Handle(0)
+        api.set_score_form(form, handle=h)
+        out[form], _ = api.leverage(X, "countsketch", 4096, 128, 8, 9, compute="f32", handle=h)
+    a = out["mixed"].cpu().numpy().astype(np.float64)
+    b = out["tf32x3"].cpu().numpy().astype(np.float64)
+    assert _max_rel(a, b) < 2e-5
+
+
+def test_unknown_score_form_is_rejected():
+    h = api.Handle(0)
+    with pytest.raises(api.L.SlsoError):
+        api.L.check(api.L.load().slso_set_score_form(h.ptr, 7))
 
 
 @pytest.mark.parametrize("n,d,k", [(70, 16, 256), (1000, 100, 48), (12345, 320, 128), (4096, 1024, 16),

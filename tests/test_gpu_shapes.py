@@ -3,11 +3,12 @@ vectors, d = 16800; Sec. 5.5 CMU-MOSI: 325 early-fused features per step, d = 97
 
 * The same generators at reduced widths (12-d and 24-d word vectors) against the whole oracle:
   float32 scores within 1e-4, the rank, R from the Gram route.
-* Full size (131072 rows): the Gram route stands (rank d, probe residual below 1e-8), sampled
-  sketch rows are the exact bucket sums, and with k = 0 every sampled row's score equals
-  x_i G^-1 x_i^T with G = SX^T SX as slso_gram forms it (itself checked against the exact Gram
-  oracle elsewhere), solved by LAPACK's Cholesky on the host: the float-float factorisation, its
-  inverse and the scores at d = 16800 and 9750, stage-wise.
+* Full size (131072 rows, k = 128 as the benchmark runs them): the Gram route stands (rank d,
+  probe residual below 1e-8), sampled sketch rows are the exact bucket sums, and every sampled
+  row's score equals ||x_i R^-1 Pi||^2 with R the Cholesky factor (LAPACK, on the host) of
+  G = SX^T SX as slso_gram forms it (itself checked against the exact Gram oracle elsewhere) and
+  Pi the oracle's JL matrix: the float-float factorisation, its inverse, M and the scores at
+  d = 16800 and 9750, stage-wise.
 """
 import numpy as np
 import pytest
@@ -46,15 +47,14 @@ def test_full_size_stagewise(name, n, d, s):
     gen = inputs.text_sequences if name == "text" else inputs.multimodal_sequences
     X = gen(n, seed=1006 if name == "text" else 1007, device="cuda")
     assert X.shape == (n, d)
-    seed_S = 2006 if name == "text" else 2007
-    sc, info = api.leverage(X, "countsketch", s, 0, seed_S, 0, compute="f32")
+    seed_S, seed_Pi, k = (2006, 3006, 128) if name == "text" else (2007, 3007, 128)
+    sc, info = api.leverage(X, "countsketch", s, k, seed_S, seed_Pi, compute="f32")
     assert info["rank"] == d and info["gram_route"] == 1 and info["gram_resid"] < 1e-8
     SX = api.sketch(X, "countsketch", s, seed_S)
     G = api.gram(SX).cpu().numpy()
     SXh = SX.cpu().numpy()
     del SX
     rng = np.random.default_rng(3)
-    Xh_rows = None
     # sampled buckets of the sketch: exact sums of their rows
     bucket, sign = O.countsketch_hash(n, s, seed_S)
     for b in rng.choice(s, 8, replace=False):
@@ -62,11 +62,12 @@ def test_full_size_stagewise(name, n, d, s):
         Xr = X[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
         want = (sign[rows][:, None] * Xr).sum(axis=0)
         assert np.max(np.abs(SXh[b] - want)) <= 1e-12 * max(np.max(np.abs(want)), 1e-300)
-    # sampled scores: x_i G^-1 x_i^T by LAPACK's Cholesky of the GPU's G
+    # sampled scores: ||x_i R^-1 Pi||^2 with R = chol(G) by LAPACK on the host (R^T y = x_i^T)
     rows = np.sort(rng.choice(n, 200, replace=False))
     Xh_rows = X[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
-    cf = sla.cho_factor(G, lower=True)
-    Y = sla.cho_solve(cf, Xh_rows.T)
-    want = np.einsum("ij,ji->i", Xh_rows, Y)
+    R = sla.cholesky(G, lower=False)
+    Y = sla.solve_triangular(R, Xh_rows.T, trans="T", lower=False)  # columns: (x_i R^-1)^T
+    P = Y.T @ O.jl_matrix(d, k, seed_Pi)
+    want = np.einsum("ij,ij->i", P, P)
     got = sc.cpu().numpy()[rows].astype(np.float64)
     assert _max_rel(got, want) < 1e-4
