@@ -384,10 +384,12 @@ def large_bench(args):
                                   f"(tensor cores), JL k={k}; leverage + dec order", "n": n, "d": d, "s": s, "k": k,
                       "sketch": "gaussian", "l2": "X larger than L2; no flush"},
            "metric": "scored rows/s", "unit": "rows/s", "steps": args.steps, "warmup": args.warmup}
-    for compute in ("f32", "bf16", "fp8"):
+    ref = None  # the float32-accurate scores: the precision ladder's reference at this size
+    top = max(1, n // 100)
+    for compute, corr in (("f32", 0.0), ("bf16", 0.0), ("bf16", CORRECT_FRAC), ("fp8", 0.0), ("fp8", CORRECT_FRAC)):
         def step():
             api.leverage(X, "gaussian", s, k, L["seed_S"], L["seed_Pi"], compute=compute, out=scores,
-                         want_info=False, handle=h)
+                         want_info=False, handle=h, correct_frac=corr)
             api.order(scores, out=order, handle=h)
         for _ in range(args.warmup):
             step()
@@ -405,11 +407,20 @@ def large_bench(args):
         api.profile(False, handle=h)
         per = {nm: v_ / args.steps for nm, (v_, c) in stages.items() if c}
         tf = 2.0 * s * n * d / (per["sketch"] / 1e3) / 1e12
-        out[compute] = {"value": n / (ms / 1e3), "ms_per_step": ms, "gpu_launches": int(launches),
-                        "stages_ms_per_step": {nm: round(v_, 3) for nm, v_ in per.items()},
-                        "sketch_tensor_tflops": tf,
-                        "sketch_frac_of_bf16_peak": tf / peaks["bf16_tflops_sustained"],
-                        "peak": {"bf16_tflops_sustained": peaks["bf16_tflops_sustained"], "source": peak_src}}
+        line = {"value": n / (ms / 1e3), "ms_per_step": ms, "gpu_launches": int(launches),
+                "stages_ms_per_step": {nm: round(v_, 3) for nm, v_ in per.items()},
+                "sketch_tensor_tflops": tf,
+                "sketch_frac_of_bf16_peak": tf / peaks["bf16_tflops_sustained"],
+                "peak": {"bf16_tflops_sustained": peaks["bf16_tflops_sustained"], "source": peak_src}}
+        if ref is None:
+            ref = scores.double().clone()
+            ref_top = set(torch.topk(ref, top).indices.cpu().tolist())
+        else:
+            rel = ((scores.double() - ref).abs() / ref.abs().clamp_min(1e-300))
+            got_top = set(torch.topk(scores.double(), top).indices.cpu().tolist())
+            line["vs_float32_path"] = {"median_rel_err": float(rel.median()), "max_rel_err": float(rel.max()),
+                                       "top1pct_overlap": len(ref_top & got_top) / top}
+        out[compute + ("_corrected" if corr else "")] = line
     print(json.dumps(out))
 
 

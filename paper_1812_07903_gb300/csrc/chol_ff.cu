@@ -80,6 +80,8 @@ __device__ __forceinline__ void dot_term(float ah, float al, float bh, float bl,
   C = __fadd_rn(C, __fadd_rn(err, e));
 }
 
+constexpr int kBarWords = 4;  // count, generation, abort, breakdown
+
 __device__ bool grid_barrier_ff(unsigned int* count, volatile unsigned int* gen, int* abort_flag) {
   __syncthreads();
   __shared__ int s_ok;
@@ -303,8 +305,8 @@ __device__ bool factor_diag(Smem& sm, const float2* A, int d, int k0) {
   return true;
 }
 
-// bar[0..1] grid barrier, bar[2] abort flag, bar[3] lookahead breakdown (zeroed by the host before
-// the launch).  Dbuf (2 x 32 x 32 float-float): the next diagonal block's inverse as CTA 0 publishes it.
+// bar[0..1] grid barrier (count, generation), bar[2] abort flag, bar[3] lookahead breakdown (all
+// zeroed by the host before the launch).  Dbuf (2 x 32 x 32 float-float): the next diagonal block's inverse as CTA 0 publishes it.
 // Right-hand sides: with the JL matrix Pi (d x k_rhs; none when k_rhs = 0) and the probes Z (d x 4),
 // both float64 row-major, Out = X'^T [Pi | Z] (Out_ic = sum over m >= i of X'_mi [Pi | Z]_mc; d x
 // (k_rhs + 4) float-float, accumulated row block by row block in part C of the step that finishes
@@ -643,21 +645,35 @@ __global__ void __launch_bounds__(256) probe_w_ff_kernel(const double* __restric
   const double* row = SX + r * d;
   float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
   ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  int cnt = 0;
-  for (int j = lane; j < d; j += 32) {
-    const ff a = split_scaled(row[j], cexp[j]);
-    const float4 y0 = *reinterpret_cast<const float4*>(Yff + 4 * j);      // probes 0, 1
-    const float4 y1 = *reinterpret_cast<const float4*>(Yff + 4 * j + 2);  // probes 2, 3
-    dot_term(a.h, a.l, y0.x, y0.y, S[0], C[0]);
-    dot_term(a.h, a.l, y0.z, y0.w, S[1], C[1]);
-    dot_term(a.h, a.l, y1.x, y1.y, S[2], C[2]);
-    dot_term(a.h, a.l, y1.z, y1.w, S[3], C[3]);
-    if ((++cnt & 15) == 0)
+  // blocks of 8 columns per lane: the 8 loads are issued before the arithmetic that uses them;
+  // the (S, C) pairs are folded after every block (8 terms)
+  for (int j0 = lane; j0 < d; j0 += 32 * 8) {
+    double xv[8];
+    int ev[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
-        S[q] = C[q] = 0.f;
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + 32 * u;
+      xv[u] = j < d ? row[j] : 0.0;
+      ev[u] = j < d ? cexp[j] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + 32 * u;
+      if (j < d) {
+        const ff a = split_scaled(xv[u], ev[u]);
+        const float4 y0 = *reinterpret_cast<const float4*>(Yff + 4 * j);      // probes 0, 1
+        const float4 y1 = *reinterpret_cast<const float4*>(Yff + 4 * j + 2);  // probes 2, 3
+        dot_term(a.h, a.l, y0.x, y0.y, S[0], C[0]);
+        dot_term(a.h, a.l, y0.z, y0.w, S[1], C[1]);
+        dot_term(a.h, a.l, y1.x, y1.y, S[2], C[2]);
+        dot_term(a.h, a.l, y1.z, y1.w, S[3], C[3]);
       }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+      S[q] = C[q] = 0.f;
+    }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -683,21 +699,29 @@ __global__ void __launch_bounds__(256) probe_v_ff_kernel(const double* __restric
     const int e = cexp[j];
     float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
     ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    int cnt = 0;
-    for (int64_t r = r0; r < r1; ++r) {
-      const ff a = split_scaled(SX[r * d + j], e);
-      const float4 w0 = *reinterpret_cast<const float4*>(Wff + 4 * r);
-      const float4 w1 = *reinterpret_cast<const float4*>(Wff + 4 * r + 2);
-      dot_term(a.h, a.l, w0.x, w0.y, S[0], C[0]);
-      dot_term(a.h, a.l, w0.z, w0.w, S[1], C[1]);
-      dot_term(a.h, a.l, w1.x, w1.y, S[2], C[2]);
-      dot_term(a.h, a.l, w1.z, w1.w, S[3], C[3]);
-      if ((++cnt & 15) == 0)
+    // blocks of 8 rows: the 8 loads are issued before the arithmetic; folds after every block
+    for (int64_t rb = r0; rb < r1; rb += 8) {
+      double xv[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
-          S[q] = C[q] = 0.f;
+      for (int u = 0; u < 8; ++u) xv[u] = rb + u < r1 ? SX[(rb + u) * d + j] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t r = rb + u;
+        if (r < r1) {
+          const ff a = split_scaled(xv[u], e);
+          const float4 w0 = *reinterpret_cast<const float4*>(Wff + 4 * r);
+          const float4 w1 = *reinterpret_cast<const float4*>(Wff + 4 * r + 2);
+          dot_term(a.h, a.l, w0.x, w0.y, S[0], C[0]);
+          dot_term(a.h, a.l, w0.z, w0.w, S[1], C[1]);
+          dot_term(a.h, a.l, w1.x, w1.y, S[2], C[2]);
+          dot_term(a.h, a.l, w1.z, w1.w, S[3], C[3]);
         }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = ff_add(acc[q], fast_two_sum(S[q], C[q]));
+        S[q] = C[q] = 0.f;
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -802,7 +826,7 @@ slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2
   int occ = 0;
   SLSO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chol_ff_kernel, kFThreads, smem));
   if (occ < 1) return fail(SLSO_ERR_CUDA, "float-float Cholesky kernel cannot be resident (smem %zu)", smem);
-  SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 4, st));
+  SLSO_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * kBarWords, st));
   int d_i = static_cast<int>(d);
   DevState* stp = h.state;
   int k_i = static_cast<int>(k);

@@ -110,7 +110,15 @@ struct Handle {
   int open_rec = -1;
   long long launches_at_enable = 0;
   int score_form = 0;              // float32 scores, k <= 128: SLSO_SCORE_FORM_* (slso_set_score_form)
+  // A second stream forked from and joined back into the call's stream (producer work that
+  // overlaps the tensor-core kernels: the Gaussian sketch's G and X^T chunks), with its events.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
 };
+
+// Create / release the handle's side stream and events (no-ops when already done / absent).
+cudaError_t side_stream_create(Handle& h);
+void side_stream_release(Handle& h);
 constexpr int kProfCap = 4096;
 
 // Begin / end a timed stage on stream st (no-ops unless profiling is on).
@@ -488,11 +496,12 @@ struct GramWork {
 GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d, int64_t k = 0);
 // With g.use_ff the factor's inverse is written to Rinv (column-major R^-1) as well, and
 // *rinv_done is set; otherwise the caller forms R^-1 from L.
-// Pi (d x k, k > 0, or NULL) must be generated before the call: with g.use_ff, M = R^-1 Pi is
-// written too (state->m_ready).
+// Pi (d x k, k > 0, or NULL) is generated before the call, on st or on another stream whose event
+// pi_ready st waits for once G is formed: with g.use_ff, M = R^-1 Pi is written too
+// (state->m_ready).
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
                             int64_t d, double* L, double* Rinv, bool* rinv_done, const double* Pi, int64_t k,
-                            double* M, cudaStream_t st);
+                            double* M, cudaStream_t st, cudaEvent_t pi_ready = nullptr);
 // chol_ff.cu: L (G's lower triangle in, R^T out) and Rinv from the float-float Cholesky.
 bool chol_ff_applies(int64_t d);
 slso_status run_chol_ff(Handle& h, double* L, const int* cexp, int64_t d, float2* A, float2* X, double* Rinv,

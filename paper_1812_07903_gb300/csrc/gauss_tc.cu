@@ -415,16 +415,25 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
   const int64_t Kc = std::min<int64_t>(kChunkRows, ceil_div(n, kGKB) * kGKB);
   const GLayout L = make_glayout(P, NT, Kc);
   if (L.S < 2) return SLSO_OK;
-  __nv_bfloat16* Gc = ar.take<__nv_bfloat16>(static_cast<size_t>(s) * Kc);
-  __nv_bfloat16* XT = ar.take<__nv_bfloat16>(static_cast<size_t>(P) * d * Kc);
+  // two chunk buffers: the side stream generates chunk i + 1 while the tensor cores take chunk i
+  __nv_bfloat16* Gc[2];
+  __nv_bfloat16* XT[2];
+  for (int b = 0; b < 2; ++b) {
+    Gc[b] = ar.take<__nv_bfloat16>(static_cast<size_t>(s) * Kc);
+    XT[b] = ar.take<__nv_bfloat16>(static_cast<size_t>(P) * d * Kc);
+  }
   *used = true;
   if (ar.measure()) return SLSO_OK;
 
-  CUtensorMap mA, mB[3];
-  bool ok = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Gc, Kc, s, Kc * 2, kGKB, kGBM);
-  for (int p = 0; p < 3; ++p)
-    ok = ok && make_map(&mB[p], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, XT + static_cast<size_t>(p < P ? p : 0) * d * Kc,
-                        Kc, d, Kc * 2, kGKB, static_cast<uint32_t>(NT));
+  CUtensorMap mA[2], mB[2][3];
+  bool ok = true;
+  for (int b = 0; b < 2; ++b) {
+    ok = ok && make_map(&mA[b], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Gc[b], Kc, s, Kc * 2, kGKB, kGBM);
+    for (int p = 0; p < 3; ++p)
+      ok = ok && make_map(&mB[b][p], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          XT[b] + static_cast<size_t>(p < P ? p : 0) * d * Kc, Kc, d, Kc * 2, kGKB,
+                          static_cast<uint32_t>(NT));
+  }
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Gaussian sketch operands");
   const double scale = 1.0 / std::sqrt(static_cast<double>(s));
   const dim3 grid_tc(static_cast<unsigned>(ceil_div(d, NT)), static_cast<unsigned>(ceil_div(s, kGBM)));
@@ -434,23 +443,40 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
   const unsigned gen_y = static_cast<unsigned>(std::max<int64_t>(
       1, std::min<int64_t>(s, ceil_div(int64_t(h.num_sms) * 8, static_cast<int64_t>(gen_x)))));
   const dim3 grid_gen(gen_x, gen_y);
-  for (int64_t k0 = 0; k0 < n; k0 += Kc) {
-    gauss_gen_kernel<<<grid_gen, kGenThreads, 0, st>>>(seed, s, n, row0, k0, Kc, Gc);
+  // Producer stream: the handle's side stream, forked from st (it starts after everything st holds)
+  // and joined back (st waits for each chunk it consumes, the last one included); without a side
+  // stream every launch goes to st in the same order.
+  const bool two = h.side != nullptr && n > Kc;
+  cudaStream_t ps = two ? h.side : st;
+  if (two) {
+    SLSO_CHECK_CUDA(cudaEventRecord(h.ev_fork, st));
+    SLSO_CHECK_CUDA(cudaStreamWaitEvent(ps, h.ev_fork, 0));
+  }
+  int64_t i = 0;
+  for (int64_t k0 = 0; k0 < n; k0 += Kc, ++i) {
+    const int b = static_cast<int>(i & 1);
+    if (two && i >= 2) SLSO_CHECK_CUDA(cudaStreamWaitEvent(ps, h.ev_free[b], 0));  // chunk i - 2 consumed
+    gauss_gen_kernel<<<grid_gen, kGenThreads, 0, ps>>>(seed, s, n, row0, k0, Kc, Gc[b]);
     SLSO_CHECK_LAUNCH();
     if (xdt == SLSO_F32)
-      xt_split_kernel<float><<<grid_xt, dim3(32, 8), 0, st>>>(static_cast<const float*>(X), n, d, ldx, k0, Kc, P,
-                                                              XT, h.state);
+      xt_split_kernel<float><<<grid_xt, dim3(32, 8), 0, ps>>>(static_cast<const float*>(X), n, d, ldx, k0, Kc, P,
+                                                              XT[b], h.state);
     else
-      xt_split_kernel<__nv_bfloat16><<<grid_xt, dim3(32, 8), 0, st>>>(static_cast<const __nv_bfloat16*>(X), n, d,
-                                                                      ldx, k0, Kc, P, XT, h.state);
+      xt_split_kernel<__nv_bfloat16><<<grid_xt, dim3(32, 8), 0, ps>>>(static_cast<const __nv_bfloat16*>(X), n, d,
+                                                                      ldx, k0, Kc, P, XT[b], h.state);
     SLSO_CHECK_LAUNCH();
+    if (two) {
+      SLSO_CHECK_CUDA(cudaEventRecord(h.ev_ready[b], ps));
+      SLSO_CHECK_CUDA(cudaStreamWaitEvent(st, h.ev_ready[b], 0));
+    }
     const int first = (k0 == 0 && !accumulate) ? 1 : 0;
     switch (NT) {
-      case 256: SLSO_TRY(launch_gauss_tc<256>(grid_tc, L, mA, mB, s, d, scale, first, SX, h.state, st)); break;
-      case 128: SLSO_TRY(launch_gauss_tc<128>(grid_tc, L, mA, mB, s, d, scale, first, SX, h.state, st)); break;
-      case 64: SLSO_TRY(launch_gauss_tc<64>(grid_tc, L, mA, mB, s, d, scale, first, SX, h.state, st)); break;
-      default: SLSO_TRY(launch_gauss_tc<32>(grid_tc, L, mA, mB, s, d, scale, first, SX, h.state, st)); break;
+      case 256: SLSO_TRY(launch_gauss_tc<256>(grid_tc, L, mA[b], mB[b], s, d, scale, first, SX, h.state, st)); break;
+      case 128: SLSO_TRY(launch_gauss_tc<128>(grid_tc, L, mA[b], mB[b], s, d, scale, first, SX, h.state, st)); break;
+      case 64: SLSO_TRY(launch_gauss_tc<64>(grid_tc, L, mA[b], mB[b], s, d, scale, first, SX, h.state, st)); break;
+      default: SLSO_TRY(launch_gauss_tc<32>(grid_tc, L, mA[b], mB[b], s, d, scale, first, SX, h.state, st)); break;
     }
+    if (two) SLSO_CHECK_CUDA(cudaEventRecord(h.ev_free[b], st));
   }
   return SLSO_OK;
 }

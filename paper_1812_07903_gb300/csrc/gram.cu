@@ -599,7 +599,7 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d, int64_t k) {
   if (g.use_ff) {
     g.Aff = ar.take<float2>(static_cast<size_t>(d) * d);
     g.Xff = ar.take<float2>(static_cast<size_t>(d) * d);
-    g.cbar = ar.take<unsigned int>(4);
+    g.cbar = ar.take<unsigned int>(4);  // grid barrier words of the float-float Cholesky
     g.Dbuf = ar.take<float2>(2 * 32 * 32);
     g.Outff = ar.take<float2>(static_cast<size_t>(d) * (k + 4));
     g.Yff = ar.take<float2>(static_cast<size_t>(d) * kProbes);
@@ -619,8 +619,9 @@ GramWork gram_take(Handle& h, Arena& ar, int64_t s, int64_t d, int64_t k) {
 
 slso_status run_gram_factor(Handle& h, const Arena& ar, const GramWork& g, const double* SX, int64_t s,
                             int64_t d, double* L, double* Rinv, bool* rinv_done, const double* Pi, int64_t k,
-                            double* M, cudaStream_t st) {
+                            double* M, cudaStream_t st, cudaEvent_t pi_ready) {
   SLSO_TRY(run_gram_matrix(h, ar, g, SX, s, d, L, st));
+  if (pi_ready) SLSO_CHECK_CUDA(cudaStreamWaitEvent(st, pi_ready, 0));  // join the side stream's Pi
   prof_begin(h, ar, ST_CHOL, st);
   if (g.use_ff) {
     probe_z_kernel<<<static_cast<unsigned>(ceil_div(d * kProbes, 256)), 256, 0, st>>>(static_cast<int>(d), g.Z,

@@ -102,6 +102,34 @@ extern "C" const char* slso_version(void) { return "slso-gb300 0.1 (sm_103a)"; }
 
 extern "C" const char* slso_last_error(void) { return g_last_error; }
 
+namespace slso {
+
+cudaError_t side_stream_create(Handle& h) {
+  if (h.side) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&h.side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h.ev_ready[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.ev_free[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) side_stream_release(h);
+  return e;
+}
+
+void side_stream_release(Handle& h) {
+  if (h.side) cudaStreamDestroy(h.side);
+  if (h.ev_fork) cudaEventDestroy(h.ev_fork);
+  for (int i = 0; i < 2; ++i) {
+    if (h.ev_ready[i]) cudaEventDestroy(h.ev_ready[i]);
+    if (h.ev_free[i]) cudaEventDestroy(h.ev_free[i]);
+    h.ev_ready[i] = h.ev_free[i] = nullptr;
+  }
+  h.side = nullptr;
+  h.ev_fork = nullptr;
+}
+
+}  // namespace slso
+
 extern "C" slso_status slso_create(slso_handle** handle, int device) {
   if (!handle) return fail(SLSO_ERR_INVALID_ARG, "handle out-pointer is NULL");
   *handle = nullptr;
@@ -116,7 +144,9 @@ extern "C" slso_status slso_create(slso_handle** handle, int device) {
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->state), sizeof(DevState));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->state_host), sizeof(DevState));
   if (e == cudaSuccess) e = cudaMemset(h->state, 0, sizeof(DevState));
+  if (e == cudaSuccess) e = side_stream_create(*h);
   if (e != cudaSuccess) {
+    side_stream_release(*h);
     if (h->state) cudaFree(h->state);
     if (h->state_host) cudaFreeHost(h->state_host);
     delete h;
@@ -140,6 +170,7 @@ extern "C" slso_status slso_destroy(slso_handle* handle) {
       }
     delete[] h->recs;
   }
+  side_stream_release(*h);
   if (h->state) cudaFree(h->state);
   if (h->state_host) cudaFreeHost(h->state_host);
   delete h;

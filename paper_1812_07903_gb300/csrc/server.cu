@@ -359,8 +359,10 @@ extern "C" slso_status slso_server_create(slso_server** out, int device, int nsl
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.h.state), sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.h.state_host), sizeof(DevState));
+    if (e == cudaSuccess) e = side_stream_create(sl.h);
     if (e != cudaSuccess) {
       for (Slot& t : s->slots) {
+        side_stream_release(t.h);
         if (t.st) cudaStreamDestroy(t.st);
         if (t.done) cudaEventDestroy(t.done);
         if (t.h.state) cudaFree(t.h.state);
@@ -398,6 +400,7 @@ extern "C" slso_status slso_server_destroy(slso_server* srv) {
       cudaFree(g.ws);
     }
     sl.graphs.clear();
+    side_stream_release(sl.h);
     cudaStreamDestroy(sl.st);
     cudaEventDestroy(sl.done);
     cudaFree(sl.h.state);

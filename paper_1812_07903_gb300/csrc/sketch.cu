@@ -277,6 +277,138 @@ __global__ void srht_combine_kernel(const Acc* __restrict__ P, int64_t n1, int64
   }
 }
 
+// Float32 SRHT chunk transform with coalesced loads and the butterflies in registers (float32 and
+// bfloat16 X).  CTA (i1, slab): chunk i1 of N2 = 2^LOG2 rows (64 <= N2 <= 4096), columns
+// [8 slab, 8 slab + 8): 512 threads = 64 row groups g x 8 columns; a warp-wide load reads four
+// rows' 32-byte column segments.  Row r = g R + t of the chunk (R = N2 / 64):
+//   phase 1: thread (g, col) holds rows g R .. g R + R - 1 and runs the log2 R butterfly levels
+//            over t in registers;
+//   exchange through shared memory (the only cross-warp step), then thread (g, col) with g < R
+//            holds rows a R + g for all 64 values of a and runs the remaining 6 levels over a;
+//   every sampled row j = j1 N2 + j2 then takes (-1)^popc(i1 & j1) T[j2] (this chunk's share of
+//            (H D X)_j) into P[i1][q][c] (row pitch dp: 32-byte segments again).
+// Shared rows are stored at r ^ ((r / R) & 3) (R >= 4) so that the four row groups of a warp
+// fall on different banks in both phases.  The D signs come from Philox once per row: lane col
+// draws the rows t = col (mod 8) of its group and the 8 lanes combine their bit masks by shuffles.
+constexpr int kSr2Threads = 512;
+constexpr int kSr2Cols = 8;
+
+template <class T, int LOG2>
+__global__ void __launch_bounds__(kSr2Threads, 1) srht_chunk_reg_kernel(
+    const T* __restrict__ X, int64_t n, int64_t d, int64_t ldx, int64_t row0, uint64_t seed,
+    const uint32_t* __restrict__ sample, int64_t s, int64_t dp, float* __restrict__ P, DevState* __restrict__ state) {
+  constexpr int N2 = 1 << LOG2, R = N2 / 64;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* S = reinterpret_cast<float*>(smem_raw);  // [N2][8], rows permuted by prow
+  auto prow = [](int r) { return R >= 4 ? (r ^ ((r / R) & 3)) : r; };
+  const int col = threadIdx.x & 7, g = threadIdx.x >> 3;
+  const int64_t i1 = blockIdx.x;
+  const int64_t c = static_cast<int64_t>(blockIdx.y) * kSr2Cols + col;
+  const int64_t rbase = i1 * N2 + static_cast<int64_t>(g) * R;  // first row of the group (block rows)
+  float v[64];
+  // the group's R rows of this column (issued before the sign draws, so the loads are in flight)
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int64_t i = rbase + t;
+    v[t] = (i < n && c < d) ? to_float_or_double(X[i * ldx + c]) : 0.f;
+  }
+  // D signs of the group's R rows: bit t set means row rbase + t is negated
+  uint32_t m_lo = 0, m_hi = 0;
+  for (int t = col; t < R; t += kSr2Cols) {
+    const int64_t i = rbase + t;
+    if (i < n) {
+      const uint64_t ig = static_cast<uint64_t>(row0 + i);
+      const U32x4 w = philox(static_cast<uint32_t>(ig), static_cast<uint32_t>(ig >> 32), 0u, TAG_SRHT_SIGN, seed);
+      if (w.x & 1u) {
+        if (t < 32) m_lo |= 1u << t;
+        else m_hi |= 1u << (t - 32);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < kSr2Cols; o <<= 1) {
+    m_lo |= __shfl_xor_sync(0xFFFFFFFFu, m_lo, o);
+    m_hi |= __shfl_xor_sync(0xFFFFFFFFu, m_hi, o);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    bad |= !isfinite(v[t]);
+    const bool neg = ((t < 32 ? m_lo >> t : m_hi >> (t - 32)) & 1u) != 0;
+    v[t] = neg ? -v[t] : v[t];
+  }
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1)
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      if ((t & h) == 0) {
+        const float a = v[t], b = v[t + h];
+        v[t] = a + b;
+        v[t + h] = a - b;
+      }
+#pragma unroll
+  for (int t = 0; t < R; ++t) S[prow(g * R + t) * kSr2Cols + col] = v[t];
+  __syncthreads();
+  if (g < R) {
+#pragma unroll
+    for (int a = 0; a < 64; ++a) v[a] = S[prow(a * R + g) * kSr2Cols + col];
+#pragma unroll
+    for (int h = 1; h < 64; h <<= 1)
+#pragma unroll
+      for (int a = 0; a < 64; ++a)
+        if ((a & h) == 0) {
+          const float x = v[a], y = v[a + h];
+          v[a] = x + y;
+          v[a + h] = x - y;
+        }
+#pragma unroll
+    for (int a = 0; a < 64; ++a) S[prow(a * R + g) * kSr2Cols + col] = v[a];
+  }
+  __syncthreads();
+  const uint32_t ib = static_cast<uint32_t>((row0 >> LOG2) + i1);  // row0: a multiple of N2
+  // sampled rows, eight at a time per thread so that their index loads overlap
+  for (int64_t q0 = g; q0 < s; q0 += 64 * 8) {
+    uint32_t jj[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t q = q0 + 64 * u;
+      jj[u] = q < s ? sample[q] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t q = q0 + 64 * u;
+      const uint32_t j1 = jj[u] >> LOG2, j2 = jj[u] & static_cast<uint32_t>(N2 - 1);
+      const float val = S[prow(static_cast<int>(j2)) * kSr2Cols + col];
+      if (q < s && c < d) P[(i1 * s + q) * dp + c] = (__popc(ib & j1) & 1) ? -val : val;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&state->nonfinite, 1);
+}
+
+// SX[q][c] (+)= (sum over i1 ascending of P[i1][q][c]) / sqrt(s) in float64; coalesced along c.
+__global__ void srht_combine_reg_kernel(const float* __restrict__ P, int64_t n1, int64_t d, int64_t dp, int64_t s,
+                                        int accum, double* __restrict__ SX) {
+  const double rs = sqrt(static_cast<double>(s));
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < s * d;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t q = e / d, c = e - q * d;
+    const float* p = P + q * dp + c;
+    const int64_t stride = s * dp;
+    double acc = 0.0;
+    int64_t i1 = 0;
+    for (; i1 + 8 <= n1; i1 += 8) {  // eight loads in flight, added in ascending i1
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = p[(i1 + u) * stride];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += static_cast<double>(t[u]);
+    }
+    for (; i1 < n1; ++i1) acc += static_cast<double>(p[i1 * stride]);
+    const double v = acc / rs;
+    SX[e] = accum ? SX[e] + v : v;
+  }
+}
+
 // ---------------------------------------------------------------- Gaussian (SIMT)
 constexpr int kGbm = 64, kGbn = 64, kGbk = 16;
 
@@ -434,10 +566,16 @@ int log2_ceil(int64_t n) {
   return m;
 }
 
+// Chunk height: float64 X, 2^12 rows of 4 columns in shared memory (128 KB); float32 / bfloat16
+// X, 2^12 rows of 8 columns (128 KB) in the register-butterfly kernel, which needs 64 rows at least
+// (smaller padded heights take the shared-memory kernel).
 template <class T>
 int srht_log2_n2(int64_t n_total) {
-  const int log2_n2_max = std::is_same<T, double>::value ? 12 : 13;  // 128 KB of shared memory
-  return std::min(log2_ceil(n_total), log2_n2_max);
+  return std::min(log2_ceil(n_total), 12);
+}
+template <class T>
+constexpr bool srht_reg_form() {
+  return !std::is_same<T, double>::value;
 }
 
 // Rows n .. n_pad - 1 of the padded X are zero, so only the ceil(n / n2) chunks holding rows of
@@ -451,6 +589,33 @@ slso_status srht(Handle& h, Arena& ar, const T* X, int64_t n, int64_t d, int64_t
   const int log2_n2 = srht_log2_n2<T>(n_total);
   const int64_t n1 = ceil_div(n, int64_t(1) << log2_n2);
   if (sample == nullptr) SLSO_TRY(srht_sample_rows(h, ar, n_total, s, seed, &sample, st));
+  if (srht_reg_form<T>() && log2_n2 >= 6) {
+    const int64_t dp = ceil_div(d, kSr2Cols) * kSr2Cols;
+    float* Pr = ar.take<float>(static_cast<size_t>(n1) * s * dp);
+    if (ar.measure()) return SLSO_OK;
+    const size_t smem = (size_t(1) << log2_n2) * kSr2Cols * sizeof(float);
+    const dim3 g1(static_cast<unsigned>(n1), static_cast<unsigned>(ceil_div(d, kSr2Cols)));
+    auto launch = [&](auto kern) -> slso_status {
+      SLSO_TRY(raise_smem_limit(kern, smem));
+      kern<<<g1, kSr2Threads, smem, st>>>(X, n, d, ldx, row0, seed, sample, s, dp, Pr, h.state);
+      SLSO_CHECK_LAUNCH();
+      return SLSO_OK;
+    };
+    switch (log2_n2) {
+      case 6: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 6>)); break;
+      case 7: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 7>)); break;
+      case 8: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 8>)); break;
+      case 9: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 9>)); break;
+      case 10: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 10>)); break;
+      case 11: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 11>)); break;
+      default: SLSO_TRY(launch(srht_chunk_reg_kernel<T, 12>)); break;
+    }
+    const int64_t total = s * d;
+    const unsigned gc = static_cast<unsigned>(std::min<int64_t>(ceil_div(total, 256), 16LL * h.num_sms));
+    srht_combine_reg_kernel<<<gc, 256, 0, st>>>(Pr, n1, d, dp, s, acc, SX);
+    SLSO_CHECK_LAUNCH();
+    return SLSO_OK;
+  }
   Acc* P = ar.take<Acc>(static_cast<size_t>(n1) * d * s);
   if (ar.measure()) return SLSO_OK;
   const size_t smem = (size_t(1) << log2_n2) * kSrhtSlab * sizeof(Acc);

@@ -1332,12 +1332,24 @@ slso_status run_solve(Handle& h, Arena& ar, const double* SX, int64_t s, int64_t
   // trinv_kernel keeps one column of R^-1 in shared memory: d doubles, above 48 KB for d > 6144
   SLSO_TRY(raise_smem_limit(trinv_kernel, sizeof(double) * d));
   if (gram) {
+    cudaEvent_t pi_ready = nullptr;
     if (k > 0) {  // M = R^-1 Pi comes out of the float-float factorisation
-      pi_kernel<<<grid1d(d * k, h), 256, 0, st>>>(d, k, seed_pi, Pi);
+      // Pi on the side stream, overlapping the Gram product; joined before the factorisation
+      cudaStream_t ps = st;
+      if (h.side) {
+        SLSO_CHECK_CUDA(cudaEventRecord(h.ev_fork, st));
+        SLSO_CHECK_CUDA(cudaStreamWaitEvent(h.side, h.ev_fork, 0));
+        ps = h.side;
+      }
+      pi_kernel<<<grid1d(d * k, h), 256, 0, ps>>>(d, k, seed_pi, Pi);
       SLSO_CHECK_LAUNCH();
+      if (h.side) {
+        SLSO_CHECK_CUDA(cudaEventRecord(h.ev_ready[0], ps));
+        pi_ready = h.ev_ready[0];
+      }
     }
     bool rinv_done = false;
-    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, Rinv, &rinv_done, Pi, k, M, st));
+    SLSO_TRY(run_gram_factor(h, ar, gw, SX, s, d, Rc, Rinv, &rinv_done, Pi, k, M, st, pi_ready));
     prof_begin(h, ar, ST_CHOL, st);
     if (!rinv_done) {
       inv_diag_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(Rc, d, d, invd, gram_ok, 1);
