@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         tk.diag = false;
         tk.rhs = true;
       } else if (task < ntri) {
-        int a = static_cast<int>((sqrt(8.0 * task + 1.0) - 1.0) * 0.5);
+        int a = static_cast<int>((sqrtf(8.f * static_cast<float>(task) + 1.f) - 1.f) * 0.5f);
         while ((a + 1) * (a + 2) / 2 <= task) ++a;
         while (a * (a + 1) / 2 > task) --a;
         const int b = task - a * (a + 1) / 2;

@@ -27,9 +27,9 @@
 // (576 threads, one CTA per SM):
 //   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and columns
 //              16 (w / 4).. of each accumulator; two int64 running sums per entry in registers.
-//   warp 16    TMA producer: the eight A slices (128 columns of SX x 32 rows) and eight B slices
-//              (64 columns x 32 rows) per stage, 64-byte swizzle.
-//   warp 17    TMEM owner (eight 64-column accumulators) and MMA issuer: 2 x 36 tcgen05.mma
+//   warp 16    TMA producer: the eight A slices (128 columns of SX x 16 rows) and eight B slices
+//              (64 columns x 16 rows) per stage, 32-byte swizzle; four stages of 48 KB.
+//   warp 17    TMEM owner (eight 64-column accumulators) and MMA issuer: 36 tcgen05.mma
 //              (kind::f16, bfloat16, M = 128, N = 64, K = 16) per stage.
 // Every mbarrier wait is bounded; a timeout sets DevState::timeout.
 #include <cuda_bf16.h>
@@ -50,16 +50,16 @@ using namespace tc;
 constexpr int kThreadsG = 576;
 constexpr int kBMg = 128;   // tile rows (columns i of SX)
 constexpr int kBNg = 64;    // tile columns (columns j of SX)
-constexpr int kKBg = 32;    // rows of SX per stage: one 64-byte bfloat16 row per slice tile
+constexpr int kKBg = 16;    // rows of SX per stage: one 32-byte bfloat16 row per slice tile
 constexpr int kSlices = 8;  // 7-bit digits of the 56-bit fixed-point value
 constexpr int kOrders = 8;  // accumulators: one per digit order 0..7
 constexpr int kWinRows = 512;  // rows of SX per exact window
 constexpr int kKbPerWin = kWinRows / kKBg;
-constexpr int kStagesG = 2;
+constexpr int kStagesG = 4;  // four stages of 48 KB: more of the L2 ingress in flight than two of 96 KB
 constexpr int kEpiWarpsG = 16;
 constexpr int kWarpProdG = 16, kWarpMmaG = 17;
-constexpr uint32_t kASliceBytes = kBMg * 64;  // 8 KB
-constexpr uint32_t kBSliceBytes = kBNg * 64;  // 4 KB
+constexpr uint32_t kASliceBytes = kBMg * kKBg * 2;  // 4 KB
+constexpr uint32_t kBSliceBytes = kBNg * kKBg * 2;  // 2 KB
 constexpr uint32_t kStageBytesG = kSlices * (kASliceBytes + kBSliceBytes);
 constexpr uint32_t kBarOffG = kStagesG * kStageBytesG;
 constexpr uint32_t kSmemG = kBarOffG + (2 * kStagesG + 2) * 8 + 16 + 1024;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kThreadsG, 1)
           tc_fence_after();
           unsigned char* stage = smem + static_cast<uint32_t>(st) * kStageBytesG;
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
+          for (int ks = 0; ks < kKBg / 16; ++ks) {
             const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
 #pragma unroll
             for (int pr = 0; pr < kPairs; ++pr) {
@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(kThreadsG, 1)
               // the first pair of each order starts its accumulator in the window's first K-step
               const bool first = pr == ord * (ord + 1) / 2;
               const uint32_t acc = (kw | ks) != 0 || !first;
-              const uint64_t a = sdesc_sw64(stage + p * kASliceBytes) + o;
-              const uint64_t bd = sdesc_sw64(stage + kSlices * kASliceBytes + qq * kBSliceBytes) + o;
+              const uint64_t a = sdesc_sw32(stage + p * kASliceBytes) + o;
+              const uint64_t bd = sdesc_sw32(stage + kSlices * kASliceBytes + qq * kBSliceBytes) + o;
               mma_f16(tmem_base + static_cast<uint32_t>(ord * kBNg), a, bd, id, acc);
             }
           }
@@ -415,9 +415,9 @@ slso_status run_gram_tc(Handle& h, const GramTcWork& w, const double* SX, int64_
   CUtensorMap mA, mB;
   const uint64_t rows = static_cast<uint64_t>(kSlices) * w.dpad;
   bool ok = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, s, rows, w.sp * 2, kKBg, kBMg,
-                     CU_TENSOR_MAP_SWIZZLE_64B) &&
+                     CU_TENSOR_MAP_SWIZZLE_32B) &&
             make_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, s, rows, w.sp * 2, kKBg, kBNg,
-                     CU_TENSOR_MAP_SWIZZLE_64B);
+                     CU_TENSOR_MAP_SWIZZLE_32B);
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Gram slices");
   SLSO_TRY(raise_smem_limit(gram_tc_kernel, kSmemG));
   gram_tc_kernel<<<static_cast<unsigned>(w.tiles * w.splits), kThreadsG, kSmemG, st>>>(

@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, so warp w converts rows 32 (w % 4) + lane of tile
 // (w - 6) / 4 (for T = 1 the warps of tile 1 only arrive).  Every wait is bounded.
 struct LayoutTm {
-  int N, KB, S, nbuf;
+  int N, KB, S, nbuf;           // stages (shared-memory tiles and TMEM A slots), accumulator sets
   int chunk, nchunk;            // K-blocks per accumulation chunk, chunks per work item
   uint32_t bh_bytes, bx_bytes;  // B hi tile (N x 64 B); each further B tile (N x 32 B or N x 64 B)
   uint32_t stage_bytes, bar_off, smem_bytes, run_col, abase, tmem_cols;
@@ -707,8 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       uint32_t dbase = 0;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-        for (int kb = 0; kb < L.KB; ++kb, ++it) {
-          const int kc = kb % L.chunk;  // K-block within its chunk
+        for (int kb = 0, kc = 0; kb < L.KB; ++kb, ++it) {  // kc: K-block within its chunk
           if (kc == 0) {                 // a fresh accumulator set for this chunk
             const int ab = cc % L.nbuf;
             if (!mbar_wait(&acc_empty[ab], ((cc / L.nbuf) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -743,9 +742,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           mma_commit(&empty[st]);
-          if (kc == L.chunk - 1 || kb == L.KB - 1) {  // the chunk is summed
+          if (++kc == (T == 1 ? L.chunk : L.KB) || kb == L.KB - 1) {  // the chunk is summed
             mma_commit(&acc_full[cc % L.nbuf]);
             ++cc;
+            kc = 0;
           }
         }
       }
@@ -766,8 +766,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
       for (int kb = 0; kb < L.KB; ++kb, ++it) {
         const int st = it % L.S;
-        // every lane acquires the TMA's bytes; the outcome is made warp-uniform (tcgen05.st is
-        // .sync.aligned)
+        // every lane acquires the TMA's bytes (the stage, and with it its TMEM slot, was freed by
+        // the MMAs before the producer refilled it); the outcome is made warp-uniform (tcgen05.st
+        // is .sync.aligned)
         const bool got = mbar_wait(&full[st], (it / L.S) & 1u, abort_flag);
         if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }
         if (u < T) {
@@ -819,21 +820,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int u = 0; u < T; ++u) sum[u] = 0.0f;
       bool ok = true;
-      for (int ci = 0; ci < L.nchunk; ++ci, ++cc) {
+      const int nchunk = T == 1 ? L.nchunk : 1;
+      for (int ci = 0; ci < nchunk; ++ci, ++cc) {
         const int ab = cc % L.nbuf;
         int got = 0;
         if (lane == 0) got = mbar_wait(&acc_full[ab], (cc / L.nbuf) & 1u, abort_flag) ? 1 : 0;
         got = __shfl_sync(0xFFFFFFFFu, got, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
         if (!got) { ok = false; break; }
         tc_fence_after();
-        const bool last = ci == L.nchunk - 1;
+        const bool last = ci == nchunk - 1;
 #pragma unroll
         for (int u = 0; u < T; ++u) {
           const uint32_t taddr = tmem_base + lanes + static_cast<uint32_t>(ab * T * L.N + u * L.N);
           for (int c0 = 0; c0 < L.N; c0 += 32) {
             float v[32];
             tmem_ld_32x32b_x32(taddr + static_cast<uint32_t>(c0), v);
-            if (L.nchunk > 1) {  // T = 1: fold into the running sum (round to nearest)
+            if (T == 1 && L.nchunk > 1) {  // fold into the running sum (round to nearest)
               const uint32_t raddr = tmem_base + lanes + L.run_col + static_cast<uint32_t>(c0);
               if (ci > 0) {
                 float rs[32];
@@ -1080,7 +1082,8 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   bool ok;
   const CUtensorMapDataType xdt_map = (xdt == SLSO_F32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   ok = make_map(&mX, xdt_map, X, d, n, ldx * esz, static_cast<uint32_t>(L.box_cols), kBM);
-  const bool tm = mode == MODE_TF32X3 && L.N <= 128 && h.score_form != SLSO_SCORE_FORM_TF32X3_SMEM;
+  // the shared-memory form sums K in one accumulator: rows longer than 2048 take the chunked form
+  const bool tm = mode == MODE_TF32X3 && L.N <= 128 && (h.score_form != SLSO_SCORE_FORM_TF32X3_SMEM || d > 2048);
   const bool hyb = tm && h.score_form == SLSO_SCORE_FORM_MIXED;
   if (mode == MODE_TF32X3) {
     if (!hyb) {  // the mixed form prepares its own pieces below
