@@ -17,9 +17,10 @@ namespace {
 
 constexpr int64_t kStaticMaxN = int64_t(1) << 20;
 // keys + alternate keys (8 bytes each for float64 scores), values + alternate values (4 bytes
-// each), 256 digit counts per 4096-key tile, plus 256-byte alignment of each piece.
+// each), 256 digit counts per 4096-key tile, the 256 digit totals, plus 256-byte alignment of
+// each piece.
 constexpr size_t kStaticBytes = size_t(kStaticMaxN) * (8 + 8 + 4 + 4) + size_t(256) * (kStaticMaxN / 4096) * 4 +
-                                size_t(16) * 256;
+                                size_t(256) * 4 + size_t(16) * 256;
 
 __device__ __align__(256) unsigned char g_order_scratch[kStaticBytes];
 

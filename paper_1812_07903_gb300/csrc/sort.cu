@@ -3,9 +3,10 @@
 //
 // Three launches per 8-bit digit, with no inter-CTA waiting:
 //   hist    each tile of 4096 keys counts its digits          -> hist[digit][tile]
-//   scan    one CTA turns the digit-major counts into offsets  (exclusive prefix)
-//   scatter each tile ranks its keys stably (warp match + per-warp counters) and writes
-//           them at offset[digit][tile] + rank.
+//   scan    one CTA per digit: exclusive prefix over the tiles in place, and the digit's total
+//   scatter each tile adds the exclusive prefix of the digit totals to its row of offsets, ranks
+//           its keys stably (warp match + per-warp counters) and writes them at
+//           offset[digit][tile] + rank.
 // Stability: tiles are contiguous and ordered, warps own contiguous 512-key runs inside a
 // tile, and a warp walks its run 32 keys at a time in index order.
 #include "common.cuh"
@@ -20,6 +21,7 @@ constexpr int kItems = 16;                    // per thread
 constexpr int kTile = kThreads * kItems;      // 4096 keys per CTA
 constexpr int kWarpRun = 32 * kItems;         // 512 consecutive keys per warp
 constexpr int kRadix = 256;
+static_assert(kThreads == kRadix, "the scatter kernel computes one digit's start per thread");
 
 template <class K>
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const K* __restrict__ keys,
@@ -40,22 +42,17 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const K* __restric
     hist[static_cast<int64_t>(i) * ntiles + blockIdx.x] = cnt[i];
 }
 
-// Exclusive prefix sum in place over `total` counts (a multiple of 4), one CTA of 1024 threads:
-// thread t owns a contiguous chunk, read with independent 16-byte loads so that they are all in
-// flight at once; the chunk sums are scanned across the CTA (warp shuffles, then one warp over
-// the warp totals) and every chunk is rewritten from its offset.
-__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__ a, int64_t total) {
-  __shared__ uint32_t wsum[32];
+// One CTA per digit: hist[digit][.] becomes its exclusive prefix over the tiles (in tile order),
+// totals[digit] the digit's count.
+__global__ void __launch_bounds__(256) radix_scan_digit_kernel(uint32_t* __restrict__ hist, int ntiles,
+                                                               uint32_t* __restrict__ totals) {
+  __shared__ uint32_t wsum[8];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int64_t q4 = total / 4;                    // uint4 groups
-  const int64_t per = (q4 + 1023) / 1024;          // groups per thread
-  const int64_t g0 = t * per, g1 = g0 + per < q4 ? g0 + per : q4;
-  uint4* a4 = reinterpret_cast<uint4*>(a);
+  uint32_t* row = hist + static_cast<int64_t>(blockIdx.x) * ntiles;
+  const int per = (ntiles + 255) / 256;
+  const int i0 = t * per, i1 = i0 + per < ntiles ? i0 + per : ntiles;
   uint32_t sum = 0;
-  for (int64_t g = g0; g < g1; ++g) {
-    const uint4 v = a4[g];
-    sum += v.x + v.y + v.z + v.w;
-  }
+  for (int i = i0; i < i1; ++i) sum += row[i];
   uint32_t x = sum;  // inclusive scan over the warp
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -64,43 +61,42 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* __restrict__
   }
   if (lane == 31) wsum[w] = x;
   __syncthreads();
-  if (w == 0) {
-    uint32_t ws = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, ws, o);
-      if (lane >= o) ws += y;
-    }
-    wsum[lane] = ws;
+  uint32_t before = 0;
+  for (int v = 0; v < w; ++v) before += wsum[v];
+  uint32_t run = before + x - sum;  // exclusive
+  for (int i = i0; i < i1; ++i) {
+    const uint32_t c = row[i];
+    row[i] = run;
+    run += c;
   }
-  __syncthreads();
-  uint32_t run = (w > 0 ? wsum[w - 1] : 0u) + x - sum;  // exclusive
-  for (int64_t g = g0; g < g1; ++g) {
-    const uint4 v = a4[g];
-    uint4 o;
-    o.x = run;
-    run += v.x;
-    o.y = run;
-    run += v.y;
-    o.z = run;
-    run += v.z;
-    o.w = run;
-    run += v.w;
-    a4[g] = o;
-  }
+  if (t == 255) totals[blockIdx.x] = before + x;
 }
 
 template <class K>
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ offs,
-    int ntiles) {
+    const uint32_t* __restrict__ totals, int ntiles) {
   __shared__ uint32_t wcnt[kWarps][kRadix];
   __shared__ uint32_t gofs[kRadix];
+  __shared__ uint32_t wtot[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
-  for (int i = threadIdx.x; i < kRadix; i += kThreads)
-    gofs[i] = offs[static_cast<int64_t>(i) * ntiles + blockIdx.x];
+  // the digits' start: exclusive prefix of the totals (kThreads == kRadix: one digit per thread)
+  {
+    const uint32_t tot = totals[threadIdx.x];
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int v = 0; v < warp; ++v) before += wtot[v];
+    gofs[threadIdx.x] = before + x - tot + offs[static_cast<int64_t>(threadIdx.x) * ntiles + blockIdx.x];
+  }
   __syncthreads();
 
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + warp * kWarpRun;
@@ -155,6 +151,7 @@ slso_status radix_sort_impl(Arena& ar, K* keys, uint32_t* vals, int64_t n, int b
   K* kalt = ar.template take<K>(n);
   uint32_t* valt = ar.template take<uint32_t>(n);
   uint32_t* hist = ar.template take<uint32_t>(static_cast<size_t>(kRadix) * ntiles);
+  uint32_t* totals = ar.template take<uint32_t>(kRadix);
   if (ar.measure()) return SLSO_OK;
   K* ka = keys;
   K* kb = kalt;
@@ -165,9 +162,9 @@ slso_status radix_sort_impl(Arena& ar, K* keys, uint32_t* vals, int64_t n, int b
     const int shift = 8 * p;
     radix_hist_kernel<K><<<ntiles, kThreads, 0, st>>>(ka, n, shift, hist, ntiles);
     SLSO_CHECK_LAUNCH();
-    radix_scan_kernel<<<1, 1024, 0, st>>>(hist, static_cast<int64_t>(kRadix) * ntiles);
+    radix_scan_digit_kernel<<<kRadix, 256, 0, st>>>(hist, ntiles, totals);
     SLSO_CHECK_LAUNCH();
-    radix_scatter_kernel<K><<<ntiles, kThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles);
+    radix_scatter_kernel<K><<<ntiles, kThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, totals, ntiles);
     SLSO_CHECK_LAUNCH();
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
