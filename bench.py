@@ -43,7 +43,9 @@ GRAM_DIGIT_PRODUCTS = 36
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each stage's kernel on the
 # 1,000,000 x 1024 workload (s = 16384, k = 128), from one ncu capture of its current source; None
 # whenever the kernel changed since, until it is captured again.
-TRAFFIC_BYTES = {"scores": None, "sketch": None, "syrk": None, "chol": None}
+# scores: 544.1 MB captured on 131072 rows (X read once), scaled by 10^6 / 131072 rows; chol: the
+# factorisation does not depend on n (d = 1024 in both).
+TRAFFIC_BYTES = {"scores": 4_151_400_000, "sketch": None, "syrk": None, "chol": 6_820_608}
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point
