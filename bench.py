@@ -330,6 +330,7 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
         "arrival_rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
         "makespan_s": makespan, "jobs_per_s": n_jobs / makespan, "rows_per_s": rows / makespan,
         "graphs": {k: counters[k] for k in ("graphs_new", "graphs_updated", "direct")},
+        "grouped": {k: counters[k] for k in ("group_launches", "grouped_jobs")},
         "repeated_shape": repeated_shape_latency(api, inputs, torch),
     }
 

@@ -305,11 +305,18 @@ slso_status slso_server_cancel(slso_server* server, int64_t ticket);
 /* counters[0..3] = {submitted, admitted, completed, queued}; bytes of scratch in use. */
 slso_status slso_server_stats(slso_server* server, int64_t* counters, size_t* mem_in_use);
 /* The first `count` of {submitted, admitted, completed, queued, scratch bytes in use, graphs
- * instantiated, graphs updated in place, leverage jobs run without a graph} (zeros beyond).
+ * instantiated, graphs updated in place, leverage jobs run without a graph, grouped score
+ * launches, jobs run in them} (zeros beyond).
  * From the second job of a shape (n, d, ldx, dtype, params, order or not) on, leverage jobs are
  * recorded into CUDA graphs by stream capture; each slot keeps the graphs of its 8 most recent
  * shapes with their workspace, within a quarter of the memory budget, and a job of a cached
- * shape updates that graph's arguments in place and replays it. */
+ * shape updates that graph's arguments in place and replays it.
+ * Grouped launches: when a slot frees up and the queue's head is a small leverage job (float32 X
+ * and compute, 1 <= k <= 128, d <= 2048, n <= 2^17, 16-byte aligned rows, no correction pass), up
+ * to 8 consecutive queued jobs of that kind with the same JL width (k rounded up to 32) that fit
+ * the budget are admitted together: each job's sketch and solve run on the slot's stream, then
+ * one persistent tensor-core launch computes all their scores from device-side job descriptors
+ * (each row exactly as the job's own launch computes it), then each job's score sum and order. */
 slso_status slso_server_counters(slso_server* server, int64_t* counters, int32_t count);
 
 /* Ordering that allocates nothing (the paper has no counterpart; this exists for callers).

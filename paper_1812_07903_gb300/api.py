@@ -365,9 +365,10 @@ class Server:
         return {"submitted": c[0], "admitted": c[1], "completed": c[2], "queued": c[3], "mem_in_use": mem.value}
 
     def counters(self):
-        """slso_server_counters: job counts, scratch in use and the graph-capture counters."""
+        """slso_server_counters: job counts, scratch in use, the graph-capture counters and the
+        grouped score launches with the jobs they ran."""
         names = ("submitted", "admitted", "completed", "queued", "mem_in_use", "graphs_new", "graphs_updated",
-                 "direct")
+                 "direct", "group_launches", "grouped_jobs")
         c = (ctypes.c_int64 * len(names))()
         L.check(L.load().slso_server_counters(self._s, c, len(names)))
         return dict(zip(names, list(c)))

@@ -115,8 +115,9 @@ slso_status fill_info(Handle& h, cudaStream_t st, slso_info* info) {
 
 namespace slso {
 
-slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
-                          int32_t xdt, const slso_params* p, void* scores, cudaStream_t st) {
+slso_status leverage_solve(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                           int32_t xdt, const slso_params* p, cudaStream_t st, const double** M, int64_t* kk,
+                           const unsigned int** colmax_out) {
   const double tau = p->tau < 0 ? default_tau(p->s, d) : p->tau;
   double* SX = ar.take<double>(static_cast<size_t>(p->s) * d);
   // FP8 scores of float32 / bfloat16 X after a CountSketch or OSNAP: the column maxima of |X| come
@@ -132,9 +133,20 @@ slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   prof_end(h, ar, st);
   SolveOut so;
   SLSO_TRY(run_solve(h, ar, SX, p->s, d, tau, p->k, p->seed_Pi, 0, &so, st, use_gram(p)));
-  const int64_t kk = p->k > 0 ? p->k : d;
+  *M = so.M;
+  *kk = p->k > 0 ? p->k : d;
+  *colmax_out = colmax;
+  return SLSO_OK;
+}
+
+slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                          int32_t xdt, const slso_params* p, void* scores, cudaStream_t st) {
+  const double* M = nullptr;
+  int64_t kk = 0;
+  const unsigned int* colmax = nullptr;
+  SLSO_TRY(leverage_solve(h, ar, X, n, d, ldx, xdt, p, st, &M, &kk, &colmax));
   prof_begin(h, ar, ST_SCORES, st);
-  SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, so.M, kk, p->compute, scores, p->correct_frac, st, colmax));
+  SLSO_TRY(run_scores(h, ar, X, n, d, ldx, xdt, M, kk, p->compute, scores, p->correct_frac, st, colmax));
   prof_end(h, ar, st);
   return SLSO_OK;
 }

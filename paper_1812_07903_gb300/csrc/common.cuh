@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libslso.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -528,6 +529,10 @@ bool use_gram(const slso_params* p);  // the Gram route is tried for this levera
 void info_from_state(const DevState& d, slso_info* info);
 slso_status leverage_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
                           int32_t xdt, const slso_params* p, void* scores, cudaStream_t st);
+// leverage_plan up to M (sketch and solve): M (d x kk) and the FP8 column maxima (or NULL).
+slso_status leverage_solve(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx,
+                           int32_t xdt, const slso_params* p, cudaStream_t st, const double** M, int64_t* kk,
+                           const unsigned int** colmax);
 
 // Approximate left singular vectors U = X V_r Sigma_r^-1 of the sketched SVD (basis.cu).
 slso_status approx_u_plan(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
@@ -543,9 +548,38 @@ slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t
                          bool* used);
 // score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
 // colmax_pre (FP8 only, optional): the column maxima of |X| already formed by the sketch pass.
+// One job of a grouped score launch (the serving path): the tensor maps of its X and of its B
+// pieces, its rows, scores and device status, its K-blocks, its first global work item (before
+// score_group_launch numbers the items: its count of work items), its JL width and form.
+struct alignas(64) ScoreGroupJob {
+  CUtensorMap tmX, tmBh, tmB1, tmB2;
+  int64_t n;
+  float* scores;
+  DevState* state;
+  int KB, work0, N, hyb;
+};
+constexpr int kMaxScoreGroup = 8;
+
+// With group != nullptr, a float32 score product that takes the two-tile tensor-memory kernel is
+// prepared exactly as for its own launch (same scratch, same B pieces) and described in *group
+// instead of launched.
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
-                          cudaStream_t st, const unsigned int* colmax_pre = nullptr);
+                          cudaStream_t st, const unsigned int* colmax_pre = nullptr,
+                          ScoreGroupJob* group = nullptr);
+// Whether a leverage call's scores can join a grouped launch: float32 X and compute, k in
+// [1, 128], d <= 2048, 16-byte aligned rows, no correction pass, the default score form.
+bool score_group_eligible(const Handle& h, const void* X, int64_t d, int64_t ldx, int32_t xdt, int64_t k,
+                          int32_t compute, double correct_frac);
+// The scratch and preparation of scores_typed for such a call, with the product described in *job
+// (state: h.state); *sums receives the score-sum scratch that score_group_sum needs afterwards.
+slso_status score_group_add(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, const double* M,
+                            int64_t kk, float* scores, ScoreGroupJob* job, double** sums, cudaStream_t st);
+// One launch over the described jobs (all with the same N and form): work items numbered job by
+// job; the descriptors are copied from host (pinned, kept until the launch has run) to device.
+slso_status score_group_launch(Handle& h, ScoreGroupJob* host, ScoreGroupJob* dev, int njobs, cudaStream_t st);
+// The score sum of one grouped job (into h.state), as the one-job path forms it.
+slso_status score_group_sum(Handle& h, const float* scores, int64_t n, double* sums, cudaStream_t st);
 
 // Y = X M (M d x kk row-major float64) written to U (float32, row stride ldu) on the tensor cores
 // for float32 / bfloat16 X (score_tc.cu); *used = false when the SIMT kernel must run instead.

@@ -302,4 +302,18 @@ slso_status score_sum(Handle& h, Arena& ar, const void* scores, int32_t sdt, int
   return launch_score_sum<float>(h, static_cast<const float*>(scores), n, sums, st);
 }
 
+
+slso_status score_group_add(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, const double* M,
+                            int64_t kk, float* scores, ScoreGroupJob* job, double** sums, cudaStream_t st) {
+  // scores_typed's scratch, in its order: the score-sum blocks, then the tensor-core product's
+  *sums = ar.take<double>(kSumBlocks);
+  bool used = false;
+  SLSO_TRY(run_scores_tc(h, ar, X, n, d, ldx, SLSO_F32, M, kk, SLSO_F32, scores, &used, st, nullptr, job));
+  if (!ar.measure() && !used) return fail(SLSO_ERR_SHAPE, "internal: grouped scores need the tensor-core product");
+  return SLSO_OK;
+}
+
+slso_status score_group_sum(Handle& h, const float* scores, int64_t n, double* sums, cudaStream_t st) {
+  return launch_score_sum<float>(h, scores, n, sums, st);
+}
 }  // namespace slso

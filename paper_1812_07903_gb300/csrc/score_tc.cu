@@ -633,12 +633,12 @@ struct LayoutTm {
 constexpr int kMaxStagesTm = 4;
 constexpr uint32_t kXtTm = kBM * 16 * 4;  // one 128-row x 16-float tile
 
-template <bool HYB, int T>
+template <bool HYB, int T, bool GROUP>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBh,
                     const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
                     const LayoutTm L, int64_t n, int nwork, float* __restrict__ scores,
-                    DevState* __restrict__ state) {
+                    DevState* __restrict__ state, const ScoreGroupJob* __restrict__ jobs, int njobs) {
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
@@ -651,6 +651,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_abort;
   const volatile int* abort_flag = &s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // GROUP: work item w belongs to the job j with jobs[j].work0 <= w < jobs[j + 1].work0 and is that
+  // job's item w - work0; every item is computed exactly as the one-job launch computes it
+  auto job_of = [&](int w, int& lw) -> int {
+    if (!GROUP) {
+      lw = w;
+      return 0;
+    }
+    int j = 0;
+    while (j + 1 < njobs && w >= jobs[j + 1].work0) ++j;
+    lw = w - jobs[j].work0;
+    return j;
+  };
+  auto kb_of = [&](int j) { return GROUP ? jobs[j].KB : L.KB; };
+  auto abort_all = [&](int code) {
+    if (!GROUP) {
+      atomicExch(&state->timeout, code);
+      return;
+    }
+    for (int j = 0; j < njobs; ++j) atomicExch(&jobs[j].state->timeout, code);
+  };
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -673,28 +693,41 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == kWarpProducer) {
     if (lane == 0) {
+      if (GROUP)  // the jobs' tensor maps were written to global memory before the launch
+        for (int j = 0; j < njobs; ++j) {
+          const CUtensorMap* maps[4] = {&jobs[j].tmX, &jobs[j].tmBh, &jobs[j].tmB1, &jobs[j].tmB2};
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps[m]) : "memory");
+        }
       int it = 0;
       bool ok = true;
       const uint32_t tx = T * kXtTm + L.bh_bytes + (HYB ? 2u : 1u) * L.bx_bytes;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-        const int y0 = w * T * kBM;
-        for (int kb = 0; kb < L.KB; ++kb, ++it) {
+        int lw;
+        const int j = job_of(w, lw);
+        const int y0 = lw * T * kBM, KB = kb_of(j);
+        const CUtensorMap* mX = GROUP ? &jobs[j].tmX : &tmX;
+        const CUtensorMap* mBh = GROUP ? &jobs[j].tmBh : &tmBh;
+        const CUtensorMap* mB1 = GROUP ? &jobs[j].tmB1 : &tmB1;
+        const CUtensorMap* mB2 = GROUP ? &jobs[j].tmB2 : &tmB2;
+        for (int kb = 0; kb < KB; ++kb, ++it) {
           const int st = it % L.S;
           if (!mbar_wait(&empty[st], ((it / L.S) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
           unsigned char* stage = smem + static_cast<uint32_t>(st) * L.stage_bytes;
           const int x = kb * 16;
           mbar_arrive_expect_tx(&full[st], tx);
 #pragma unroll
-          for (int u = 0; u < T; ++u) tma_load_2d(stage + u * kXtTm, &tmX, &full[st], x, y0 + u * kBM);
+          for (int u = 0; u < T; ++u) tma_load_2d(stage + u * kXtTm, mX, &full[st], x, y0 + u * kBM);
           unsigned char* b = stage + T * kXtTm;
-          tma_load_2d(b, &tmBh, &full[st], x, 0);
-          tma_load_2d(b + L.bh_bytes, &tmB1, &full[st], x, 0);
-          if (HYB) tma_load_2d(b + L.bh_bytes + L.bx_bytes, &tmB2, &full[st], x, 0);
+          tma_load_2d(b, mBh, &full[st], x, 0);
+          tma_load_2d(b + L.bh_bytes, mB1, &full[st], x, 0);
+          if (HYB) tma_load_2d(b + L.bh_bytes + L.bx_bytes, mB2, &full[st], x, 0);
         }
       }
       if (!ok) {
         atomicExch(&s_abort, 1);
-        atomicExch(&state->timeout, 3);
+        abort_all(3);
         for (int j = (it > L.S ? it - L.S : 0); j < it; ++j)  // let issued copies land (bounded)
           mbar_wait(&full[j % L.S], (j / L.S) & 1u, nullptr, 50000000ull);
       }
@@ -707,7 +740,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       uint32_t dbase = 0;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-        for (int kb = 0, kc = 0; kb < L.KB; ++kb, ++it) {  // kc: K-block within its chunk
+        int lw;
+        const int KB = kb_of(job_of(w, lw));
+        for (int kb = 0, kc = 0; kb < KB; ++kb, ++it) {  // kc: K-block within its chunk
           if (kc == 0) {                 // a fresh accumulator set for this chunk
             const int ab = cc % L.nbuf;
             if (!mbar_wait(&acc_empty[ab], ((cc / L.nbuf) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -742,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           mma_commit(&empty[st]);
-          if (++kc == (T == 1 ? L.chunk : L.KB) || kb == L.KB - 1) {  // the chunk is summed
+          if (++kc == (T == 1 ? L.chunk : KB) || kb == KB - 1) {  // the chunk is summed
             mma_commit(&acc_full[cc % L.nbuf]);
             ++cc;
             kc = 0;
@@ -751,7 +786,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) {
         atomicExch(&s_abort, 1);
-        atomicExch(&state->timeout, 3);
+        abort_all(3);
       }
       // all MMAs issued by this thread have completed before TMEM is released
       if (it > 0) mbar_wait(&empty[(it - 1) % L.S], ((it - 1) / L.S) & 1u, nullptr, 50000000ull);
@@ -764,7 +799,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     int it = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
-      for (int kb = 0; kb < L.KB; ++kb, ++it) {
+      int lw;
+      const int KB = kb_of(job_of(w, lw));
+      for (int kb = 0; kb < KB; ++kb, ++it) {
         const int st = it % L.S;
         // every lane acquires the TMA's bytes (the stage, and with it its TMEM slot, was freed by
         // the MMAs before the producer refilled it); the outcome is made warp-uniform (tcgen05.st
@@ -810,7 +847,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (!ok && lane == 0) {
       atomicExch(&s_abort, 1);
-      atomicExch(&state->timeout, 3);
+      abort_all(3);
     }
   } else {  // warps 0-3: epilogue; warp w reads TMEM lanes 32w..32w+31 = tile rows 32w..32w+31
     int cc = 0;
@@ -861,14 +898,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         if (lane == 0) {
           atomicExch(&s_abort, 1);
-          atomicExch(&state->timeout, 3);
+          abort_all(3);
         }
         break;
       }
+      int lw;
+      const int j = job_of(w, lw);
+      const int64_t nj = GROUP ? jobs[j].n : n;
+      float* out = GROUP ? jobs[j].scores : scores;
 #pragma unroll
       for (int u = 0; u < T; ++u) {
-        const int64_t row = (static_cast<int64_t>(w) * T + u) * kBM + warp * 32 + lane;
-        if (row < n) scores[row] = sum[u];
+        const int64_t row = (static_cast<int64_t>(lw) * T + u) * kBM + warp * 32 + lane;
+        if (row < nj) out[row] = sum[u];
       }
     }
   }
@@ -1029,7 +1070,7 @@ __global__ void prep_b_fp8_kernel(const double* __restrict__ M, int64_t d, int64
 // take the SIMT kernel instead (k > 256, unaligned X, or an unsupported dtype pair).
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                           const double* M, int64_t kk, int32_t compute, float* scores, bool* used,
-                          cudaStream_t st, const unsigned int* colmax_pre) {
+                          cudaStream_t st, const unsigned int* colmax_pre, ScoreGroupJob* group) {
   *used = false;
   int mode = -1;
   if (xdt == SLSO_F32 && compute == SLSO_F32) mode = MODE_TF32X3;
@@ -1084,6 +1125,7 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   ok = make_map(&mX, xdt_map, X, d, n, ldx * esz, static_cast<uint32_t>(L.box_cols), kBM);
   // the shared-memory form sums K in one accumulator: rows longer than 2048 take the chunked form
   const bool tm = mode == MODE_TF32X3 && L.N <= 128 && (h.score_form != SLSO_SCORE_FORM_TF32X3_SMEM || d > 2048);
+  if (group && !tm) return fail(SLSO_ERR_SHAPE, "internal: grouped scores need the tensor-memory form");
   const bool hyb = tm && h.score_form == SLSO_SCORE_FORM_MIXED;
   if (mode == MODE_TF32X3) {
     if (!hyb) {  // the mixed form prepares its own pieces below
@@ -1174,15 +1216,30 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     }
     if (!okt) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
     const int nwork = (ntiles + tiles - 1) / tiles;
+    if (group) {  // described for a grouped launch instead of launched
+      if (tiles != 2) return fail(SLSO_ERR_SHAPE, "internal: grouped scores need rows of at most 2048");
+      group->tmX = mXt;
+      group->tmBh = mBh;
+      group->tmB1 = mB1t;
+      group->tmB2 = mB2t;
+      group->n = n;
+      group->scores = scores;
+      group->state = h.state;
+      group->KB = T.KB;
+      group->work0 = nwork;  // the job's work items until score_group_launch numbers them
+      group->N = L.N;
+      group->hyb = hyb ? 1 : 0;
+      return SLSO_OK;
+    }
     const int gridt = std::min(nwork, h.num_sms);
     auto launch = [&](auto kern) -> slso_status {
       SLSO_TRY(raise_smem_limit(kern, T.smem_bytes));
-      kern<<<gridt, kThreads, T.smem_bytes, st>>>(mXt, mBh, mB1t, mB2t, T, n, nwork, scores, h.state);
+      kern<<<gridt, kThreads, T.smem_bytes, st>>>(mXt, mBh, mB1t, mB2t, T, n, nwork, scores, h.state, nullptr, 0);
       SLSO_CHECK_LAUNCH();
       return SLSO_OK;
     };
-    if (hyb) return tiles == 2 ? launch(score_tm_kernel<true, 2>) : launch(score_tm_kernel<true, 1>);
-    return tiles == 2 ? launch(score_tm_kernel<false, 2>) : launch(score_tm_kernel<false, 1>);
+    if (hyb) return tiles == 2 ? launch(score_tm_kernel<true, 2, false>) : launch(score_tm_kernel<true, 1, false>);
+    return tiles == 2 ? launch(score_tm_kernel<false, 2, false>) : launch(score_tm_kernel<false, 1, false>);
   }
   if (mode == MODE_TF32X3 && L.N <= 128) {
     // two 128-row tiles per work item share each B K-block
@@ -1283,6 +1340,55 @@ slso_status run_product_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64
                                                         nullptr, U, ldu, kk, h.state);
   SLSO_CHECK_LAUNCH();
   return SLSO_OK;
+}
+
+
+bool score_group_eligible(const Handle& h, const void* X, int64_t d, int64_t ldx, int32_t xdt, int64_t k,
+                          int32_t compute, double correct_frac) {
+  return xdt == SLSO_F32 && compute == SLSO_F32 && k >= 1 && k <= 128 && d >= 1 && d <= 2048 &&
+         correct_frac == 0.0 && h.score_form == SLSO_SCORE_FORM_MIXED && X != nullptr &&
+         reinterpret_cast<uintptr_t>(X) % 16 == 0 && (ldx * 4) % 16 == 0 && encode_fn() != nullptr;
+}
+
+slso_status score_group_launch(Handle& h, ScoreGroupJob* host, ScoreGroupJob* dev, int njobs, cudaStream_t st) {
+  if (njobs < 1 || njobs > kMaxScoreGroup) return fail(SLSO_ERR_INVALID_ARG, "grouped scores: %d jobs", njobs);
+  const int N = host[0].N;
+  const bool hyb = host[0].hyb != 0;
+  int total = 0;
+  for (int j = 0; j < njobs; ++j) {
+    if (host[j].N != N || (host[j].hyb != 0) != hyb)
+      return fail(SLSO_ERR_INVALID_ARG, "grouped scores need one JL width and one form");
+    const int items = host[j].work0;  // run_scores_tc left the job's work items there
+    host[j].work0 = total;
+    total += items;
+  }
+  if (total == 0) return SLSO_OK;
+  // the same layout as the one-job two-tile launch (it depends on N and the form only)
+  LayoutTm T{};
+  T.N = N;
+  T.KB = 0;  // per job
+  T.chunk = 0;
+  T.nchunk = 1;
+  T.bh_bytes = static_cast<uint32_t>(N) * 64u;
+  T.bx_bytes = hyb ? static_cast<uint32_t>(N) * 32u : T.bh_bytes;
+  T.stage_bytes = 2 * kXtTm + T.bh_bytes + (hyb ? 2u : 1u) * T.bx_bytes;
+  T.S = kMaxStagesTm;
+  T.nbuf = (2 * 2 * N + T.S * 64 <= 512) ? 2 : 1;
+  T.run_col = 0;
+  T.abase = static_cast<uint32_t>(T.nbuf * 2 * N);
+  T.tmem_cols = 512;
+  T.bar_off = static_cast<uint32_t>(T.S) * T.stage_bytes;
+  T.smem_bytes = T.bar_off + (3 * kMaxStagesTm + 4) * 8 + 8 + 1024;
+  SLSO_CHECK_CUDA(cudaMemcpyAsync(dev, host, sizeof(ScoreGroupJob) * njobs, cudaMemcpyHostToDevice, st));
+  const int grid = std::min(total, h.num_sms);
+  auto launch = [&](auto kern) -> slso_status {
+    SLSO_TRY(raise_smem_limit(kern, T.smem_bytes));
+    kern<<<grid, kThreads, T.smem_bytes, st>>>(host[0].tmX, host[0].tmBh, host[0].tmB1, host[0].tmB2, T, 0, total,
+                                                nullptr, host[0].state, dev, njobs);
+    SLSO_CHECK_LAUNCH();
+    return SLSO_OK;
+  };
+  return hyb ? launch(score_tm_kernel<true, 2, true>) : launch(score_tm_kernel<false, 2, true>);
 }
 
 }  // namespace slso

@@ -64,7 +64,17 @@ struct Slot {
   Job* job = nullptr;
   void* ws = nullptr;
   std::vector<GraphEntry> graphs;
+  // a grouped launch: the slot's jobs (job == group[0]), each with its own device status words,
+  // scratch, and descriptor of its score product (pinned on the host, copied to the device)
+  std::vector<Job*> group;
+  DevState* gstate = nullptr;
+  DevState* gstate_host = nullptr;
+  ScoreGroupJob* gdesc_host = nullptr;
+  ScoreGroupJob* gdesc_dev = nullptr;
+  void* gws[kMaxScoreGroup] = {};
 };
+
+constexpr int64_t kGroupMaxRows = int64_t(1) << 17;  // jobs of at most this many rows are grouped
 
 constexpr size_t kGraphsPerSlot = 8;
 constexpr size_t kSeenShapes = 256;
@@ -81,6 +91,7 @@ struct Server {
   int64_t n_submitted = 0, n_admitted = 0, n_completed = 0;
   // graph statistics: new instantiations, in-place updates, direct (uncaptured) leverage runs
   int64_t n_graph_new = 0, n_graph_update = 0, n_graph_direct = 0;
+  int64_t n_group_launches = 0, n_grouped_jobs = 0;  // grouped score launches and the jobs they ran
   size_t graph_bytes = 0;  // workspaces held by cached graphs (all slots)
   uint64_t use_clock = 0;
   bool capture_ok = true;  // cleared if the CUDA driver refuses to capture the launches
@@ -272,6 +283,106 @@ void start_job(Server& srv, Slot& sl, Job* j) {
   cudaEventRecord(sl.done, sl.st);
 }
 
+// A leverage job whose scores can share a grouped launch: float32 X and compute, k <= 128,
+// d <= 2048, at most kGroupMaxRows rows, no correction pass.  Jobs group with those of the same
+// JL width (rounded up to 32).
+bool group_eligible(const Slot& sl, const Job* j) {
+  const slso_job& d = j->desc;
+  return d.job == SLSO_JOB_LEVERAGE && d.n <= kGroupMaxRows &&
+         score_group_eligible(sl.h, d.X, d.d, d.ldx, d.xdt, d.params.k, d.params.compute, d.params.correct_frac);
+}
+int64_t group_width(const Job* j) { return (j->desc.params.k + 31) / 32; }
+
+// Enqueue a group's work on its slot (worker thread, lock not held): every job's sketch and solve
+// with its own status words and scratch, one grouped score launch over all of them, then every
+// job's score sum and order.  A job that fails before the launch is left out of it.
+void start_group(Server& srv, Slot& sl) {
+  const int m = static_cast<int>(sl.group.size());
+  std::vector<Arena> ars;
+  std::vector<double*> sums(m, nullptr);
+  std::vector<int> in(m, 0);
+  ars.reserve(m);
+  int nd = 0;
+  for (int i = 0; i < m; ++i) {
+    Job* j = sl.group[i];
+    const slso_job& d = j->desc;
+    Handle hj = sl.h;
+    hj.state = sl.gstate + i;
+    hj.state_host = sl.gstate_host + i;
+    sl.gws[i] = nullptr;
+    slso_status stt = SLSO_OK;
+    if (cudaMemsetAsync(hj.state, 0, sizeof(DevState), sl.st) != cudaSuccess) stt = SLSO_ERR_CUDA;
+    if (stt == SLSO_OK && cudaMallocAsync(&sl.gws[i], j->bytes + 256, sl.st) != cudaSuccess) {
+      cudaGetLastError();
+      sl.gws[i] = nullptr;
+      stt = SLSO_ERR_OOM;
+    }
+    ars.emplace_back(static_cast<char*>(sl.gws[i]), j->bytes + 256, false);
+    const double* M = nullptr;
+    int64_t kk = 0;
+    const unsigned int* colmax = nullptr;
+    if (stt == SLSO_OK) stt = leverage_solve(hj, ars[i], d.X, d.n, d.d, d.ldx, d.xdt, &d.params, sl.st, &M, &kk, &colmax);
+    if (stt == SLSO_OK)
+      stt = score_group_add(hj, ars[i], d.X, d.n, d.d, d.ldx, M, kk, static_cast<float*>(d.scores),
+                            &sl.gdesc_host[nd], &sums[i], sl.st);
+    j->status = stt;
+    if (stt == SLSO_OK) {
+      in[i] = 1;
+      ++nd;
+    }
+  }
+  if (nd > 0 && score_group_launch(sl.h, sl.gdesc_host, sl.gdesc_dev, nd, sl.st) != SLSO_OK)
+    for (int i = 0; i < m; ++i)
+      if (in[i]) {
+        sl.group[i]->status = SLSO_ERR_CUDA;
+        in[i] = 0;
+      }
+  for (int i = 0; i < m; ++i) {
+    if (!in[i]) continue;
+    Job* j = sl.group[i];
+    const slso_job& d = j->desc;
+    Handle hj = sl.h;
+    hj.state = sl.gstate + i;
+    hj.state_host = sl.gstate_host + i;
+    slso_status stt = score_group_sum(hj, static_cast<const float*>(d.scores), d.n, sums[i], sl.st);
+    if (stt == SLSO_OK && d.order) stt = order_scores(hj, ars[i], d.scores, SLSO_F32, d.n, d.order, sl.st);
+    j->status = stt;
+  }
+  for (int i = 0; i < m; ++i)
+    if (sl.gws[i]) cudaFreeAsync(sl.gws[i], sl.st);
+  cudaEventRecord(sl.done, sl.st);
+  std::lock_guard<std::mutex> lk(srv.mu);
+  ++srv.n_group_launches;
+  srv.n_grouped_jobs += nd;
+}
+
+// Collect a finished group (worker thread, lock held): every job's status words.
+void finish_group(Server& s, Slot& sl) {
+  const int m = static_cast<int>(sl.group.size());
+  const bool copied =
+      cudaMemcpy(sl.gstate_host, sl.gstate, sizeof(DevState) * m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  for (int i = 0; i < m; ++i) {
+    Job* j = sl.group[i];
+    if (j->status == SLSO_OK) {
+      if (!copied) {
+        j->status = SLSO_ERR_CUDA;
+      } else {
+        const DevState& d = sl.gstate_host[i];
+        info_from_state(d, &j->info);
+        if (d.timeout) j->status = SLSO_ERR_TIMEOUT;
+        else if (d.nonfinite) j->status = SLSO_ERR_NONFINITE;
+      }
+    }
+    j->t_done = now_ms();
+    j->done = true;
+    s.in_use -= j->bytes;
+    ++s.n_completed;
+  }
+  sl.group.clear();
+  sl.job = nullptr;
+  s.cv_done.notify_all();
+}
+
 // Collect a finished job (worker thread, lock held).
 void finish_job(Server& s, Slot& sl) {
   Job* j = sl.job;
@@ -302,8 +413,12 @@ void worker_main(Server* s) {
       if (!sl.job) continue;
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
-      if (q != cudaSuccess) sl.job->status = SLSO_ERR_CUDA;
-      finish_job(*s, sl);
+      if (q != cudaSuccess) {
+        sl.job->status = SLSO_ERR_CUDA;
+        for (Job* g : sl.group) g->status = SLSO_ERR_CUDA;
+      }
+      if (sl.group.empty()) finish_job(*s, sl);
+      else finish_group(*s, sl);
       progressed = true;
     }
     while (!s->queue.empty()) {
@@ -315,6 +430,33 @@ void worker_main(Server* s) {
           break;
         }
       if (!free_slot || s->in_use + j->bytes > s->budget) break;  // FIFO: no overtaking
+      // consecutive queued jobs that can share one grouped score launch go to this slot together
+      if (free_slot->gstate && group_eligible(*free_slot, j)) {
+        size_t bytes = j->bytes;
+        size_t cnt = 1;
+        while (cnt < s->queue.size() && cnt < static_cast<size_t>(kMaxScoreGroup)) {
+          Job* nx = s->queue[cnt];
+          if (!group_eligible(*free_slot, nx) || group_width(nx) != group_width(j) ||
+              s->in_use + bytes + nx->bytes > s->budget)
+            break;
+          bytes += nx->bytes;
+          ++cnt;
+        }
+        if (cnt >= 2) {
+          free_slot->group.assign(s->queue.begin(), s->queue.begin() + static_cast<std::ptrdiff_t>(cnt));
+          for (size_t c = 0; c < cnt; ++c) s->queue.pop_front();
+          const double t = now_ms();
+          for (Job* g : free_slot->group) g->t_admit = t;
+          s->in_use += bytes;
+          s->n_admitted += static_cast<int64_t>(cnt);
+          free_slot->job = j;
+          lk.unlock();
+          start_group(*s, *free_slot);
+          lk.lock();
+          progressed = true;
+          continue;
+        }
+      }
       s->queue.pop_front();
       s->in_use += j->bytes;
       j->t_admit = now_ms();
@@ -360,9 +502,20 @@ extern "C" slso_status slso_server_create(slso_server** out, int device, int nsl
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.h.state), sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&sl.h.state_host), sizeof(DevState));
     if (e == cudaSuccess) e = side_stream_create(sl.h);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&sl.gstate), sizeof(DevState) * kMaxScoreGroup);
+    if (e == cudaSuccess)
+      e = cudaMallocHost(reinterpret_cast<void**>(&sl.gstate_host), sizeof(DevState) * kMaxScoreGroup);
+    if (e == cudaSuccess)
+      e = cudaMallocHost(reinterpret_cast<void**>(&sl.gdesc_host), sizeof(ScoreGroupJob) * kMaxScoreGroup);
+    if (e == cudaSuccess)
+      e = cudaMalloc(reinterpret_cast<void**>(&sl.gdesc_dev), sizeof(ScoreGroupJob) * kMaxScoreGroup);
     if (e != cudaSuccess) {
       for (Slot& t : s->slots) {
         side_stream_release(t.h);
+        if (t.gstate) cudaFree(t.gstate);
+        if (t.gstate_host) cudaFreeHost(t.gstate_host);
+        if (t.gdesc_host) cudaFreeHost(t.gdesc_host);
+        if (t.gdesc_dev) cudaFree(t.gdesc_dev);
         if (t.st) cudaStreamDestroy(t.st);
         if (t.done) cudaEventDestroy(t.done);
         if (t.h.state) cudaFree(t.h.state);
@@ -401,6 +554,10 @@ extern "C" slso_status slso_server_destroy(slso_server* srv) {
     }
     sl.graphs.clear();
     side_stream_release(sl.h);
+    if (sl.gstate) cudaFree(sl.gstate);
+    if (sl.gstate_host) cudaFreeHost(sl.gstate_host);
+    if (sl.gdesc_host) cudaFreeHost(sl.gdesc_host);
+    if (sl.gdesc_dev) cudaFree(sl.gdesc_dev);
     cudaStreamDestroy(sl.st);
     cudaEventDestroy(sl.done);
     cudaFree(sl.h.state);
@@ -492,7 +649,8 @@ extern "C" slso_status slso_server_counters(slso_server* srv, int64_t* counters,
   Server* s = reinterpret_cast<Server*>(srv);
   std::lock_guard<std::mutex> lk(s->mu);
   const int64_t v[] = {s->n_submitted, s->n_admitted, s->n_completed, static_cast<int64_t>(s->queue.size()),
-                       static_cast<int64_t>(s->in_use), s->n_graph_new, s->n_graph_update, s->n_graph_direct};
+                       static_cast<int64_t>(s->in_use), s->n_graph_new, s->n_graph_update, s->n_graph_direct,
+                       s->n_group_launches, s->n_grouped_jobs};
   for (int32_t i = 0; i < count; ++i) counters[i] = i < static_cast<int32_t>(sizeof(v) / sizeof(v[0])) ? v[i] : 0;
   return SLSO_OK;
 }

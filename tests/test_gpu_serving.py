@@ -95,3 +95,32 @@ def test_repeated_shapes_replay_captured_graphs():
     c = srv.counters()
     srv.close()
     assert c["direct"] == len(shapes) and c["graphs_new"] == len(shapes) and c["graphs_updated"] == len(shapes)
+
+
+def test_queued_small_jobs_share_a_grouped_launch():
+    """Small float32 jobs queued behind a long one are admitted together and scored by one grouped
+    tensor-core launch (the counters show it); every result equals its direct call bit for bit."""
+    blocker = inputs.gaussian_mixture(1 << 20, 256, seed=1, device="cuda")
+    small = []
+    for j in range(6):
+        n = [5000, 20000, 777, 65536, 12345, 3000][j]
+        d = [64, 100, 36, 128, 64, 96][j]
+        kind = ["countsketch", "srht", "gaussian"][j % 3]
+        X = inputs.gaussian_mixture(n, d, seed=200 + j, device="cuda")
+        small.append(dict(X=X, kind=kind, s=inputs.serving_sketch_rows(n, d, kind), seed_S=40 + j, seed_Pi=50 + j))
+    want = []
+    for jb in small:
+        sc, info = api.leverage(jb["X"], jb["kind"], jb["s"], 64, jb["seed_S"], jb["seed_Pi"], compute="f32")
+        want.append((sc.clone(), api.order(sc).clone(), info["rank"]))
+    torch.cuda.synchronize()
+    srv = api.Server(slots=1, mem_budget_bytes=4 << 30)
+    tb = srv.submit_leverage(blocker, "countsketch", 8192, 64, 3, 4)
+    tickets = [srv.submit_leverage(jb["X"], jb["kind"], jb["s"], 64, jb["seed_S"], jb["seed_Pi"]) for jb in small]
+    assert srv.poll(tb)[0] == 0
+    for t, (sc0, o0, r0) in zip(tickets, want):
+        st, info, times, (sc, o) = srv.poll(t)
+        assert st == 0 and info["rank"] == r0
+        assert torch.equal(sc, sc0) and torch.equal(o, o0)
+    c = srv.counters()
+    srv.close()
+    assert c["group_launches"] >= 1 and c["grouped_jobs"] >= 2
