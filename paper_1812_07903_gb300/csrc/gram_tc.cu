@@ -69,9 +69,16 @@ constexpr int kTimeoutIdG = 6;
 constexpr int kSplitBalanceSms = 152;  // GB300's SM count: fixed, so the plan does not depend on the device
 constexpr int64_t kMaxRowsTc = int64_t(1) << 20;  // keeps |T_hi|, |T_lo| < 2^53
 
-// The digit pairs (p, q), p + q <= 7, by order; the first pair of each order starts its accumulator.
-__constant__ unsigned char c_pair_p[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2,
-                                               3, 4, 5, 0, 1, 2, 3, 4, 5, 6, 0, 1, 2, 3, 4, 5, 6, 7};
+// The digit pairs (p, q), p + q <= 7, by order t = p + q: pair index pr = t (t + 1) / 2 + p; the
+// first pair of each order starts its accumulator.  Compile-time functions of the (unrolled) pair
+// index, so that the MMA issuer spends no instructions on them.
+__host__ __device__ constexpr int pair_order(int pr) {
+  int t = 0;
+  while ((t + 1) * (t + 2) / 2 <= pr) ++t;
+  return t;
+}
+__host__ __device__ constexpr int pair_p(int pr) { return pr - pair_order(pr) * (pair_order(pr) + 1) / 2; }
+static_assert(pair_order(35) == 7 && pair_p(35) == 7 && pair_p(6) == 0 && pair_order(6) == 3, "pair table");
 
 // rint(a 2^(55 - e)) for |a| < 2^e, from a's bits (integer operations only: the float64 pipe is
 // narrow on this part).  Round half away from zero; non-finite a sets bad.
@@ -253,19 +260,20 @@ __global__ void __launch_bounds__(kThreadsG, 1)
           }
           tc_fence_after();
           unsigned char* stage = smem + static_cast<uint32_t>(st) * kStageBytesG;
+          // the slices' descriptors differ from the stage's first ones only in the start address
+          // field (address >> 4, bits 0-13; every address here is below 2^18, so no carry)
+          const uint64_t a0 = sdesc_sw32(stage), b0 = sdesc_sw32(stage + kSlices * kASliceBytes);
 #pragma unroll
           for (int ks = 0; ks < kKBg / 16; ++ks) {
             const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
 #pragma unroll
             for (int pr = 0; pr < kPairs; ++pr) {
-              // pairs by order t: indices t (t + 1) / 2 .. + t, p ascending, q = t - p
-              const int ord = pr < 1 ? 0 : pr < 3 ? 1 : pr < 6 ? 2 : pr < 10 ? 3 : pr < 15 ? 4 : pr < 21 ? 5 : pr < 28 ? 6 : 7;
-              const int p = c_pair_p[pr], qq = ord - p;
+              const int ord = pair_order(pr), p = pair_p(pr), qq = ord - p;
               // the first pair of each order starts its accumulator in the window's first K-step
-              const bool first = pr == ord * (ord + 1) / 2;
+              const bool first = p == 0;
               const uint32_t acc = (kw | ks) != 0 || !first;
-              const uint64_t a = sdesc_sw32(stage + p * kASliceBytes) + o;
-              const uint64_t bd = sdesc_sw32(stage + kSlices * kASliceBytes + qq * kBSliceBytes) + o;
+              const uint64_t a = a0 + static_cast<uint64_t>(p * (kASliceBytes >> 4)) + o;
+              const uint64_t bd = b0 + static_cast<uint64_t>(qq * (kBSliceBytes >> 4)) + o;
               mma_f16(tmem_base + static_cast<uint32_t>(ord * kBNg), a, bd, id, acc);
             }
           }
