@@ -546,12 +546,10 @@ slso_status sample_order(Handle& h, Arena& ar, const void* scores, int32_t sdt, 
 slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                          int64_t s, uint64_t seed, int64_t row0, bool accumulate, double* SX, cudaStream_t st,
                          bool* used);
-// score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
-// colmax_pre (FP8 only, optional): the column maxima of |X| already formed by the sketch pass.
 // One job of a grouped score launch (the serving path): the tensor maps of its X and of its B
 // pieces, its rows, scores and device status, its K-blocks, its first global work item (before
 // score_group_launch numbers the items: its count of work items), its JL width and form.
-struct alignas(64) ScoreGroupJob {
+struct ScoreGroupJob {
   CUtensorMap tmX, tmBh, tmB1, tmB2;
   int64_t n;
   float* scores;
@@ -560,6 +558,8 @@ struct alignas(64) ScoreGroupJob {
 };
 constexpr int kMaxScoreGroup = 8;
 
+// score_tc.cu: tensor-core scores; *used = false when the shapes need the SIMT kernel
+// colmax_pre (FP8 only, optional): the column maxima of |X| already formed by the sketch pass.
 // With group != nullptr, a float32 score product that takes the two-tile tensor-memory kernel is
 // prepared exactly as for its own launch (same scratch, same B pieces) and described in *group
 // instead of launched.

@@ -123,19 +123,30 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restric
   const int e = j < d ? cexp[j] : 0;
   for (int rr = ty; rr < 32; rr += 8) {
     const int64_t i = i0 + rr;
-    long long r = 0;
-    if (j < d && i < s) r = fixed55(SX[i * d + j], e, bad);
+    long long F = 0;
+    if (j < d && i < s) F = fixed55(SX[i * d + j], e, bad);
+    // balanced base-128 digits of F = sum_p d_p 2^(49 - 7p), d_7..d_1 in [-64, 63], |d_0| <= 64,
+    // from the bottom in 32-bit arithmetic: the low 28 bits give d_7..d_4 and a carry into the
+    // high part, which gives d_3..d_0
+    int dg[kSlices];
+    int x = static_cast<int>(static_cast<unsigned int>(F) & 0x0FFFFFFFu);
+#pragma unroll
+    for (int p = kSlices - 1; p >= 4; --p) {
+      dg[p] = ((x + 64) & 127) - 64;
+      x = (x - dg[p]) >> 7;  // exact division; the carry out of the last step is 0 or 1
+    }
+    int y = static_cast<int>(F >> 28) + x;  // |y| < 2^27 + 1
+#pragma unroll
+    for (int p = 3; p >= 1; --p) {
+      dg[p] = ((y + 64) & 127) - 64;
+      y = (y - dg[p]) >> 7;
+    }
+    dg[0] = y;  // |F| < 2^55 keeps it within [-64, 64]
 #pragma unroll
     for (int p = 0; p < kSlices; ++p) {
-      long long q = r;
-      if (p < kSlices - 1) {
-        const int w = 49 - 7 * p;
-        q = (r + (1ll << (w - 1))) >> w;
-        r -= q * (1ll << w);
-      }
       // E_p = d_p 2^(21 - 7p): exact in float32 and in bfloat16 (|d_p| <= 64)
       const float scale = __int_as_float((127 + 21 - 7 * p) << 23);  // 2^(21 - 7p)
-      tile[p][tx][rr] = __float2bfloat16_rn(static_cast<float>(q) * scale);
+      tile[p][tx][rr] = __float2bfloat16_rn(static_cast<float>(dg[p]) * scale);
     }
   }
   __syncthreads();

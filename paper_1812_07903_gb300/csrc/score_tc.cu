@@ -736,6 +736,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idt = idesc(FMT_TF32, FMT_TF32, kBM, static_cast<uint32_t>(L.N));
       const uint32_t idb = idesc(FMT_BF16, FMT_BF16, kBM, static_cast<uint32_t>(L.N));
+      // stage 0's B descriptors; a stage's differ only in the start address field (address >> 4,
+      // bits 0-13; shared memory is below 2^18 bytes, so no carry)
+      unsigned char* b_0 = smem + T * kXtTm;
+      const uint64_t bh_0 = sdesc_sw64(b_0), b1_0 = HYB ? sdesc_sw32(b_0 + L.bh_bytes) : sdesc_sw64(b_0 + L.bh_bytes);
+      const uint64_t b2_off = static_cast<uint64_t>(L.bx_bytes >> 4);
       int it = 0, cc = 0;  // K-blocks and accumulation chunks issued so far
       bool ok = true;
       uint32_t dbase = 0;
@@ -752,8 +757,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int st = it % L.S;
           if (!mbar_wait(&cvt[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
           tc_fence_after();
-          unsigned char* b = smem + static_cast<uint32_t>(st) * L.stage_bytes + T * kXtTm;
-          const uint64_t bh = sdesc_sw64(b);
+          const uint64_t soff = static_cast<uint64_t>((static_cast<uint32_t>(st) * L.stage_bytes) >> 4);
+          const uint64_t bh = bh_0 + soff, b1 = b1_0 + soff, b2 = b1 + b2_off;
           const uint32_t aslot = tmem_base + L.abase + static_cast<uint32_t>(st * 32 * T);
 #pragma unroll
           for (int u = 0; u < T; ++u) {
@@ -762,10 +767,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (HYB) {
               mma_tf32_ts(du, a, bh, idt, kc != 0);
               mma_tf32_ts(du, a + 8, bh + 2, idt, 1u);  // + 32 bytes along K
-              mma_f16_ts(du, a + 16, sdesc_sw32(b + L.bh_bytes), idb, 1u);                // bf16(Xlo) bf16(Mhi)
-              mma_f16_ts(du, a + 24, sdesc_sw32(b + L.bh_bytes + L.bx_bytes), idb, 1u);  // bf16(Xhi) bf16(Mlo)
+              mma_f16_ts(du, a + 16, b1, idb, 1u);  // bf16(Xlo) bf16(Mhi)
+              mma_f16_ts(du, a + 24, b2, idb, 1u);  // bf16(Xhi) bf16(Mlo)
             } else {
-              const uint64_t bl = sdesc_sw64(b + L.bh_bytes);
+              const uint64_t bl = b1;
 #pragma unroll
               for (int ks = 0; ks < 2; ++ks) {
                 const uint64_t o = static_cast<uint64_t>(ks * 2);
