@@ -39,6 +39,13 @@ struct ff {
   float h, l;
 };
 
+// x 2^k, the same correctly rounded value as ldexp(x, k), by one multiplication when 2^k is a
+// normal float64
+__device__ __forceinline__ double times_pow2(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+  return ldexp(x, k);
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
   for (int64_t e = gtid; e < dd; e += gstride) {
     const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
     if (j <= i) {
-      const double g = ldexp(L[e], -cexp[i] - cexp[j]);
+      const double g = times_pow2(L[e], -cexp[i] - cexp[j]);
       const float h = __double2float_rn(g);
       A[e] = make_float2(h, __double2float_rn(g - static_cast<double>(h)));
     }
@@ -589,17 +596,17 @@ __global__ void __launch_bounds__(kFThreads, 1)
     const int i = static_cast<int>(e / d), j = static_cast<int>(e % d);
     if (j <= i) {
       const float2 a = A[e];
-      L[e] = ldexp(static_cast<double>(a.x) + static_cast<double>(a.y), cexp[i]);
+      L[e] = times_pow2(static_cast<double>(a.x) + static_cast<double>(a.y), cexp[i]);
     }
     const float2 x = X[e];  // X'[i][j]: (R^-1)_ji at Rinv[i d + j]
-    Rinv[e] = j <= i ? ldexp(static_cast<double>(x.x) + static_cast<double>(x.y), -cexp[j]) : 0.0;
+    Rinv[e] = j <= i ? times_pow2(static_cast<double>(x.x) + static_cast<double>(x.y), -cexp[j]) : 0.0;
   }
   // M = R^-1 Pi = diag(2^-e) Out[:, :k] (float64) and Y'' = Out[:, k..k+3] (float-float)
   const int width = k_rhs + 4;
   for (int64_t e = gtid; e < static_cast<int64_t>(d) * width; e += gstride) {
     const int i = static_cast<int>(e / width), c = static_cast<int>(e % width);
     const float2 o = Out[e];
-    if (c < k_rhs) M[static_cast<int64_t>(i) * k_rhs + c] = ldexp(static_cast<double>(o.x) + static_cast<double>(o.y), -cexp[i]);
+    if (c < k_rhs) M[static_cast<int64_t>(i) * k_rhs + c] = times_pow2(static_cast<double>(o.x) + static_cast<double>(o.y), -cexp[i]);
     else Yff[i * 4 + (c - k_rhs)] = o;
   }
   if (k_rhs > 0 && blockIdx.x == 0 && threadIdx.x == 0) st->m_ready = 1;
@@ -616,17 +623,19 @@ __device__ __forceinline__ ff split_scaled(double a, int e) {
   const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a));
   const int ex = static_cast<int>((u >> 52) & 0x7FFu);
   if (ex == 0x7FF) return {CUDART_NAN_F, 0.f};
-  if (ex == 0) {  // zero or subnormal: the float64 path (rare)
+  const int E = ex - 1075 - e;  // |a 2^-e| = m 2^E, m in [2^52, 2^53)
+  if (ex == 0 || E < -126 || E + 29 > 127) {  // zero, subnormal or far below the column's maximum: the float64 path (rare)
     const double v = ldexp(a, -e);
     const float h = __double2float_rn(v);
     return {h, __double2float_rn(v - static_cast<double>(h))};
   }
-  const long long m = static_cast<long long>((u & ((1ull << 52) - 1)) | (1ull << 52));
-  const int E = ex - 1075 - e;  // |a 2^-e| = m 2^E
-  const long long hi = (m + (1ll << 28)) >> 29;
-  const long long lo = m - hi * (1ll << 29);
-  float fh = ldexpf(static_cast<float>(hi), E + 29);
-  float fl = ldexpf(static_cast<float>(lo), E);
+  // m = hi 2^29 + lo with hi = round(m / 2^29) (at most 2^24) and |lo| <= 2^28, in 32-bit integers;
+  // the powers of two are built from their bits (both in float32's normal range here)
+  const unsigned int rnd = static_cast<unsigned int>(u >> 28) & 1u;
+  const unsigned int hi = (static_cast<unsigned int>(u >> 29) & 0x7FFFFFu) + (1u << 23) + rnd;
+  const int lo = static_cast<int>(static_cast<unsigned int>(u) & 0x1FFFFFFFu) - static_cast<int>(rnd << 29);
+  float fh = static_cast<float>(hi) * __int_as_float((E + 29 + 127) << 23);
+  float fl = static_cast<float>(lo) * __int_as_float((E + 127) << 23);
   if (u >> 63) {
     fh = -fh;
     fl = -fl;
