@@ -696,7 +696,8 @@ __global__ void __launch_bounds__(256) probe_w_ff_kernel(const double* __restric
   }
 }
 
-// vpart[b][j][q] = sum over the rows r of chunk b of SX'[r, j] W[r, q] (float-float).
+// vpart[b][j][q] = sum over the rows r of chunk b of SX'[r, j] W[r, q] (float-float).  Grid: chunks
+// x column blocks of 256 (one column per thread).
 __global__ void __launch_bounds__(256) probe_v_ff_kernel(const double* __restrict__ SX, int64_t s, int d,
                                                          const int* __restrict__ cexp, const float2* __restrict__ Wff,
                                                          int64_t rows_per_chunk, float2* __restrict__ vpart,
@@ -704,7 +705,8 @@ __global__ void __launch_bounds__(256) probe_v_ff_kernel(const double* __restric
   if (*reinterpret_cast<const volatile int32_t*>(&st->gram_ok) == 0) return;
   const int64_t r0 = blockIdx.x * rows_per_chunk;
   const int64_t r1 = r0 + rows_per_chunk < s ? r0 + rows_per_chunk : s;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (j < d) {
     const int e = cexp[j];
     float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
     ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -812,7 +814,8 @@ slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, cons
   SLSO_CHECK_LAUNCH();
   const int64_t rpc = ceil_div(s, chunks);
   const unsigned vb = static_cast<unsigned>(ceil_div(s, rpc));
-  probe_v_ff_kernel<<<vb, 256, 0, st>>>(SX, s, d_i, cexp, Wff, rpc, vpart, h.state);
+  probe_v_ff_kernel<<<dim3(vb, static_cast<unsigned>(ceil_div(d, 256))), 256, 0, st>>>(SX, s, d_i, cexp, Wff, rpc,
+                                                                                       vpart, h.state);
   SLSO_CHECK_LAUNCH();
   probe_vsum_ff_kernel<<<static_cast<unsigned>(ceil_div(d * 4, 256)), 256, 0, st>>>(vpart, static_cast<int>(vb), d_i,
                                                                                     Vff, h.state);

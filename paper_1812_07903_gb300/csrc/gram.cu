@@ -59,10 +59,21 @@ __global__ void __launch_bounds__(256) gram_colmax_kernel(const double* __restri
                                                           unsigned long long* __restrict__ colmax) {
   const int64_t r0 = blockIdx.x * rows_per_block;
   const int64_t r1 = r0 + rows_per_block < s ? r0 + rows_per_block : s;
+  // |x| compared as the integer bits of a non-negative float64 (the same order as the values, with
+  // no float64 instruction: that pipe is narrow on this part); eight loads in flight per thread
+  constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    double m = 0.0;
-    for (int64_t r = r0; r < r1; ++r) m = fmax(m, fabs(SX[r * d + j]));
-    if (m > 0.0) atomicMax(colmax + j, static_cast<unsigned long long>(__double_as_longlong(m)));
+    unsigned long long m = 0;
+    int64_t r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = static_cast<unsigned long long>(__double_as_longlong(SX[(r + u) * d + j]));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) m = max(m, v[u] & kMag);
+    }
+    for (; r < r1; ++r) m = max(m, static_cast<unsigned long long>(__double_as_longlong(SX[r * d + j])) & kMag);
+    if (m > 0) atomicMax(colmax + j, m);
   }
 }
 
