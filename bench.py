@@ -43,9 +43,9 @@ GRAM_DIGIT_PRODUCTS = 36
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each stage's kernel on the
 # 1,000,000 x 1024 workload (s = 16384, k = 128), from one ncu capture of its current source; None
 # whenever the kernel changed since, until it is captured again.
-# scores: 544.1 MB captured on 131072 rows (X read once), scaled by 10^6 / 131072 rows; chol: the
-# factorisation does not depend on n (d = 1024 in both).
-TRAFFIC_BYTES = {"scores": 4_151_400_000, "sketch": None, "syrk": None, "chol": 6_820_608}
+# scores: captured on 131072 rows (X read once), scaled by 10^6 / 131072 rows; syrk (gram_tc_kernel)
+# and chol (chol_ff_kernel): the sketch and the solve do not depend on n (s = 16384, d = 1024 in both).
+TRAFFIC_BYTES = {"scores": None, "sketch": None, "syrk": 272_007_936, "chol": 6_848_000}
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point
@@ -319,6 +319,16 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
     makespan = time.perf_counter() - start
     counters = srv.counters()
     srv.close()
+    # each job's own service time, run alone through the direct entry points: the slowdown
+    # (latency in the trace / time alone) separates queueing from the spread of job sizes
+    alone = []
+    for jb in jobs:
+        t1 = time.perf_counter()
+        sc, _ = api.leverage(jb["X"], jb["kind"], jb["s"], jb["k"], jb["seed"], jb["seed"] + 1, want_info=False)
+        api.order(sc)
+        torch.cuda.synchronize()
+        alone.append((time.perf_counter() - t1) * 1e3)
+    slow = sorted(l_ / a for l_, a in zip(lat, alone))
     lat.sort()
     pct = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]  # noqa: E731
     rows = sum(jb["n"] for jb in jobs)
@@ -328,6 +338,9 @@ def serving_bench(api, inputs, torch, n_jobs, slots=4, load=0.7, seed=4004):
                     "CountSketch/SRHT/Gaussian 1/3 each, k=64",
         "slots": slots, "jobs": n_jobs, "failed": bad, "calibrated_service_ms": service_s * 1e3,
         "arrival_rate_per_s": rate, "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
+        "slowdown": {"p50": slow[len(slow) // 2], "p99": slow[min(len(slow) - 1, int(math.ceil(0.99 * len(slow))) - 1)],
+                     "max": slow[-1], "alone_p50_ms": sorted(alone)[len(alone) // 2],
+                     "alone_p99_ms": sorted(alone)[min(len(alone) - 1, int(math.ceil(0.99 * len(alone))) - 1)]},
         "makespan_s": makespan, "jobs_per_s": n_jobs / makespan, "rows_per_s": rows / makespan,
         "graphs": {k: counters[k] for k in ("graphs_new", "graphs_updated", "direct")},
         "grouped": {k: counters[k] for k in ("group_launches", "grouped_jobs")},

@@ -710,11 +710,17 @@ __global__ void __launch_bounds__(256) probe_v_ff_kernel(const double* __restric
     const int e = cexp[j];
     float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
     ff acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    // blocks of 8 rows: the 8 loads are issued before the arithmetic; folds after every block
+    // blocks of 8 rows: the next block's 8 loads are issued before this block's arithmetic;
+    // folds after every block
+    double xn[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xn[u] = r0 + u < r1 ? SX[(r0 + u) * d + j] : 0.0;
     for (int64_t rb = r0; rb < r1; rb += 8) {
       double xv[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) xv[u] = rb + u < r1 ? SX[(rb + u) * d + j] : 0.0;
+      for (int u = 0; u < 8; ++u) xv[u] = xn[u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xn[u] = rb + 8 + u < r1 ? SX[(rb + 8 + u) * d + j] : 0.0;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int64_t r = rb + u;
@@ -742,18 +748,38 @@ __global__ void __launch_bounds__(256) probe_v_ff_kernel(const double* __restric
   }
 }
 
-// V''[j][q] = the chunk partials added in chunk order.
-__global__ void probe_vsum_ff_kernel(const float2* __restrict__ vpart, int chunks, int d, float2* __restrict__ V,
-                                     const DevState* __restrict__ st) {
+// V''[j][q] = the chunk partials added in a fixed order: a CTA takes 32 consecutive entries
+// e = 4j + q (coalesced), warp w adds the chunks b = w, w + 8, ... and the eight warp sums are
+// added in warp order.
+__global__ void __launch_bounds__(256) probe_vsum_ff_kernel(const float2* __restrict__ vpart, int chunks, int d,
+                                                            float2* __restrict__ V, const DevState* __restrict__ st) {
   if (*reinterpret_cast<const volatile int32_t*>(&st->gram_ok) == 0) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d * 4) return;
+  __shared__ float2 part[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
   ff v{0.f, 0.f};
-  for (int b = 0; b < chunks; ++b) {
-    const float2 p = vpart[static_cast<int64_t>(b) * d * 4 + e];
-    v = ff_add(v, ff{p.x, p.y});
+  if (e < d * 4) {
+    int b = w;
+    for (; b + 24 < chunks; b += 32) {  // four loads in flight
+      float2 p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p[u] = vpart[static_cast<int64_t>(b + 8 * u) * d * 4 + e];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v = ff_add(v, ff{p[u].x, p[u].y});
+    }
+    for (; b < chunks; b += 8) {
+      const float2 p = vpart[static_cast<int64_t>(b) * d * 4 + e];
+      v = ff_add(v, ff{p.x, p.y});
+    }
   }
-  V[e] = make_float2(v.h, v.l);
+  part[w][lane] = make_float2(v.h, v.l);
+  __syncthreads();
+  if (w == 0 && e < d * 4) {
+    ff t{0.f, 0.f};
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) t = ff_add(t, ff{part[ww][lane].x, part[ww][lane].y});
+    V[e] = make_float2(t.h, t.l);
+  }
 }
 
 // eres[c] = sum_q ((X' V'')_cq - Z_cq)^2 (float64 at the end): one CTA of 128 threads per row c.
@@ -817,8 +843,8 @@ slso_status run_probe_ff(Handle& h, const double* SX, int64_t s, int64_t d, cons
   probe_v_ff_kernel<<<dim3(vb, static_cast<unsigned>(ceil_div(d, 256))), 256, 0, st>>>(SX, s, d_i, cexp, Wff, rpc,
                                                                                        vpart, h.state);
   SLSO_CHECK_LAUNCH();
-  probe_vsum_ff_kernel<<<static_cast<unsigned>(ceil_div(d * 4, 256)), 256, 0, st>>>(vpart, static_cast<int>(vb), d_i,
-                                                                                    Vff, h.state);
+  probe_vsum_ff_kernel<<<static_cast<unsigned>(ceil_div(d * 4, 32)), 256, 0, st>>>(vpart, static_cast<int>(vb), d_i,
+                                                                                   Vff, h.state);
   SLSO_CHECK_LAUNCH();
   probe_u_ff_kernel<<<static_cast<unsigned>(d), 128, 0, st>>>(X, d_i, Vff, Z, eres, h.state);
   SLSO_CHECK_LAUNCH();

@@ -599,18 +599,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Float32-accurate scores with the X operands in tensor memory, k <= 128.  The converters read
-// each float32 row of the TMA's tile from shared memory once and write its operand pieces to
-// TMEM with tcgen05.st, and the MMAs take A from TMEM: shared memory then carries only the TMA's
-// writes, the converters' reads and the B operand reads (the form that keeps X's operands in
-// shared memory also writes them there and reads them back for every product, and shared-memory
-// bandwidth bounded it).  K-blocks of 16 floats (64-byte rows, 64B swizzle).  Products, all
-// accumulated in float32 in TMEM:
-//   HYB = false (3xTF32): Xhi Mhi + Xhi Mlo + Xlo Mhi with tf32 pieces (6 tf32 MMAs of K 8 per
-//               K-block and tile).
+// Float32-accurate scores with X's low operand pieces in tensor memory, k <= 128.  X = Xhi + Xlo
+// with Xhi = X truncated to tf32 (its top 19 bits) and Xlo = X - Xhi (exact in float32, below
+// 2^-10 |X|).  The tf32 MMAs take A straight from the TMA's float32 tile in shared memory: the
+// tensor core reads a float32 operand of kind::tf32 as its top 19 bits, which is Xhi.  The
+// converters read each row of the tile once and write only what the raw tile cannot give to
+// TMEM with tcgen05.st; those MMAs take A from TMEM.  K-blocks of 16 floats (64-byte rows, 64B
+// swizzle).  Products, all accumulated in float32 in TMEM:
+//   HYB = false (3xTF32): Xhi Mhi + Xhi Mlo (A from shared memory) + Xlo Mhi (A = tf32(Xlo) in
+//               TMEM): 6 tf32 MMAs of K 8 per K-block and tile.
 //   HYB = true:   Xhi Mhi in tf32 (exact products) plus bf16(Xlo) bf16(Mhi) + bf16(Xhi) bf16(Mlo)
 //               in bfloat16 (2 tf32 + 2 bf16 MMAs of K 16: 2/3 of the tensor time): each dropped
 //               or rounded term is below 2^-18 |x_il m_lj|.
+// B = M^T is packed once per call so that one K-block of one column is one 128-byte row: its tf32
+// high part (16 x 4 bytes), then either the bfloat16 high and low parts (16 x 2 bytes each) or the
+// tf32 low part; one 128B-swizzled TMA box per stage carries all of B's pieces, and each product
+// addresses its piece by the offset of its 32 bytes within the row.  The MMA thread issues a
+// stage's shared-memory products as soon as the TMA's bytes land and the TMEM products once the
+// converters are done.
 // T = 2: a work item is two 128-row tiles that share each K-block of B, the whole K summed in one
 //   accumulator per tile (nbuf sets of 2N columns: the epilogue of one item overlaps the next).
 // T = 1, for long rows: the tensor core's float32 accumulation rounds its sums toward zero, a bias
@@ -619,19 +625,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 //   each summed into a fresh accumulator (two, ping-pong), and the epilogue adds every chunk into
 //   a running sum kept in TMEM with round-to-nearest float32 additions.
 // TMEM: the accumulators from column 0 (T = 1: then the running sum, N columns), then one A slot
-// of 32 T columns per stage: per tile 32 columns = Xhi (16 tf32) and either Xlo (16 tf32) or
-// bf16(Xlo), bf16(Xhi) (8 columns each, two elements per column).  Converter warp w may only reach
-// TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, so warp w converts rows 32 (w % 4) + lane of tile
-// (w - 6) / 4 (for T = 1 the warps of tile 1 only arrive).  Every wait is bounded.
+// of 16 T columns per stage: per tile 16 columns = either tf32(Xlo) (16 tf32) or bf16(Xlo),
+// bf16(Xhi) (8 columns each, two elements per column).  Converter warp w may only reach TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, so warp w converts rows 32 (w % 4) + lane of tile (w - 6) / 4
+// (for T = 1 the warps of tile 1 only arrive).  Every wait is bounded.
 struct LayoutTm {
   int N, KB, S, nbuf;           // stages (shared-memory tiles and TMEM A slots), accumulator sets
   int chunk, nchunk;            // K-blocks per accumulation chunk, chunks per work item
-  uint32_t bh_bytes, bx_bytes;  // B hi tile (N x 64 B); each further B tile (N x 32 B or N x 64 B)
+  uint32_t bh_bytes;            // the packed B tile (N x 128 B)
   uint32_t stage_bytes, bar_off, smem_bytes, run_col, abase, tmem_cols;
 };
 
-constexpr int kMaxStagesTm = 4;
+constexpr int kMaxStagesTm = 7;
 constexpr uint32_t kXtTm = kBM * 16 * 4;  // one 128-row x 16-float tile
+constexpr int kSlotTm = 16;               // TMEM A columns per tile and stage
 
 template <bool HYB, int T, bool GROUP>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -702,15 +709,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       int it = 0;
       bool ok = true;
-      const uint32_t tx = T * kXtTm + L.bh_bytes + (HYB ? 2u : 1u) * L.bx_bytes;
+      const uint32_t tx = T * kXtTm + L.bh_bytes;
       for (int w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
         int lw;
         const int j = job_of(w, lw);
         const int y0 = lw * T * kBM, KB = kb_of(j);
         const CUtensorMap* mX = GROUP ? &jobs[j].tmX : &tmX;
         const CUtensorMap* mBh = GROUP ? &jobs[j].tmBh : &tmBh;
-        const CUtensorMap* mB1 = GROUP ? &jobs[j].tmB1 : &tmB1;
-        const CUtensorMap* mB2 = GROUP ? &jobs[j].tmB2 : &tmB2;
         for (int kb = 0; kb < KB; ++kb, ++it) {
           const int st = it % L.S;
           if (!mbar_wait(&empty[st], ((it / L.S) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -719,10 +724,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive_expect_tx(&full[st], tx);
 #pragma unroll
           for (int u = 0; u < T; ++u) tma_load_2d(stage + u * kXtTm, mX, &full[st], x, y0 + u * kBM);
-          unsigned char* b = stage + T * kXtTm;
-          tma_load_2d(b, mBh, &full[st], x, 0);
-          tma_load_2d(b + L.bh_bytes, mB1, &full[st], x, 0);
-          if (HYB) tma_load_2d(b + L.bh_bytes + L.bx_bytes, mB2, &full[st], x, 0);
+          tma_load_2d(stage + T * kXtTm, mBh, &full[st], 2 * x, 0);  // the packed B: 32 words per K-block
         }
       }
       if (!ok) {
@@ -736,11 +738,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idt = idesc(FMT_TF32, FMT_TF32, kBM, static_cast<uint32_t>(L.N));
       const uint32_t idb = idesc(FMT_BF16, FMT_BF16, kBM, static_cast<uint32_t>(L.N));
-      // stage 0's B descriptors; a stage's differ only in the start address field (address >> 4,
+      // stage 0's descriptors; a stage's differ only in the start address field (address >> 4,
       // bits 0-13; shared memory is below 2^18 bytes, so no carry)
-      unsigned char* b_0 = smem + T * kXtTm;
-      const uint64_t bh_0 = sdesc_sw64(b_0), b1_0 = HYB ? sdesc_sw32(b_0 + L.bh_bytes) : sdesc_sw64(b_0 + L.bh_bytes);
-      const uint64_t b2_off = static_cast<uint64_t>(L.bx_bytes >> 4);
+      const uint64_t x_0 = sdesc_sw64(smem);  // X's float32 tile u at + u kXtTm: A of the tf32 products
+      const uint64_t bh_0 = sdesc_sw128(smem + T * kXtTm);  // packed B rows; pieces at + 0, 64, 96 bytes
+      const uint64_t xt_off = static_cast<uint64_t>(kXtTm >> 4);
       int it = 0, cc = 0;  // K-blocks and accumulation chunks issued so far
       bool ok = true;
       uint32_t dbase = 0;
@@ -755,32 +757,49 @@ __global__ void __launch_bounds__(kThreads, 1)
             dbase = tmem_base + static_cast<uint32_t>(ab * T * L.N);
           }
           const int st = it % L.S;
-          if (!mbar_wait(&cvt[st], (it / L.S) & 1u, abort_flag)) { ok = false; break; }
+          const uint32_t par = (it / L.S) & 1u;
+          if (!mbar_wait(&full[st], par, abort_flag)) { ok = false; break; }
           tc_fence_after();
           const uint64_t soff = static_cast<uint64_t>((static_cast<uint32_t>(st) * L.stage_bytes) >> 4);
-          const uint64_t bh = bh_0 + soff, b1 = b1_0 + soff, b2 = b1 + b2_off;
-          const uint32_t aslot = tmem_base + L.abase + static_cast<uint32_t>(st * 32 * T);
+          const uint64_t bh = bh_0 + soff, b1 = bh + 4, b2 = bh + 6;  // HYB: bf16(Mhi), bf16(Mlo); else b1 = Mlo
+          // the products with A = X's raw tile (its tf32 high part): as soon as the bytes landed;
+          // consecutive MMAs alternate between the tiles' accumulators
 #pragma unroll
-          for (int u = 0; u < T; ++u) {
-            const uint32_t du = dbase + static_cast<uint32_t>(u * L.N);
-            const uint32_t a = aslot + static_cast<uint32_t>(u * 32);
-            if (HYB) {
-              mma_tf32_ts(du, a, bh, idt, kc != 0);
-              mma_tf32_ts(du, a + 8, bh + 2, idt, 1u);  // + 32 bytes along K
-              mma_f16_ts(du, a + 16, b1, idb, 1u);  // bf16(Xlo) bf16(Mhi)
-              mma_f16_ts(du, a + 24, b2, idb, 1u);  // bf16(Xhi) bf16(Mlo)
-            } else {
-              const uint64_t bl = b1;
+          for (int hk = 0; hk < 2; ++hk)  // the two K halves of 8 (+ 32 bytes along K)
 #pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t o = static_cast<uint64_t>(ks * 2);
-                const uint32_t ak = a + static_cast<uint32_t>(ks * 8);
-                mma_tf32_ts(du, ak, bh + o, idt, (kc | ks) != 0);
-                mma_tf32_ts(du, ak, bl + o, idt, 1u);
-                mma_tf32_ts(du, ak + 16, bh + o, idt, 1u);
-              }
+            for (int u = 0; u < T; ++u) {
+              const uint32_t du = dbase + static_cast<uint32_t>(u * L.N);
+              const uint64_t xa = x_0 + soff + static_cast<uint64_t>(u) * xt_off + static_cast<uint64_t>(2 * hk);
+              mma_tf32(du, xa, bh + 2 * hk, idt, (kc | hk) != 0);
             }
+          if (!HYB)  // Xhi Mlo
+#pragma unroll
+            for (int hk = 0; hk < 2; ++hk)
+#pragma unroll
+              for (int u = 0; u < T; ++u) {
+                const uint32_t du = dbase + static_cast<uint32_t>(u * L.N);
+                const uint64_t xa = x_0 + soff + static_cast<uint64_t>(u) * xt_off + static_cast<uint64_t>(2 * hk);
+                mma_tf32(du, xa, b1 + 2 * hk, idt, 1u);
+              }
+          if (!mbar_wait(&cvt[st], par, abort_flag)) {  // the MMAs issued above complete first
+            mma_commit(&empty[st]);
+            ++it;
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t aslot = tmem_base + L.abase + static_cast<uint32_t>(st * kSlotTm * T);
+#pragma unroll
+          for (int pc = 0; pc < 2; ++pc)
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+              const uint32_t du = dbase + static_cast<uint32_t>(u * L.N);
+              const uint32_t a = aslot + static_cast<uint32_t>(u * kSlotTm + 8 * pc);
+              if (HYB)  // bf16(Xlo) bf16(Mhi), then bf16(Xhi) bf16(Mlo)
+                mma_f16_ts(du, a, pc ? b2 : b1, idb, 1u);
+              else      // tf32(Xlo) Mhi, the two K halves
+                mma_tf32_ts(du, a, bh + 2 * pc, idt, 1u);
+            }
           mma_commit(&empty[st]);
           if (++kc == (T == 1 ? L.chunk : KB) || kb == KB - 1) {  // the chunk is summed
             mma_commit(&acc_full[cc % L.nbuf]);
@@ -826,25 +845,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             x[4 * c + 2] = v.z;
             x[4 * c + 3] = v.w;
           }
-          uint32_t a[32];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) a[e] = rne_tf32(x[e]);
+          // Xhi = x with its low 13 bits cleared: what the tensor core reads from the raw tile
+          uint32_t a[16];
           if (HYB) {
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
-              const float l0 = __uint_as_float(x[e]) - __uint_as_float(a[e]);
-              const float l1 = __uint_as_float(x[e + 1]) - __uint_as_float(a[e + 1]);
-              const __nv_bfloat162 lp = __floats2bfloat162_rn(l0, l1);  // .x (low half) = element e
-              const __nv_bfloat162 hp = __floats2bfloat162_rn(__uint_as_float(a[e]), __uint_as_float(a[e + 1]));
-              a[16 + e / 2] = *reinterpret_cast<const uint32_t*>(&lp);
-              a[24 + e / 2] = *reinterpret_cast<const uint32_t*>(&hp);
+              const float h0 = __uint_as_float(x[e] & 0xFFFFE000u), h1 = __uint_as_float(x[e + 1] & 0xFFFFE000u);
+              const __nv_bfloat162 lp =
+                  __floats2bfloat162_rn(__uint_as_float(x[e]) - h0, __uint_as_float(x[e + 1]) - h1);  // .x = element e
+              const __nv_bfloat162 hp = __floats2bfloat162_rn(h0, h1);
+              a[e / 2] = *reinterpret_cast<const uint32_t*>(&lp);
+              a[8 + e / 2] = *reinterpret_cast<const uint32_t*>(&hp);
             }
           } else {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              a[16 + e] = rne_tf32(__float_as_uint(__uint_as_float(x[e]) - __uint_as_float(a[e])));
+              a[e] = rne_tf32(__float_as_uint(__uint_as_float(x[e]) - __uint_as_float(x[e] & 0xFFFFE000u)));
           }
-          tmem_st_32x32b_x32(tmem_base + lane_addr + L.abase + static_cast<uint32_t>(st * 32 * T + u * 32), a);
+          tmem_st_32x32b_x16(tmem_base + lane_addr + L.abase + static_cast<uint32_t>((st * T + u) * kSlotTm), a);
           tc_fence_before();
         }
         mbar_arrive(&cvt[st]);
@@ -927,19 +945,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// B = M^T pieces for the mixed tf32/bfloat16 products: Bh = tf32(m) (float32 bits), and the
-// bfloat16 roundings of Bh and of m - Bh.
-__global__ void prep_b_hyb_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
-                                  float* __restrict__ Bh, __nv_bfloat16* __restrict__ Bhb,
-                                  __nv_bfloat16* __restrict__ Blb) {
+// B = M^T packed for score_tm_kernel: row c holds, for each K-block b of 16, 32 words: tf32(m) for
+// k = 16b .. 16b + 15, then (hyb) the bfloat16 roundings of tf32(m) and of m - tf32(m), 16 each,
+// or the tf32 rounding of m - tf32(m).
+__global__ void prep_b_packed_kernel(const double* __restrict__ M, int64_t d, int64_t kk, int64_t N, int64_t Kpad,
+                                     int hyb, float* __restrict__ B) {
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < N * Kpad;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t c = e / Kpad, k = e % Kpad;
     const double m = (c < kk && k < d) ? M[k * kk + c] : 0.0;
     const float hi = __uint_as_float(rne_tf32(__float_as_uint(static_cast<float>(m))));
-    Bh[e] = hi;
-    Bhb[e] = __float2bfloat16_rn(hi);
-    Blb[e] = __float2bfloat16_rn(static_cast<float>(m - static_cast<double>(hi)));
+    float* row = B + (c * (Kpad / 16) + k / 16) * 32;
+    const int q = static_cast<int>(k % 16);
+    row[q] = hi;
+    if (hyb) {
+      __nv_bfloat16* r16 = reinterpret_cast<__nv_bfloat16*>(row + 16);
+      r16[q] = __float2bfloat16_rn(hi);
+      r16[16 + q] = __float2bfloat16_rn(static_cast<float>(m - static_cast<double>(hi)));
+    } else {
+      row[16 + q] = __uint_as_float(rne_tf32(__float_as_uint(static_cast<float>(m - static_cast<double>(hi)))));
+    }
   }
 }
 
@@ -1071,6 +1096,33 @@ __global__ void prep_b_fp8_kernel(const double* __restrict__ M, int64_t d, int64
 
 }  // namespace
 
+// TMEM columns, stages and shared memory of the score_tm layout (T.N set).  Two tiles: nbuf
+// accumulator sets of 2N columns (two when that still leaves four A slots); one tile: two chunk
+// accumulators and the running sum, 3N columns.  Then as many stages as TMEM's 512 columns and
+// 227 KB of shared memory hold, at most kMaxStagesTm.
+static void tm_stages(LayoutTm& T, int tiles) {
+  const int slot = kSlotTm * tiles;
+  T.bh_bytes = static_cast<uint32_t>(T.N) * 128u;
+  T.stage_bytes = static_cast<uint32_t>(tiles) * kXtTm + T.bh_bytes;
+  int acc;
+  if (tiles == 2) {
+    T.nbuf = (4 * T.N + 4 * slot <= 512) ? 2 : 1;
+    T.run_col = 0;
+    acc = T.nbuf * 2 * T.N;
+  } else {
+    T.nbuf = 2;
+    T.run_col = static_cast<uint32_t>(2 * T.N);
+    acc = 3 * T.N;
+  }
+  T.abase = static_cast<uint32_t>(acc);
+  const uint32_t fixed = (3 * kMaxStagesTm + 4) * 8 + 8 + 1024;
+  const int by_smem = static_cast<int>((227u * 1024u - fixed) / T.stage_bytes);
+  T.S = std::min(kMaxStagesTm, std::min((512 - acc) / slot, by_smem));
+  T.tmem_cols = 512;
+  T.bar_off = static_cast<uint32_t>(T.S) * T.stage_bytes;
+  T.smem_bytes = T.bar_off + fixed;
+}
+
 // Scores on the tensor cores when the shapes allow it; *used = false means the caller must
 // take the SIMT kernel instead (k > 256, unaligned X, or an unsupported dtype pair).
 slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
@@ -1106,8 +1158,8 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   unsigned int* colmax = nullptr;
   float* cscale = nullptr;
   float* escale = nullptr;
-  if (mode == MODE_TF32X3) {
-    B0 = ar.take<float>(static_cast<size_t>(L.N) * Kpad);
+  if (mode == MODE_TF32X3) {  // B0 also holds the packed B of the tensor-memory form (2 N Kpad words)
+    B0 = ar.take<float>(2 * static_cast<size_t>(L.N) * Kpad);
     B1 = ar.take<float>(static_cast<size_t>(L.N) * Kpad);
   } else if (fp8) {
     B0 = ar.take<__nv_fp8_storage_t>(static_cast<size_t>(L.N) * Kpad);
@@ -1133,7 +1185,7 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
   if (group && !tm) return fail(SLSO_ERR_SHAPE, "internal: grouped scores need the tensor-memory form");
   const bool hyb = tm && h.score_form == SLSO_SCORE_FORM_MIXED;
   if (mode == MODE_TF32X3) {
-    if (!hyb) {  // the mixed form prepares its own pieces below
+    if (!tm) {  // the tensor-memory form packs its own pieces below
       prep_b_tf32_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<float*>(B0), static_cast<float*>(B1));
       SLSO_CHECK_LAUNCH();
     }
@@ -1183,42 +1235,16 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     const int tiles = T.KB > 128 ? 1 : 2;
     T.chunk = tiles == 1 ? 32 : T.KB;
     T.nchunk = static_cast<int>(ceil_div(T.KB, T.chunk));
-    T.bh_bytes = static_cast<uint32_t>(L.N) * 64u;
-    T.bx_bytes = hyb ? static_cast<uint32_t>(L.N) * 32u : T.bh_bytes;
-    T.stage_bytes = tiles * kXtTm + T.bh_bytes + (hyb ? 2u : 1u) * T.bx_bytes;
-    T.S = kMaxStagesTm;
-    if (tiles == 2) {
-      T.nbuf = (2 * 2 * L.N + T.S * 64 <= 512) ? 2 : 1;
-      T.run_col = 0;
-      T.abase = static_cast<uint32_t>(T.nbuf * 2 * L.N);
-    } else {  // two chunk accumulators, the running sum, then the A slots: 3N + 4 x 32 <= 512
-      T.nbuf = 2;
-      T.run_col = static_cast<uint32_t>(2 * L.N);
-      T.abase = static_cast<uint32_t>(3 * L.N);
-    }
-    T.tmem_cols = 512;
-    T.bar_off = static_cast<uint32_t>(T.S) * T.stage_bytes;
-    T.smem_bytes = T.bar_off + (3 * kMaxStagesTm + 4) * 8 + 8 + 1024;
-    // B pieces (Kpad is a multiple of 32 floats, so of 16)
+    tm_stages(T, tiles);
+    // B packed (Kpad is a multiple of 32 floats, so of 16): N rows of Kpad / 16 blocks of 32 words
     CUtensorMap mXt, mBh, mB1t, mB2t;
-    bool okt = make_map(&mXt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * esz, 16, kBM, CU_TENSOR_MAP_SWIZZLE_64B) &&
-               make_map(&mBh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, Kpad, L.N, Kpad * 4, 16, L.N,
-                        CU_TENSOR_MAP_SWIZZLE_64B);
-    if (hyb) {
-      __nv_bfloat16* Bhb = static_cast<__nv_bfloat16*>(B1);  // the float B1 holds both bf16 pieces
-      __nv_bfloat16* Blb = Bhb + static_cast<size_t>(L.N) * Kpad;
-      prep_b_hyb_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, static_cast<float*>(B0), Bhb, Blb);
-      SLSO_CHECK_LAUNCH();
-      okt = okt &&
-            make_map(&mB1t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bhb, Kpad, L.N, Kpad * 2, 16, L.N,
-                     CU_TENSOR_MAP_SWIZZLE_32B) &&
-            make_map(&mB2t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Blb, Kpad, L.N, Kpad * 2, 16, L.N,
-                     CU_TENSOR_MAP_SWIZZLE_32B);
-    } else {
-      okt = okt && make_map(&mB1t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B1, Kpad, L.N, Kpad * 4, 16, L.N,
-                            CU_TENSOR_MAP_SWIZZLE_64B);
-      mB2t = mB1t;
-    }
+    prep_b_packed_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, hyb ? 1 : 0, static_cast<float*>(B0));
+    SLSO_CHECK_LAUNCH();
+    const bool okt = make_map(&mXt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * esz, 16, kBM,
+                              CU_TENSOR_MAP_SWIZZLE_64B) &&
+                     make_map(&mBh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, 2 * Kpad, L.N, 2 * Kpad * 4, 32, L.N,
+                              CU_TENSOR_MAP_SWIZZLE_128B);
+    mB1t = mB2t = mBh;  // unused by the kernel
     if (!okt) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
     const int nwork = (ntiles + tiles - 1) / tiles;
     if (group) {  // described for a grouped launch instead of launched
@@ -1374,16 +1400,7 @@ slso_status score_group_launch(Handle& h, ScoreGroupJob* host, ScoreGroupJob* de
   T.KB = 0;  // per job
   T.chunk = 0;
   T.nchunk = 1;
-  T.bh_bytes = static_cast<uint32_t>(N) * 64u;
-  T.bx_bytes = hyb ? static_cast<uint32_t>(N) * 32u : T.bh_bytes;
-  T.stage_bytes = 2 * kXtTm + T.bh_bytes + (hyb ? 2u : 1u) * T.bx_bytes;
-  T.S = kMaxStagesTm;
-  T.nbuf = (2 * 2 * N + T.S * 64 <= 512) ? 2 : 1;
-  T.run_col = 0;
-  T.abase = static_cast<uint32_t>(T.nbuf * 2 * N);
-  T.tmem_cols = 512;
-  T.bar_off = static_cast<uint32_t>(T.S) * T.stage_bytes;
-  T.smem_bytes = T.bar_off + (3 * kMaxStagesTm + 4) * 8 + 8 + 1024;
+  tm_stages(T, 2);
   SLSO_CHECK_CUDA(cudaMemcpyAsync(dev, host, sizeof(ScoreGroupJob) * njobs, cudaMemcpyHostToDevice, st));
   const int grid = std::min(total, h.num_sms);
   auto launch = [&](auto kern) -> slso_status {

@@ -5,8 +5,9 @@
 //   hist    each tile of 4096 keys counts its digits          -> hist[digit][tile]
 //   scan    one CTA per digit: exclusive prefix over the tiles in place, and the digit's total
 //   scatter each tile adds the exclusive prefix of the digit totals to its row of offsets, ranks
-//           its keys stably (warp match + per-warp counters) and writes them at
-//           offset[digit][tile] + rank.
+//           its keys stably (warp match + per-warp counters), places them in shared memory in
+//           digit order and writes every digit's run to offset[digit][tile] + rank with
+//           consecutive threads on consecutive addresses (keys, then values, through one buffer).
 // Stability: tiles are contiguous and ordered, warps own contiguous 512-key runs inside a
 // tile, and a warp walks its run 32 keys at a time in index order.
 #include "common.cuh"
@@ -79,7 +80,9 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint32_t* __restrict__ totals, int ntiles) {
   __shared__ uint32_t wcnt[kWarps][kRadix];
   __shared__ uint32_t gofs[kRadix];
+  __shared__ uint32_t lstart[kRadix];
   __shared__ uint32_t wtot[kWarps];
+  __shared__ __align__(16) unsigned char sbuf[kTile * sizeof(K)];  // the tile in digit order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
   // the digits' start: exclusive prefix of the totals (kThreads == kRadix: one digit per thread)
@@ -122,25 +125,64 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     }
   }
   __syncthreads();
-  // exclusive prefix over warps for every digit
-  for (int dg = threadIdx.x; dg < kRadix; dg += kThreads) {
+  // exclusive prefix over warps for every digit, and the tile-local start of every digit (the
+  // exclusive prefix of the tile's digit counts; one digit per thread)
+  {
+    const int dg = threadIdx.x;
     uint32_t run = 0;
     for (int w = 0; w < kWarps; ++w) {
       const uint32_t c = wcnt[w][dg];
       wcnt[w][dg] = run;
       run += c;
     }
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[warp] = x;  // the digit starts' use of wtot ended at the barrier above
+    __syncthreads();
+    uint32_t before = 0;
+    for (int v = 0; v < warp; ++v) before += wtot[v];
+    lstart[dg] = before + x - run;
   }
   __syncthreads();
+  // tile-local position of every key: the digit's start, then the warps before, then the rank
+  K* kbuf = reinterpret_cast<K*>(sbuf);
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t idx = base + r * 32 + lane;
     if (idx < n) {
       const uint32_t dg = static_cast<uint32_t>(key[r] >> shift) & 0xFFu;
-      const uint32_t pos = gofs[dg] + wcnt[warp][dg] + rank[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      rank[r] += lstart[dg] + wcnt[warp][dg];
+      kbuf[rank[r]] = key[r];
     }
+  }
+  __syncthreads();
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kTile;
+  const int tn = static_cast<int>(n - t0 < kTile ? n - t0 : kTile);  // keys in this tile
+  uint32_t dgs[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int p = i * kThreads + threadIdx.x;
+    if (p < tn) {
+      const K k = kbuf[p];
+      const uint32_t dg = static_cast<uint32_t>(k >> shift) & 0xFFu;
+      dgs[i] = dg;
+      kout[gofs[dg] + static_cast<uint32_t>(p) - lstart[dg]] = k;
+    }
+  }
+  __syncthreads();
+  uint32_t* vbuf = reinterpret_cast<uint32_t*>(sbuf);
+#pragma unroll
+  for (int r = 0; r < kItems; ++r)
+    if (base + r * 32 + lane < n) vbuf[rank[r]] = val[r];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int p = i * kThreads + threadIdx.x;
+    if (p < tn) vout[gofs[dgs[i]] + static_cast<uint32_t>(p) - lstart[dgs[i]]] = vbuf[p];
   }
 }
 
