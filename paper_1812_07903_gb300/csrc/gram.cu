@@ -53,7 +53,8 @@ __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
 }
 
 // Column scales: colmax[j] = max_r |SX[r, j]| as its float64 bit pattern (non-negative doubles
-// order like their bits, so atomicMax gives the exact maximum in any order).
+// order like their bits, so atomicMax gives the exact maximum in any order).  Grid: row chunks x
+// column blocks of 256 (one column per thread).
 __global__ void __launch_bounds__(256) gram_colmax_kernel(const double* __restrict__ SX, int64_t s, int d,
                                                           int64_t rows_per_block,
                                                           unsigned long long* __restrict__ colmax) {
@@ -62,7 +63,8 @@ __global__ void __launch_bounds__(256) gram_colmax_kernel(const double* __restri
   // |x| compared as the integer bits of a non-negative float64 (the same order as the values, with
   // no float64 instruction: that pipe is narrow on this part); eight loads in flight per thread
   constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (j < d) {
     unsigned long long m = 0;
     int64_t r = r0;
     for (; r + 8 <= r1; r += 8) {
@@ -655,7 +657,8 @@ slso_status run_gram_matrix(Handle& h, const Arena& ar, const GramWork& g, const
   prof_begin(h, ar, ST_CHOL, st);
   SLSO_CHECK_CUDA(cudaMemsetAsync(g.colmax, 0, sizeof(unsigned long long) * d, st));
   const int cb = 2 * h.num_sms;
-  gram_colmax_kernel<<<static_cast<unsigned>(cb), 256, 0, st>>>(SX, s, d_i, ceil_div(s, cb), g.colmax);
+  gram_colmax_kernel<<<dim3(static_cast<unsigned>(cb), static_cast<unsigned>(ceil_div(d, 256))), 256, 0, st>>>(
+      SX, s, d_i, ceil_div(s, cb), g.colmax);
   SLSO_CHECK_LAUNCH();
   gram_scale_kernel<<<static_cast<unsigned>(ceil_div(d, 256)), 256, 0, st>>>(g.colmax, d_i, g.cexp, g.cscale);
   SLSO_CHECK_LAUNCH();
