@@ -109,22 +109,34 @@ __device__ __forceinline__ long long fixed55(double a, int e, bool& bad) {
 }
 
 // Slices E_p (p < 8) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
-// (8 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 32; K = rows of SX contiguous); rows
-// j >= d are zero.  Block (x: row block, y: column block): 32 rows x 32 columns of SX; threads (32, 8).
+// (8 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 64; K = rows of SX contiguous); rows
+// j >= d are zero.  Block (x: row block, y: column block): 64 rows x 32 columns of SX; threads
+// (32, 8): a warp reads 32 consecutive float64 of a row, each thread 8 rows (loads issued first),
+// and a warp writes 64 consecutive bfloat16 (128 bytes) of a slice row.
+constexpr int kSliceRows = 64;
 __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restrict__ SX, int64_t s, int d, int dpad,
                                                          int64_t sp, const int* __restrict__ cexp,
                                                          __nv_bfloat16* __restrict__ E, int* __restrict__ bad_flag) {
-  __shared__ __nv_bfloat16 tile[kSlices][32][34];  // [p][column][row]
+  __shared__ __align__(4) __nv_bfloat16 tile[kSlices][32][kSliceRows + 2];  // [p][column][row]
   const int j0 = blockIdx.y * 32;
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kSliceRows;
   const int tx = threadIdx.x, ty = threadIdx.y;
   bool bad = false;
   const int j = j0 + tx;
   const int e = j < d ? cexp[j] : 0;
-  for (int rr = ty; rr < 32; rr += 8) {
+  constexpr int kPer = kSliceRows / 8;
+  double xv[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int64_t i = i0 + ty + 8 * k;
+    xv[k] = (j < d && i < s) ? SX[i * d + j] : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int rr = ty + 8 * k;
     const int64_t i = i0 + rr;
     long long F = 0;
-    if (j < d && i < s) F = fixed55(SX[i * d + j], e, bad);
+    if (j < d && i < s) F = fixed55(xv[k], e, bad);
     // balanced base-128 digits of F = sum_p d_p 2^(49 - 7p), d_7..d_1 in [-64, 63], |d_0| <= 64,
     // from the bottom in 32-bit arithmetic: the low 28 bits give d_7..d_4 and a carry into the
     // high part, which gives d_3..d_0
@@ -154,7 +166,8 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restric
   for (int p = 0; p < kSlices; ++p)
     for (int cc = ty; cc < 32; cc += 8) {
       const int64_t row = static_cast<int64_t>(p) * dpad + j0 + cc;
-      E[row * sp + i0 + tx] = tile[p][cc][tx];
+      *reinterpret_cast<__nv_bfloat162*>(E + row * sp + i0 + 2 * tx) =
+          *reinterpret_cast<const __nv_bfloat162*>(&tile[p][cc][2 * tx]);
     }
   if (__syncthreads_or(bad) && tx == 0 && ty == 0) atomicOr(bad_flag, 1);
 }
@@ -393,7 +406,7 @@ bool gram_tc_applies(int64_t s, int64_t d) { return encode_fn() != nullptr && s 
 
 void gram_tc_take(Arena& ar, int64_t s, int64_t d, GramTcWork* w) {
   w->dpad = static_cast<int>(ceil_div(d, kBMg) * kBMg);
-  w->sp = ceil_div(s, 32) * 32;
+  w->sp = ceil_div(s, kSliceRows) * kSliceRows;
   const int nbI = static_cast<int>(ceil_div(d, kBMg));
   w->nbJ = static_cast<int>(ceil_div(d, kBNg));
   int tiles = 0;
@@ -428,7 +441,7 @@ slso_status run_gram_tc(Handle& h, const GramTcWork& w, const double* SX, int64_
                         double* L, cudaStream_t st) {
   const int d_i = static_cast<int>(d);
   SLSO_CHECK_CUDA(cudaMemsetAsync(w.bad, 0, sizeof(int), st));
-  const dim3 gs(static_cast<unsigned>(w.sp / 32), static_cast<unsigned>(w.dpad / 32));
+  const dim3 gs(static_cast<unsigned>(w.sp / kSliceRows), static_cast<unsigned>(w.dpad / 32));
   gram_slice_kernel<<<gs, dim3(32, 8), 0, st>>>(SX, s, d_i, w.dpad, w.sp, cexp, w.E, w.bad);
   SLSO_CHECK_LAUNCH();
   CUtensorMap mA, mB;
