@@ -45,7 +45,7 @@ GRAM_DIGIT_PRODUCTS = 36
 # whenever the kernel changed since, until it is captured again.
 # scores: captured on 131072 rows (X read once), scaled by 10^6 / 131072 rows; syrk (gram_tc_kernel)
 # and chol (chol_ff_kernel): the sketch and the solve do not depend on n (s = 16384, d = 1024 in both).
-TRAFFIC_BYTES = {"scores": None, "sketch": None, "syrk": 272_007_936, "chol": 6_848_000}
+TRAFFIC_BYTES = {"scores": 4_153_843_750, "sketch": None, "syrk": 272_007_936, "chol": 6_848_000}
 CORRECT_FRAC = 0.015  # rescore the top 1.5% rows in float32 (1% target plus margin)
 OSNAP_NNZ = 4  # nonzeros per column of the OSNAP sketch
 STREAM_BLOCK = 262144  # rows per block of the out-of-core entry point
@@ -61,7 +61,7 @@ def stage_rooflines(per, n, d, s, k, peaks, peak_src):
     if "scores" in per:  # X read once, l written; Y = X M never leaves the SM
         b = n * d * 4.0 + n * 4.0
         a = b / (per["scores"] / 1e3) / 1e9
-        out["scores"] = {"kernel": "score_tm_kernel (X M on tcgen05, X's pieces in TMEM, row norms)", "bound": "hbm",
+        out["scores"] = {"kernel": "score_tm_kernel (X M on tcgen05: tf32 products from X's raw tile, bf16 pieces in TMEM; row norms)", "bound": "hbm",
                          "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm, "traffic": tr("scores"),
                          "algorithmic": b, "peak_source": peak_src, "ms": per["scores"]}
     if "sketch" in per:  # X read once, SX (float64) written once

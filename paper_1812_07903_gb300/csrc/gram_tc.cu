@@ -156,9 +156,13 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restric
     dg[0] = y;  // |F| < 2^55 keeps it within [-64, 64]
 #pragma unroll
     for (int p = 0; p < kSlices; ++p) {
-      // E_p = d_p 2^(21 - 7p): exact in float32 and in bfloat16 (|d_p| <= 64)
+      // E_p = d_p 2^(21 - 7p), exact in float32 and in bfloat16 (|d_p| <= 64), without conversion
+      // instructions: the float with the bits of 2^23 + 2^22 + d_p is exactly 1.5 2^23 + d_p, one
+      // FMA with the power of two takes 1.5 2^23 back off exactly, and the product's low 16 bits
+      // are zero (at most 7 significant bits), so its upper half is the bfloat16
       const float scale = __int_as_float((127 + 21 - 7 * p) << 23);  // 2^(21 - 7p)
-      tile[p][tx][rr] = __float2bfloat16_rn(static_cast<float>(dg[p]) * scale);
+      const float v = fmaf(__int_as_float(0x4B400000 + dg[p]), scale, -12582912.0f * scale);
+      tile[p][tx][rr] = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(v) >> 16));
     }
   }
   __syncthreads();
