@@ -27,8 +27,9 @@
 // (576 threads, one CTA per SM):
 //   warps 0-15 epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and columns
 //              16 (w / 4).. of each accumulator; two int64 running sums per entry in registers.
-//   warp 16    TMA producer: the eight A slices (128 columns of SX x 16 rows) and eight B slices
-//              (64 columns x 16 rows) per stage, 32-byte swizzle; four stages of 48 KB.
+//   warp 16    TMA producer: per stage the eight A slices (128 columns of SX x 16 rows) and eight B
+//              slices (64 columns x 16 rows) in four 128B-swizzled boxes (slices 0-3 and 4-7 of A
+//              and of B, each row 128 bytes = 4 slices x 16 values); four stages of 48 KB.
 //   warp 17    TMEM owner (eight 64-column accumulators) and MMA issuer: 36 tcgen05.mma
 //              (kind::f16, bfloat16, M = 128, N = 64, K = 16) per stage.
 // Every mbarrier wait is bounded; a timeout sets DevState::timeout.
@@ -58,8 +59,10 @@ constexpr int kKbPerWin = kWinRows / kKBg;
 constexpr int kStagesG = 4;  // four stages of 48 KB: more of the L2 ingress in flight than two of 96 KB
 constexpr int kEpiWarpsG = 16;
 constexpr int kWarpProdG = 16, kWarpMmaG = 17;
-constexpr uint32_t kASliceBytes = kBMg * kKBg * 2;  // 4 KB
+constexpr uint32_t kASliceBytes = kBMg * kKBg * 2;  // 4 KB: one slice of the A tile
 constexpr uint32_t kBSliceBytes = kBNg * kKBg * 2;  // 2 KB
+constexpr uint32_t kAGroupBytes = 4 * kASliceBytes;  // four slices' K-block rows of 128 bytes (16 KB)
+constexpr uint32_t kBGroupBytes = 4 * kBSliceBytes;  // 8 KB
 constexpr uint32_t kStageBytesG = kSlices * (kASliceBytes + kBSliceBytes);
 constexpr uint32_t kBarOffG = kStagesG * kStageBytesG;
 constexpr uint32_t kSmemG = kBarOffG + (2 * kStagesG + 2) * 8 + 16 + 1024;
@@ -108,16 +111,21 @@ __device__ __forceinline__ long long fixed55(double a, int e, bool& bad) {
   return (u >> 63) ? -F : F;
 }
 
-// Slices E_p (p < 8) of the scaled SX, transposed: slice p of column j of SX is row p dpad + j of a
-// (8 dpad) x sp bfloat16 matrix (row pitch sp, a multiple of 64; K = rows of SX contiguous); rows
-// j >= d are zero.  Block (x: row block, y: column block): 64 rows x 32 columns of SX; threads
-// (32, 8): a warp reads 32 consecutive float64 of a row, each thread 8 rows (loads issued first),
-// and a warp writes 64 consecutive bfloat16 (128 bytes) of a slice row.
+// Slices E_p (p < 8) of the scaled SX, transposed and interleaved: column j of SX is row j of a
+// dpad x (8 sp) bfloat16 matrix (rows j >= d are zero) that holds, for each K-block of 16 rows of
+// SX, the 16 values of slice 0, then of slice 1, ..., slice 7 (256 bytes); sp, the padded number of
+// rows of SX, is a multiple of 64.  A 128-byte TMA box then carries four slices of one K-block.
+// Block (x: row block, y: column block): 64 rows x 32 columns of SX; threads (32, 8): a warp reads
+// 32 consecutive float64 of a row, each thread 8 rows (loads issued first); the block writes each
+// column's 1 KB run (4 K-blocks x 8 slices x 16) with a warp on 128 consecutive bytes.
 constexpr int kSliceRows = 64;
 __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restrict__ SX, int64_t s, int d, int dpad,
                                                          int64_t sp, const int* __restrict__ cexp,
                                                          __nv_bfloat16* __restrict__ E, int* __restrict__ bad_flag) {
-  __shared__ __align__(4) __nv_bfloat16 tile[kSlices][32][kSliceRows + 2];  // [p][column][row]
+  // [p][column][row], rows of 66 values; slice p at p kPStride, so that the warps' reads of four
+  // slices' runs fall on different banks (kPStride is 8 words past a multiple of 32 words)
+  constexpr int kRowS = kSliceRows + 2, kPStride = 32 * kRowS + 16;
+  __shared__ __align__(16) __nv_bfloat16 tile[kSlices * kPStride];
   const int j0 = blockIdx.y * 32;
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kSliceRows;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -162,17 +170,22 @@ __global__ void __launch_bounds__(256) gram_slice_kernel(const double* __restric
       // are zero (at most 7 significant bits), so its upper half is the bfloat16
       const float scale = __int_as_float((127 + 21 - 7 * p) << 23);  // 2^(21 - 7p)
       const float v = fmaf(__int_as_float(0x4B400000 + dg[p]), scale, -12582912.0f * scale);
-      tile[p][tx][rr] = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(v) >> 16));
+      tile[p * kPStride + tx * kRowS + rr] = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(v) >> 16));
     }
   }
   __syncthreads();
+  // column j0 + cc: 512 values from E[(j0 + cc) 8 sp + 8 i0]; value o is slice (o / 16) % 8 of row
+  // 16 (o / 128) + o % 16 of the block
+  for (int cc = ty; cc < 32; cc += 8) {
+    __nv_bfloat16* out = E + static_cast<int64_t>(j0 + cc) * 8 * sp + 8 * i0;
 #pragma unroll
-  for (int p = 0; p < kSlices; ++p)
-    for (int cc = ty; cc < 32; cc += 8) {
-      const int64_t row = static_cast<int64_t>(p) * dpad + j0 + cc;
-      *reinterpret_cast<__nv_bfloat162*>(E + row * sp + i0 + 2 * tx) =
-          *reinterpret_cast<const __nv_bfloat162*>(&tile[p][cc][2 * tx]);
+    for (int m = 0; m < 8; ++m) {
+      const int o = 2 * (tx + 32 * m);
+      const int p = (o >> 4) & 7, r = ((o >> 7) << 4) + (o & 15);
+      *reinterpret_cast<__nv_bfloat162*>(out + o) =
+          *reinterpret_cast<const __nv_bfloat162*>(&tile[p * kPStride + cc * kRowS + r]);
     }
+  }
   if (__syncthreads_or(bad) && tx == 0 && ty == 0) atomicOr(bad_flag, 1);
 }
 
@@ -254,11 +267,11 @@ __global__ void __launch_bounds__(kThreadsG, 1)
         }
         unsigned char* stage = smem + static_cast<uint32_t>(st) * kStageBytesG;
         mbar_arrive_expect_tx(&full[st], kStageBytesG);
-        const int x = (kb0 + kb) * kKBg;
+        const int x = (kb0 + kb) * kKBg * kSlices;  // the K-block's 128 values (8 slices x 16)
 #pragma unroll
-        for (int p = 0; p < kSlices; ++p) {
-          tma_load_2d(stage + p * kASliceBytes, &tmA, &full[st], x, p * dpad + I * kBMg);
-          tma_load_2d(stage + kSlices * kASliceBytes + p * kBSliceBytes, &tmB, &full[st], x, p * dpad + J * kBNg);
+        for (int g = 0; g < 2; ++g) {  // slices 4g .. 4g + 3: one 128-byte box row per column
+          tma_load_2d(stage + g * kAGroupBytes, &tmA, &full[st], x + 64 * g, I * kBMg);
+          tma_load_2d(stage + 2 * kAGroupBytes + g * kBGroupBytes, &tmB, &full[st], x + 64 * g, J * kBNg);
         }
       }
       if (!ok) {
@@ -289,8 +302,9 @@ __global__ void __launch_bounds__(kThreadsG, 1)
           tc_fence_after();
           unsigned char* stage = smem + static_cast<uint32_t>(st) * kStageBytesG;
           // the slices' descriptors differ from the stage's first ones only in the start address
-          // field (address >> 4, bits 0-13; every address here is below 2^18, so no carry)
-          const uint64_t a0 = sdesc_sw32(stage), b0 = sdesc_sw32(stage + kSlices * kASliceBytes);
+          // field (address >> 4, bits 0-13; every address here is below 2^18, so no carry): slice
+          // p sits in group p / 4 at 32 (p % 4) bytes into each 128-byte row
+          const uint64_t a0 = sdesc_sw128(stage), b0 = sdesc_sw128(stage + 2 * kAGroupBytes);
 #pragma unroll
           for (int ks = 0; ks < kKBg / 16; ++ks) {
             const uint64_t o = static_cast<uint64_t>(ks * 2);  // 32 bytes along K
@@ -300,8 +314,8 @@ __global__ void __launch_bounds__(kThreadsG, 1)
               // the first pair of each order starts its accumulator in the window's first K-step
               const bool first = p == 0;
               const uint32_t acc = (kw | ks) != 0 || !first;
-              const uint64_t a = a0 + static_cast<uint64_t>(p * (kASliceBytes >> 4)) + o;
-              const uint64_t bd = b0 + static_cast<uint64_t>(qq * (kBSliceBytes >> 4)) + o;
+              const uint64_t a = a0 + static_cast<uint64_t>((p >> 2) * (kAGroupBytes >> 4) + (p & 3) * 2) + o;
+              const uint64_t bd = b0 + static_cast<uint64_t>((qq >> 2) * (kBGroupBytes >> 4) + (qq & 3) * 2) + o;
               mma_f16(tmem_base + static_cast<uint32_t>(ord * kBNg), a, bd, id, acc);
             }
           }
@@ -449,11 +463,11 @@ slso_status run_gram_tc(Handle& h, const GramTcWork& w, const double* SX, int64_
   gram_slice_kernel<<<gs, dim3(32, 8), 0, st>>>(SX, s, d_i, w.dpad, w.sp, cexp, w.E, w.bad);
   SLSO_CHECK_LAUNCH();
   CUtensorMap mA, mB;
-  const uint64_t rows = static_cast<uint64_t>(kSlices) * w.dpad;
-  bool ok = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, s, rows, w.sp * 2, kKBg, kBMg,
-                     CU_TENSOR_MAP_SWIZZLE_32B) &&
-            make_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, s, rows, w.sp * 2, kKBg, kBNg,
-                     CU_TENSOR_MAP_SWIZZLE_32B);
+  const uint64_t inner = static_cast<uint64_t>(kSlices) * w.sp;  // values per column of SX
+  bool ok = make_map(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, inner, w.dpad, inner * 2, 64, kBMg,
+                     CU_TENSOR_MAP_SWIZZLE_128B) &&
+            make_map(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w.E, inner, w.dpad, inner * 2, 64, kBNg,
+                     CU_TENSOR_MAP_SWIZZLE_128B);
   if (!ok) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Gram slices");
   SLSO_TRY(raise_smem_limit(gram_tc_kernel, kSmemG));
   gram_tc_kernel<<<static_cast<unsigned>(w.tiles * w.splits), kThreadsG, kSmemG, st>>>(
