@@ -546,11 +546,11 @@ slso_status sample_order(Handle& h, Arena& ar, const void* scores, int32_t sdt, 
 slso_status run_gauss_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_t d, int64_t ldx, int32_t xdt,
                          int64_t s, uint64_t seed, int64_t row0, bool accumulate, double* SX, cudaStream_t st,
                          bool* used);
-// One job of a grouped score launch (the serving path): the tensor maps of its X and of its B
-// pieces, its rows, scores and device status, its K-blocks, its first global work item (before
+// One job of a grouped score launch (the serving path): the tensor maps of its X and of its
+// packed B, its rows, scores and device status, its K-blocks, its first global work item (before
 // score_group_launch numbers the items: its count of work items), its JL width and form.
 struct ScoreGroupJob {
-  CUtensorMap tmX, tmBh, tmB1, tmB2;
+  CUtensorMap tmX, tmBh;
   int64_t n;
   float* scores;
   DevState* state;

@@ -643,7 +643,6 @@ constexpr int kSlotTm = 16;               // TMEM A columns per tile and stage
 template <bool HYB, int T, bool GROUP>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBh,
-                    const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2,
                     const LayoutTm L, int64_t n, int nwork, float* __restrict__ scores,
                     DevState* __restrict__ state, const ScoreGroupJob* __restrict__ jobs, int njobs) {
   extern __shared__ unsigned char smem_dyn[];
@@ -702,9 +701,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       if (GROUP)  // the jobs' tensor maps were written to global memory before the launch
         for (int j = 0; j < njobs; ++j) {
-          const CUtensorMap* maps[4] = {&jobs[j].tmX, &jobs[j].tmBh, &jobs[j].tmB1, &jobs[j].tmB2};
+          const CUtensorMap* maps[2] = {&jobs[j].tmX, &jobs[j].tmBh};
 #pragma unroll
-          for (int m = 0; m < 4; ++m)
+          for (int m = 0; m < 2; ++m)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps[m]) : "memory");
         }
       int it = 0;
@@ -1237,22 +1236,19 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     T.nchunk = static_cast<int>(ceil_div(T.KB, T.chunk));
     tm_stages(T, tiles);
     // B packed (Kpad is a multiple of 32 floats, so of 16): N rows of Kpad / 16 blocks of 32 words
-    CUtensorMap mXt, mBh, mB1t, mB2t;
+    CUtensorMap mXt, mBh;
     prep_b_packed_kernel<<<pg, 256, 0, st>>>(M, d, kk, L.N, Kpad, hyb ? 1 : 0, static_cast<float*>(B0));
     SLSO_CHECK_LAUNCH();
     const bool okt = make_map(&mXt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, d, n, ldx * esz, 16, kBM,
                               CU_TENSOR_MAP_SWIZZLE_64B) &&
                      make_map(&mBh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B0, 2 * Kpad, L.N, 2 * Kpad * 4, 32, L.N,
                               CU_TENSOR_MAP_SWIZZLE_128B);
-    mB1t = mB2t = mBh;  // unused by the kernel
     if (!okt) return fail(SLSO_ERR_CUDA, "cuTensorMapEncodeTiled rejected a score operand layout");
     const int nwork = (ntiles + tiles - 1) / tiles;
     if (group) {  // described for a grouped launch instead of launched
       if (tiles != 2) return fail(SLSO_ERR_SHAPE, "internal: grouped scores need rows of at most 2048");
       group->tmX = mXt;
       group->tmBh = mBh;
-      group->tmB1 = mB1t;
-      group->tmB2 = mB2t;
       group->n = n;
       group->scores = scores;
       group->state = h.state;
@@ -1265,7 +1261,7 @@ slso_status run_scores_tc(Handle& h, Arena& ar, const void* X, int64_t n, int64_
     const int gridt = std::min(nwork, h.num_sms);
     auto launch = [&](auto kern) -> slso_status {
       SLSO_TRY(raise_smem_limit(kern, T.smem_bytes));
-      kern<<<gridt, kThreads, T.smem_bytes, st>>>(mXt, mBh, mB1t, mB2t, T, n, nwork, scores, h.state, nullptr, 0);
+      kern<<<gridt, kThreads, T.smem_bytes, st>>>(mXt, mBh, T, n, nwork, scores, h.state, nullptr, 0);
       SLSO_CHECK_LAUNCH();
       return SLSO_OK;
     };
@@ -1405,8 +1401,8 @@ slso_status score_group_launch(Handle& h, ScoreGroupJob* host, ScoreGroupJob* de
   const int grid = std::min(total, h.num_sms);
   auto launch = [&](auto kern) -> slso_status {
     SLSO_TRY(raise_smem_limit(kern, T.smem_bytes));
-    kern<<<grid, kThreads, T.smem_bytes, st>>>(host[0].tmX, host[0].tmBh, host[0].tmB1, host[0].tmB2, T, 0, total,
-                                                nullptr, host[0].state, dev, njobs);
+    kern<<<grid, kThreads, T.smem_bytes, st>>>(host[0].tmX, host[0].tmBh, T, 0, total, nullptr, host[0].state,
+                                                dev, njobs);
     SLSO_CHECK_LAUNCH();
     return SLSO_OK;
   };
