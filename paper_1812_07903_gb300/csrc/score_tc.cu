@@ -618,7 +618,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // stage's shared-memory products as soon as the TMA's bytes land and the TMEM products once the
 // converters are done.
 // T = 2: a work item is two 128-row tiles that share each K-block of B, the whole K summed in one
-//   accumulator per tile (nbuf sets of 2N columns: the epilogue of one item overlaps the next).
+//   accumulator per tile (nbuf sets of 2N columns; with two sets, which fit for k <= 64, the
+//   epilogue of one item overlaps the next item's MMAs).
 // T = 1, for long rows: the tensor core's float32 accumulation rounds its sums toward zero, a bias
 //   that grows with the number of MMAs summed into one accumulator (about 2^-25 of the sum per
 //   MMA: 1e-4 over the ~4000 MMAs of a 16800-long row).  K is cut into chunks of L.chunk K-blocks,
